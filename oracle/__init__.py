@@ -1,0 +1,23 @@
+"""FP64 CPU oracle for the direct-QPAT propagation path.
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, literal restatement
+of the paper's discretisation (Javaherian & Holman, "Direct quantitative
+photoacoustic tomography for realistic acoustic media"), used to check the
+CUDA path.  Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it.  The product path never calls it and it
+shares no code with the CUDA kernels: the two meet only at the seeded input
+generators in ``phantoms.py``.
+
+Modules
+- ``acoustic``: k-space PSTD forward operator H_a (Section 3.2.3, eqs.
+  num-vel, num-rho, num-p, num-m with the additive source s1) and its exact
+  discrete transpose H_a^* (Section 3.2.4, Lemma 2).
+- ``optics``: finite-difference diffusion approximation (Section 2.1, eq. DA)
+  with its Frechet derivative and adjoint in mu (Lemma 1).
+- ``qpat``: the composite maps H = H_a H_o, J and J^* (Section 3.2.2,
+  eqs. com_des and J_des).
+
+Every function is pinned by tests in ``tests/test_oracle_*.py`` against
+closed forms, invariants, brute force or the paper's printed values; none is
+marked "parity unpinned".
+"""
