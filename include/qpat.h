@@ -1,0 +1,165 @@
+/*
+ * qpat.h -- C ABI of the GB300 (sm_103a) direct-QPAT propagation library.
+ *
+ * The library evaluates the discretised opto-acoustic forward map of
+ * Javaherian & Holman, "Direct quantitative photoacoustic tomography for
+ * realistic acoustic media":
+ *
+ *   P-hat = H_a H_o[mu]                    (Section 3.2.2, eq. com_des)
+ *   dP-hat = H_a J_o[mu] dmu               (eq. J_des)
+ *   dmu-bar = J_o^*[mu] H_a^*(w)           (adjoint map below eq. J_des)
+ *
+ * where H_o is the diffusion-approximation optical map (Section 2.1, eq. DA;
+ * heating h = mu phi, eq. h; p0 = Gamma h with Gamma = 1) and H_a is the
+ * k-space pseudo-spectral acoustic map of Section 3.2.3 (eqs. num-vel,
+ * num-rho, num-p, num-m with the additive source of eq. s1), whose adjoint is
+ * the exact discrete transpose (Section 3.2.4, Lemma 2, eq. t41).
+ *
+ * Conventions (all entry points):
+ *  - Grids are 2D.  Arrays are row-major with x fastest: a full-grid field
+ *    is [ny][nx], an interior field is [n[1]][n[0]].  The FFT grid is the
+ *    interior plus `pml` nodes on every side (the PML is added outside the
+ *    stated grid, Section 3.2.2).  Node j along an axis of N nodes sits at
+ *    x = (j - (N - 1)/2) * dx.
+ *  - Time series are [nt][ns] (sample n = 0 .. nt-1, sensor fastest);
+ *    batched buffers add a leading batch index.
+ *  - "prec" buffers hold double for QPAT_FP64 contexts and float for
+ *    QPAT_FP32 contexts.  Optical vectors (mu, dmu, gradients, fluence) are
+ *    always double.
+ *  - Every device pointer is caller-owned CUDA device memory of the current
+ *    device.  Work is enqueued on the context's stream and the call returns
+ *    without waiting, except where a call says it synchronises.  Host
+ *    pointers are only read during the call.
+ *  - Errors are returned as qpat_status; the context keeps a message
+ *    (qpat_last_error).  No entry point aborts the process.
+ */
+#ifndef QPAT_H
+#define QPAT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qpat_ctx qpat_ctx;
+
+typedef enum {
+  QPAT_OK = 0,
+  QPAT_EINVAL = 1,      /* bad argument (sizes, pointers, ranges) */
+  QPAT_EUNSTABLE = 2,   /* time step violates the stability check */
+  QPAT_ENONFINITE = 3,  /* a NaN/Inf appeared in the fields */
+  QPAT_ENOCONV = 4,     /* diffusion solve hit its iteration cap */
+  QPAT_ETIMEOUT = 5,    /* reserved: a bounded device wait gave up */
+  QPAT_ENOMEM = 6,      /* device allocation failed */
+  QPAT_ECUDA = 7        /* any other CUDA runtime error */
+} qpat_status;
+
+typedef enum { QPAT_FP64 = 0, QPAT_FP32 = 1 } qpat_precision;
+
+/* Problem description.  Values <= 0 in the optional fields select defaults. */
+typedef struct {
+  int n[2];            /* interior nodes along x, y (the optical grid) */
+  int pml;             /* PML nodes added on each side; nx = n[0] + 2 pml must be even */
+  double dx;           /* grid spacing [m] (isotropic) */
+  double dt;           /* time step [s] */
+  int nt;              /* recorded samples per series (>= 2) */
+  double c_ref;        /* k-space reference speed [m/s]; <= 0: max(c) */
+  double pml_alpha;    /* PML strength [Np per grid point]; <= 0: 2 */
+  double y;            /* absorption power-law exponent (1 < y < 3, y != 2) */
+  int lossless;        /* 1: no absorption/dispersion (alpha0 ignored) */
+  int max_batch;       /* largest batch any call will use; <= 0: 1 */
+  double gamma_d;      /* Robin factor of eq. DA; <= 0: 1/pi */
+  int pcg_max_iter;    /* diffusion-solve iteration cap; <= 0: 20000 */
+  double pcg_tol;      /* relative residual target; <= 0: 1e-13 */
+} qpat_config;
+
+/* Medium, host memory, FP64, read during qpat_create only.
+ * c, rho, alpha0_db: full FFT grid [ny][nx] (PML region included).
+ * alpha0_db in dB MHz^-y cm^-1 (eq. Twelve uses it in Np (rad/s)^-y m^-1);
+ * may be NULL when lossless.  kappa: optical diffusion [m] on the interior
+ * grid [n1][n0] (fixed, not an unknown). */
+typedef struct {
+  const double* c;
+  const double* rho;
+  const double* alpha0_db;
+  const double* kappa;
+} qpat_medium;
+
+/* Create a context on the current device.
+ * sensor_xy: host [ns][2] sensor positions [m] (bilinear interpolation of the
+ * node grid, eq. num-m).  stream: a cudaStream_t (NULL = legacy default).
+ * Allocates and fills all device tables (FP64-computed k-space symbols, PML
+ * diagonals, medium coefficients, FFT twiddles) and the workspace for
+ * max_batch problems.  Synchronises the stream before returning.
+ * Errors: EINVAL (sizes, odd grid, an FFT extent with a prime factor above 7,
+ * sensors outside the grid, nt < 2), EUNSTABLE (c_max dt / dx above
+ * 2 / (pi sqrt 2), the pseudo-spectral leapfrog limit, which the k-space
+ * correction only relaxes), ENOMEM, ECUDA.  On error *out is NULL. */
+qpat_status qpat_create(const qpat_config* cfg, const qpat_medium* med,
+                        const double* sensor_xy, int ns, qpat_precision prec,
+                        void* stream, qpat_ctx** out);
+
+/* Free every device allocation of the context (synchronises its stream). */
+qpat_status qpat_destroy(qpat_ctx* ctx);
+
+/* Change the stream later calls enqueue on. */
+qpat_status qpat_set_stream(qpat_ctx* ctx, void* stream);
+
+/* Message describing the last error of this context ("" if none). */
+const char* qpat_last_error(const qpat_ctx* ctx);
+
+/* Sizes: out[0] = nx, out[1] = ny (FFT grid), out[2] = interior N,
+ * out[3] = ns, out[4] = nt, out[5] = max_batch. */
+qpat_status qpat_get_sizes(const qpat_ctx* ctx, long long out[6]);
+
+/* Wait for the context's stream and report device-side failures found by
+ * the kernels since the last check (ENONFINITE).  Clears the flags. */
+qpat_status qpat_sync(qpat_ctx* ctx);
+
+/* H_a (Section 3.2.3): batch of initial pressures -> sensor series.
+ * p0:   device prec [batch][N] interior initial pressure (0 in the PML).
+ * data: device prec [batch][nt][ns] output.  1 <= batch <= max_batch. */
+qpat_status qpat_acoustic_forward(qpat_ctx* ctx, int batch, const void* p0, void* data);
+
+/* H_a^* (Lemma 2, eq. t41, computed as the exact transpose of H_a).
+ * data: device prec [batch][nt][ns]; p0_adj: device prec [batch][N] output. */
+qpat_status qpat_acoustic_adjoint(qpat_ctx* ctx, int batch, const void* data, void* p0_adj);
+
+/* Diffusion solve (eq. DA, finite-volume form): A(mu) phi = G(illum).
+ * mu: device double [batch][N] absorption [1/m]; illum: bit s set = unit
+ * inward current on side s (0: x low, 1: x high, 2: y low, 3: y high);
+ * phi: device double [batch][N] output.  Synchronises (iteration control);
+ * ENOCONV if the cap is reached before pcg_tol. */
+qpat_status qpat_da_solve(qpat_ctx* ctx, int batch, const double* mu, unsigned illum,
+                          double* phi);
+
+/* Composite forward P-hat = H_a(mu o phi) (eq. com_des).
+ * mu: device double [batch][N]; data: device prec [batch][nt][ns];
+ * phi0_out: optional device double [batch][N] receiving the fluence. */
+qpat_status qpat_forward(qpat_ctx* ctx, int batch, const double* mu, unsigned illum,
+                         void* data, double* phi0_out);
+
+/* Jacobian-vector product dP-hat = H_a(dmu o phi0 + mu o dphi),
+ * A(mu) dphi = -h^2 dmu o phi0 (eq. dh_des, J_des).
+ * phi0: optional device double [batch][N] fluence of mu (NULL: solved here).
+ * dmu: device double [batch][N]; dP: device prec [batch][nt][ns]. */
+qpat_status qpat_jvp(qpat_ctx* ctx, int batch, const double* mu, const double* phi0,
+                     const double* dmu, unsigned illum, void* dP);
+
+/* Vector-Jacobian product g = phi0 o (hbar + H~), hbar = H_a^*(w),
+ * A(mu) H~ = -h^2 mu o hbar (Lemma 1 mu row; eqs. system_adjoint, prodtproj).
+ * w: device prec [batch][nt][ns]; g: device double [batch][N] output. */
+qpat_status qpat_vjp(qpat_ctx* ctx, int batch, const double* mu, const double* phi0,
+                     const void* w, unsigned illum, double* g);
+
+/* FP64 inner products <a_b, c_b> of two device prec vectors [batch][len]
+ * with compensated (Neumaier) accumulation; out: host double [batch].
+ * Synchronises. */
+qpat_status qpat_dot(qpat_ctx* ctx, int batch, long long len, const void* a, const void* b,
+                     double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QPAT_H */

@@ -1,0 +1,317 @@
+"""ctypes binding of ``include/qpat.h`` (argument marshalling only).
+
+Every function here converts torch tensors to raw device pointers and calls
+the entry point of the same name in ``libqpat.so``; all arithmetic runs in
+the library's CUDA kernels.  Outputs are allocated with torch on the tensor's
+device, and each call enqueues on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+_LIB_PATH = os.path.join(_PKG, "libqpat.so")
+_HEADER = os.path.join(_ROOT, "include", "qpat.h")
+
+STATUS = {0: "QPAT_OK", 1: "QPAT_EINVAL", 2: "QPAT_EUNSTABLE", 3: "QPAT_ENONFINITE",
+          4: "QPAT_ENOCONV", 5: "QPAT_ETIMEOUT", 6: "QPAT_ENOMEM", 7: "QPAT_ECUDA"}
+FP64, FP32 = 0, 1
+
+
+class QpatError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class qpat_config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 2), ("pml", ctypes.c_int), ("dx", ctypes.c_double),
+                ("dt", ctypes.c_double), ("nt", ctypes.c_int), ("c_ref", ctypes.c_double),
+                ("pml_alpha", ctypes.c_double), ("y", ctypes.c_double), ("lossless", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("gamma_d", ctypes.c_double),
+                ("pcg_max_iter", ctypes.c_int), ("pcg_tol", ctypes.c_double)]
+
+
+class qpat_medium(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("alpha0_db", ctypes.c_void_p),
+                ("kappa", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libqpat.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "qpat_create": [ctypes.POINTER(qpat_config), ctypes.POINTER(qpat_medium), vp, i, i, vp,
+                        ctypes.POINTER(vp)],
+        "qpat_destroy": [vp],
+        "qpat_set_stream": [vp, vp],
+        "qpat_get_sizes": [vp, ctypes.POINTER(ll)],
+        "qpat_sync": [vp],
+        "qpat_acoustic_forward": [vp, i, vp, vp],
+        "qpat_acoustic_adjoint": [vp, i, vp, vp],
+        "qpat_da_solve": [vp, i, vp, ctypes.c_uint, vp],
+        "qpat_forward": [vp, i, vp, ctypes.c_uint, vp, vp],
+        "qpat_jvp": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
+        "qpat_vjp": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
+        "qpat_dot": [vp, i, ll, vp, vp, ctypes.POINTER(d)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.qpat_last_error.argtypes = [vp]
+    lib.qpat_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of every entry point declared in include/qpat.h."""
+    text = open(_HEADER).read()
+    return sorted(set(re.findall(r"\b(qpat_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(ctx_ptr, status):
+    if status != 0:
+        msg = load().qpat_last_error(ctx_ptr) if ctx_ptr else b""
+        raise QpatError(status, (msg or b"").decode())
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else t.data_ptr()
+
+
+def _host(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Context:
+    """Owns a ``qpat_ctx``: medium, sensors, grid and workspace on one GPU."""
+
+    def __init__(self, c, rho, alpha0_db, kappa, sensors, *, dx, dt, nt, pml, y=1.5, lossless=False,
+                 precision="fp32", max_batch=1, c_ref=0.0, pml_alpha=0.0, gamma_d=0.0,
+                 pcg_max_iter=0, pcg_tol=0.0, device=None):
+        import torch
+        lib = load()
+        c = _host(c)
+        rho = _host(rho)
+        kappa = _host(kappa)
+        sensors = _host(sensors).reshape(-1, 2)
+        self.ny, self.nx = c.shape
+        self.n0, self.n1 = kappa.shape[1], kappa.shape[0]
+        cfg = qpat_config()
+        cfg.n[0], cfg.n[1] = self.n0, self.n1
+        cfg.pml, cfg.dx, cfg.dt, cfg.nt = int(pml), float(dx), float(dt), int(nt)
+        cfg.c_ref, cfg.pml_alpha, cfg.y = float(c_ref), float(pml_alpha), float(y)
+        cfg.lossless, cfg.max_batch = int(bool(lossless)), int(max_batch)
+        cfg.gamma_d, cfg.pcg_max_iter, cfg.pcg_tol = float(gamma_d), int(pcg_max_iter), float(pcg_tol)
+        keep = [c, rho, kappa, sensors]
+        al = None
+        if not lossless:
+            al = _host(alpha0_db)
+            keep.append(al)
+        med = qpat_medium(c.ctypes.data, rho.ctypes.data, None if al is None else al.ctypes.data,
+                          kappa.ctypes.data)
+        self.precision = precision
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.nt, self.ns, self.max_batch = int(nt), sensors.shape[0], int(max_batch)
+        self.N = self.n0 * self.n1
+        self.dx = float(dx)
+        out = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream().cuda_stream
+            st = lib.qpat_create(ctypes.byref(cfg), ctypes.byref(med), sensors.ctypes.data,
+                                 sensors.shape[0], FP32 if precision == "fp32" else FP64,
+                                 ctypes.c_void_p(stream), ctypes.byref(out))
+        if st != 0:
+            raise QpatError(st, "qpat_create failed (details on stderr)")
+        self._ptr = out
+        self._lib = lib
+
+    # -- plumbing ---------------------------------------------------------
+    def _stream(self):
+        import torch
+        _check(self._ptr, self._lib.qpat_set_stream(self._ptr, ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+
+    def _empty(self, *shape, dtype=None):
+        import torch
+        return torch.empty(*shape, dtype=dtype or self.dtype, device=self.device)
+
+    def _in(self, t, dtype, shape_tail):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise TypeError("expected a CUDA tensor")
+        if t.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {t.dtype}")
+        t = t.contiguous()
+        if t.dim() == len(shape_tail):
+            t = t.unsqueeze(0)
+        if tuple(t.shape[1:]) != tuple(shape_tail):
+            raise ValueError(f"expected trailing shape {shape_tail}, got {tuple(t.shape)}")
+        return t
+
+    def close(self):
+        if getattr(self, "_ptr", None):
+            self._lib.qpat_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sizes(self):
+        arr = (ctypes.c_longlong * 6)()
+        _check(self._ptr, self._lib.qpat_get_sizes(self._ptr, arr))
+        return list(arr)
+
+    def sync(self):
+        _check(self._ptr, self._lib.qpat_sync(self._ptr))
+
+    # -- entry points ----------------------------------------------------
+    def acoustic_forward(self, p0, out=None):
+        p0 = self._in(p0, self.dtype, (self.n1, self.n0))
+        B = p0.shape[0]
+        out = self._empty(B, self.nt, self.ns) if out is None else out
+        self._stream()
+        _check(self._ptr, self._lib.qpat_acoustic_forward(self._ptr, B, _ptr(p0), _ptr(out)))
+        return out
+
+    def acoustic_adjoint(self, data, out=None):
+        data = self._in(data, self.dtype, (self.nt, self.ns))
+        B = data.shape[0]
+        out = self._empty(B, self.n1, self.n0) if out is None else out
+        self._stream()
+        _check(self._ptr, self._lib.qpat_acoustic_adjoint(self._ptr, B, _ptr(data), _ptr(out)))
+        return out
+
+    def da_solve(self, mu, illum):
+        import torch
+        mu = self._in(mu, torch.float64, (self.n1, self.n0))
+        out = self._empty(mu.shape[0], self.n1, self.n0, dtype=torch.float64)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_da_solve(self._ptr, mu.shape[0], _ptr(mu), int(illum), _ptr(out)))
+        return out
+
+    def forward(self, mu, illum, return_phi=False):
+        import torch
+        mu = self._in(mu, torch.float64, (self.n1, self.n0))
+        B = mu.shape[0]
+        out = self._empty(B, self.nt, self.ns)
+        phi = self._empty(B, self.n1, self.n0, dtype=torch.float64) if return_phi else None
+        self._stream()
+        _check(self._ptr, self._lib.qpat_forward(self._ptr, B, _ptr(mu), int(illum), _ptr(out), _ptr(phi)))
+        return (out, phi) if return_phi else out
+
+    def jvp(self, mu, dmu, illum, phi0=None):
+        import torch
+        mu = self._in(mu, torch.float64, (self.n1, self.n0))
+        dmu = self._in(dmu, torch.float64, (self.n1, self.n0))
+        if phi0 is not None:
+            phi0 = self._in(phi0, torch.float64, (self.n1, self.n0))
+        B = dmu.shape[0]
+        out = self._empty(B, self.nt, self.ns)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_jvp(self._ptr, B, _ptr(mu), _ptr(phi0), _ptr(dmu), int(illum), _ptr(out)))
+        return out
+
+    def vjp(self, mu, w, illum, phi0=None):
+        import torch
+        mu = self._in(mu, torch.float64, (self.n1, self.n0))
+        w = self._in(w, self.dtype, (self.nt, self.ns))
+        if phi0 is not None:
+            phi0 = self._in(phi0, torch.float64, (self.n1, self.n0))
+        B = w.shape[0]
+        out = self._empty(B, self.n1, self.n0, dtype=torch.float64)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_vjp(self._ptr, B, _ptr(mu), _ptr(phi0), _ptr(w), int(illum), _ptr(out)))
+        return out
+
+    def dot(self, a, b):
+        a = a.contiguous()
+        b = b.contiguous()
+        if a.dtype != self.dtype or b.dtype != self.dtype or a.shape != b.shape:
+            raise TypeError("dot wants two tensors of the context precision and equal shape")
+        B = a.shape[0] if a.dim() > 1 else 1
+        L = a.numel() // B
+        out = (ctypes.c_double * B)()
+        self._stream()
+        _check(self._ptr, self._lib.qpat_dot(self._ptr, B, L, _ptr(a), _ptr(b), out))
+        return list(out)
+
+
+# C-ABI-named wrappers -------------------------------------------------------
+def qpat_create(*args, **kw) -> Context:
+    return Context(*args, **kw)
+
+
+def qpat_destroy(ctx: Context):
+    ctx.close()
+
+
+def qpat_acoustic_forward(ctx: Context, p0, out=None):
+    return ctx.acoustic_forward(p0, out)
+
+
+def qpat_acoustic_adjoint(ctx: Context, data, out=None):
+    return ctx.acoustic_adjoint(data, out)
+
+
+def qpat_da_solve(ctx: Context, mu, illum):
+    return ctx.da_solve(mu, illum)
+
+
+def qpat_forward(ctx: Context, mu, illum, return_phi=False):
+    return ctx.forward(mu, illum, return_phi)
+
+
+def qpat_jvp(ctx: Context, mu, dmu, illum, phi0=None):
+    return ctx.jvp(mu, dmu, illum, phi0)
+
+
+def qpat_vjp(ctx: Context, mu, w, illum, phi0=None):
+    return ctx.vjp(mu, w, illum, phi0)
+
+
+def qpat_dot(ctx: Context, a, b):
+    return ctx.dot(a, b)
+
+
+def qpat_sync(ctx: Context):
+    ctx.sync()
+
+
+def qpat_get_sizes(ctx: Context):
+    return ctx.sizes()
+
+
+def context_from_workload(w, precision="fp32", max_batch=1, nt=None, **kw) -> Context:
+    """Context for a ``phantoms.Workload`` (medium, sensors, dt from its recipe)."""
+    import phantoms
+    c, rho, alpha = phantoms.acoustic_medium(w)
+    dt = phantoms.time_step(w, c)
+    return Context(c, rho, alpha, phantoms.optical_diffusion(w), phantoms.sensor_positions(w),
+                   dx=w.dx, dt=dt, nt=w.nt if nt is None else nt, pml=w.pml, y=w.y, lossless=w.lossless,
+                   precision=precision, max_batch=max_batch, **kw)

@@ -1,0 +1,613 @@
+// C ABI of the direct-QPAT propagation library (see include/qpat.h).
+//
+// A context owns the device tables and the workspace for up to max_batch
+// problems on one grid and medium.  The forward operator H_a is the launch
+// sequence of Section 3.2.3 (one row/column pass chain per time step, from
+// n = -1 to Nt - 2); H_a^* runs the transposed steps in reverse (Section
+// 3.2.4).  The composite maps chain the FP64 diffusion solve, the heating
+// map and H_a / H_a^* (eqs. com_des, J_des, Lemma 1).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "qpat.h"
+#include "qpat_internal.h"
+
+using namespace qpat;
+
+struct qpat_ctx {
+  int prec = QPAT_FP32;
+  cudaStream_t stream = nullptr;
+  qpat_config cfg{};
+  int nx = 0, ny = 0, nxh = 0, pitch = 0, n0 = 0, n1 = 0, pml = 0, ns = 0, nt = 0, maxb = 1;
+  long long N = 0, G = 0;
+  double dx = 0, dt = 0, c_ref = 0, c_max = 0;
+  std::string err;
+  std::vector<void*> dev_allocs;
+  std::vector<void*> host_allocs;
+  PropArgs<float> pf{};
+  PropArgs<double> pd{};
+  DAArgs da{};
+  PCGWork pcg{};
+  int* d_err = nullptr;
+  int* h_err = nullptr;
+  void* tw_p0 = nullptr;       // [B][N] prec: heating handed to H_a
+  void* tw_hbar = nullptr;     // [B][N] prec: H_a^* output
+  double* d_phi = nullptr;     // [B][N]
+  double* d_rhs = nullptr;     // [B][N]
+  double* d_tmp = nullptr;     // [B][N]
+  double* d_dot_partial = nullptr;
+  double* d_dot_out = nullptr;
+  double* h_dot_out = nullptr;
+};
+
+namespace {
+
+qpat_status fail(qpat_ctx* c, qpat_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+qpat_status cuda_fail(qpat_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? QPAT_ENOMEM : QPAT_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define QCK(expr)                                                  \
+  do {                                                             \
+    cudaError_t e_ = (expr);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr);         \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(qpat_ctx* c, P** p, size_t bytes) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, bytes < 16 ? 16 : bytes);
+  if (e == cudaSuccess) {
+    c->dev_allocs.push_back(v);
+    *p = reinterpret_cast<P*>(v);
+  }
+  return e;
+}
+
+bool factor_plan(int L, FFTPlan& p) {
+  p.L = L;
+  p.nstages = 0;
+  int r = L;
+  int twos = 0;
+  while (r % 2 == 0) { r /= 2; ++twos; }
+  while (twos >= 3) { p.radix[p.nstages++] = 8; twos -= 3; }
+  if (twos == 2) p.radix[p.nstages++] = 4;
+  if (twos == 1) p.radix[p.nstages++] = 2;
+  for (int q : {3, 5, 7}) {
+    while (r % q == 0) {
+      if (p.nstages >= kMaxStages) return false;
+      p.radix[p.nstages++] = q;
+      r /= q;
+    }
+  }
+  return r == 1 && p.nstages <= kMaxStages;
+}
+
+template <typename T>
+PropArgs<T>& args(qpat_ctx* c);
+template <>
+PropArgs<float>& args<float>(qpat_ctx* c) { return c->pf; }
+template <>
+PropArgs<double>& args<double>(qpat_ctx* c) { return c->pd; }
+
+// Device tables + workspace for working precision T.
+template <typename T>
+qpat_status build_context(qpat_ctx* c, const qpat_medium* med, const double* sensor_xy) {
+  typedef typename V2<T>::t C;
+  PropArgs<T>& a = args<T>(c);
+  a.nx = c->nx; a.ny = c->ny; a.nxh = c->nxh; a.pitch = c->pitch; a.pml = c->pml;
+  a.n0 = c->n0; a.n1 = c->n1; a.ns = c->ns; a.nt = c->nt;
+  if (!factor_plan(c->nx, a.px) || !factor_plan(c->ny, a.py))
+    return fail(c, QPAT_EINVAL, "FFT extents must factor into 2, 3, 5 and 7");
+  // column tile width: widest of 8/4/2/1 columns whose tile fits 100 KB of shared memory
+  a.cb = 1;
+  for (int cb : {8, 4, 2}) {
+    if (col_smem_bytes<T>(c->ny, cb) <= 100 * 1024 && cb * 4 <= c->nxh) { a.cb = cb; break; }
+  }
+  if (row_smem_bytes<T>(c->nx) > 227 * 1024 || col_smem_bytes<T>(c->ny, a.cb) > 227 * 1024)
+    return fail(c, QPAT_EINVAL, "grid too large for the shared-memory FFT passes");
+  a.dt = (T)c->dt;
+  const long long G = c->G, N = c->N;
+  const int B = c->maxb;
+  TableOut<T> o{};
+  QCK(dalloc(c, &o.Cc, G * sizeof(T)));
+  QCK(dalloc(c, &o.rho0, G * sizeof(T)));
+  QCK(dalloc(c, &o.dtrsx, G * sizeof(T)));
+  QCK(dalloc(c, &o.dtrsy, G * sizeof(T)));
+  QCK(dalloc(c, &o.tau, G * sizeof(T)));
+  QCK(dalloc(c, &o.eta, G * sizeof(T)));
+  QCK(dalloc(c, &o.ax, c->nx * sizeof(T)));
+  QCK(dalloc(c, &o.asx, c->nx * sizeof(T)));
+  QCK(dalloc(c, &o.ay, c->ny * sizeof(T)));
+  QCK(dalloc(c, &o.asy, c->ny * sizeof(T)));
+  const long long KT = (long long)c->ny * c->nxh;
+  QCK(dalloc(c, &o.kap, KT * sizeof(T)));
+  QCK(dalloc(c, &o.kp1, KT * sizeof(T)));
+  QCK(dalloc(c, &o.kp2, KT * sizeof(T)));
+  QCK(dalloc(c, &o.shxp, c->nxh * sizeof(C)));
+  QCK(dalloc(c, &o.shxm, c->nxh * sizeof(C)));
+  QCK(dalloc(c, &o.shyp, c->ny * sizeof(C)));
+  QCK(dalloc(c, &o.shym, c->ny * sizeof(C)));
+  QCK(dalloc(c, &o.twx, c->nx * sizeof(C)));
+  QCK(dalloc(c, &o.twy, c->ny * sizeof(C)));
+  // FP64 medium staging
+  double *dc = nullptr, *drho = nullptr, *dal = nullptr;
+  QCK(cudaMalloc(&dc, G * sizeof(double)));
+  QCK(cudaMalloc(&drho, G * sizeof(double)));
+  QCK(cudaMalloc(&dal, G * sizeof(double)));
+  QCK(cudaMemcpyAsync(dc, med->c, G * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  QCK(cudaMemcpyAsync(drho, med->rho, G * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (!c->cfg.lossless) QCK(cudaMemcpyAsync(dal, med->alpha0_db, G * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  QCK(build_tables<T>(o, dc, drho, dal, c->nx, c->ny, c->nxh, c->pml, c->dx, c->dt, c->c_ref,
+                      c->cfg.pml_alpha, c->cfg.y, c->cfg.lossless, c->stream));
+  QCK(cudaStreamSynchronize(c->stream));
+  cudaFree(dc);
+  cudaFree(drho);
+  cudaFree(dal);
+  a.Cc = o.Cc; a.rho0 = o.rho0; a.dtrsx = o.dtrsx; a.dtrsy = o.dtrsy; a.tau = o.tau; a.eta = o.eta;
+  a.ax = o.ax; a.asx = o.asx; a.ay = o.ay; a.asy = o.asy;
+  a.kap = o.kap; a.kp1 = o.kp1; a.kp2 = o.kp2;
+  a.shxp = o.shxp; a.shxm = o.shxm; a.shyp = o.shyp; a.shym = o.shym;
+  a.twx = o.twx; a.twy = o.twy;
+
+  // sensors: bilinear weights on the node grid (gather form) and the
+  // transposed scatter as a per-row, per-point gather (deterministic)
+  std::vector<int> sidx(4 * (size_t)c->ns);
+  std::vector<T> sw(4 * (size_t)c->ns);
+  std::vector<std::tuple<int, int, int, double>> ent;   // row, col, sensor, weight
+  for (int s = 0; s < c->ns; ++s) {
+    int base[2];
+    double frac[2];
+    const int Nax[2] = {c->nx, c->ny};
+    for (int ax = 0; ax < 2; ++ax) {
+      const double g = sensor_xy[2 * s + ax] / c->dx + (Nax[ax] - 1) / 2.0;
+      const int j0 = (int)floor(g);
+      const double f = g - j0;
+      if (!(g == g) || j0 < 0 || j0 > Nax[ax] - 1 || (j0 == Nax[ax] - 1 && f > 0))
+        return fail(c, QPAT_EINVAL, "sensor " + std::to_string(s) + " lies outside the grid");
+      base[ax] = j0;
+      frac[ax] = f;
+    }
+    for (int corner = 0; corner < 4; ++corner) {
+      const int bx = corner & 1, by = (corner >> 1) & 1;
+      const double wgt = (bx ? frac[0] : 1.0 - frac[0]) * (by ? frac[1] : 1.0 - frac[1]);
+      const int ix = std::min(base[0] + bx, c->nx - 1), iy = std::min(base[1] + by, c->ny - 1);
+      sidx[4 * s + corner] = iy * c->nx + ix;
+      sw[4 * s + corner] = (T)wgt;
+      if (wgt != 0.0) ent.emplace_back(iy, ix, s, wgt);
+    }
+  }
+  std::sort(ent.begin(), ent.end());
+  std::vector<int> rowptr(c->ny + 1, 0), pcol, pent, esens;
+  std::vector<T> ew;
+  {
+    int prev_r = -1, prev_c = -1;
+    for (size_t e = 0; e < ent.size(); ++e) {
+      const int r = std::get<0>(ent[e]), col = std::get<1>(ent[e]);
+      if (r != prev_r || col != prev_c) {
+        pcol.push_back(col);
+        pent.push_back((int)e);
+        rowptr[r + 1] += 1;
+        prev_r = r;
+        prev_c = col;
+      }
+      esens.push_back(std::get<2>(ent[e]));
+      ew.push_back((T)std::get<3>(ent[e]));
+    }
+    pent.push_back((int)ent.size());
+    for (int r = 0; r < c->ny; ++r) rowptr[r + 1] += rowptr[r];
+  }
+  int *d_sidx, *d_rowptr, *d_pcol, *d_pent, *d_esens;
+  T *d_sw, *d_ew;
+  QCK(dalloc(c, &d_sidx, sidx.size() * sizeof(int)));
+  QCK(dalloc(c, &d_sw, sw.size() * sizeof(T)));
+  QCK(dalloc(c, &d_rowptr, rowptr.size() * sizeof(int)));
+  QCK(dalloc(c, &d_pcol, std::max<size_t>(1, pcol.size()) * sizeof(int)));
+  QCK(dalloc(c, &d_pent, pent.size() * sizeof(int)));
+  QCK(dalloc(c, &d_esens, std::max<size_t>(1, esens.size()) * sizeof(int)));
+  QCK(dalloc(c, &d_ew, std::max<size_t>(1, ew.size()) * sizeof(T)));
+  QCK(cudaMemcpy(d_sidx, sidx.data(), sidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  QCK(cudaMemcpy(d_sw, sw.data(), sw.size() * sizeof(T), cudaMemcpyHostToDevice));
+  QCK(cudaMemcpy(d_rowptr, rowptr.data(), rowptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!pcol.empty()) QCK(cudaMemcpy(d_pcol, pcol.data(), pcol.size() * sizeof(int), cudaMemcpyHostToDevice));
+  QCK(cudaMemcpy(d_pent, pent.data(), pent.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!esens.empty()) QCK(cudaMemcpy(d_esens, esens.data(), esens.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!ew.empty()) QCK(cudaMemcpy(d_ew, ew.data(), ew.size() * sizeof(T), cudaMemcpyHostToDevice));
+  a.sidx = d_sidx; a.sw = d_sw; a.rowptr = d_rowptr; a.pcol = d_pcol; a.pent = d_pent; a.esens = d_esens; a.ew = d_ew;
+
+  // workspace
+  a.gstride = G;
+  a.sstride = 2LL * c->ny * c->pitch;
+  T *vx, *vy, *rx, *ry, *pbuf;
+  C* spec;
+  QCK(dalloc(c, &vx, (size_t)B * G * sizeof(T)));
+  QCK(dalloc(c, &vy, (size_t)B * G * sizeof(T)));
+  QCK(dalloc(c, &rx, (size_t)B * G * sizeof(T)));
+  QCK(dalloc(c, &ry, (size_t)B * G * sizeof(T)));
+  QCK(dalloc(c, &pbuf, (size_t)B * G * sizeof(T)));
+  QCK(dalloc(c, &spec, (size_t)B * a.sstride * sizeof(C)));
+  QCK(cudaMemset(spec, 0, (size_t)B * a.sstride * sizeof(C)));
+  a.vx = vx; a.vy = vy; a.rx = rx; a.ry = ry; a.pbuf = pbuf; a.spec = spec;
+  QCK(dalloc(c, &c->tw_p0, (size_t)B * N * sizeof(T)));
+  QCK(dalloc(c, &c->tw_hbar, (size_t)B * N * sizeof(T)));
+  a.err = c->d_err;
+  prop_init_attributes<T>();
+  return QPAT_OK;
+}
+
+template <typename T>
+void zero_state(qpat_ctx* c, int batch) {
+  PropArgs<T>& a = args<T>(c);
+  const size_t bytes = (size_t)batch * c->G * sizeof(T);
+  cudaMemsetAsync(a.vx, 0, bytes, c->stream);
+  cudaMemsetAsync(a.vy, 0, bytes, c->stream);
+  cudaMemsetAsync(a.rx, 0, bytes, c->stream);
+  cudaMemsetAsync(a.ry, 0, bytes, c->stream);
+}
+
+// H_a: launch sequence of the forward loop n = -1 .. Nt - 2 (Section 3.2.3).
+template <typename T>
+qpat_status run_forward(qpat_ctx* c, int batch, const T* p0, T* data) {
+  PropArgs<T> a = args<T>(c);
+  cudaStream_t s = c->stream;
+  a.p0 = p0;
+  a.data = data;
+  zero_state<T>(c, batch);
+  const int nt = c->nt;
+  if (!c->cfg.lossless) {
+    a.n = 0;
+    a.flags = kSkipInput | kSource;          // step n = -1 from zero fields
+    launch_row<T>(a, F_R3, batch, s);
+    a.flags = 0;
+    launch_col<T>(a, F_C3, batch, s);
+    for (int n = 0; n <= nt - 2; ++n) {
+      a.n = n;
+      a.flags = 0;
+      launch_row<T>(a, F_R1, batch, s);      // p_n
+      launch_col<T>(a, F_C1, batch, s);      // sample n, d/dr^+ p_n
+      launch_row<T>(a, F_R2, batch, s);      // v^(n+1/2)
+      launch_col<T>(a, F_C2, batch, s);      // d/dr^- v
+      a.flags = (n == 0) ? kSource : 0;
+      launch_row<T>(a, F_R3, batch, s);      // rho^(n+1)
+      a.flags = 0;
+      launch_col<T>(a, F_C3, batch, s);      // Y_dis, Y_abs
+    }
+    a.n = nt - 1;
+    a.flags = kSkipOutput;
+    launch_row<T>(a, F_R1, batch, s);        // p_(Nt-1)
+    launch_gather<T>(a, batch, s);
+  } else {
+    a.n = 0;
+    a.flags = kSkipInput | kSource;
+    launch_row<T>(a, F_R3L, batch, s);       // p_0
+    for (int n = 0; n <= nt - 2; ++n) {
+      a.n = n;
+      a.flags = 0;
+      launch_col<T>(a, F_C1, batch, s);
+      launch_row<T>(a, F_R2, batch, s);
+      launch_col<T>(a, F_C2, batch, s);
+      a.flags = (n == 0) ? kSource : 0;
+      launch_row<T>(a, F_R3L, batch, s);     // p_(n+1)
+    }
+    a.n = nt - 1;
+    launch_gather<T>(a, batch, s);
+  }
+  QCK(cudaGetLastError());
+  return QPAT_OK;
+}
+
+// H_a^*: transposed steps in reverse, n = Nt - 2 .. -1 (Section 3.2.4).
+template <typename T>
+qpat_status run_adjoint(qpat_ctx* c, int batch, const T* w, T* p0adj) {
+  PropArgs<T> a = args<T>(c);
+  cudaStream_t s = c->stream;
+  a.w = w;
+  a.p0adj = p0adj;
+  zero_state<T>(c, batch);
+  const int nt = c->nt;
+  for (int n = nt - 2; n >= -1; --n) {
+    a.n = n + 1;                                   // the sample p_(n+1) produced
+    const int first = (n == nt - 2) ? kSkipInput : 0;
+    const int acc = (n == 0) ? kAccWrite : (n == -1 ? kAccAdd : 0);
+    const int last = (n == -1) ? kSkipOutput : 0;
+    if (!c->cfg.lossless) {
+      a.flags = first;
+      launch_row<T>(a, A_R1, batch, s);
+      a.flags = 0;
+      launch_col<T>(a, A_C2, batch, s);
+      a.flags = acc | last;
+      launch_row<T>(a, A_R3, batch, s);
+    } else {
+      a.flags = first | acc | last;
+      launch_row<T>(a, A_R1L, batch, s);
+    }
+    if (n > -1) {
+      a.flags = 0;
+      launch_col<T>(a, A_C4, batch, s);
+      launch_row<T>(a, A_R5, batch, s);
+      launch_col<T>(a, A_C6, batch, s);
+    }
+  }
+  QCK(cudaGetLastError());
+  return QPAT_OK;
+}
+
+qpat_status check_batch(qpat_ctx* c, int batch) {
+  if (!c) return QPAT_EINVAL;
+  if (batch < 1 || batch > c->maxb)
+    return fail(c, QPAT_EINVAL, "batch " + std::to_string(batch) + " outside 1.." + std::to_string(c->maxb));
+  return QPAT_OK;
+}
+
+qpat_status solve_da(qpat_ctx* c, int batch, const double* mu, const double* rhs, double* x) {
+  cudaError_t e = cudaSuccess;
+  const int used = pcg_solve(c->da, mu, batch, rhs, x, c->pcg, c->cfg.pcg_max_iter, c->cfg.pcg_tol, c->stream, &e);
+  if (e != cudaSuccess) return cuda_fail(c, e, "diffusion solve");
+  if (used < 0) return fail(c, QPAT_ENOCONV, "diffusion solve reached its iteration cap");
+  return QPAT_OK;
+}
+
+qpat_status fluence(qpat_ctx* c, int batch, const double* mu, unsigned illum, double* phi) {
+  QCK(da_rhs_from_sides(c->da, illum, batch, c->d_rhs, c->stream));
+  return solve_da(c, batch, mu, c->d_rhs, phi);
+}
+
+}  // namespace
+
+extern "C" {
+
+qpat_status qpat_create(const qpat_config* cfg, const qpat_medium* med, const double* sensor_xy, int ns,
+                        qpat_precision prec, void* stream, qpat_ctx** out) {
+  if (!out) return QPAT_EINVAL;
+  *out = nullptr;
+  if (!cfg || !med || !med->c || !med->rho || !med->kappa || !sensor_xy || ns < 1) return QPAT_EINVAL;
+  qpat_ctx* c = new qpat_ctx();
+  c->cfg = *cfg;
+  c->prec = prec;
+  c->stream = (cudaStream_t)stream;
+  auto bad = [&](qpat_status st, const std::string& m) {
+    fprintf(stderr, "qpat_create: %s\n", m.c_str());
+    qpat_destroy(c);
+    return st;
+  };
+  if (prec != QPAT_FP32 && prec != QPAT_FP64) return bad(QPAT_EINVAL, "unknown precision");
+  if (cfg->n[0] < 1 || cfg->n[1] < 1 || cfg->pml < 0) return bad(QPAT_EINVAL, "bad grid size");
+  if (!(cfg->dx > 0) || !(cfg->dt > 0)) return bad(QPAT_EINVAL, "dx and dt must be positive");
+  if (cfg->nt < 2) return bad(QPAT_EINVAL, "nt must be at least 2");
+  c->n0 = cfg->n[0];
+  c->n1 = cfg->n[1];
+  c->pml = cfg->pml;
+  c->nx = c->n0 + 2 * c->pml;
+  c->ny = c->n1 + 2 * c->pml;
+  if (c->nx % 2 || c->ny % 2) return bad(QPAT_EINVAL, "FFT grid extents must be even");
+  if (c->nx < 8 || c->ny < 8) return bad(QPAT_EINVAL, "FFT grid extents must be at least 8");
+  c->nxh = c->nx / 2 + 1;
+  c->pitch = (c->nxh + 3) / 4 * 4;
+  c->N = (long long)c->n0 * c->n1;
+  c->G = (long long)c->nx * c->ny;
+  c->ns = ns;
+  c->nt = cfg->nt;
+  c->dx = cfg->dx;
+  c->dt = cfg->dt;
+  c->maxb = cfg->max_batch > 0 ? cfg->max_batch : 1;
+  if (!(c->cfg.pml_alpha > 0)) c->cfg.pml_alpha = 2.0;
+  if (!(c->cfg.gamma_d > 0)) c->cfg.gamma_d = 1.0 / M_PI;
+  if (c->cfg.pcg_max_iter <= 0) c->cfg.pcg_max_iter = 20000;
+  if (!(c->cfg.pcg_tol > 0)) c->cfg.pcg_tol = 1e-13;
+  if (!c->cfg.lossless) {
+    if (!med->alpha0_db) return bad(QPAT_EINVAL, "alpha0_db is required unless lossless");
+    if (!(cfg->y > 1.0 && cfg->y < 3.0) || fabs(cfg->y - 2.0) < 1e-12)
+      return bad(QPAT_EINVAL, "power-law exponent y must lie in (1, 3) and differ from 2");
+  }
+  double cmax = 0.0;
+  for (long long g = 0; g < c->G; ++g) {
+    const double v = med->c[g], r = med->rho[g];
+    if (!(v > 0) || !(r > 0)) return bad(QPAT_EINVAL, "c and rho must be positive and finite");
+    if (!c->cfg.lossless && !(med->alpha0_db[g] >= 0)) return bad(QPAT_EINVAL, "alpha0 must be >= 0");
+    cmax = std::max(cmax, v);
+  }
+  for (long long g = 0; g < c->N; ++g)
+    if (!(med->kappa[g] > 0)) return bad(QPAT_EINVAL, "kappa must be positive and finite");
+  c->c_max = cmax;
+  c->c_ref = cfg->c_ref > 0 ? cfg->c_ref : cmax;
+  if (cmax * c->dt / c->dx > 2.0 / (M_PI * sqrt(2.0)))
+    return bad(QPAT_EUNSTABLE, "c_max dt / dx exceeds 2 / (pi sqrt 2)");
+
+  cudaError_t e;
+#define QCKC(expr)                                                                  \
+  do {                                                                              \
+    e = (expr);                                                                     \
+    if (e != cudaSuccess) return bad(e == cudaErrorMemoryAllocation ? QPAT_ENOMEM : QPAT_ECUDA, \
+                                     std::string(#expr) + ": " + cudaGetErrorString(e)); \
+  } while (0)
+  QCKC(dalloc(c, &c->d_err, sizeof(int)));
+  QCKC(cudaMemset(c->d_err, 0, sizeof(int)));
+  QCKC(cudaMallocHost(&c->h_err, sizeof(int)));
+  c->host_allocs.push_back(c->h_err);
+  qpat_status st = (prec == QPAT_FP32) ? build_context<float>(c, med, sensor_xy)
+                                       : build_context<double>(c, med, sensor_xy);
+  if (st != QPAT_OK) return bad(st, c->err);
+
+  // diffusion solve
+  const int B = c->maxb;
+  const long long N = c->N;
+  c->da.n0 = c->n0;
+  c->da.n1 = c->n1;
+  c->da.N = (int)N;
+  c->da.h = c->dx;
+  c->da.gamma = c->cfg.gamma_d;
+  double *diag0, *cxf, *cyf, *bside, *dkappa;
+  QCKC(dalloc(c, &diag0, N * sizeof(double)));
+  QCKC(dalloc(c, &cxf, N * sizeof(double)));
+  QCKC(dalloc(c, &cyf, N * sizeof(double)));
+  QCKC(dalloc(c, &bside, 4 * N * sizeof(double)));
+  QCKC(dalloc(c, &dkappa, N * sizeof(double)));
+  QCKC(cudaMemcpy(dkappa, med->kappa, N * sizeof(double), cudaMemcpyHostToDevice));
+  QCKC(da_setup(c->da, diag0, cxf, cyf, bside, dkappa, c->stream));
+  PCGWork& w = c->pcg;
+  for (double** p : {&w.x, &w.r, &w.z, &w.p, &w.q, &w.dinv, &w.b}) QCKC(dalloc(c, p, B * N * sizeof(double)));
+  QCKC(dalloc(c, &w.partial, (size_t)B * kPartials * 4 * sizeof(double)));
+  QCKC(dalloc(c, &w.scal, (size_t)B * 8 * sizeof(double)));
+  QCKC(cudaMallocHost(&w.hostscal, (size_t)B * 8 * sizeof(double)));
+  c->host_allocs.push_back(w.hostscal);
+  QCKC(dalloc(c, &c->d_phi, B * N * sizeof(double)));
+  QCKC(dalloc(c, &c->d_rhs, B * N * sizeof(double)));
+  QCKC(dalloc(c, &c->d_tmp, B * N * sizeof(double)));
+  QCKC(dalloc(c, &c->d_dot_partial, (size_t)B * kPartials * 4 * sizeof(double)));
+  QCKC(dalloc(c, &c->d_dot_out, (size_t)B * sizeof(double)));
+  QCKC(cudaMallocHost(&c->h_dot_out, (size_t)B * sizeof(double)));
+  c->host_allocs.push_back(c->h_dot_out);
+  QCKC(cudaStreamSynchronize(c->stream));
+#undef QCKC
+  *out = c;
+  return QPAT_OK;
+}
+
+qpat_status qpat_destroy(qpat_ctx* c) {
+  if (!c) return QPAT_OK;
+  cudaStreamSynchronize(c->stream);
+  for (void* p : c->dev_allocs) cudaFree(p);
+  for (void* p : c->host_allocs) cudaFreeHost(p);
+  delete c;
+  return QPAT_OK;
+}
+
+qpat_status qpat_set_stream(qpat_ctx* c, void* stream) {
+  if (!c) return QPAT_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  return QPAT_OK;
+}
+
+const char* qpat_last_error(const qpat_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+qpat_status qpat_get_sizes(const qpat_ctx* c, long long out[6]) {
+  if (!c || !out) return QPAT_EINVAL;
+  out[0] = c->nx;
+  out[1] = c->ny;
+  out[2] = c->N;
+  out[3] = c->ns;
+  out[4] = c->nt;
+  out[5] = c->maxb;
+  return QPAT_OK;
+}
+
+qpat_status qpat_sync(qpat_ctx* c) {
+  if (!c) return QPAT_EINVAL;
+  QCK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  QCK(cudaStreamSynchronize(c->stream));
+  if (*c->h_err) {
+    QCK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    QCK(cudaStreamSynchronize(c->stream));
+    if (*c->h_err & 1) return fail(c, QPAT_ENONFINITE, "non-finite value in the acoustic fields");
+  }
+  return QPAT_OK;
+}
+
+qpat_status qpat_acoustic_forward(qpat_ctx* c, int batch, const void* p0, void* data) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!p0 || !data) return fail(c, QPAT_EINVAL, "null buffer");
+  return c->prec == QPAT_FP32 ? run_forward<float>(c, batch, (const float*)p0, (float*)data)
+                              : run_forward<double>(c, batch, (const double*)p0, (double*)data);
+}
+
+qpat_status qpat_acoustic_adjoint(qpat_ctx* c, int batch, const void* data, void* p0_adj) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!p0_adj || !data) return fail(c, QPAT_EINVAL, "null buffer");
+  return c->prec == QPAT_FP32 ? run_adjoint<float>(c, batch, (const float*)data, (float*)p0_adj)
+                              : run_adjoint<double>(c, batch, (const double*)data, (double*)p0_adj);
+}
+
+qpat_status qpat_da_solve(qpat_ctx* c, int batch, const double* mu, unsigned illum, double* phi) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!mu || !phi) return fail(c, QPAT_EINVAL, "null buffer");
+  if (illum == 0 || illum > 15u) return fail(c, QPAT_EINVAL, "illumination mask must select sides 0..3");
+  return fluence(c, batch, mu, illum, phi);
+}
+
+qpat_status qpat_forward(qpat_ctx* c, int batch, const double* mu, unsigned illum, void* data, double* phi0_out) {
+  qpat_status st = qpat_da_solve(c, batch, mu, illum, c ? c->d_phi : nullptr);
+  if (st != QPAT_OK) return st;
+  if (!data) return fail(c, QPAT_EINVAL, "null buffer");
+  const int N = (int)c->N;
+  // heating h = mu o phi (eq. h), p0 = h (Gamma = 1)
+  if (c->prec == QPAT_FP32) QCK(da_heating_T<float>(batch, N, mu, c->d_phi, nullptr, nullptr, (float*)c->tw_p0, c->stream));
+  else QCK(da_heating_T<double>(batch, N, mu, c->d_phi, nullptr, nullptr, (double*)c->tw_p0, c->stream));
+  if (phi0_out)
+    QCK(cudaMemcpyAsync(phi0_out, c->d_phi, (size_t)batch * N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return qpat_acoustic_forward(c, batch, c->tw_p0, data);
+}
+
+qpat_status qpat_jvp(qpat_ctx* c, int batch, const double* mu, const double* phi0, const double* dmu, unsigned illum,
+                     void* dP) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!mu || !dmu || !dP) return fail(c, QPAT_EINVAL, "null buffer");
+  const int N = (int)c->N;
+  if (!phi0) {
+    st = qpat_da_solve(c, batch, mu, illum, c->d_phi);
+    if (st != QPAT_OK) return st;
+    phi0 = c->d_phi;
+  }
+  // A dphi = -h^2 dmu o phi0 (eq. dh_des)
+  QCK(da_hadamard(batch, N, -c->dx * c->dx, dmu, phi0, c->d_rhs, c->stream));
+  st = solve_da(c, batch, mu, c->d_rhs, c->d_tmp);
+  if (st != QPAT_OK) return st;
+  if (c->prec == QPAT_FP32) QCK(da_heating_T<float>(batch, N, dmu, phi0, mu, c->d_tmp, (float*)c->tw_p0, c->stream));
+  else QCK(da_heating_T<double>(batch, N, dmu, phi0, mu, c->d_tmp, (double*)c->tw_p0, c->stream));
+  return qpat_acoustic_forward(c, batch, c->tw_p0, dP);
+}
+
+qpat_status qpat_vjp(qpat_ctx* c, int batch, const double* mu, const double* phi0, const void* w, unsigned illum,
+                     double* g) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!mu || !w || !g) return fail(c, QPAT_EINVAL, "null buffer");
+  const int N = (int)c->N;
+  st = qpat_acoustic_adjoint(c, batch, w, c->tw_hbar);
+  if (st != QPAT_OK) return st;
+  if (!phi0) {
+    st = qpat_da_solve(c, batch, mu, illum, c->d_phi);
+    if (st != QPAT_OK) return st;
+    phi0 = c->d_phi;
+  }
+  // A H~ = -h^2 mu o hbar (eq. system_adjoint); g = phi0 o (hbar + H~) (eq. prodtproj)
+  const double sc = -c->dx * c->dx;
+  if (c->prec == QPAT_FP32) QCK(da_adjoint_rhs<float>(batch, N, sc, mu, (const float*)c->tw_hbar, c->d_rhs, c->stream));
+  else QCK(da_adjoint_rhs<double>(batch, N, sc, mu, (const double*)c->tw_hbar, c->d_rhs, c->stream));
+  st = solve_da(c, batch, mu, c->d_rhs, c->d_tmp);
+  if (st != QPAT_OK) return st;
+  if (c->prec == QPAT_FP32) QCK(da_adjoint_out<float>(batch, N, phi0, (const float*)c->tw_hbar, c->d_tmp, g, c->stream));
+  else QCK(da_adjoint_out<double>(batch, N, phi0, (const double*)c->tw_hbar, c->d_tmp, g, c->stream));
+  return QPAT_OK;
+}
+
+qpat_status qpat_dot(qpat_ctx* c, int batch, long long len, const void* a, const void* b, double* out) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!a || !b || !out || len < 0) return fail(c, QPAT_EINVAL, "bad dot arguments");
+  if (c->prec == QPAT_FP32)
+    QCK(dot_compensated<float>(batch, len, (const float*)a, (const float*)b, c->d_dot_partial, c->d_dot_out, c->stream));
+  else
+    QCK(dot_compensated<double>(batch, len, (const double*)a, (const double*)b, c->d_dot_partial, c->d_dot_out,
+                                c->stream));
+  QCK(cudaMemcpyAsync(c->h_dot_out, c->d_dot_out, batch * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  QCK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < batch; ++i) out[i] = c->h_dot_out[i];
+  return QPAT_OK;
+}
+
+}  // extern "C"

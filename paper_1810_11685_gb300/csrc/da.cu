@@ -1,0 +1,350 @@
+// Diffusion-approximation optical solve (Section 2.1, eq. DA) in FP64.
+//
+// Cell-centred finite volumes on the interior grid (the optical grid is the
+// acoustic interior): an interior face between cells a, b carries
+// kappa_f (phi_a - phi_b) with the harmonic mean kappa_f (2D, the face
+// length h cancels the 1/h of the gradient); the Robin condition
+// phi + kappa/(2 gamma) dphi/dn = I/gamma, eliminated through the half-cell
+// gradient, adds 2 gamma kappa h / (gamma h + kappa) to the diagonal and
+// 2 kappa I h / (gamma h + kappa) to the right-hand side per boundary face;
+// absorption adds mu h^2.  The matrix is symmetric positive definite and is
+// solved by Jacobi-preconditioned conjugate gradients with FP64 dot products
+// (deterministic two-level reductions), batched over problems.
+#include "qpat_internal.h"
+
+namespace qpat {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+__global__ void da_setup_kernel(int n0, int n1, double h, double gam, const double* kappa, double* diag0,
+                                double* cxf, double* cyf, double* bside) {
+  const int N = n0 * n1;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
+    const int i = g % n0, j = g / n0;
+    const double k = kappa[g];
+    double d = 0.0;
+    if (i > 0) d += harmonic(k, kappa[g - 1]);
+    if (i < n0 - 1) d += harmonic(k, kappa[g + 1]);
+    if (j > 0) d += harmonic(k, kappa[g - n0]);
+    if (j < n1 - 1) d += harmonic(k, kappa[g + n0]);
+    const double robin = 2.0 * gam * k * h / (gam * h + k);
+    const double src = 2.0 * k * h / (gam * h + k);
+    const bool on[4] = {i == 0, i == n0 - 1, j == 0, j == n1 - 1};
+    for (int s = 0; s < 4; ++s) {
+      if (on[s]) d += robin;
+      bside[(long long)s * N + g] = on[s] ? src : 0.0;
+    }
+    diag0[g] = d;
+    cxf[g] = (i < n0 - 1) ? harmonic(k, kappa[g + 1]) : 0.0;
+    cyf[g] = (j < n1 - 1) ? harmonic(k, kappa[g + n0]) : 0.0;
+  }
+}
+
+cudaError_t da_setup(DAArgs& a, double* d_diag0, double* d_cxf, double* d_cyf, double* d_bside,
+                     const double* d_kappa, cudaStream_t s) {
+  da_setup_kernel<<<256, kThreads, 0, s>>>(a.n0, a.n1, a.h, a.gamma, d_kappa, d_diag0, d_cxf, d_cyf, d_bside);
+  a.diag0 = d_diag0;
+  a.cxf = d_cxf;
+  a.cyf = d_cyf;
+  a.bside = d_bside;
+  return cudaGetLastError();
+}
+
+__global__ void rhs_sides_kernel(DAArgs a, unsigned mask, double* rhs) {
+  const int b = blockIdx.y;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int s = 0; s < 4; ++s)
+      if ((mask >> s) & 1u) v += a.bside[(long long)s * a.N + g];
+    rhs[(long long)b * a.N + g] = v;
+  }
+}
+
+cudaError_t da_rhs_from_sides(const DAArgs& a, unsigned mask, int batch, double* rhs, cudaStream_t s) {
+  rhs_sides_kernel<<<dim3(64, batch), kThreads, 0, s>>>(a, mask, rhs);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ double apply_A(const DAArgs& a, const double* mu, const double* x, int g, double h2) {
+  const int i = g % a.n0, j = g / a.n0;
+  double y = (a.diag0[g] + mu[g] * h2) * x[g];
+  if (i > 0) y -= a.cxf[g - 1] * x[g - 1];
+  if (i < a.n0 - 1) y -= a.cxf[g] * x[g + 1];
+  if (j > 0) y -= a.cyf[g - a.n0] * x[g - a.n0];
+  if (j < a.n1 - 1) y -= a.cyf[g] * x[g + a.n0];
+  return y;
+}
+
+// Block-wide sum of up to 3 values, deterministic tree order; thread 0 writes.
+__device__ __forceinline__ void block_sum3(double v0, double v1, double v2, double* out) {
+  __shared__ double sh[3][kThreads];
+  sh[0][threadIdx.x] = v0;
+  sh[1][threadIdx.x] = v1;
+  sh[2][threadIdx.x] = v2;
+  __syncthreads();
+  for (int st = kThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sh[0][0];
+    out[1] = sh[1][0];
+    out[2] = sh[2][0];
+  }
+}
+
+// scal layout per problem: [0] rz (even its), [1] rz (odd its), [2] pq, [3] rr, [4] bb, [5] done
+__global__ void pcg_init_kernel(DAArgs a, const double* mu, const double* rhs, PCGWork w) {
+  const int b = blockIdx.y;
+  const long long o = (long long)b * a.N;
+  const double h2 = a.h * a.h;
+  double rz = 0, rr = 0, bb = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
+    const double di = 1.0 / (a.diag0[g] + mu[o + g] * h2);
+    const double r = rhs[o + g];
+    w.dinv[o + g] = di;
+    w.x[o + g] = 0.0;
+    w.r[o + g] = r;
+    w.z[o + g] = di * r;
+    w.p[o + g] = di * r;
+    rz += r * di * r;
+    rr += r * r;
+    bb += r * r;
+  }
+  block_sum3(rz, rr, bb, w.partial + ((long long)b * kPartials + blockIdx.x) * 4);
+}
+
+// Sum the partials of problem blockIdx.x into scal slots.
+__global__ void pcg_reduce_kernel(PCGWork w, int s0, int s1, int s2) {
+  const int b = blockIdx.x;
+  const double* p = w.partial + (long long)b * kPartials * 4;
+  double v0 = 0, v1 = 0, v2 = 0;
+  for (int t = threadIdx.x; t < kPartials; t += blockDim.x) {
+    v0 += p[4 * t];
+    v1 += p[4 * t + 1];
+    v2 += p[4 * t + 2];
+  }
+  __shared__ double res[3];
+  block_sum3(v0, v1, v2, res);
+  if (threadIdx.x == 0) {
+    double* sc = w.scal + 8 * b;
+    if (s0 >= 0) sc[s0] = res[0];
+    if (s1 >= 0) sc[s1] = res[1];
+    if (s2 >= 0) sc[s2] = res[2];
+  }
+}
+
+__global__ void pcg_spmv_kernel(DAArgs a, const double* mu, PCGWork w) {
+  const int b = blockIdx.y;
+  const long long o = (long long)b * a.N;
+  const double h2 = a.h * a.h;
+  double pq = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
+    const double q = apply_A(a, mu + o, w.p + o, g, h2);
+    w.q[o + g] = q;
+    pq += w.p[o + g] * q;
+  }
+  block_sum3(pq, 0.0, 0.0, w.partial + ((long long)b * kPartials + blockIdx.x) * 4);
+}
+
+__global__ void pcg_update_kernel(DAArgs a, PCGWork w, int parity) {
+  const int b = blockIdx.y;
+  const long long o = (long long)b * a.N;
+  const double* sc = w.scal + 8 * b;
+  const bool done = sc[5] != 0.0;
+  const double rz = sc[parity], pq = sc[2];
+  const double alpha = (done || pq == 0.0) ? 0.0 : rz / pq;
+  double rz1 = 0, rr = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
+    const double x = w.x[o + g] + alpha * w.p[o + g];
+    const double r = w.r[o + g] - alpha * w.q[o + g];
+    const double z = w.dinv[o + g] * r;
+    w.x[o + g] = x;
+    w.r[o + g] = r;
+    w.z[o + g] = z;
+    rz1 += r * z;
+    rr += r * r;
+  }
+  block_sum3(rz1, rr, 0.0, w.partial + ((long long)b * kPartials + blockIdx.x) * 4);
+}
+
+__global__ void pcg_pupdate_kernel(DAArgs a, PCGWork w, int parity) {
+  const int b = blockIdx.y;
+  const long long o = (long long)b * a.N;
+  const double* sc = w.scal + 8 * b;
+  const bool done = sc[5] != 0.0;
+  const double rz_old = sc[parity], rz_new = sc[parity ^ 1];
+  const double beta = (done || rz_old == 0.0) ? 0.0 : rz_new / rz_old;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x)
+    w.p[o + g] = w.z[o + g] + beta * w.p[o + g];
+}
+
+__global__ void pcg_mark_done_kernel(PCGWork w, int batch, double tol2) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double* sc = w.scal + 8 * b;
+  if (sc[3] <= tol2 * sc[4]) sc[5] = 1.0;
+}
+
+__global__ void copy_kernel(long long n, const double* in, double* out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = in[t];
+}
+
+int pcg_solve(const DAArgs& a, const double* mu, int batch, const double* rhs, double* x, PCGWork& w,
+              int max_iter, double tol, cudaStream_t s, cudaError_t* err) {
+  const dim3 grid(kPartials, batch);
+  const double tol2 = tol * tol;
+  cudaMemsetAsync(w.scal, 0, sizeof(double) * 8 * batch, s);
+  pcg_init_kernel<<<grid, kThreads, 0, s>>>(a, mu, rhs, w);
+  pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, 0, 3, 4);
+  int it = 0;
+  int used = -1;
+  const int check_every = 16;
+  while (it < max_iter) {
+    const int parity = it & 1;
+    pcg_spmv_kernel<<<grid, kThreads, 0, s>>>(a, mu, w);
+    pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, 2, -1, -1);
+    pcg_update_kernel<<<grid, kThreads, 0, s>>>(a, w, parity);
+    pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, parity ^ 1, 3, -1);
+    pcg_pupdate_kernel<<<grid, kThreads, 0, s>>>(a, w, parity);
+    pcg_mark_done_kernel<<<(batch + 127) / 128, 128, 0, s>>>(w, batch, tol2);
+    ++it;
+    if (it % check_every == 0 || it == max_iter) {
+      cudaMemcpyAsync(w.hostscal, w.scal, sizeof(double) * 8 * batch, cudaMemcpyDeviceToHost, s);
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { *err = e; return -1; }
+      bool all = true;
+      for (int b = 0; b < batch; ++b) all = all && (w.hostscal[8 * b + 5] != 0.0);
+      if (all) { used = it; break; }
+    }
+  }
+  copy_kernel<<<256, kThreads, 0, s>>>((long long)batch * a.N, w.x, x);
+  *err = cudaGetLastError();
+  return used;
+}
+
+__global__ void hadamard_kernel(long long n, double alpha, const double* u, const double* v, double* out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = alpha * u[t] * v[t];
+}
+
+cudaError_t da_hadamard(int batch, int N, double alpha, const double* u, const double* v, double* out,
+                        cudaStream_t s) {
+  hadamard_kernel<<<512, kThreads, 0, s>>>((long long)batch * N, alpha, u, v, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void heating_kernel(long long n, const double* a1, const double* b1, const double* a2, const double* b2,
+                               T* out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double v = a1[t] * b1[t];
+    if (a2) v += a2[t] * b2[t];
+    out[t] = (T)v;
+  }
+}
+
+template <typename T>
+cudaError_t da_heating_T(int batch, int N, const double* a1, const double* b1, const double* a2, const double* b2,
+                         T* out, cudaStream_t s) {
+  heating_kernel<T><<<512, kThreads, 0, s>>>((long long)batch * N, a1, b1, a2, b2, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void adjoint_out_kernel(long long n, const double* phi, const T* hbar, const double* ht, double* g) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    g[t] = phi[t] * ((double)hbar[t] + ht[t]);
+}
+
+template <typename T>
+cudaError_t da_adjoint_out(int batch, int N, const double* phi, const T* hbar, const double* ht, double* g,
+                           cudaStream_t s) {
+  adjoint_out_kernel<T><<<512, kThreads, 0, s>>>((long long)batch * N, phi, hbar, ht, g);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void to_double_kernel(long long n, const T* in, double* out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = (double)in[t];
+}
+
+template <typename T>
+cudaError_t T_to_double(long long n, const T* in, double* out, cudaStream_t s) {
+  to_double_kernel<T><<<512, kThreads, 0, s>>>(n, in, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void adjoint_rhs_kernel(long long n, double scale, const double* mu, const T* hbar, double* out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = scale * mu[t] * (double)hbar[t];
+}
+
+template <typename T>
+cudaError_t da_adjoint_rhs(int batch, int N, double scale, const double* mu, const T* hbar, double* out,
+                           cudaStream_t s) {
+  adjoint_rhs_kernel<T><<<512, kThreads, 0, s>>>((long long)batch * N, scale, mu, hbar, out);
+  return cudaGetLastError();
+}
+
+// Inner products in FP64: per thread a Neumaier-compensated running sum of
+// the FP64 products, a fixed-order tree over the block, and a compensated
+// sequential sum of the block partials.
+__device__ __forceinline__ void neumaier(double& s, double& c, double v) {
+  const double t = s + v;
+  if (fabs(s) >= fabs(v)) c += (s - t) + v;
+  else c += (v - t) + s;
+  s = t;
+}
+
+template <typename T>
+__global__ void dot_partial_kernel(long long len, const T* a, const T* b, double* partial) {
+  const int bb = blockIdx.y;
+  const T* x = a + (long long)bb * len;
+  const T* y = b + (long long)bb * len;
+  double s = 0, c = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x)
+    neumaier(s, c, (double)x[t] * (double)y[t]);
+  block_sum3(s, c, 0.0, partial + ((long long)bb * kPartials + blockIdx.x) * 4);
+}
+
+__global__ void dot_final_kernel(const double* partial, double* out, int batch) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double s = 0, c = 0;
+  for (int t = 0; t < kPartials; ++t) {
+    neumaier(s, c, partial[((long long)b * kPartials + t) * 4]);
+    neumaier(s, c, partial[((long long)b * kPartials + t) * 4 + 1]);
+  }
+  out[b] = s + c;
+}
+
+template <typename T>
+cudaError_t dot_compensated(int batch, long long len, const T* a, const T* b, double* d_partial, double* d_out,
+                            cudaStream_t s) {
+  dot_partial_kernel<T><<<dim3(kPartials, batch), kThreads, 0, s>>>(len, a, b, d_partial);
+  dot_final_kernel<<<(batch + 127) / 128, 128, 0, s>>>(d_partial, d_out, batch);
+  return cudaGetLastError();
+}
+
+#define QPAT_DA_INST(T)                                                                                  \
+  template cudaError_t da_heating_T<T>(int, int, const double*, const double*, const double*,           \
+                                       const double*, T*, cudaStream_t);                                 \
+  template cudaError_t da_adjoint_out<T>(int, int, const double*, const T*, const double*, double*,      \
+                                         cudaStream_t);                                                  \
+  template cudaError_t T_to_double<T>(long long, const T*, double*, cudaStream_t);                      \
+  template cudaError_t da_adjoint_rhs<T>(int, int, double, const double*, const T*, double*, cudaStream_t); \
+  template cudaError_t dot_compensated<T>(int, long long, const T*, const T*, double*, double*, cudaStream_t);
+QPAT_DA_INST(float)
+QPAT_DA_INST(double)
+
+}  // namespace qpat

@@ -1,0 +1,401 @@
+// k-space PSTD time stepping kernels (sm_103a).
+//
+// One time step of the acoustic model (Section 3.2.3: eqs. num-vel, num-rho,
+// num-p, num-m) and of its exact transpose (Section 3.2.4, Lemma 2) is a
+// chain of alternating passes over the 2D FFT grid:
+//
+//   row pass    : inverse x-FFT of the incoming half spectra (two grid rows
+//                 packed into one complex transform), the pointwise PML /
+//                 medium update of eqs. num-vel / num-rho / num-p, and the
+//                 forward x-FFT of the outgoing fields (again two rows per
+//                 complex transform), all in shared memory;
+//   column pass : forward y-FFT of a tile of half-spectrum columns, the
+//                 spectral symbol of eq. grr (i k_i e^{+-i k_i dx/2} kappa) or
+//                 of the fractional Laplacians Y_dis / Y_abs, and the inverse
+//                 y-FFT, in shared memory.
+//
+// Every pass is in place on a two-slot half-spectrum buffer per problem, so
+// a step touches the state fields once and the spectra twice per operator
+// application.  The batch index is blockIdx.y: many problems on the same
+// grid and medium share each launch.
+#include "qpat_internal.h"
+
+namespace qpat {
+
+template <int PH> struct RowIO;
+template <> struct RowIO<F_R1> { static constexpr int kin = 2, kout = 1; };
+template <> struct RowIO<F_R2> { static constexpr int kin = 2, kout = 2; };
+template <> struct RowIO<F_R3> { static constexpr int kin = 2, kout = 2; };
+template <> struct RowIO<F_R3L> { static constexpr int kin = 2, kout = 1; };
+template <> struct RowIO<A_R1> { static constexpr int kin = 1, kout = 2; };
+template <> struct RowIO<A_R1L> { static constexpr int kin = 1, kout = 2; };
+template <> struct RowIO<A_R3> { static constexpr int kin = 2, kout = 2; };
+template <> struct RowIO<A_R5> { static constexpr int kin = 2, kout = 2; };
+
+template <int PH> struct ColIO;
+template <> struct ColIO<F_C1> { static constexpr int kin = 1, kout = 2; };
+template <> struct ColIO<F_C2> { static constexpr int kin = 2, kout = 2; };
+template <> struct ColIO<F_C3> { static constexpr int kin = 2, kout = 2; };
+template <> struct ColIO<A_C2> { static constexpr int kin = 2, kout = 2; };
+template <> struct ColIO<A_C4> { static constexpr int kin = 2, kout = 2; };
+template <> struct ColIO<A_C6> { static constexpr int kin = 2, kout = 1; };
+
+constexpr int kRowThreads = 256;
+constexpr int kColThreads = 256;
+
+template <typename T>
+size_t row_smem_bytes(int nx) {
+  typedef typename V2<T>::t C;
+  return 4 * (size_t)nx * sizeof(C) + 2 * (size_t)nx * sizeof(T);
+}
+template <typename T>
+size_t col_smem_bytes(int ny, int cb) {
+  typedef typename V2<T>::t C;
+  return 4 * (size_t)cb * (ny + 1) * sizeof(C);
+}
+
+// ---------------------------------------------------------------------------
+// Row pass: rows j0 = 2*blockIdx.x and j0 + 1 of problem blockIdx.y.
+// ---------------------------------------------------------------------------
+template <typename T, int PH>
+__global__ void __launch_bounds__(kRowThreads) row_kernel(const PropArgs<T> a) {
+  typedef typename V2<T>::t C;
+  constexpr int KIN = RowIO<PH>::kin;
+  constexpr int KOUT = RowIO<PH>::kout;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = a.nx;
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + 2 * nx;
+  T* sc = reinterpret_cast<T*>(buf1 + 2 * nx);       // [2][nx] sensor adjoint source
+  const int b = blockIdx.y;
+  const int j0 = 2 * blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  C* spec = a.spec + (long long)b * a.sstride;
+  const long long slot = (long long)a.ny * a.pitch;
+  const bool skip_in = (a.flags & kSkipInput) != 0;
+  const long long gb = (long long)b * a.gstride;
+
+  // 1. inverse x-transform: Z(k) = A(k) + i B(k) over the Hermitian-extended
+  //    half spectra of rows j0 (A) and j0+1 (B); the unnormalised inverse
+  //    z = conj(FFT(conj Z)) holds row j0 in Re z and row j0+1 in Im z.
+  C* res = buf0;
+  if (!skip_in) {
+    for (int s = 0; s < KIN; ++s) {
+      const C* r0 = spec + s * slot + (long long)j0 * a.pitch;
+      const C* r1 = r0 + a.pitch;
+      for (int k = tid; k < nx; k += nth) {
+        C A, B;
+        if (k <= nx / 2) {
+          A = r0[k];
+          B = r1[k];
+          if (k == 0 || k == nx / 2) { A.y = (T)0; B.y = (T)0; }
+        } else {
+          A = cconj(r0[nx - k]);
+          B = cconj(r1[nx - k]);
+        }
+        buf0[s * nx + k] = cmake<C>(A.x - B.y, -(A.y + B.x));   // conj(A + i B)
+      }
+    }
+    __syncthreads();
+    res = fft_batch(a.px, buf0, buf1, KIN, nx, a.twx);
+  }
+  C* oth = (res == buf0) ? buf1 : buf0;
+
+  // adjoint of the sensor sampling, M^T w_(n), as a deterministic gather
+  if (PH == A_R1 || PH == A_R1L) {
+    for (int i = tid; i < 2 * nx; i += nth) sc[i] = (T)0;
+    __syncthreads();
+    const T* wn = a.w + ((long long)b * a.nt + a.n) * a.ns;
+    for (int rr = 0; rr < 2; ++rr) {
+      const int j = j0 + rr;
+      for (int q = a.rowptr[j] + tid; q < a.rowptr[j + 1]; q += nth) {
+        T acc = (T)0;
+        for (int e = a.pent[q]; e < a.pent[q + 1]; ++e) acc += a.ew[e] * wn[a.esens[e]];
+        sc[rr * nx + a.pcol[q]] = acc;
+      }
+    }
+    __syncthreads();
+  }
+
+  // 2. pointwise update; outgoing fields are packed two rows per complex value
+  bool bad = false;
+  for (int i = tid; i < nx; i += nth) {
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const int j = j0 + rr;
+      const long long g = (long long)j * nx + i;
+      T in0 = (T)0, in1 = (T)0;
+      if (!skip_in) {
+        // res = FFT(conj Z) = conj(z): row j0 is Re, row j0+1 is -Im
+        C z0 = res[i];
+        in0 = rr ? -z0.y : z0.x;
+        if (KIN > 1) {
+          C z1 = res[nx + i];
+          in1 = rr ? -z1.y : z1.x;
+        }
+      }
+      T out0 = (T)0, out1 = (T)0;
+      const bool interior = (i >= a.pml) && (i < a.pml + a.n0) && (j >= a.pml) && (j < a.pml + a.n1);
+      const long long ii = interior ? (long long)(j - a.pml) * a.n0 + (i - a.pml) : 0;
+      if (PH == F_R1) {
+        // eq. num-p: p = c^2 [ (I - eta Y_dis) sum rho_i + tau Y_abs u ]
+        const T r = a.rx[gb + g] + a.ry[gb + g];
+        const T p = a.Cc[g] * ((r - a.eta[g] * in0) + a.tau[g] * in1);
+        a.pbuf[gb + g] = p;
+        bad |= !isfinite(p);
+        out0 = p;
+      } else if (PH == F_R2) {
+        // eq. num-vel: v_i <- A_i (A_i v_i - dt/rho_i d/dr_i^+ p)
+        const T sx = a.asx[i], sy = a.asy[j];
+        const T vx = sx * (sx * a.vx[gb + g] - a.dtrsx[g] * in0);
+        const T vy = sy * (sy * a.vy[gb + g] - a.dtrsy[g] * in1);
+        a.vx[gb + g] = vx;
+        a.vy[gb + g] = vy;
+        out0 = vx;
+        out1 = vy;
+      } else if (PH == F_R3 || PH == F_R3L) {
+        // eq. num-rho with the additive source of eq. s1 (dt s_i = P0 / (2 d c^2))
+        T q = (T)0;
+        if ((a.flags & kSource) && interior) q = a.p0[(long long)b * a.n0 * a.n1 + ii] / ((T)4 * a.Cc[g]);
+        const T ax = a.ax[i], ay = a.ay[j], r0 = a.rho0[g];
+        const T rx = ax * (ax * a.rx[gb + g] - a.dt * r0 * in0) + q;
+        const T ry = ay * (ay * a.ry[gb + g] - a.dt * r0 * in1) + q;
+        a.rx[gb + g] = rx;
+        a.ry[gb + g] = ry;
+        if (PH == F_R3) {
+          out0 = rx + ry;                            // sum_i rho_i
+          out1 = ax * r0 * in0 + ay * r0 * in1;      // sum_i A_i rho0 d/dr_i^- v_i
+        } else {
+          const T p = a.Cc[g] * (rx + ry);
+          a.pbuf[gb + g] = p;
+          bad |= !isfinite(p);
+          out0 = p;
+        }
+      } else if (PH == A_R1) {
+        const T pb = in0 + sc[rr * nx + i];
+        const T Cp = a.Cc[g] * pb;
+        a.pbuf[gb + g] = Cp;
+        out0 = a.eta[g] * Cp;
+        out1 = a.tau[g] * Cp;
+      } else if (PH == A_R1L || PH == A_R3) {
+        T Cp, ya = (T)0;
+        if (PH == A_R1L) {
+          Cp = a.Cc[g] * (in0 + sc[rr * nx + i]);
+        } else {
+          Cp = a.pbuf[gb + g];
+          ya = in1;
+        }
+        const T rpart = (PH == A_R1L) ? Cp : Cp - in0;   // (I - Y_dis eta) C p-bar
+        const T ax = a.ax[i], ay = a.ay[j], r0 = a.rho0[g];
+        const T rtx = a.rx[gb + g] + rpart;
+        const T rty = a.ry[gb + g] + rpart;
+        out0 = r0 * ax * (ya - a.dt * rtx);
+        out1 = r0 * ay * (ya - a.dt * rty);
+        a.rx[gb + g] = ax * ax * rtx;
+        a.ry[gb + g] = ay * ay * rty;
+        bad |= !isfinite(rtx + rty);
+        if (interior && (a.flags & (kAccWrite | kAccAdd))) {
+          T* dst = a.p0adj + (long long)b * a.n0 * a.n1 + ii;
+          const T val = (rtx + rty) / ((T)4 * a.Cc[g]);
+          if (a.flags & kAccWrite) *dst = val;
+          else *dst += val;
+        }
+      } else if (PH == A_R5) {
+        const T sx = a.asx[i], sy = a.asy[j];
+        const T vtx = a.vx[gb + g] + in0;
+        const T vty = a.vy[gb + g] + in1;
+        a.vx[gb + g] = sx * sx * vtx;
+        a.vy[gb + g] = sy * sy * vty;
+        out0 = sx * a.dtrsx[g] * vtx;
+        out1 = sy * a.dtrsy[g] * vty;
+      }
+      if (rr == 0) {
+        oth[i].x = out0;
+        if (KOUT > 1) oth[nx + i].x = out1;
+      } else {
+        oth[i].y = out0;
+        if (KOUT > 1) oth[nx + i].y = out1;
+      }
+    }
+  }
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(a.err, 1);
+  if (a.flags & kSkipOutput) return;
+
+  // 3. forward x-transform of the packed rows and split into two half spectra:
+  //    A(k) = (Z(k) + conj Z(-k)) / 2, B(k) = -i (Z(k) - conj Z(-k)) / 2
+  C* res2 = fft_batch(a.px, oth, res, KOUT, nx, a.twx);
+  for (int o = 0; o < KOUT; ++o) {
+    C* w0 = spec + o * slot + (long long)j0 * a.pitch;
+    C* w1 = w0 + a.pitch;
+    for (int k = tid; k <= nx / 2; k += nth) {
+      const C Z = res2[o * nx + k];
+      const C Zm = cconj(res2[o * nx + (k == 0 ? 0 : nx - k)]);
+      w0[k] = cscale(cadd(Z, Zm), (T)0.5);
+      w1[k] = cscale(cmul_mi(csub(Z, Zm)), (T)0.5);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass: half-spectrum columns kx0 .. kx0+cb-1 of problem blockIdx.y.
+// ---------------------------------------------------------------------------
+template <typename T, int PH>
+__global__ void __launch_bounds__(kColThreads) col_kernel(const PropArgs<T> a) {
+  typedef typename V2<T>::t C;
+  constexpr int KIN = ColIO<PH>::kin;
+  constexpr int KOUT = ColIO<PH>::kout;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cb = a.cb, ny = a.ny, S = ny + 1, nxh = a.nxh;
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + 2 * cb * S;
+  const int b = blockIdx.y;
+  const int kx0 = blockIdx.x * cb;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  C* spec = a.spec + (long long)b * a.sstride;
+  const long long slot = (long long)ny * a.pitch;
+
+  if (PH == F_C1) {
+    // eq. num-m: bilinear sampling of p_n (written by the previous row pass)
+    const T* pb = a.pbuf + (long long)b * a.gstride;
+    T* dn = a.data + ((long long)b * a.nt + a.n) * a.ns;
+    for (int s = blockIdx.x * nth + tid; s < a.ns; s += gridDim.x * nth) {
+      T acc = (T)0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc += a.sw[4 * s + c] * pb[a.sidx[4 * s + c]];
+      dn[s] = acc;
+    }
+  }
+
+  for (int s = 0; s < KIN; ++s) {
+    for (int idx = tid; idx < ny * cb; idx += nth) {
+      const int ky = idx / cb, c = idx - ky * cb, kx = kx0 + c;
+      C v = cmake<C>((T)0, (T)0);
+      if (kx < nxh) v = spec[s * slot + (long long)ky * a.pitch + kx];
+      buf0[(s * cb + c) * S + ky] = v;
+    }
+  }
+  __syncthreads();
+  C* res = fft_batch(a.py, buf0, buf1, KIN * cb, S, a.twy);
+  C* oth = (res == buf0) ? buf1 : buf0;
+
+  for (int idx = tid; idx < ny * cb; idx += nth) {
+    const int c = idx / ny, ky = idx - c * ny, kx = kx0 + c;
+    C o0 = cmake<C>((T)0, (T)0), o1 = o0;
+    if (kx < nxh) {
+      const C X0 = res[c * S + ky];
+      const C X1 = (KIN > 1) ? res[(cb + c) * S + ky] : X0;
+      const long long t = (long long)ky * nxh + kx;
+      if (PH == F_C1) {          // d/dr_x^+, d/dr_y^+ of p (eq. grr)
+        const T k = a.kap[t];
+        o0 = cscale(cmul(a.shxp[kx], X0), k);
+        o1 = cscale(cmul(a.shyp[ky], X0), k);
+      } else if (PH == F_C2) {   // d/dr_x^- v_x, d/dr_y^- v_y
+        const T k = a.kap[t];
+        o0 = cscale(cmul(a.shxm[kx], X0), k);
+        o1 = cscale(cmul(a.shym[ky], X1), k);
+      } else if (PH == F_C3 || PH == A_C2) {   // Y_dis, Y_abs (real, even symbols)
+        o0 = cscale(X0, a.kp1[t]);
+        o1 = cscale(X1, a.kp2[t]);
+      } else if (PH == A_C4) {   // (d/dr_i^-)^T: conjugate symbols
+        const T k = a.kap[t];
+        o0 = cscale(cmul(cconj(a.shxm[kx]), X0), k);
+        o1 = cscale(cmul(cconj(a.shym[ky]), X1), k);
+      } else if (PH == A_C6) {   // -sum_i (d/dr_i^+)^T
+        const T k = a.kap[t];
+        o0 = cscale(cadd(cmul(cconj(a.shxp[kx]), X0), cmul(cconj(a.shyp[ky]), X1)), -k);
+      }
+    }
+    oth[c * S + ky] = cconj(o0);
+    if (KOUT > 1) oth[(cb + c) * S + ky] = cconj(o1);
+  }
+  __syncthreads();
+  C* res2 = fft_batch(a.py, oth, res, KOUT * cb, S, a.twy);
+  for (int o = 0; o < KOUT; ++o) {
+    for (int idx = tid; idx < ny * cb; idx += nth) {
+      const int ky = idx / cb, c = idx - ky * cb, kx = kx0 + c;
+      if (kx < nxh) spec[o * slot + (long long)ky * a.pitch + kx] = cconj(res2[(o * cb + c) * S + ky]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void gather_kernel(const PropArgs<T> a) {
+  const int b = blockIdx.y;
+  const T* pb = a.pbuf + (long long)b * a.gstride;
+  T* dn = a.data + ((long long)b * a.nt + a.n) * a.ns;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.ns; s += gridDim.x * blockDim.x) {
+    T acc = (T)0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc += a.sw[4 * s + c] * pb[a.sidx[4 * s + c]];
+    dn[s] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int PH>
+static void set_row_attr() {
+  cudaFuncSetAttribute(row_kernel<T, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+template <typename T, int PH>
+static void set_col_attr() {
+  cudaFuncSetAttribute(col_kernel<T, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+template <typename T>
+int prop_init_attributes() {
+  set_row_attr<T, F_R1>(); set_row_attr<T, F_R2>(); set_row_attr<T, F_R3>(); set_row_attr<T, F_R3L>();
+  set_row_attr<T, A_R1>(); set_row_attr<T, A_R1L>(); set_row_attr<T, A_R3>(); set_row_attr<T, A_R5>();
+  set_col_attr<T, F_C1>(); set_col_attr<T, F_C2>(); set_col_attr<T, F_C3>();
+  set_col_attr<T, A_C2>(); set_col_attr<T, A_C4>(); set_col_attr<T, A_C6>();
+  return 0;
+}
+
+template <typename T>
+void launch_row(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
+  dim3 grid(a.ny / 2, batch);
+  const size_t sm = row_smem_bytes<T>(a.nx);
+  switch (phase) {
+    case F_R1: row_kernel<T, F_R1><<<grid, kRowThreads, sm, s>>>(a); break;
+    case F_R2: row_kernel<T, F_R2><<<grid, kRowThreads, sm, s>>>(a); break;
+    case F_R3: row_kernel<T, F_R3><<<grid, kRowThreads, sm, s>>>(a); break;
+    case F_R3L: row_kernel<T, F_R3L><<<grid, kRowThreads, sm, s>>>(a); break;
+    case A_R1: row_kernel<T, A_R1><<<grid, kRowThreads, sm, s>>>(a); break;
+    case A_R1L: row_kernel<T, A_R1L><<<grid, kRowThreads, sm, s>>>(a); break;
+    case A_R3: row_kernel<T, A_R3><<<grid, kRowThreads, sm, s>>>(a); break;
+    case A_R5: row_kernel<T, A_R5><<<grid, kRowThreads, sm, s>>>(a); break;
+    default: break;
+  }
+}
+
+template <typename T>
+void launch_col(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
+  dim3 grid((a.nxh + a.cb - 1) / a.cb, batch);
+  const size_t sm = col_smem_bytes<T>(a.ny, a.cb);
+  switch (phase) {
+    case F_C1: col_kernel<T, F_C1><<<grid, kColThreads, sm, s>>>(a); break;
+    case F_C2: col_kernel<T, F_C2><<<grid, kColThreads, sm, s>>>(a); break;
+    case F_C3: col_kernel<T, F_C3><<<grid, kColThreads, sm, s>>>(a); break;
+    case A_C2: col_kernel<T, A_C2><<<grid, kColThreads, sm, s>>>(a); break;
+    case A_C4: col_kernel<T, A_C4><<<grid, kColThreads, sm, s>>>(a); break;
+    case A_C6: col_kernel<T, A_C6><<<grid, kColThreads, sm, s>>>(a); break;
+    default: break;
+  }
+}
+
+template <typename T>
+void launch_gather(const PropArgs<T>& a, int batch, cudaStream_t s) {
+  dim3 grid((a.ns + 255) / 256, batch);
+  gather_kernel<T><<<grid, 256, 0, s>>>(a);
+}
+
+#define QPAT_INST(T)                                                              \
+  template size_t row_smem_bytes<T>(int);                                         \
+  template size_t col_smem_bytes<T>(int, int);                                    \
+  template int prop_init_attributes<T>();                                         \
+  template void launch_row<T>(const PropArgs<T>&, int, int, cudaStream_t);        \
+  template void launch_col<T>(const PropArgs<T>&, int, int, cudaStream_t);        \
+  template void launch_gather<T>(const PropArgs<T>&, int, cudaStream_t);
+QPAT_INST(float)
+QPAT_INST(double)
+
+}  // namespace qpat

@@ -1,0 +1,166 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <string>
+#include <vector>
+
+#include "fft_smem.cuh"
+
+namespace qpat {
+
+// Flags of one propagation kernel launch.
+enum : int {
+  kSkipInput = 1,    // the incoming spectral slots are zero (first step)
+  kSource = 2,       // additive source active at this step (eq. s1, n = -1, 0)
+  kAccWrite = 4,     // adjoint: write the source adjoint into p0_adj
+  kAccAdd = 8,       // adjoint: add the source adjoint into p0_adj
+  kSkipOutput = 16,  // no outgoing spectral slots needed (last step)
+};
+
+// Propagation phases.  F_*: forward step (Section 3.2.3), A_*: transposed
+// step (Section 3.2.4).  R = row pass (x FFTs + pointwise), C = column pass
+// (y FFTs + spectral operator).
+enum Phase : int {
+  F_R1 = 0,   // pressure from rho and the fractional-Laplacian terms (num-p)
+  F_R2 = 1,   // velocity update (num-vel)
+  F_R3 = 2,   // density update + source (num-rho); lossless: also pressure
+  F_R3L = 3,
+  F_C1 = 10,  // d/dr^+ of p, and sensor gather (num-m)
+  F_C2 = 11,  // d/dr^- of v
+  F_C3 = 12,  // Y_dis, Y_abs
+  A_R1 = 20,  // adjoint of num-m and of the pressure update (lossy)
+  A_R1L = 21, // same, lossless, fused with the transposed density update
+  A_R3 = 22,  // transposed density update (+ source adjoint)
+  A_R5 = 23,  // transposed velocity update
+  A_C2 = 30,  // Y_dis^T, Y_abs^T
+  A_C4 = 31,  // (d/dr^-)^T
+  A_C6 = 32,  // -(d/dr^+)^T summed over axes
+};
+
+template <typename T>
+struct PropArgs {
+  typedef typename V2<T>::t C;
+  int nx, ny, nxh, pitch, pml, n0, n1, ns, nt;
+  int cb;                 // columns per column-pass CTA
+  FFTPlan px, py;
+  const C* twx;
+  const C* twy;
+  // medium diagonals on the full grid [ny][nx]
+  const T* Cc;            // c^2
+  const T* rho0;          // ambient density at nodes
+  const T* dtrsx;         // dt / rho0 at (x + dx/2)
+  const T* dtrsy;         // dt / rho0 at (y + dx/2)
+  const T* tau;
+  const T* eta;
+  // PML diagonals A_i (per axis, nodes and staggered)
+  const T* ax;
+  const T* asx;
+  const T* ay;
+  const T* asy;
+  T dt;
+  // k-space symbols on the half spectrum [ny][nxh], each divided by nx*ny
+  const T* kap;           // sinc(c_ref |k| dt / 2)
+  const T* kp1;           // |k|^(y-1)
+  const T* kp2;           // |k|^(y-2), 0 at k = 0
+  const C* shxp;          // i kx exp(+i kx dx/2)  [nxh]
+  const C* shxm;          // i kx exp(-i kx dx/2)  [nxh]
+  const C* shyp;          // [ny]
+  const C* shym;          // [ny]
+  // sensors: gather form [ns][4], and scatter form (CSR over grid rows)
+  const int* sidx;
+  const T* sw;
+  const int* rowptr;      // [ny + 1] range of grid points per row
+  const int* pcol;        // [npts] column of each grid point
+  const int* pent;        // [npts + 1] range of (sensor, weight) entries per point
+  const int* esens;
+  const T* ew;
+  // workspace, batch strides in elements
+  T* vx; T* vy; T* rx; T* ry;
+  long long gstride;      // nx*ny
+  C* spec;                // [B][2][ny][pitch]
+  long long sstride;      // 2*ny*pitch
+  T* pbuf;                // [B][ny][nx]
+  // per call
+  const T* p0;            // [B][N] interior source (forward)
+  T* data;                // [B][nt][ns] (forward output)
+  const T* w;             // [B][nt][ns] (adjoint input)
+  T* p0adj;               // [B][N] (adjoint output)
+  int n;                  // sample index this launch reads or writes
+  int flags;
+  int* err;               // device flags word (bit 0: non-finite)
+};
+
+template <typename T>
+void launch_row(const PropArgs<T>& a, int phase, int batch, cudaStream_t s);
+template <typename T>
+void launch_col(const PropArgs<T>& a, int phase, int batch, cudaStream_t s);
+template <typename T>
+void launch_gather(const PropArgs<T>& a, int batch, cudaStream_t s);
+template <typename T>
+size_t row_smem_bytes(int nx);
+template <typename T>
+size_t col_smem_bytes(int ny, int cb);
+template <typename T>
+int prop_init_attributes();
+
+// Table construction (tables.cu)
+template <typename T>
+struct TableOut {
+  typedef typename V2<T>::t C;
+  T *Cc, *rho0, *dtrsx, *dtrsy, *tau, *eta;
+  T *ax, *asx, *ay, *asy;
+  T *kap, *kp1, *kp2;
+  C *shxp, *shxm, *shyp, *shym;
+  C *twx, *twy;
+};
+template <typename T>
+cudaError_t build_tables(const TableOut<T>& o, const double* d_c, const double* d_rho, const double* d_alpha_db,
+                         int nx, int ny, int nxh, int pml, double dx, double dt, double c_ref, double pml_alpha,
+                         double y, int lossless, cudaStream_t s);
+
+// FP64 helpers (da.cu)
+struct DAArgs {
+  int n0, n1, N;
+  double h, gamma;
+  const double* diag0;     // face + Robin terms [N]
+  const double* cxf;       // coefficient to the +x neighbour [N]
+  const double* cyf;       // coefficient to the +y neighbour [N]
+  const double* bside;     // [4][N] right-hand side of a unit current on each side
+};
+cudaError_t da_setup(DAArgs& a, double* d_diag0, double* d_cxf, double* d_cyf, double* d_bside,
+                     const double* d_kappa, cudaStream_t s);
+
+struct PCGWork {
+  double *x, *r, *z, *p, *q, *dinv, *b;   // [B][N]
+  double *partial;                         // [B][kPartials][4]
+  double *scal;                            // [B][8]
+  double *hostscal;                        // pinned [B][8]
+};
+// Solve A(mu_b) x_b = rhs_b for a batch; x holds the result.  Returns the
+// number of iterations used, or -1 if the cap was reached.
+int pcg_solve(const DAArgs& a, const double* mu, int batch, const double* rhs, double* x, PCGWork& w,
+              int max_iter, double tol, cudaStream_t s, cudaError_t* err);
+cudaError_t da_rhs_from_sides(const DAArgs& a, unsigned mask, int batch, double* rhs, cudaStream_t s);
+// out_b = alpha * (u_b o v_b)   (all [B][N] FP64)
+cudaError_t da_hadamard(int batch, int N, double alpha, const double* u, const double* v, double* out,
+                        cudaStream_t s);
+// dh = dmu o phi + mu o dphi, written in T
+template <typename T>
+cudaError_t da_heating_T(int batch, int N, const double* a1, const double* b1, const double* a2,
+                         const double* b2, T* out, cudaStream_t s);
+// g = phi o (hbar + ht) with hbar in T
+template <typename T>
+cudaError_t da_adjoint_out(int batch, int N, const double* phi, const T* hbar, const double* ht, double* g,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t T_to_double(long long n, const T* in, double* out, cudaStream_t s);
+// out = -h^d * mu o T-valued hbar
+template <typename T>
+cudaError_t da_adjoint_rhs(int batch, int N, double scale, const double* mu, const T* hbar, double* out,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t dot_compensated(int batch, long long len, const T* a, const T* b, double* d_partial, double* d_out,
+                            cudaStream_t s);
+constexpr int kPartials = 256;
+
+}  // namespace qpat
