@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput of the direct-QPAT acoustic hot path on GB300.
+
+Workload (seeded, synthetic): 2D 512 x 512 interior at dx = 0.05 mm with a
+32-cell PML on every side (576 x 576 FFT grid), six elliptic inclusions
+(c 1400-1650 m/s, rho 900-1100 kg/m^3, alpha0 0.5-1.0 dB MHz^-y cm^-1),
+y = 1.5, CFL 0.3, Nt = 2000, 256 sensors on the interior perimeter.  One
+step = one forward H_a and one adjoint H_a^* propagation of Nt time steps
+for each of ``--batch`` independent problems (initial pressures / adjoint
+sources), in FP32 with FP64-built operator tables.
+
+metric: forward+adjoint cell-steps per second, a cell-step being one FFT-grid
+cell (PML included) advanced one time step by one propagation.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload instead (see ``oracle/``).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import phantoms  # noqa: E402
+
+METRIC = "fwd+adjoint cell-steps/s"
+UNIT = "cell-steps/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--batch", type=int, default=8, help="independent problems per step")
+    p.add_argument("--nt", type=int, default=None, help="override Nt (default: workload's 2000)")
+    p.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/roofline/cpu legs")
+    return p.parse_args()
+
+
+def workload():
+    return phantoms.C2
+
+
+def config_dict(w, batch, nt, extra=None):
+    d = {"workload": f"2d {w.n}x{w.n} interior, {w.grid}x{w.grid} FFT grid (pml {w.pml}), "
+                     f"Nt={nt}, {w.n_sensors} perimeter sensors, y={w.y}, fwd+adj per problem",
+         "grid": w.grid, "interior": w.n, "nt": nt, "batch": batch, "sensors": w.n_sensors,
+         "seq_len": nt, "global_batch": batch,
+         "l2": "flushed between timed steps (256 MiB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_rate(w, nt_sample, seed=0):
+    """Cell-steps/s of the FP64 oracle (forward + adjoint, nt_sample steps
+    each) on this host, setup excluded."""
+    from oracle import acoustic
+    S = acoustic.setup_from_workload(w, nt=nt_sample)
+    p0 = phantoms.smooth_p0(w, seed)
+    W = phantoms.random_field((nt_sample, w.n_sensors), seed + 1)
+    t0 = time.perf_counter()
+    acoustic.forward(S, p0)
+    acoustic.adjoint(S, W)
+    t = time.perf_counter() - t0
+    return w.grid * w.grid * nt_sample * 2 / t, t
+
+
+def cpu_baseline(w, target_s=12.0):
+    probe_nt = 6
+    _, t = oracle_rate(w, probe_nt)
+    nt_s = max(4, min(400, int(probe_nt * target_s / max(t, 1e-3))))
+    v, t = oracle_rate(w, nt_s, seed=1)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, 1 problem, forward+adjoint of {nt_s} steps each on the "
+                      f"{w.grid}x{w.grid} grid ({t:.1f} s wall), single thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload()
+    nt = args.nt or w.nt
+    for _ in range(args.warmup):
+        oracle_rate(w, 4)
+    probe_nt = 6
+    _, t = oracle_rate(w, probe_nt)
+    nt_s = max(4, min(200, int(probe_nt * 8.0 / max(t, 1e-3))))
+    rates, times = [], []
+    for k in range(args.steps):
+        v, t = oracle_rate(w, nt_s, seed=k)
+        rates.append(v)
+        times.append(t)
+    total_cells = w.grid * w.grid * nt_s * 2 * args.steps
+    value = total_cells / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(w, 1, nt, {"reference_sample_nt": nt_s}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: forward+adjoint of {nt_s} of the {nt} time steps, "
+                                       f"1 problem, FP64 numpy, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, path, index):
+        self.path, self.index, self.proc = path, index, None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, n in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1810_11685_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def pass_bytes(phase, w, batch, elt=4):
+    """Algorithmic bytes of one launch of a propagation pass: every input and
+    output field of each problem read or written once (half spectra as
+    complex values, per-problem state fields), plus the medium diagonals and
+    k-space tables, which all problems of the batch share, read once."""
+    G = w.grid * w.grid
+    H = w.grid * (w.grid // 2 + 1)
+    spec = {"F_R1": (2, 1), "F_R2": (2, 2), "F_R3": (2, 2), "A_R1": (1, 2), "A_R3": (2, 2), "A_R5": (2, 2),
+            "F_C1": (1, 2), "F_C2": (2, 2), "F_C3": (2, 2), "A_C2": (2, 2), "A_C4": (2, 2), "A_C6": (2, 1)}
+    state = {"F_R1": 3, "F_R2": 4, "F_R3": 4, "A_R1": 1, "A_R3": 5, "A_R5": 4}      # per problem
+    medium = {"F_R1": 3, "F_R2": 2, "F_R3": 1, "A_R1": 3, "A_R3": 1, "A_R5": 2}     # shared
+    tables = {"F_C1": 1, "F_C2": 1, "F_C3": 2, "A_C2": 2, "A_C4": 1, "A_C6": 1}     # shared, half grid
+    kin, kout = spec[phase]
+    b = batch * (kin + kout) * H * 2 * elt
+    if phase in state:
+        b += (batch * state[phase] + medium[phase]) * G * elt
+    else:
+        b += tables[phase] * H * elt
+    return b
+
+
+def run_ours(args):
+    import torch
+    from paper_1810_11685_gb300.binding import context_from_workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload()
+    nt = args.nt or w.nt
+    B = args.batch
+    ctx = context_from_workload(w, precision="fp32", max_batch=B, nt=nt)
+    G = w.grid * w.grid
+    N = w.n * w.n
+    cells_per_step = B * G * nt * 2
+
+    rng = np.random.default_rng(100 + rank)
+    p0_h = np.stack([phantoms.smooth_p0(w, seed=rank * B + b) for b in range(B)]).astype(np.float32)
+    w_h = rng.standard_normal((B, nt, w.n_sensors)).astype(np.float32)
+    p0 = torch.as_tensor(p0_h, device=dev)
+    W = torch.as_tensor(w_h, device=dev)
+    data = torch.empty(B, nt, w.n_sensors, device=dev)
+    padj = torch.empty(B, w.n, w.n, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.acoustic_forward(p0, out=data)
+        ctx.acoustic_adjoint(W, out=padj)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ctx.sync()
+    launches0 = ctx.stats()["launches"]
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk_path = os.path.join(tempfile.gettempdir(), f"qpat_clocks_{rank}.csv")
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(clk_path, local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record()
+            step()
+            evs[k][1].record()
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ctx.sync()
+    launches = ctx.stats()["launches"] - launches0
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist is not None:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = world * cells_per_step * args.steps / (t_ms / 1e3)
+    clocks = clk.summary()
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # end to end through the C ABI with host buffers: pinned H2D of this
+        # step's inputs, the propagations, D2H of both results
+        p0_pin = torch.from_numpy(p0_h).pin_memory()
+        w_pin = torch.from_numpy(w_h).pin_memory()
+        out_pin = torch.empty(B, nt, w.n_sensors).pin_memory()
+        adj_pin = torch.empty(B, w.n, w.n).pin_memory()
+        e2e_ms = []
+        for k in range(max(2, args.steps)):
+            flush.fill_(float(k))
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            p0.copy_(p0_pin, non_blocking=True)
+            W.copy_(w_pin, non_blocking=True)
+            step()
+            out_pin.copy_(data, non_blocking=True)
+            adj_pin.copy_(padj, non_blocking=True)
+            e.record()
+            torch.cuda.synchronize()
+            e2e_ms.append(s.elapsed_time(e))
+        h2d = p0_h.nbytes + w_h.nbytes
+        d2h = out_pin.numel() * 4 + adj_pin.numel() * 4
+        extras["e2e"] = {"value": cells_per_step / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+        # per-pass device time from CUDA events on the library's stream
+        per = {}
+        for ph in ["F_R1", "F_C1", "F_R2", "F_C2", "F_R3", "F_C3", "A_R1", "A_C2", "A_R3", "A_C4", "A_R5", "A_C6"]:
+            ctx.profile(ph)
+            step()
+            ms, n = ctx.profile_read()
+            ctx.profile(None)
+            per[ph] = {"ms_total": ms, "launches": n, "us_per_launch": 1e3 * ms / max(n, 1)}
+        top = max(per, key=lambda k: per[k]["ms_total"])
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+        alg = pass_bytes(top, w, B)
+        ach = alg / (per[top]["us_per_launch"] * 1e-6) / 1e9
+        traffic = None
+        try:
+            tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+            if tr.get("source_hash") == source_hash() and top in tr.get("per_launch", {}):
+                traffic = tr["per_launch"][top]
+        except Exception:
+            pass
+        extras["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                              "frac": ach / peak, "traffic": traffic, "kernel": top,
+                              "alg_bytes_per_launch": alg, "peak_source": peak_src}
+        step_ms = t_ms / args.steps
+        extras["step_b_alg"] = {"bytes_per_cell_step": 60, "achieved_gbs": cells_per_step * 60 / (step_ms / 1e3) / 1e9,
+                                "frac_of_hbm": cells_per_step * 60 / (step_ms / 1e3) / 1e9 / peak}
+        extras["passes"] = {k: round(v["us_per_launch"], 2) for k, v in per.items()}
+
+        # the plain FP64 form on the same GPU: one problem, same workload
+        ctx64 = context_from_workload(w, precision="fp64", max_batch=1, nt=nt)
+        p64 = p0[:1].double().contiguous()
+        W64 = W[:1].double().contiguous()
+        ctx64.acoustic_forward(p64)
+        ctx64.acoustic_adjoint(W64)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        s.record()
+        ctx64.acoustic_forward(p64)
+        ctx64.acoustic_adjoint(W64)
+        e.record()
+        torch.cuda.synchronize()
+        ctx64.sync()
+        v64 = G * nt * 2 / (s.elapsed_time(e) / 1e3)
+        extras["fp64_plain"] = {"value": v64, "unit": UNIT, "batch": 1,
+                                "fp32_batched_over_fp64_plain": value / world / v64}
+        ctx64.close()
+        extras["cpu_baseline"] = cpu_baseline(w)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(w, B, nt, {"parallelism": f"replicas x{world}, no collective"}),
+                "clocks": clocks, "gpu_launches": int(launches), "impl": "ours",
+                "source_hash": source_hash()}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

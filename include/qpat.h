@@ -159,6 +159,18 @@ qpat_status qpat_vjp(qpat_ctx* ctx, int batch, const double* mu, const double* p
 qpat_status qpat_dot(qpat_ctx* ctx, int batch, long long len, const void* a, const void* b,
                      double* out);
 
+/* Instrumentation (no counterpart in the paper).
+ * qpat_get_stats: out[0] = propagation kernels launched by this context so
+ * far, out[1] = launches currently held by the phase profiler.
+ * qpat_profile: from now on bracket every launch of pass `phase` (an
+ * internal pass id, see paper_1810_11685_gb300/binding.py PHASES; -1 turns
+ * profiling off) with CUDA events on the context's stream.
+ * qpat_profile_read: synchronise, return the summed device time [ms] and the
+ * number of profiled launches, and reset the profiler. */
+qpat_status qpat_get_stats(const qpat_ctx* ctx, long long out[2]);
+qpat_status qpat_profile(qpat_ctx* ctx, int phase);
+qpat_status qpat_profile_read(qpat_ctx* ctx, double* total_ms, long long* count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,9 @@ _HEADER = os.path.join(_ROOT, "include", "qpat.h")
 STATUS = {0: "QPAT_OK", 1: "QPAT_EINVAL", 2: "QPAT_EUNSTABLE", 3: "QPAT_ENONFINITE",
           4: "QPAT_ENOCONV", 5: "QPAT_ETIMEOUT", 6: "QPAT_ENOMEM", 7: "QPAT_ECUDA"}
 FP64, FP32 = 0, 1
+# internal pass ids of the propagation kernels (csrc/qpat_internal.h, enum Phase)
+PHASES = {"F_R1": 0, "F_R2": 1, "F_R3": 2, "F_R3L": 3, "F_C1": 10, "F_C2": 11, "F_C3": 12,
+          "A_R1": 20, "A_R1L": 21, "A_R3": 22, "A_R5": 23, "A_C2": 30, "A_C4": 31, "A_C6": 32}
 
 
 class QpatError(RuntimeError):
@@ -74,6 +77,9 @@ def load():
         "qpat_jvp": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
         "qpat_vjp": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
         "qpat_dot": [vp, i, ll, vp, vp, ctypes.POINTER(d)],
+        "qpat_get_stats": [vp, ctypes.POINTER(ll)],
+        "qpat_profile": [vp, i],
+        "qpat_profile_read": [vp, ctypes.POINTER(d), ctypes.POINTER(ll)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -189,6 +195,23 @@ class Context:
 
     def sync(self):
         _check(self._ptr, self._lib.qpat_sync(self._ptr))
+
+    def stats(self):
+        arr = (ctypes.c_longlong * 2)()
+        _check(self._ptr, self._lib.qpat_get_stats(self._ptr, arr))
+        return {"launches": arr[0], "profiled": arr[1]}
+
+    def profile(self, phase):
+        """Bracket every launch of pass ``phase`` (name or id; None = off) with CUDA events."""
+        pid = -1 if phase is None else (PHASES[phase] if isinstance(phase, str) else int(phase))
+        _check(self._ptr, self._lib.qpat_profile(self._ptr, pid))
+
+    def profile_read(self):
+        """(summed device ms, launches) of the profiled pass; resets the profiler."""
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        _check(self._ptr, self._lib.qpat_profile_read(self._ptr, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     # -- entry points ----------------------------------------------------
     def acoustic_forward(self, p0, out=None):

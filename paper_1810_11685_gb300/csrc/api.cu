@@ -44,6 +44,11 @@ struct qpat_ctx {
   double* d_dot_partial = nullptr;
   double* d_dot_out = nullptr;
   double* h_dot_out = nullptr;
+  // launch accounting and per-phase event timing
+  long long launches = 0;
+  int prof_phase = -1;
+  std::vector<cudaEvent_t> prof_events;
+  size_t prof_used = 0;
 };
 
 namespace {
@@ -256,6 +261,29 @@ void zero_state(qpat_ctx* c, int batch) {
   cudaMemsetAsync(a.ry, 0, bytes, c->stream);
 }
 
+
+// Launch one pass, counting it and, when this phase is being profiled,
+// bracketing it with CUDA events on the context's stream.
+template <typename T>
+void pass(qpat_ctx* c, const PropArgs<T>& a, int phase, int batch, bool is_row) {
+  const bool prof = (c->prof_phase == phase);
+  if (prof) {
+    while (c->prof_events.size() < c->prof_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      c->prof_events.push_back(e);
+    }
+    if (c->prof_events.size() >= c->prof_used + 2) cudaEventRecord(c->prof_events[c->prof_used], c->stream);
+  }
+  if (is_row) launch_row<T>(a, phase, batch, c->stream);
+  else launch_col<T>(a, phase, batch, c->stream);
+  ++c->launches;
+  if (prof && c->prof_events.size() >= c->prof_used + 2) {
+    cudaEventRecord(c->prof_events[c->prof_used + 1], c->stream);
+    c->prof_used += 2;
+  }
+}
+
 // H_a: launch sequence of the forward loop n = -1 .. Nt - 2 (Section 3.2.3).
 template <typename T>
 qpat_status run_forward(qpat_ctx* c, int batch, const T* p0, T* data) {
@@ -268,40 +296,42 @@ qpat_status run_forward(qpat_ctx* c, int batch, const T* p0, T* data) {
   if (!c->cfg.lossless) {
     a.n = 0;
     a.flags = kSkipInput | kSource;          // step n = -1 from zero fields
-    launch_row<T>(a, F_R3, batch, s);
+    pass<T>(c, a, F_R3, batch, true);
     a.flags = 0;
-    launch_col<T>(a, F_C3, batch, s);
+    pass<T>(c, a, F_C3, batch, false);
     for (int n = 0; n <= nt - 2; ++n) {
       a.n = n;
       a.flags = 0;
-      launch_row<T>(a, F_R1, batch, s);      // p_n
-      launch_col<T>(a, F_C1, batch, s);      // sample n, d/dr^+ p_n
-      launch_row<T>(a, F_R2, batch, s);      // v^(n+1/2)
-      launch_col<T>(a, F_C2, batch, s);      // d/dr^- v
+      pass<T>(c, a, F_R1, batch, true);      // p_n
+      pass<T>(c, a, F_C1, batch, false);      // sample n, d/dr^+ p_n
+      pass<T>(c, a, F_R2, batch, true);      // v^(n+1/2)
+      pass<T>(c, a, F_C2, batch, false);      // d/dr^- v
       a.flags = (n == 0) ? kSource : 0;
-      launch_row<T>(a, F_R3, batch, s);      // rho^(n+1)
+      pass<T>(c, a, F_R3, batch, true);      // rho^(n+1)
       a.flags = 0;
-      launch_col<T>(a, F_C3, batch, s);      // Y_dis, Y_abs
+      pass<T>(c, a, F_C3, batch, false);      // Y_dis, Y_abs
     }
     a.n = nt - 1;
     a.flags = kSkipOutput;
-    launch_row<T>(a, F_R1, batch, s);        // p_(Nt-1)
+    pass<T>(c, a, F_R1, batch, true);        // p_(Nt-1)
     launch_gather<T>(a, batch, s);
+    ++c->launches;
   } else {
     a.n = 0;
     a.flags = kSkipInput | kSource;
-    launch_row<T>(a, F_R3L, batch, s);       // p_0
+    pass<T>(c, a, F_R3L, batch, true);       // p_0
     for (int n = 0; n <= nt - 2; ++n) {
       a.n = n;
       a.flags = 0;
-      launch_col<T>(a, F_C1, batch, s);
-      launch_row<T>(a, F_R2, batch, s);
-      launch_col<T>(a, F_C2, batch, s);
+      pass<T>(c, a, F_C1, batch, false);
+      pass<T>(c, a, F_R2, batch, true);
+      pass<T>(c, a, F_C2, batch, false);
       a.flags = (n == 0) ? kSource : 0;
-      launch_row<T>(a, F_R3L, batch, s);     // p_(n+1)
+      pass<T>(c, a, F_R3L, batch, true);     // p_(n+1)
     }
     a.n = nt - 1;
     launch_gather<T>(a, batch, s);
+    ++c->launches;
   }
   QCK(cudaGetLastError());
   return QPAT_OK;
@@ -323,20 +353,20 @@ qpat_status run_adjoint(qpat_ctx* c, int batch, const T* w, T* p0adj) {
     const int last = (n == -1) ? kSkipOutput : 0;
     if (!c->cfg.lossless) {
       a.flags = first;
-      launch_row<T>(a, A_R1, batch, s);
+      pass<T>(c, a, A_R1, batch, true);
       a.flags = 0;
-      launch_col<T>(a, A_C2, batch, s);
+      pass<T>(c, a, A_C2, batch, false);
       a.flags = acc | last;
-      launch_row<T>(a, A_R3, batch, s);
+      pass<T>(c, a, A_R3, batch, true);
     } else {
       a.flags = first | acc | last;
-      launch_row<T>(a, A_R1L, batch, s);
+      pass<T>(c, a, A_R1L, batch, true);
     }
     if (n > -1) {
       a.flags = 0;
-      launch_col<T>(a, A_C4, batch, s);
-      launch_row<T>(a, A_R5, batch, s);
-      launch_col<T>(a, A_C6, batch, s);
+      pass<T>(c, a, A_C4, batch, false);
+      pass<T>(c, a, A_R5, batch, true);
+      pass<T>(c, a, A_C6, batch, false);
     }
   }
   QCK(cudaGetLastError());
@@ -479,6 +509,7 @@ qpat_status qpat_destroy(qpat_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (void* p : c->dev_allocs) cudaFree(p);
   for (void* p : c->host_allocs) cudaFreeHost(p);
+  for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
   delete c;
   return QPAT_OK;
 }
@@ -607,6 +638,35 @@ qpat_status qpat_dot(qpat_ctx* c, int batch, long long len, const void* a, const
   QCK(cudaMemcpyAsync(c->h_dot_out, c->d_dot_out, batch * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   QCK(cudaStreamSynchronize(c->stream));
   for (int i = 0; i < batch; ++i) out[i] = c->h_dot_out[i];
+  return QPAT_OK;
+}
+
+qpat_status qpat_get_stats(const qpat_ctx* c, long long out[2]) {
+  if (!c || !out) return QPAT_EINVAL;
+  out[0] = c->launches;
+  out[1] = (long long)c->prof_used / 2;
+  return QPAT_OK;
+}
+
+qpat_status qpat_profile(qpat_ctx* c, int phase) {
+  if (!c) return QPAT_EINVAL;
+  c->prof_phase = phase;
+  c->prof_used = 0;
+  return QPAT_OK;
+}
+
+qpat_status qpat_profile_read(qpat_ctx* c, double* total_ms, long long* count) {
+  if (!c || !total_ms || !count) return QPAT_EINVAL;
+  QCK(cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  for (size_t k = 0; k + 1 < c->prof_used; k += 2) {
+    float ms = 0.f;
+    QCK(cudaEventElapsedTime(&ms, c->prof_events[k], c->prof_events[k + 1]));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *count = (long long)c->prof_used / 2;
+  c->prof_used = 0;
   return QPAT_OK;
 }
 
