@@ -72,6 +72,8 @@ typedef struct {
   double gamma_d;      /* Robin factor of eq. DA; <= 0: 1/pi */
   int pcg_max_iter;    /* diffusion-solve iteration cap; <= 0: 20000 */
   double pcg_tol;      /* relative residual target; <= 0: 1e-13 */
+  int generic_fft;     /* 1: use the generic shared-memory FFT passes even where a
+                          register-FFT specialisation of the extent exists */
 } qpat_config;
 
 /* Medium, host memory, FP64, read during qpat_create only.

@@ -146,6 +146,15 @@ qpat_status build_context(qpat_ctx* c, const qpat_medium* med, const double* sen
   QCK(dalloc(c, &o.shym, c->ny * sizeof(C)));
   QCK(dalloc(c, &o.twx, c->nx * sizeof(C)));
   QCK(dalloc(c, &o.twy, c->ny * sizeof(C)));
+  // register-FFT column passes for the lengths that have them (unless
+  // disabled).  Measured on GB300 they win only in FP32 column passes: the
+  // FP64 ones spill, and the row passes' pointwise loads need more resident
+  // warps than the 24-point-per-thread FFT leaves room for.
+  const bool fast_ok = !c->cfg.generic_fft && sizeof(T) == 4;
+  if (fast_ok && fast_length_split(c->ny) > 0) {
+    QCK(dalloc(c, &o.fy_ab, c->ny * sizeof(C)));
+    QCK(dalloc(c, &o.fy_ba, c->ny * sizeof(C)));
+  }
   // FP64 medium staging
   double *dc = nullptr, *drho = nullptr, *dal = nullptr;
   QCK(cudaMalloc(&dc, G * sizeof(double)));
@@ -165,6 +174,7 @@ qpat_status build_context(qpat_ctx* c, const qpat_medium* med, const double* sen
   a.kap = o.kap; a.kp1 = o.kp1; a.kp2 = o.kp2;
   a.shxp = o.shxp; a.shxm = o.shxm; a.shyp = o.shyp; a.shym = o.shym;
   a.twx = o.twx; a.twy = o.twy;
+  a.fx_ab = o.fx_ab; a.fx_ba = o.fx_ba; a.fy_ab = o.fy_ab; a.fy_ba = o.fy_ba;
 
   // sensors: bilinear weights on the node grid (gather form) and the
   // transposed scatter as a per-row, per-point gather (deterministic)
@@ -341,7 +351,6 @@ qpat_status run_forward(qpat_ctx* c, int batch, const T* p0, T* data) {
 template <typename T>
 qpat_status run_adjoint(qpat_ctx* c, int batch, const T* w, T* p0adj) {
   PropArgs<T> a = args<T>(c);
-  cudaStream_t s = c->stream;
   a.w = w;
   a.p0adj = p0adj;
   zero_state<T>(c, batch);

@@ -18,7 +18,7 @@
 // a step touches the state fields once and the spectra twice per operator
 // application.  The batch index is blockIdx.y: many problems on the same
 // grid and medium share each launch.
-#include "qpat_internal.h"
+#include "pass_ops.cuh"
 
 namespace qpat {
 
@@ -73,7 +73,6 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const PropArgs<T> a) {
   C* spec = a.spec + (long long)b * a.sstride;
   const long long slot = (long long)a.ny * a.pitch;
   const bool skip_in = (a.flags & kSkipInput) != 0;
-  const long long gb = (long long)b * a.gstride;
 
   // 1. inverse x-transform: Z(k) = A(k) + i B(k) over the Hermitian-extended
   //    half spectra of rows j0 (A) and j0+1 (B); the unnormalised inverse
@@ -105,15 +104,7 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const PropArgs<T> a) {
   if (PH == A_R1 || PH == A_R1L) {
     for (int i = tid; i < 2 * nx; i += nth) sc[i] = (T)0;
     __syncthreads();
-    const T* wn = a.w + ((long long)b * a.nt + a.n) * a.ns;
-    for (int rr = 0; rr < 2; ++rr) {
-      const int j = j0 + rr;
-      for (int q = a.rowptr[j] + tid; q < a.rowptr[j + 1]; q += nth) {
-        T acc = (T)0;
-        for (int e = a.pent[q]; e < a.pent[q + 1]; ++e) acc += a.ew[e] * wn[a.esens[e]];
-        sc[rr * nx + a.pcol[q]] = acc;
-      }
-    }
+    sensor_scatter_rows<T>(a, b, j0, sc, tid, nth);
     __syncthreads();
   }
 
@@ -122,8 +113,6 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const PropArgs<T> a) {
   for (int i = tid; i < nx; i += nth) {
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
-      const int j = j0 + rr;
-      const long long g = (long long)j * nx + i;
       T in0 = (T)0, in1 = (T)0;
       if (!skip_in) {
         // res = FFT(conj Z) = conj(z): row j0 is Re, row j0+1 is -Im
@@ -134,81 +123,9 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const PropArgs<T> a) {
           in1 = rr ? -z1.y : z1.x;
         }
       }
-      T out0 = (T)0, out1 = (T)0;
-      const bool interior = (i >= a.pml) && (i < a.pml + a.n0) && (j >= a.pml) && (j < a.pml + a.n1);
-      const long long ii = interior ? (long long)(j - a.pml) * a.n0 + (i - a.pml) : 0;
-      if (PH == F_R1) {
-        // eq. num-p: p = c^2 [ (I - eta Y_dis) sum rho_i + tau Y_abs u ]
-        const T r = a.rx[gb + g] + a.ry[gb + g];
-        const T p = a.Cc[g] * ((r - a.eta[g] * in0) + a.tau[g] * in1);
-        a.pbuf[gb + g] = p;
-        bad |= !isfinite(p);
-        out0 = p;
-      } else if (PH == F_R2) {
-        // eq. num-vel: v_i <- A_i (A_i v_i - dt/rho_i d/dr_i^+ p)
-        const T sx = a.asx[i], sy = a.asy[j];
-        const T vx = sx * (sx * a.vx[gb + g] - a.dtrsx[g] * in0);
-        const T vy = sy * (sy * a.vy[gb + g] - a.dtrsy[g] * in1);
-        a.vx[gb + g] = vx;
-        a.vy[gb + g] = vy;
-        out0 = vx;
-        out1 = vy;
-      } else if (PH == F_R3 || PH == F_R3L) {
-        // eq. num-rho with the additive source of eq. s1 (dt s_i = P0 / (2 d c^2))
-        T q = (T)0;
-        if ((a.flags & kSource) && interior) q = a.p0[(long long)b * a.n0 * a.n1 + ii] / ((T)4 * a.Cc[g]);
-        const T ax = a.ax[i], ay = a.ay[j], r0 = a.rho0[g];
-        const T rx = ax * (ax * a.rx[gb + g] - a.dt * r0 * in0) + q;
-        const T ry = ay * (ay * a.ry[gb + g] - a.dt * r0 * in1) + q;
-        a.rx[gb + g] = rx;
-        a.ry[gb + g] = ry;
-        if (PH == F_R3) {
-          out0 = rx + ry;                            // sum_i rho_i
-          out1 = ax * r0 * in0 + ay * r0 * in1;      // sum_i A_i rho0 d/dr_i^- v_i
-        } else {
-          const T p = a.Cc[g] * (rx + ry);
-          a.pbuf[gb + g] = p;
-          bad |= !isfinite(p);
-          out0 = p;
-        }
-      } else if (PH == A_R1) {
-        const T pb = in0 + sc[rr * nx + i];
-        const T Cp = a.Cc[g] * pb;
-        a.pbuf[gb + g] = Cp;
-        out0 = a.eta[g] * Cp;
-        out1 = a.tau[g] * Cp;
-      } else if (PH == A_R1L || PH == A_R3) {
-        T Cp, ya = (T)0;
-        if (PH == A_R1L) {
-          Cp = a.Cc[g] * (in0 + sc[rr * nx + i]);
-        } else {
-          Cp = a.pbuf[gb + g];
-          ya = in1;
-        }
-        const T rpart = (PH == A_R1L) ? Cp : Cp - in0;   // (I - Y_dis eta) C p-bar
-        const T ax = a.ax[i], ay = a.ay[j], r0 = a.rho0[g];
-        const T rtx = a.rx[gb + g] + rpart;
-        const T rty = a.ry[gb + g] + rpart;
-        out0 = r0 * ax * (ya - a.dt * rtx);
-        out1 = r0 * ay * (ya - a.dt * rty);
-        a.rx[gb + g] = ax * ax * rtx;
-        a.ry[gb + g] = ay * ay * rty;
-        bad |= !isfinite(rtx + rty);
-        if (interior && (a.flags & (kAccWrite | kAccAdd))) {
-          T* dst = a.p0adj + (long long)b * a.n0 * a.n1 + ii;
-          const T val = (rtx + rty) / ((T)4 * a.Cc[g]);
-          if (a.flags & kAccWrite) *dst = val;
-          else *dst += val;
-        }
-      } else if (PH == A_R5) {
-        const T sx = a.asx[i], sy = a.asy[j];
-        const T vtx = a.vx[gb + g] + in0;
-        const T vty = a.vy[gb + g] + in1;
-        a.vx[gb + g] = sx * sx * vtx;
-        a.vy[gb + g] = sy * sy * vty;
-        out0 = sx * a.dtrsx[g] * vtx;
-        out1 = sy * a.dtrsy[g] * vty;
-      }
+      const T scv = (PH == A_R1 || PH == A_R1L) ? sc[rr * nx + i] : (T)0;
+      T out0, out1;
+      row_point<T>(a, PH, b, i, j0 + rr, in0, in1, scv, out0, out1, bad);
       if (rr == 0) {
         oth[i].x = out0;
         if (KOUT > 1) oth[nx + i].x = out1;
@@ -254,17 +171,7 @@ __global__ void __launch_bounds__(kColThreads) col_kernel(const PropArgs<T> a) {
   C* spec = a.spec + (long long)b * a.sstride;
   const long long slot = (long long)ny * a.pitch;
 
-  if (PH == F_C1) {
-    // eq. num-m: bilinear sampling of p_n (written by the previous row pass)
-    const T* pb = a.pbuf + (long long)b * a.gstride;
-    T* dn = a.data + ((long long)b * a.nt + a.n) * a.ns;
-    for (int s = blockIdx.x * nth + tid; s < a.ns; s += gridDim.x * nth) {
-      T acc = (T)0;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc += a.sw[4 * s + c] * pb[a.sidx[4 * s + c]];
-      dn[s] = acc;
-    }
-  }
+  if (PH == F_C1) sensor_gather<T>(a, b, blockIdx.x * nth + tid, gridDim.x * nth);   // eq. num-m
 
   for (int s = 0; s < KIN; ++s) {
     for (int idx = tid; idx < ny * cb; idx += nth) {
@@ -284,26 +191,7 @@ __global__ void __launch_bounds__(kColThreads) col_kernel(const PropArgs<T> a) {
     if (kx < nxh) {
       const C X0 = res[c * S + ky];
       const C X1 = (KIN > 1) ? res[(cb + c) * S + ky] : X0;
-      const long long t = (long long)ky * nxh + kx;
-      if (PH == F_C1) {          // d/dr_x^+, d/dr_y^+ of p (eq. grr)
-        const T k = a.kap[t];
-        o0 = cscale(cmul(a.shxp[kx], X0), k);
-        o1 = cscale(cmul(a.shyp[ky], X0), k);
-      } else if (PH == F_C2) {   // d/dr_x^- v_x, d/dr_y^- v_y
-        const T k = a.kap[t];
-        o0 = cscale(cmul(a.shxm[kx], X0), k);
-        o1 = cscale(cmul(a.shym[ky], X1), k);
-      } else if (PH == F_C3 || PH == A_C2) {   // Y_dis, Y_abs (real, even symbols)
-        o0 = cscale(X0, a.kp1[t]);
-        o1 = cscale(X1, a.kp2[t]);
-      } else if (PH == A_C4) {   // (d/dr_i^-)^T: conjugate symbols
-        const T k = a.kap[t];
-        o0 = cscale(cmul(cconj(a.shxm[kx]), X0), k);
-        o1 = cscale(cmul(cconj(a.shym[ky]), X1), k);
-      } else if (PH == A_C6) {   // -sum_i (d/dr_i^+)^T
-        const T k = a.kap[t];
-        o0 = cscale(cadd(cmul(cconj(a.shxp[kx]), X0), cmul(cconj(a.shyp[ky]), X1)), -k);
-      }
+      col_point<T, C>(a, PH, kx, ky, X0, X1, o0, o1);
     }
     oth[c * S + ky] = cconj(o0);
     if (KOUT > 1) oth[(cb + c) * S + ky] = cconj(o1);
@@ -320,15 +208,7 @@ __global__ void __launch_bounds__(kColThreads) col_kernel(const PropArgs<T> a) {
 
 template <typename T>
 __global__ void gather_kernel(const PropArgs<T> a) {
-  const int b = blockIdx.y;
-  const T* pb = a.pbuf + (long long)b * a.gstride;
-  T* dn = a.data + ((long long)b * a.nt + a.n) * a.ns;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.ns; s += gridDim.x * blockDim.x) {
-    T acc = (T)0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc += a.sw[4 * s + c] * pb[a.sidx[4 * s + c]];
-    dn[s] = acc;
-  }
+  sensor_gather<T>(a, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -350,8 +230,27 @@ int prop_init_attributes() {
   return 0;
 }
 
+#define QPAT_FAST_CASES(X) X(24) X(40) X(48) X(54) X(56) X(168) X(288) X(432) X(576)
+
+int fast_length_split(int L) {
+  switch (L) {
+#define QPAT_SPLIT_CASE(n) case n: return fast_split_a(n);
+    QPAT_FAST_CASES(QPAT_SPLIT_CASE)
+#undef QPAT_SPLIT_CASE
+    default: return 0;
+  }
+}
+
 template <typename T>
 void launch_row(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
+  if (a.fx_ab) {
+    switch (a.nx) {
+#define QPAT_ROW_CASE(n) case n: launch_row_fast_len<T, n>(a, phase, batch, s); return;
+      QPAT_FAST_CASES(QPAT_ROW_CASE)
+#undef QPAT_ROW_CASE
+      default: break;
+    }
+  }
   dim3 grid(a.ny / 2, batch);
   const size_t sm = row_smem_bytes<T>(a.nx);
   switch (phase) {
@@ -369,6 +268,14 @@ void launch_row(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
 
 template <typename T>
 void launch_col(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
+  if (a.fy_ab) {
+    switch (a.ny) {
+#define QPAT_COL_CASE(n) case n: launch_col_fast_len<T, n>(a, phase, batch, s); return;
+      QPAT_FAST_CASES(QPAT_COL_CASE)
+#undef QPAT_COL_CASE
+      default: break;
+    }
+  }
   dim3 grid((a.nxh + a.cb - 1) / a.cb, batch);
   const size_t sm = col_smem_bytes<T>(a.ny, a.cb);
   switch (phase) {

@@ -45,6 +45,11 @@ struct PropArgs {
   FFTPlan px, py;
   const C* twx;
   const C* twy;
+  // register-FFT twiddles W_L^(l k1) of the L = A * B splits (null: generic path)
+  const C* fx_ab;         // [A][B] for rows, L = nx
+  const C* fx_ba;         // [B][A]
+  const C* fy_ab;         // columns, L = ny
+  const C* fy_ba;
   // medium diagonals on the full grid [ny][nx]
   const T* Cc;            // c^2
   const T* rho0;          // ambient density at nodes
@@ -96,6 +101,13 @@ template <typename T>
 void launch_col(const PropArgs<T>& a, int phase, int batch, cudaStream_t s);
 template <typename T>
 void launch_gather(const PropArgs<T>& a, int batch, cudaStream_t s);
+// length-specialised passes (fast_kernels.cuh), one translation unit per length
+template <typename T, int L>
+void launch_row_fast_len(const PropArgs<T>& a, int ph, int batch, cudaStream_t s);
+template <typename T, int L>
+void launch_col_fast_len(const PropArgs<T>& a, int ph, int batch, cudaStream_t s);
+// A of the register-FFT split L = A * B, 0 if L has no specialised passes
+int fast_length_split(int L);
 template <typename T>
 size_t row_smem_bytes(int nx);
 template <typename T>
@@ -112,6 +124,7 @@ struct TableOut {
   T *kap, *kp1, *kp2;
   C *shxp, *shxm, *shyp, *shym;
   C *twx, *twy;
+  C *fx_ab, *fx_ba, *fy_ab, *fy_ba;   // optional (register-FFT lengths only)
 };
 template <typename T>
 cudaError_t build_tables(const TableOut<T>& o, const double* d_c, const double* d_rho, const double* d_alpha_db,

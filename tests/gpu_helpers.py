@@ -12,10 +12,10 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def make_pair(w, precision="fp64", max_batch=1, nt=None):
+def make_pair(w, precision="fp64", max_batch=1, nt=None, **kw):
     """(GPU context, oracle setup) for workload ``w``."""
     from paper_1810_11685_gb300.binding import context_from_workload
-    ctx = context_from_workload(w, precision=precision, max_batch=max_batch, nt=nt)
+    ctx = context_from_workload(w, precision=precision, max_batch=max_batch, nt=nt, **kw)
     S = acoustic.setup_from_workload(w, nt=nt)
     return ctx, S
 

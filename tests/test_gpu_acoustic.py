@@ -15,11 +15,14 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 CASES = {
-    # interior n, pml -> FFT extents 56 (8 7), 40 (8 5), 54 (2 27)
+    # interior n, pml -> FFT extents 56 (8 7), 40 (8 5), 54 (2 27): register-FFT passes;
+    # 64 and 70 (2 5 7) have no specialisation and run the generic passes
     "lossy-56": dict(n=40, pml=8, nt=70),
     "lossless-56": dict(n=40, pml=8, nt=70, lossless=True),
     "lossy-40-y11": dict(n=30, pml=5, nt=50, y=1.1),
     "lossy-54": dict(n=44, pml=5, nt=64, seed=3),
+    "lossy-64": dict(n=48, pml=8, nt=40, seed=6),
+    "lossless-70": dict(n=60, pml=5, nt=40, lossless=True, seed=8),
 }
 
 
@@ -29,10 +32,11 @@ def workload(name):
     return phantoms.small(**kw)
 
 
+@pytest.mark.parametrize("generic", [False, True])
 @pytest.mark.parametrize("name", list(CASES))
-def test_forward_fp64_matches_oracle(name):
+def test_forward_fp64_matches_oracle(name, generic):
     w = workload(name)
-    ctx, S = make_pair(w, "fp64")
+    ctx, S = make_pair(w, "fp64", generic_fft=generic)
     p0 = phantoms.smooth_p0(w) + 0.1 * phantoms.random_field(w.interior_shape, 3)
     ref = acoustic.forward(S, p0)
     got = to_np(ctx.acoustic_forward(to_gpu(p0, torch.float64)))[0]
@@ -40,10 +44,11 @@ def test_forward_fp64_matches_oracle(name):
     assert rel_l2(got, ref) <= 1e-10
 
 
+@pytest.mark.parametrize("generic", [False, True])
 @pytest.mark.parametrize("name", list(CASES))
-def test_adjoint_fp64_matches_oracle(name):
+def test_adjoint_fp64_matches_oracle(name, generic):
     w = workload(name)
-    ctx, S = make_pair(w, "fp64")
+    ctx, S = make_pair(w, "fp64", generic_fft=generic)
     W = phantoms.random_field((w.nt, w.n_sensors), 4)
     ref = acoustic.adjoint(S, W)
     got = to_np(ctx.acoustic_adjoint(to_gpu(W, torch.float64)))[0]
@@ -51,10 +56,11 @@ def test_adjoint_fp64_matches_oracle(name):
     assert rel_l2(got, ref) <= 1e-10
 
 
-@pytest.mark.parametrize("name", ["lossy-56", "lossless-56"])
-def test_forward_fp32_matches_oracle(name):
+@pytest.mark.parametrize("generic", [False, True])
+@pytest.mark.parametrize("name", ["lossy-56", "lossless-56", "lossy-64"])
+def test_forward_fp32_matches_oracle(name, generic):
     w = workload(name)
-    ctx, S = make_pair(w, "fp32")
+    ctx, S = make_pair(w, "fp32", generic_fft=generic)
     p0 = phantoms.smooth_p0(w)
     ref = acoustic.forward(S, p0)
     got = to_np(ctx.acoustic_forward(to_gpu(p0, torch.float32)))[0]
@@ -121,3 +127,53 @@ def test_nonfinite_detection():
     assert e.value.status == 3
     ctx.acoustic_forward(to_gpu(np.ones(w.interior_shape), torch.float32))
     ctx.sync()   # flag cleared, healthy call passes
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
+def test_c2_grid_first_steps(prec, tol):
+    """The bench workload's grid (512^2 interior, 576^2 FFT grid, 256 perimeter
+    sensors, y = 1.5), first 120 of its 2000 steps, forward and adjoint against
+    the oracle on the same seeded inputs, batch of 2 in the launch.  The
+    initial pressures are white noise so that the perimeter sensors see
+    signal from the first step (smooth central sources would not reach them
+    within 120 steps, leaving only rounding-level data)."""
+    w = phantoms.C2
+    ctx, S = make_pair(w, prec, max_batch=2, nt=120)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    p0 = np.stack([phantoms.random_field(w.interior_shape, 40), phantoms.random_field(w.interior_shape, 41)])
+    got = to_np(ctx.acoustic_forward(to_gpu(p0, dt)))
+    for b in range(2):
+        assert rel_l2(got[b], acoustic.forward(S, p0[b])) <= tol
+    W = phantoms.random_field((120, w.n_sensors), 9)
+    got = to_np(ctx.acoustic_adjoint(to_gpu(W, dt)))[0]
+    assert rel_l2(got, acoustic.adjoint(S, W)) <= tol
+
+
+def test_specialised_and_generic_passes_agree_fp32():
+    """Same workload through both FFT implementations (bit patterns differ,
+    values agree to FP32 rounding)."""
+    w = phantoms.small(n=40, pml=8, nt=200, n_sensors=16, seed=2)
+    a, _ = make_pair(w, "fp32")
+    g, _ = make_pair(w, "fp32", generic_fft=True)
+    p0 = to_gpu(phantoms.smooth_p0(w), torch.float32)
+    assert rel_l2(to_np(a.acoustic_forward(p0)), to_np(g.acoustic_forward(p0))) <= 1e-5
+
+
+def test_c2_fp32_full_length_against_fp64_gpu():
+    """Full 2000-step series on the bench grid: the FP32 path against the FP64
+    GPU path (itself pinned to the oracle above), relative L2 <= 2e-4, and the
+    FP32 dot-product test at full size."""
+    w = phantoms.C2
+    c32, _ = make_pair(w, "fp32", nt=w.nt)
+    c64, _ = make_pair(w, "fp64", nt=w.nt)
+    p0 = phantoms.smooth_p0(w)
+    d32 = to_np(c32.acoustic_forward(to_gpu(p0, torch.float32)))
+    d64 = to_np(c64.acoustic_forward(to_gpu(p0, torch.float64)))
+    assert rel_l2(d32, d64) <= 2e-4
+    W = phantoms.random_field((w.nt, w.n_sensors), 3)
+    a32 = to_np(c32.acoustic_adjoint(to_gpu(W, torch.float32)))
+    a64 = to_np(c64.acoustic_adjoint(to_gpu(W, torch.float64)))
+    assert rel_l2(a32, a64) <= 2e-4
+    lhs = float(np.sum(d32[0].astype(np.float64) * W))
+    rhs = float(np.sum(p0 * a32[0]))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
