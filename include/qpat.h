@@ -173,6 +173,24 @@ qpat_status qpat_get_stats(const qpat_ctx* ctx, long long out[2]);
 qpat_status qpat_profile(qpat_ctx* ctx, int phase);
 qpat_status qpat_profile_read(qpat_ctx* ctx, double* total_ms, long long* count);
 
+/* Inner products <a_b, c_b> exactly as qpat_dot computes them, for callers
+ * that may not allocate device memory where they call it (a frozen memory
+ * pool, a host framework that owns all device allocations, an inner solver
+ * loop where cudaMalloc would synchronise the device) and hold no context.
+ * The paper has no counterpart: this is an interface convenience.
+ * prec: QPAT_FP32 or QPAT_FP64 element type of a and b (device, [batch][len]);
+ * out: device double [batch]; stream: cudaStream_t (NULL = legacy default).
+ * Allocates nothing: the scratch is a fixed 512 KiB device array inside the
+ * library, so batch is limited to 1..64 (EINVAL beyond, message in
+ * qpat_noalloc_last_error).  The first call on each device looks up that
+ * array's address with the device current; make it before any stream
+ * capture.  Calls share the array: overlapping calls race and must be
+ * ordered by the caller.  Enqueue-only; returns without waiting. */
+qpat_status qpat_dot_noalloc(int prec, int batch, long long len, const void* a, const void* b,
+                             double* out, void* stream);
+/* Message of the last failing qpat_dot_noalloc call on this host thread. */
+const char* qpat_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

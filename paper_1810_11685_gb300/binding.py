@@ -88,6 +88,10 @@ def load():
         f.restype = ctypes.c_int
     lib.qpat_last_error.argtypes = [vp]
     lib.qpat_last_error.restype = ctypes.c_char_p
+    lib.qpat_dot_noalloc.argtypes = [i, i, ll, vp, vp, vp, vp]
+    lib.qpat_dot_noalloc.restype = ctypes.c_int
+    lib.qpat_noalloc_last_error.argtypes = []
+    lib.qpat_noalloc_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -322,6 +326,24 @@ def qpat_vjp(ctx: Context, mu, w, illum, phi0=None):
 
 def qpat_dot(ctx: Context, a, b):
     return ctx.dot(a, b)
+
+
+def qpat_dot_noalloc(a, b, out=None):
+    """<a_b, b_b> in FP64 without any device allocation inside the library
+    (``out``: a preallocated CUDA float64 tensor of shape [batch]; the
+    caller owns every buffer).  a, b: CUDA float32/float64 [batch][len]."""
+    import torch
+    lib = load()
+    if a.dtype != b.dtype or a.shape != b.shape or a.dim() != 2:
+        raise TypeError("qpat_dot_noalloc wants two [batch][len] tensors of one dtype")
+    if out is None:
+        out = torch.empty(a.shape[0], dtype=torch.float64, device=a.device)
+    prec = FP32 if a.dtype == torch.float32 else FP64
+    st = lib.qpat_dot_noalloc(prec, a.shape[0], a.shape[1], _ptr(a), _ptr(b), _ptr(out),
+                              ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream))
+    if st != 0:
+        raise QpatError(st, lib.qpat_noalloc_last_error().decode())
+    return out
 
 
 def qpat_sync(ctx: Context):
