@@ -73,7 +73,9 @@ typedef struct {
   int pcg_max_iter;    /* diffusion-solve iteration cap; <= 0: 20000 */
   double pcg_tol;      /* relative residual target; <= 0: 1e-13 */
   int generic_fft;     /* 1: use the generic shared-memory FFT passes even where a
-                          register-FFT specialisation of the extent exists */
+                          length-specialised pass exists for the extent */
+  int no_graphs;       /* 1: launch every pass directly instead of replaying a
+                          CUDA graph of the time loop captured on first use */
 } qpat_config;
 
 /* Medium, host memory, FP64, read during qpat_create only.

@@ -39,7 +39,7 @@ class qpat_config(ctypes.Structure):
                 ("pml_alpha", ctypes.c_double), ("y", ctypes.c_double), ("lossless", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("gamma_d", ctypes.c_double),
                 ("pcg_max_iter", ctypes.c_int), ("pcg_tol", ctypes.c_double),
-                ("generic_fft", ctypes.c_int)]
+                ("generic_fft", ctypes.c_int), ("no_graphs", ctypes.c_int)]
 
 
 class qpat_medium(ctypes.Structure):
@@ -121,7 +121,8 @@ class Context:
 
     def __init__(self, c, rho, alpha0_db, kappa, sensors, *, dx, dt, nt, pml, y=1.5, lossless=False,
                  precision="fp32", max_batch=1, c_ref=0.0, pml_alpha=0.0, gamma_d=0.0,
-                 pcg_max_iter=0, pcg_tol=0.0, generic_fft=False, device=None):
+                 pcg_max_iter=0, pcg_tol=0.0, generic_fft=False, no_graphs=False,
+                 device=None):
         import torch
         lib = load()
         c = _host(c)
@@ -137,6 +138,7 @@ class Context:
         cfg.lossless, cfg.max_batch = int(bool(lossless)), int(max_batch)
         cfg.gamma_d, cfg.pcg_max_iter, cfg.pcg_tol = float(gamma_d), int(pcg_max_iter), float(pcg_tol)
         cfg.generic_fft = int(bool(generic_fft))
+        cfg.no_graphs = int(bool(no_graphs))
         keep = [c, rho, kappa, sensors]
         al = None
         if not lossless:

@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <cstdio>
 #include <string>
 #include <tuple>
@@ -47,6 +48,8 @@ struct qpat_ctx {
   // launch accounting and per-phase event timing
   long long launches = 0;
   int prof_phase = -1;
+  cudaStream_t cap_stream = nullptr;
+  std::map<int, std::pair<cudaGraphExec_t, long long>> graphs;   // (dir, batch) -> graph, kernels
   std::vector<cudaEvent_t> prof_events;
   size_t prof_used = 0;
 };
@@ -146,15 +149,6 @@ qpat_status build_context(qpat_ctx* c, const qpat_medium* med, const double* sen
   QCK(dalloc(c, &o.shym, c->ny * sizeof(C)));
   QCK(dalloc(c, &o.twx, c->nx * sizeof(C)));
   QCK(dalloc(c, &o.twy, c->ny * sizeof(C)));
-  // register-FFT column passes for the lengths that have them (unless
-  // disabled).  Measured on GB300 they win only in FP32 column passes: the
-  // FP64 ones spill, and the row passes' pointwise loads need more resident
-  // warps than the 24-point-per-thread FFT leaves room for.
-  const bool fast_ok = !c->cfg.generic_fft && sizeof(T) == 4;
-  if (fast_ok && fast_length_split(c->ny) > 0) {
-    QCK(dalloc(c, &o.fy_ab, c->ny * sizeof(C)));
-    QCK(dalloc(c, &o.fy_ba, c->ny * sizeof(C)));
-  }
   // FP64 medium staging
   double *dc = nullptr, *drho = nullptr, *dal = nullptr;
   QCK(cudaMalloc(&dc, G * sizeof(double)));
@@ -174,7 +168,9 @@ qpat_status build_context(qpat_ctx* c, const qpat_medium* med, const double* sen
   a.kap = o.kap; a.kp1 = o.kp1; a.kp2 = o.kp2;
   a.shxp = o.shxp; a.shxm = o.shxm; a.shyp = o.shyp; a.shym = o.shym;
   a.twx = o.twx; a.twy = o.twy;
-  a.fx_ab = o.fx_ab; a.fx_ba = o.fx_ba; a.fy_ab = o.fy_ab; a.fy_ba = o.fy_ba;
+  // length-specialised passes where the extent has them (unless disabled)
+  a.fast_rows = !c->cfg.generic_fft && fast_rows_supported(c->nx, (int)sizeof(T));
+  a.fast_cols = !c->cfg.generic_fft && fast_cols_supported(c->ny, (int)sizeof(T));
 
   // sensors: bilinear weights on the node grid (gather form) and the
   // transposed scatter as a per-row, per-point gather (deterministic)
@@ -256,26 +252,28 @@ qpat_status build_context(qpat_ctx* c, const qpat_medium* med, const double* sen
   a.vx = vx; a.vy = vy; a.rx = rx; a.ry = ry; a.pbuf = pbuf; a.spec = spec;
   QCK(dalloc(c, &c->tw_p0, (size_t)B * N * sizeof(T)));
   QCK(dalloc(c, &c->tw_hbar, (size_t)B * N * sizeof(T)));
+  IoPtrs<T>* io = nullptr;
+  QCK(dalloc(c, &io, sizeof(IoPtrs<T>)));
+  a.io = io;
   a.err = c->d_err;
-  prop_init_attributes<T>();
+  prop_init_attributes<T>(c->nx, c->ny, a.fast_rows, a.fast_cols);
   return QPAT_OK;
 }
 
 template <typename T>
-void zero_state(qpat_ctx* c, int batch) {
+void zero_state(qpat_ctx* c, int batch, cudaStream_t s) {
   PropArgs<T>& a = args<T>(c);
   const size_t bytes = (size_t)batch * c->G * sizeof(T);
-  cudaMemsetAsync(a.vx, 0, bytes, c->stream);
-  cudaMemsetAsync(a.vy, 0, bytes, c->stream);
-  cudaMemsetAsync(a.rx, 0, bytes, c->stream);
-  cudaMemsetAsync(a.ry, 0, bytes, c->stream);
+  cudaMemsetAsync(a.vx, 0, bytes, s);
+  cudaMemsetAsync(a.vy, 0, bytes, s);
+  cudaMemsetAsync(a.rx, 0, bytes, s);
+  cudaMemsetAsync(a.ry, 0, bytes, s);
 }
 
-
-// Launch one pass, counting it and, when this phase is being profiled,
-// bracketing it with CUDA events on the context's stream.
+// Launch one pass on stream s, counting it and, when this phase is being
+// profiled (direct launches only), bracketing it with CUDA events.
 template <typename T>
-void pass(qpat_ctx* c, const PropArgs<T>& a, int phase, int batch, bool is_row) {
+void pass(qpat_ctx* c, const PropArgs<T>& a, int phase, int batch, bool is_row, cudaStream_t s, long long& count) {
   const bool prof = (c->prof_phase == phase);
   if (prof) {
     while (c->prof_events.size() < c->prof_used + 2) {
@@ -283,77 +281,71 @@ void pass(qpat_ctx* c, const PropArgs<T>& a, int phase, int batch, bool is_row) 
       if (cudaEventCreate(&e) != cudaSuccess) break;
       c->prof_events.push_back(e);
     }
-    if (c->prof_events.size() >= c->prof_used + 2) cudaEventRecord(c->prof_events[c->prof_used], c->stream);
+    if (c->prof_events.size() >= c->prof_used + 2) cudaEventRecord(c->prof_events[c->prof_used], s);
   }
-  if (is_row) launch_row<T>(a, phase, batch, c->stream);
-  else launch_col<T>(a, phase, batch, c->stream);
-  ++c->launches;
+  if (is_row) launch_row<T>(a, phase, batch, s);
+  else launch_col<T>(a, phase, batch, s);
+  ++count;
   if (prof && c->prof_events.size() >= c->prof_used + 2) {
-    cudaEventRecord(c->prof_events[c->prof_used + 1], c->stream);
+    cudaEventRecord(c->prof_events[c->prof_used + 1], s);
     c->prof_used += 2;
   }
 }
 
-// H_a: launch sequence of the forward loop n = -1 .. Nt - 2 (Section 3.2.3).
+// H_a: launch sequence of the forward loop n = -1 .. Nt - 2 (Section 3.2.3),
+// enqueued on stream s; the caller's buffers are read through a.io.
 template <typename T>
-qpat_status run_forward(qpat_ctx* c, int batch, const T* p0, T* data) {
+long long seq_forward(qpat_ctx* c, int batch, cudaStream_t s) {
   PropArgs<T> a = args<T>(c);
-  cudaStream_t s = c->stream;
-  a.p0 = p0;
-  a.data = data;
-  zero_state<T>(c, batch);
+  long long cnt = 0;
+  zero_state<T>(c, batch, s);
   const int nt = c->nt;
   if (!c->cfg.lossless) {
     a.n = 0;
     a.flags = kSkipInput | kSource;          // step n = -1 from zero fields
-    pass<T>(c, a, F_R3, batch, true);
+    pass<T>(c, a, F_R3, batch, true, s, cnt);
     a.flags = 0;
-    pass<T>(c, a, F_C3, batch, false);
+    pass<T>(c, a, F_C3, batch, false, s, cnt);
     for (int n = 0; n <= nt - 2; ++n) {
       a.n = n;
       a.flags = 0;
-      pass<T>(c, a, F_R1, batch, true);      // p_n
-      pass<T>(c, a, F_C1, batch, false);      // sample n, d/dr^+ p_n
-      pass<T>(c, a, F_R2, batch, true);      // v^(n+1/2)
-      pass<T>(c, a, F_C2, batch, false);      // d/dr^- v
+      pass<T>(c, a, F_R1, batch, true, s, cnt);    // p_n
+      pass<T>(c, a, F_C1, batch, false, s, cnt);   // sample n, d/dr^+ p_n
+      pass<T>(c, a, F_R2, batch, true, s, cnt);    // v^(n+1/2)
+      pass<T>(c, a, F_C2, batch, false, s, cnt);   // d/dr^- v
       a.flags = (n == 0) ? kSource : 0;
-      pass<T>(c, a, F_R3, batch, true);      // rho^(n+1)
+      pass<T>(c, a, F_R3, batch, true, s, cnt);    // rho^(n+1)
       a.flags = 0;
-      pass<T>(c, a, F_C3, batch, false);      // Y_dis, Y_abs
+      pass<T>(c, a, F_C3, batch, false, s, cnt);   // Y_dis, Y_abs
     }
     a.n = nt - 1;
     a.flags = kSkipOutput;
-    pass<T>(c, a, F_R1, batch, true);        // p_(Nt-1)
-    launch_gather<T>(a, batch, s);
-    ++c->launches;
+    pass<T>(c, a, F_R1, batch, true, s, cnt);      // p_(Nt-1)
   } else {
     a.n = 0;
     a.flags = kSkipInput | kSource;
-    pass<T>(c, a, F_R3L, batch, true);       // p_0
+    pass<T>(c, a, F_R3L, batch, true, s, cnt);     // p_0
     for (int n = 0; n <= nt - 2; ++n) {
       a.n = n;
       a.flags = 0;
-      pass<T>(c, a, F_C1, batch, false);
-      pass<T>(c, a, F_R2, batch, true);
-      pass<T>(c, a, F_C2, batch, false);
+      pass<T>(c, a, F_C1, batch, false, s, cnt);
+      pass<T>(c, a, F_R2, batch, true, s, cnt);
+      pass<T>(c, a, F_C2, batch, false, s, cnt);
       a.flags = (n == 0) ? kSource : 0;
-      pass<T>(c, a, F_R3L, batch, true);     // p_(n+1)
+      pass<T>(c, a, F_R3L, batch, true, s, cnt);   // p_(n+1)
     }
     a.n = nt - 1;
-    launch_gather<T>(a, batch, s);
-    ++c->launches;
   }
-  QCK(cudaGetLastError());
-  return QPAT_OK;
+  launch_gather<T>(a, batch, s);
+  return cnt + 1;
 }
 
 // H_a^*: transposed steps in reverse, n = Nt - 2 .. -1 (Section 3.2.4).
 template <typename T>
-qpat_status run_adjoint(qpat_ctx* c, int batch, const T* w, T* p0adj) {
+long long seq_adjoint(qpat_ctx* c, int batch, cudaStream_t s) {
   PropArgs<T> a = args<T>(c);
-  a.w = w;
-  a.p0adj = p0adj;
-  zero_state<T>(c, batch);
+  long long cnt = 0;
+  zero_state<T>(c, batch, s);
   const int nt = c->nt;
   for (int n = nt - 2; n >= -1; --n) {
     a.n = n + 1;                                   // the sample p_(n+1) produced
@@ -362,23 +354,60 @@ qpat_status run_adjoint(qpat_ctx* c, int batch, const T* w, T* p0adj) {
     const int last = (n == -1) ? kSkipOutput : 0;
     if (!c->cfg.lossless) {
       a.flags = first;
-      pass<T>(c, a, A_R1, batch, true);
+      pass<T>(c, a, A_R1, batch, true, s, cnt);
       a.flags = 0;
-      pass<T>(c, a, A_C2, batch, false);
+      pass<T>(c, a, A_C2, batch, false, s, cnt);
       a.flags = acc | last;
-      pass<T>(c, a, A_R3, batch, true);
+      pass<T>(c, a, A_R3, batch, true, s, cnt);
     } else {
       a.flags = first | acc | last;
-      pass<T>(c, a, A_R1L, batch, true);
+      pass<T>(c, a, A_R1L, batch, true, s, cnt);
     }
     if (n > -1) {
       a.flags = 0;
-      pass<T>(c, a, A_C4, batch, false);
-      pass<T>(c, a, A_R5, batch, true);
-      pass<T>(c, a, A_C6, batch, false);
+      pass<T>(c, a, A_C4, batch, false, s, cnt);
+      pass<T>(c, a, A_R5, batch, true, s, cnt);
+      pass<T>(c, a, A_C6, batch, false, s, cnt);
     }
   }
+  return cnt;
+}
+
+// Run H_a (dir 0) or H_a^* (dir 1) on the caller's buffers.  The launch
+// sequence is captured once per (direction, batch) into a CUDA graph on a
+// private stream and replayed on the context's stream; only a one-thread
+// kernel that writes the buffer pointers into the device struct a.io
+// precedes each replay.  With graphs disabled, or while a pass is being
+// profiled, the sequence is launched directly.
+template <typename T>
+qpat_status run_prop(qpat_ctx* c, int dir, int batch, const T* p0, T* data, const T* w, T* p0adj) {
+  PropArgs<T>& a = args<T>(c);
+  IoPtrs<T>* io = const_cast<IoPtrs<T>*>(a.io);
+  launch_set_io<T>(io, p0, data, w, p0adj, c->stream);
   QCK(cudaGetLastError());
+  const bool direct = c->cfg.no_graphs || c->prof_phase >= 0;
+  if (direct) {
+    c->launches += dir == 0 ? seq_forward<T>(c, batch, c->stream) : seq_adjoint<T>(c, batch, c->stream);
+    QCK(cudaGetLastError());
+    return QPAT_OK;
+  }
+  const int key = dir * 1000000 + batch;
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    if (!c->cap_stream) QCK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    QCK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const long long n = dir == 0 ? seq_forward<T>(c, batch, c->cap_stream) : seq_adjoint<T>(c, batch, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiation");
+    it = c->graphs.emplace(key, std::make_pair(ex, n)).first;
+  }
+  QCK(cudaGraphLaunch(it->second.first, c->stream));
+  c->launches += it->second.second;
   return QPAT_OK;
 }
 
@@ -516,6 +545,8 @@ qpat_status qpat_create(const qpat_config* cfg, const qpat_medium* med, const do
 qpat_status qpat_destroy(qpat_ctx* c) {
   if (!c) return QPAT_OK;
   cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void* p : c->dev_allocs) cudaFree(p);
   for (void* p : c->host_allocs) cudaFreeHost(p);
   for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
@@ -558,16 +589,17 @@ qpat_status qpat_acoustic_forward(qpat_ctx* c, int batch, const void* p0, void* 
   qpat_status st = check_batch(c, batch);
   if (st != QPAT_OK) return st;
   if (!p0 || !data) return fail(c, QPAT_EINVAL, "null buffer");
-  return c->prec == QPAT_FP32 ? run_forward<float>(c, batch, (const float*)p0, (float*)data)
-                              : run_forward<double>(c, batch, (const double*)p0, (double*)data);
+  return c->prec == QPAT_FP32 ? run_prop<float>(c, 0, batch, (const float*)p0, (float*)data, nullptr, nullptr)
+                              : run_prop<double>(c, 0, batch, (const double*)p0, (double*)data, nullptr, nullptr);
 }
 
 qpat_status qpat_acoustic_adjoint(qpat_ctx* c, int batch, const void* data, void* p0_adj) {
   qpat_status st = check_batch(c, batch);
   if (st != QPAT_OK) return st;
   if (!p0_adj || !data) return fail(c, QPAT_EINVAL, "null buffer");
-  return c->prec == QPAT_FP32 ? run_adjoint<float>(c, batch, (const float*)data, (float*)p0_adj)
-                              : run_adjoint<double>(c, batch, (const double*)data, (double*)p0_adj);
+  return c->prec == QPAT_FP32
+             ? run_prop<float>(c, 1, batch, nullptr, nullptr, (const float*)data, (float*)p0_adj)
+             : run_prop<double>(c, 1, batch, nullptr, nullptr, (const double*)data, (double*)p0_adj);
 }
 
 qpat_status qpat_da_solve(qpat_ctx* c, int batch, const double* mu, unsigned illum, double* phi) {

@@ -1,47 +1,68 @@
-// Length-specialised propagation passes on the register-resident FFT.
+// Length-specialised propagation passes on compile-time Stockham FFTs.
 //
-// Row pass (one thread group per pair of grid rows j0, j0+1):
-//   load the incoming half spectra, Hermitian-extend them and pack the two
-//   rows into one complex sequence (stride-B layout) -> inverse x-FFT via
-//   conj(FFT(conj .)) -> every thread now owns grid points l + A k2 of both
-//   rows in registers -> pointwise update (row_point) -> forward x-FFT of the
-//   packed outgoing fields (its stride-A input layout is exactly what the
-//   thread holds) -> split into two half spectra through shared memory.
+// Row pass (one thread group per pair of grid rows j0, j0 + 1):
+//   load the incoming half spectra straight into registers, Hermitian-extend
+//   them and pack the two rows into one complex sequence -> inverse x-FFT via
+//   conj(FFT(conj .)) with the radices of the forward plan reversed -> each
+//   thread ends holding grid points j + r L/Q1 of both rows -> pointwise
+//   update (row_point) in registers -> forward x-FFT, whose first stage reads
+//   exactly those registers -> split into two half spectra through shared
+//   memory -> store.
 // Column pass (one thread group per half-spectrum column, CBW adjacent
-//   columns per CTA so that global accesses are contiguous):
-//   load a column (stride-B layout) -> forward y-FFT -> spectral symbol
-//   (col_point) on the registers -> inverse y-FFT (stride-A input layout) ->
-//   store in the original layout.
-// Each transform touches shared memory once (one exchange), against one
-// round trip per radix stage in the generic kernels.
+//   columns per CTA, column index fastest so that global accesses of a warp
+//   are contiguous):
+//   load rows j + r L/Q1 of the column -> forward y-FFT -> spectral symbol
+//   (col_point) on the registers -> inverse y-FFT (reversed radices), which
+//   ends in the load layout -> store.
 #pragma once
 #include "fft_reg.cuh"
 #include "pass_ops.cuh"
 
 namespace qpat {
 
-template <int A, int B>
-struct FastGeom {
-  static constexpr int L = A * B;
-  static constexpr int TPT = A > B ? A : B;
-  static constexpr int XAB = XLayout<A, B>::XS;
-  static constexpr int XBA = XLayout<B, A>::XS;
-  static constexpr int XS = XAB > XBA ? XAB : XBA;        // per-slot exchange size (>= L)
-  static constexpr int RP = (128 / TPT) > 0 ? (128 / TPT) : 1;                       // row pairs per CTA
-  static constexpr int CBW = (128 / TPT) >= 8 ? 8 : 4;                               // columns per CTA
+// Forward radix plans (Q3 = 1: two stages).  The inverse uses them reversed.
+template <int L> struct SPlan { static constexpr int Q1 = 0, Q2 = 0, Q3 = 0; };
+template <> struct SPlan<24> { static constexpr int Q1 = 4, Q2 = 6, Q3 = 1; };
+template <> struct SPlan<40> { static constexpr int Q1 = 5, Q2 = 8, Q3 = 1; };
+template <> struct SPlan<48> { static constexpr int Q1 = 6, Q2 = 8, Q3 = 1; };
+template <> struct SPlan<54> { static constexpr int Q1 = 6, Q2 = 9, Q3 = 1; };
+template <> struct SPlan<56> { static constexpr int Q1 = 7, Q2 = 8, Q3 = 1; };
+template <> struct SPlan<168> { static constexpr int Q1 = 12, Q2 = 14, Q3 = 1; };
+template <> struct SPlan<288> { static constexpr int Q1 = 8, Q2 = 6, Q3 = 6; };
+template <> struct SPlan<432> { static constexpr int Q1 = 6, Q2 = 8, Q3 = 9; };
+template <> struct SPlan<576> { static constexpr int Q1 = 8, Q2 = 8, Q3 = 9; };
+template <> struct SPlan<1024> { static constexpr int Q1 = 8, Q2 = 8, Q3 = 16; };
+template <> struct SPlan<1080> { static constexpr int Q1 = 10, Q2 = 12, Q3 = 9; };
+
+template <int L>
+struct SGeom {
+  static constexpr int Q1 = SPlan<L>::Q1, Q2 = SPlan<L>::Q2, Q3 = SPlan<L>::Q3;
+  static constexpr bool three = Q3 > 1;
+  static constexpr int QL = three ? Q3 : Q2;                    // last forward radix
+  // inverse plan: reversed radices
+  static constexpr int P1 = QL, P2 = three ? Q2 : Q1, P3 = three ? Q1 : 1;
+  static constexpr int minQ = three ? (Q1 < Q2 ? (Q1 < Q3 ? Q1 : Q3) : (Q2 < Q3 ? Q2 : Q3)) : (Q1 < Q2 ? Q1 : Q2);
+  static constexpr int TPT = L / minQ;
+  static constexpr int SL = spad_size(L);
+  static constexpr int RP = (192 / TPT) > 0 ? (192 / TPT) : 1;   // row pairs per CTA
+  static constexpr int CBW = TPT <= 32 ? 8 : 4;                  // columns per CTA
 };
 
-template <typename T, int A, int B, int KIN, int KOUT>
-__global__ void __launch_bounds__(FastGeom<A, B>::RP * FastGeom<A, B>::TPT)
-row_fast(const PropArgs<T> a, const int ph) {
+template <typename T, int L, int PH>
+__global__ void __launch_bounds__(SGeom<L>::RP * SGeom<L>::TPT)
+row_fast(const PropArgs<T> a) {
+  constexpr int ph = PH, KIN = row_kin(PH), KOUT = row_kout(PH);
   typedef typename V2<T>::t C;
-  typedef FastGeom<A, B> G;
-  constexpr int L = G::L, TPT = G::TPT, XS = G::XS, RP = G::RP;
+  typedef SGeom<L> G;
+  constexpr int TPT = G::TPT, SL = G::SL, RP = G::RP, NSX = (KIN > KOUT ? KIN : KOUT);
+  constexpr int Q1 = G::Q1, QL = G::QL, P1 = G::P1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = threadIdx.x / TPT;
-  const int l = threadIdx.x - m * TPT;
-  C* ex = reinterpret_cast<C*>(smem_raw) + m * 2 * XS;
-  T* sc = reinterpret_cast<T*>(reinterpret_cast<C*>(smem_raw) + RP * 2 * XS) + m * 2 * L;
+  const int j = threadIdx.x - m * TPT;
+  C* tws = reinterpret_cast<C*>(smem_raw);                       // W_L^m table
+  C* bufA = tws + L + m * 2 * NSX * SL;
+  C* bufB = bufA + NSX * SL;
+  T* sc = reinterpret_cast<T*>(tws + L + RP * 2 * NSX * SL) + m * 2 * L;
   const int b = blockIdx.y;
   const int jp = blockIdx.x * RP + m;
   const bool valid = jp < (a.ny >> 1);
@@ -50,18 +71,29 @@ row_fast(const PropArgs<T> a, const int ph) {
   const long long slot = (long long)a.ny * a.pitch;
   const bool skip_in = (a.flags & kSkipInput) != 0;
 
-  // 1. inverse x-transform of the incoming half spectra
-  C y[KIN][B];
+  // twiddle table to shared memory, and every pointwise operand of this
+  // thread's grid points into registers, before any transform: their
+  // latencies overlap the loads of the spectra and the first FFT stage
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
+  RowIn<T> st[2][Q1];
+#pragma unroll
+  for (int r = 0; r < Q1; ++r)
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+      st[rr][r] = (j < L / Q1 && valid) ? row_load<T>(a, ph, b, j + r * (L / Q1), j0 + rr) : RowIn<T>{};
+
+  // 1. inverse x-transform of the incoming half spectra (reversed plan)
+  C y[KIN][Q1];
   if (!skip_in) {
-    C v[KIN][A];
-    if (l < B) {
+    C v[KIN][P1];
+    if (j < L / P1) {
 #pragma unroll
       for (int s = 0; s < KIN; ++s) {
         const C* r0 = spec + s * slot + (long long)j0 * a.pitch;
         const C* r1 = r0 + a.pitch;
 #pragma unroll
-        for (int n1 = 0; n1 < A; ++n1) {
-          const int n = B * n1 + l;
+        for (int r = 0; r < P1; ++r) {
+          const int n = j + r * (L / P1);
           C P, Q;
           if (2 * n <= L) {
             P = r0[n];
@@ -71,61 +103,59 @@ row_fast(const PropArgs<T> a, const int ph) {
             P = cconj(r0[L - n]);
             Q = cconj(r1[L - n]);
           }
-          v[s][n1] = cmake<C>(P.x - Q.y, -(P.y + Q.x));   // conj(P + i Q)
+          v[s][r] = cmake<C>(P.x - Q.y, -(P.y + Q.x));   // conj(P + i Q)
         }
       }
     }
-    fft_group<A, B, KIN>(v, y, ex, XS, a.fx_ab, l);
+    fft_stockham<L, G::P1, G::P2, G::P3, KIN>(v, y, bufA, bufB, SL, j, tws);
   } else {
 #pragma unroll
     for (int s = 0; s < KIN; ++s)
 #pragma unroll
-      for (int k = 0; k < B; ++k) y[s][k] = cmake<C>((T)0, (T)0);
+      for (int r = 0; r < Q1; ++r) y[s][r] = cmake<C>((T)0, (T)0);
   }
 
   // adjoint sensor source M^T w_n on the two rows (A_R1, A_R1L)
   if (KIN == 1) {
-    for (int i = l; i < 2 * L; i += TPT) sc[i] = (T)0;
+    for (int i = j; i < 2 * L; i += TPT) sc[i] = (T)0;
     __syncthreads();
-    if (valid) sensor_scatter_rows<T>(a, b, j0, sc, l, TPT);
+    if (valid) sensor_scatter_rows<T>(a, b, j0, sc, j, TPT);
     __syncthreads();
   }
 
-  // 2. pointwise update on the grid points this thread owns: i = l + A k2
-  C o[KOUT][B];
+  // 2. pointwise update on grid points i = j + r L/Q1 of both rows;
+  //    y = FFT(conj Z) = conj(z): row j0 is Re, row j0+1 is -Im
+  C o[KOUT][Q1];
   bool bad = false;
 #pragma unroll
-  for (int k2 = 0; k2 < B; ++k2) {
-    T r0v[2] = {(T)0, (T)0}, r1v[2] = {(T)0, (T)0};
-    if (l < A && valid) {
-      const int i = l + A * k2;
+  for (int r = 0; r < Q1; ++r) {
+    T u0[2] = {(T)0, (T)0}, u1[2] = {(T)0, (T)0};
+    if (j < L / Q1 && valid) {
+      const int i = j + r * (L / Q1);
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
-        const T in0 = rr ? -y[0][k2].y : y[0][k2].x;
-        const T in1 = (KIN > 1) ? (rr ? -y[KIN - 1][k2].y : y[KIN - 1][k2].x) : (T)0;
+        const T in0 = rr ? -y[0][r].y : y[0][r].x;
+        const T in1 = (KIN > 1) ? (rr ? -y[KIN - 1][r].y : y[KIN - 1][r].x) : (T)0;
         const T scv = (KIN == 1) ? sc[rr * L + i] : (T)0;
-        T out0, out1;
-        row_point<T>(a, ph, b, i, j0 + rr, in0, in1, scv, out0, out1, bad);
-        r0v[rr] = out0;
-        r1v[rr] = out1;
+        row_point<T>(a, ph, b, i, j0 + rr, in0, in1, scv, st[rr][r], u0[rr], u1[rr], bad);
       }
     }
-    o[0][k2] = cmake<C>(r0v[0], r0v[1]);
-    if (KOUT > 1) o[KOUT - 1][k2] = cmake<C>(r1v[0], r1v[1]);
+    o[0][r] = cmake<C>(u0[0], u0[1]);
+    if (KOUT > 1) o[KOUT - 1][r] = cmake<C>(u1[0], u1[1]);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.err, 1);
   if (a.flags & kSkipOutput) return;
 
-  // 3. forward x-transform of the packed outgoing rows (stride-A layout)
-  C X[KOUT][A];
-  fft_group<B, A, KOUT>(o, X, ex, XS, a.fx_ba, l);
-  // thread l < B holds Z[l + B k] for k < A; split Z into the two rows'
-  // half spectra A(k) = (Z(k) + conj Z(-k))/2, B(k) = -i (Z(k) - conj Z(-k))/2
-  if (l < B) {
+  // 3. forward x-transform of the packed outgoing rows
+  C X[KOUT][QL];
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KOUT>(o, X, bufA, bufB, SL, j, tws);
+  // thread j < L/QL holds Z[j + r L/QL]; split Z into the two rows' half
+  // spectra A(k) = (Z(k) + conj Z(-k))/2, B(k) = -i (Z(k) - conj Z(-k))/2
+  if (j < L / QL) {
 #pragma unroll
     for (int s = 0; s < KOUT; ++s)
 #pragma unroll
-      for (int k = 0; k < A; ++k) ex[s * XS + l + B * k] = X[s][k];
+      for (int r = 0; r < QL; ++r) bufA[s * SL + spad(j + r * (L / QL))] = X[s][r];
   }
   __syncthreads();
   if (valid) {
@@ -133,9 +163,9 @@ row_fast(const PropArgs<T> a, const int ph) {
     for (int s = 0; s < KOUT; ++s) {
       C* w0 = spec + s * slot + (long long)j0 * a.pitch;
       C* w1 = w0 + a.pitch;
-      for (int k = l; 2 * k <= L; k += TPT) {
-        const C Z = ex[s * XS + k];
-        const C Zm = cconj(ex[s * XS + (k == 0 ? 0 : L - k)]);
+      for (int k = j; 2 * k <= L; k += TPT) {
+        const C Z = bufA[s * SL + spad(k)];
+        const C Zm = cconj(bufA[s * SL + spad(k == 0 ? 0 : L - k)]);
         w0[k] = cscale(cadd(Z, Zm), (T)0.5);
         w1[k] = cscale(cmul_mi(csub(Z, Zm)), (T)0.5);
       }
@@ -143,16 +173,28 @@ row_fast(const PropArgs<T> a, const int ph) {
   }
 }
 
-template <typename T, int A, int B, int KIN, int KOUT>
-__global__ void __launch_bounds__(FastGeom<A, B>::CBW * FastGeom<A, B>::TPT)
-col_fast(const PropArgs<T> a, const int ph) {
+// Per-column shared-memory stride: congruent to 16/CBW complex values mod 16
+// so that the CBW columns of a half warp fall on distinct banks.
+template <int L, int NSX, int CBW>
+__host__ __device__ constexpr int col_stride() {
+  return 2 * NSX * SGeom<L>::SL + ((16 / CBW - (2 * NSX * SGeom<L>::SL) % 16) + 16) % 16;
+}
+
+template <typename T, int L, int PH>
+__global__ void __launch_bounds__(SGeom<L>::CBW * SGeom<L>::TPT)
+col_fast(const PropArgs<T> a) {
+  constexpr int ph = PH, KIN = col_kin(PH), KOUT = col_kout(PH);
   typedef typename V2<T>::t C;
-  typedef FastGeom<A, B> G;
-  constexpr int XS = G::XS, CBW = G::CBW;
+  typedef SGeom<L> G;
+  constexpr int SL = G::SL, CBW = G::CBW, NSX = (KIN > KOUT ? KIN : KOUT);
+  constexpr int Q1 = G::Q1, QL = G::QL;
+  constexpr int CS = col_stride<L, NSX, CBW>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % CBW;
-  const int l = threadIdx.x / CBW;
-  C* ex = reinterpret_cast<C*>(smem_raw) + c * 2 * XS;
+  const int j = threadIdx.x / CBW;
+  C* tws = reinterpret_cast<C*>(smem_raw);                       // W_L^m table
+  C* bufA = tws + L + c * CS;
+  C* bufB = bufA + NSX * SL;
   const int b = blockIdx.y;
   const int kx = blockIdx.x * CBW + c;
   const bool valid = kx < a.nxh;
@@ -162,86 +204,123 @@ col_fast(const PropArgs<T> a, const int ph) {
 
   if (ph == F_C1) sensor_gather<T>(a, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 
-  C v[KIN][A];
-  if (l < B) {
+  C v[KIN][Q1];
+  if (j < L / Q1) {
 #pragma unroll
     for (int s = 0; s < KIN; ++s)
 #pragma unroll
-      for (int n1 = 0; n1 < A; ++n1) v[s][n1] = spec[s * slot + (long long)(B * n1 + l) * a.pitch + kxs];
+      for (int r = 0; r < Q1; ++r) v[s][r] = spec[s * slot + (long long)(j + r * (L / Q1)) * a.pitch + kxs];
   }
-  C X[KIN][B];
-  fft_group<A, B, KIN>(v, X, ex, XS, a.fy_ab, l);
-  // thread l < A holds X[ky = l + A k2]
-  C o[KOUT][B];
+  // twiddles to shared memory and the symbol operands of this thread's
+  // points into registers before the transforms
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twy[t];
+  ColIn<T, C> cst[QL];
 #pragma unroll
-  for (int k2 = 0; k2 < B; ++k2) {
+  for (int r = 0; r < QL; ++r)
+    cst[r] = (j < L / QL && valid) ? col_load<T, C>(a, ph, kx, j + r * (L / QL)) : ColIn<T, C>{};
+  const C sx = col_sx<T, C>(a, ph, kxs);
+  C X[KIN][QL];
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KIN>(v, X, bufA, bufB, SL, j, tws);
+  // thread j < L/QL holds X[ky = j + r L/QL]
+  C o[KOUT][QL];
+#pragma unroll
+  for (int r = 0; r < QL; ++r) {
     C o0 = cmake<C>((T)0, (T)0), o1 = o0;
-    if (l < A && valid) col_point<T, C>(a, ph, kx, l + A * k2, X[0][k2], X[KIN - 1][k2], o0, o1);
-    o[0][k2] = cconj(o0);
-    if (KOUT > 1) o[KOUT - 1][k2] = cconj(o1);
+    if (j < L / QL && valid) col_apply<T, C>(ph, cst[r], sx, X[0][r], X[KIN - 1][r], o0, o1);
+    o[0][r] = cconj(o0);
+    if (KOUT > 1) o[KOUT - 1][r] = cconj(o1);
   }
-  C Y[KOUT][A];
-  fft_group<B, A, KOUT>(o, Y, ex, XS, a.fy_ba, l);
-  // thread l < B holds the inverse at rows l + B k
-  if (l < B && valid) {
+  C Y[KOUT][Q1];
+  fft_stockham<L, G::P1, G::P2, G::P3, KOUT>(o, Y, bufA, bufB, SL, j, tws);
+  if (j < L / Q1 && valid) {
 #pragma unroll
     for (int s = 0; s < KOUT; ++s)
 #pragma unroll
-      for (int k = 0; k < A; ++k) spec[s * slot + (long long)(l + B * k) * a.pitch + kx] = cconj(Y[s][k]);
+      for (int r = 0; r < Q1; ++r)
+        spec[s * slot + (long long)(j + r * (L / Q1)) * a.pitch + kx] = cconj(Y[s][r]);
   }
 }
 
-template <typename T, int A, int B, int KIN, int KOUT>
-void run_row_fast(const PropArgs<T>& a, int ph, int batch, cudaStream_t s) {
-  typedef FastGeom<A, B> G;
+template <typename T, int L, int PH>
+constexpr size_t row_fast_smem() {
   typedef typename V2<T>::t C;
-  const size_t sm = G::RP * 2 * G::XS * sizeof(C) + (KIN == 1 ? G::RP * 2 * G::L * sizeof(T) : 0);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(row_fast<T, A, B, KIN, KOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
+  constexpr int KIN = row_kin(PH), KOUT = row_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT);
+  return (L + SGeom<L>::RP * 2 * NSX * SGeom<L>::SL) * sizeof(C) + (KIN == 1 ? SGeom<L>::RP * 2 * L * sizeof(T) : 0);
+}
+template <typename T, int L, int PH>
+constexpr size_t col_fast_smem() {
+  typedef typename V2<T>::t C;
+  constexpr int KIN = col_kin(PH), KOUT = col_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT);
+  return ((size_t)L + (size_t)SGeom<L>::CBW * col_stride<L, NSX, SGeom<L>::CBW>()) * sizeof(C);
+}
+
+template <typename T, int L, int PH>
+void set_row_fast_attr() {
+  cudaFuncSetAttribute(row_fast<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fast_smem<T, L, PH>());
+}
+template <typename T, int L, int PH>
+void set_col_fast_attr() {
+  cudaFuncSetAttribute(col_fast<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_fast_smem<T, L, PH>());
+}
+
+// Dynamic shared-memory limits of all pass kernels of length L; called at
+// context creation, outside any stream capture.
+template <typename T, int L>
+void prepare_fast_len() {
+  set_row_fast_attr<T, L, F_R1>(); set_row_fast_attr<T, L, F_R2>(); set_row_fast_attr<T, L, F_R3>();
+  set_row_fast_attr<T, L, F_R3L>(); set_row_fast_attr<T, L, A_R1>(); set_row_fast_attr<T, L, A_R1L>();
+  set_row_fast_attr<T, L, A_R3>(); set_row_fast_attr<T, L, A_R5>();
+  set_col_fast_attr<T, L, F_C1>(); set_col_fast_attr<T, L, F_C2>(); set_col_fast_attr<T, L, F_C3>();
+  set_col_fast_attr<T, L, A_C2>(); set_col_fast_attr<T, L, A_C4>(); set_col_fast_attr<T, L, A_C6>();
+}
+
+template <typename T, int L, int PH>
+void run_row_fast(const PropArgs<T>& a, int batch, cudaStream_t s) {
+  typedef SGeom<L> G;
   dim3 grid((a.ny / 2 + G::RP - 1) / G::RP, batch);
-  row_fast<T, A, B, KIN, KOUT><<<grid, G::RP * G::TPT, sm, s>>>(a, ph);
+  row_fast<T, L, PH><<<grid, G::RP * G::TPT, row_fast_smem<T, L, PH>(), s>>>(a);
 }
 
-template <typename T, int A, int B, int KIN, int KOUT>
-void run_col_fast(const PropArgs<T>& a, int ph, int batch, cudaStream_t s) {
-  typedef FastGeom<A, B> G;
-  typedef typename V2<T>::t C;
-  const size_t sm = G::CBW * 2 * G::XS * sizeof(C);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(col_fast<T, A, B, KIN, KOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
+template <typename T, int L, int PH>
+void run_col_fast(const PropArgs<T>& a, int batch, cudaStream_t s) {
+  typedef SGeom<L> G;
   dim3 grid((a.nxh + G::CBW - 1) / G::CBW, batch);
-  col_fast<T, A, B, KIN, KOUT><<<grid, G::CBW * G::TPT, sm, s>>>(a, ph);
+  col_fast<T, L, PH><<<grid, G::CBW * G::TPT, col_fast_smem<T, L, PH>(), s>>>(a);
 }
 
 // Entry points of one specialised length L (one translation unit each).
 template <typename T, int L>
 void launch_row_fast_len(const PropArgs<T>& a, int ph, int batch, cudaStream_t s) {
-  constexpr int A = fast_split_a(L), B = L / (A > 0 ? A : 1);
-  const int kin = row_kin(ph), kout = row_kout(ph);
-  if (kin == 2 && kout == 2) run_row_fast<T, A, B, 2, 2>(a, ph, batch, s);
-  else if (kin == 2) run_row_fast<T, A, B, 2, 1>(a, ph, batch, s);
-  else run_row_fast<T, A, B, 1, 2>(a, ph, batch, s);
+  switch (ph) {
+    case F_R1: run_row_fast<T, L, F_R1>(a, batch, s); break;
+    case F_R2: run_row_fast<T, L, F_R2>(a, batch, s); break;
+    case F_R3: run_row_fast<T, L, F_R3>(a, batch, s); break;
+    case F_R3L: run_row_fast<T, L, F_R3L>(a, batch, s); break;
+    case A_R1: run_row_fast<T, L, A_R1>(a, batch, s); break;
+    case A_R1L: run_row_fast<T, L, A_R1L>(a, batch, s); break;
+    case A_R3: run_row_fast<T, L, A_R3>(a, batch, s); break;
+    case A_R5: run_row_fast<T, L, A_R5>(a, batch, s); break;
+    default: break;
+  }
 }
 
 template <typename T, int L>
 void launch_col_fast_len(const PropArgs<T>& a, int ph, int batch, cudaStream_t s) {
-  constexpr int A = fast_split_a(L), B = L / (A > 0 ? A : 1);
-  const int kin = col_kin(ph), kout = col_kout(ph);
-  if (kin == 2 && kout == 2) run_col_fast<T, A, B, 2, 2>(a, ph, batch, s);
-  else if (kin == 1) run_col_fast<T, A, B, 1, 2>(a, ph, batch, s);
-  else run_col_fast<T, A, B, 2, 1>(a, ph, batch, s);
+  switch (ph) {
+    case F_C1: run_col_fast<T, L, F_C1>(a, batch, s); break;
+    case F_C2: run_col_fast<T, L, F_C2>(a, batch, s); break;
+    case F_C3: run_col_fast<T, L, F_C3>(a, batch, s); break;
+    case A_C2: run_col_fast<T, L, A_C2>(a, batch, s); break;
+    case A_C4: run_col_fast<T, L, A_C4>(a, batch, s); break;
+    case A_C6: run_col_fast<T, L, A_C6>(a, batch, s); break;
+    default: break;
+  }
 }
 
+// FP32 only: in FP64 the generic passes are faster on GB300.
 #define QPAT_FAST_LENGTH(L)                                                                              \
+  template void prepare_fast_len<float, L>();                                                            \
   template void launch_row_fast_len<float, L>(const PropArgs<float>&, int, int, cudaStream_t);         \
-  template void launch_row_fast_len<double, L>(const PropArgs<double>&, int, int, cudaStream_t);       \
-  template void launch_col_fast_len<float, L>(const PropArgs<float>&, int, int, cudaStream_t);         \
-  template void launch_col_fast_len<double, L>(const PropArgs<double>&, int, int, cudaStream_t);
+  template void launch_col_fast_len<float, L>(const PropArgs<float>&, int, int, cudaStream_t);
 
 }  // namespace qpat

@@ -1,4 +1,4 @@
-// Register-FFT propagation passes for the small FFT extents 24, 40, 48, 54, 56
+// Compile-time Stockham propagation passes for the small FFT extents 24, 40, 48, 54, 56
 // (see fast_kernels.cuh).
 #include "fast_kernels.cuh"
 namespace qpat {

@@ -1,18 +1,17 @@
-// Register-resident FFTs of compile-time length (sm_103a).
+// Compile-time Stockham FFTs with register end points (sm_103a).
 //
-// A length-L transform with L = A * B is split Cooley-Tukey style over a
-// group of max(A, B) threads:
-//
-//   X[k1 + A k2] = sum_n2 W_L^(n2 k1) W_B^(n2 k2) sum_n1 x[B n1 + n2] W_A^(n1 k1)
-//
-// Thread l < B holds x[B n1 + l] (n1 < A) in registers and does the A-point
-// DFT there; after the twiddle W_L^(l k1) the values are exchanged once
-// through shared memory, and thread l' < A does the B-point DFT over n2 and
-// ends holding X[l' + A k2] (k2 < B).  The A- and B-point DFTs themselves
-// are fully unrolled mixed-radix (2, 3, 4, 5, 7, 8) Cooley-Tukey recursions
-// whose twiddles are compile-time constants, computed by constexpr Taylor
-// series in double precision.  The inter-thread twiddles W_L^(l k1) come from
-// a device table built in FP64 (see tables.cu).
+// A length-L transform with L = Q1 * Q2 [* Q3] runs on a group of
+// TPT = L / min(Q) threads.  In stage s of radix R (stride Ns = product of the
+// earlier radices) thread j < L/R holds the R values x[j + r L/R] in
+// registers, multiplies them by W_L^{(j mod Ns) r L/(Ns R)}, performs an
+// R-point DFT, and the results go to position (j/Ns) Ns R + (j mod Ns) + r Ns
+// (Stockham self-sorting order).  Between stages the values pass through
+// shared memory; the first stage starts from registers (loaded straight from
+// global memory) and the last stage leaves them in registers, thread j
+// holding X[j + r L/Q_last].  The R-point DFTs are fully unrolled mixed-radix
+// Cooley-Tukey recursions whose twiddles are compile-time constants
+// (constexpr Taylor series in double precision); the stage twiddles come
+// from a W_L^m table built in FP64 on the device.
 #pragma once
 #include <type_traits>
 
@@ -115,47 +114,81 @@ __device__ __forceinline__ void dft(C (&a)[N]) {
   }
 }
 
-// Shared-memory strides of the exchange: an odd row stride, and a per-
-// sequence size congruent to 2 mod 8 complex values, keep the 8-byte
-// accesses of a half warp on distinct banks for the thread layouts used.
-template <int A, int B>
-struct XLayout {
-  static constexpr int SB = B + ((B % 2 == 0) ? 1 : 0);    // row stride of the [A][SB] tile
-  static constexpr int raw = A * SB;
-  static constexpr int XS = raw + ((2 - raw % 8) + 8) % 8;  // per-sequence size, == 2 mod 8
-};
+// Shared-memory index with one complex of padding per 16, so that the
+// strided Stockham stores of a half warp spread over the banks.
+__device__ __forceinline__ int spad(int n) { return n + (n >> 4); }
+__host__ __device__ constexpr int spad_size(int L) { return L + (L >> 4) + 1; }
 
-// Cooperative length-A*B forward FFT of NS sequences by one thread group.
-// In:  thread l < B holds in[s][n1] = x_s[B n1 + l], n1 < A.
-// Out: thread l < A holds out[s][k2] = X_s[l + A k2], k2 < B.
-// ex:  the group's exchange area, NS * XLayout<A,B>::XS complex values (the
-//      stride between sequences is `xs`); tw: W_L^(l k1) at tw[k1 * B + l].
-// All threads of the CTA must call it (it contains __syncthreads).
-template <int A, int B, int NS, typename C>
-__device__ __forceinline__ void fft_group(C (&in)[NS][A], C (&out)[NS][B], C* ex, int xs, const C* __restrict__ tw,
-                                          int l) {
-  constexpr int SB = XLayout<A, B>::SB;
-  if (l < B) {
+// Twiddle and DFT of one radix-R butterfly of a stage with stride Ns, for NS
+// sequences at once.  a[s][r] = x_s[j + r L/R] on entry, the butterfly's
+// outputs (for positions (j/Ns) Ns R + (j mod Ns) + r Ns) on exit.
+template <int L, int R, int Ns, int NS, typename C>
+__device__ __forceinline__ void butterfly(C (&a)[NS][R], int j, const C* __restrict__ tw) {
+  if constexpr (Ns > 1) {
+    constexpr int step = L / (Ns * R);
+    const int k = j % Ns;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) dft<A>(in[s]);
+    for (int r = 1; r < R; ++r) {
+      const C w = tw[k * r * step];          // exponent < L, no reduction needed
 #pragma unroll
-    for (int k1 = 1; k1 < A; ++k1) {
-      const C w = tw[k1 * B + l];
-#pragma unroll
-      for (int s = 0; s < NS; ++s) in[s][k1] = cmul(in[s][k1], w);
+      for (int s = 0; s < NS; ++s) a[s][r] = cmul(a[s][r], w);
     }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) dft<R>(a[s]);
+}
+
+template <int R, int Ns>
+__device__ __forceinline__ int stockham_pos(int j, int r) {
+  return (j / Ns) * Ns * R + (j % Ns) + r * Ns;
+}
+
+// Forward FFT of NS sequences of length L = Q1 Q2 Q3 (Q3 = 1: two stages) by
+// the thread group; j is the thread's index in the group.
+// in:  a1[s][r] = x_s[j + r L/Q1] for j < L/Q1 (others ignored)
+// out: a3[s][r] = X_s[j + r L/Qlast] for j < L/Qlast
+// bufA, bufB: NS * spad_size(L) complex each, sequences `sl` apart.
+// Every thread of the CTA must call it (it synchronises the CTA).
+template <int L, int Q1, int Q2, int Q3, int NS, typename C>
+__device__ __forceinline__ void fft_stockham(C (&a1)[NS][Q1], C (&a3)[NS][(Q3 > 1 ? Q3 : Q2)], C* bufA, C* bufB,
+                                             int sl, int j, const C* __restrict__ tw) {
+  static_assert(Q1 * Q2 * Q3 == L, "radices must multiply to L");
+  if (j < L / Q1) {
+    butterfly<L, Q1, 1, NS>(a1, j, tw);
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
-      for (int k1 = 0; k1 < A; ++k1) ex[s * xs + k1 * SB + l] = in[s][k1];
+      for (int r = 0; r < Q1; ++r) bufA[s * sl + spad(stockham_pos<Q1, 1>(j, r))] = a1[s][r];
   }
   __syncthreads();
-  if (l < A) {
+  if constexpr (Q3 == 1) {
+    if (j < L / Q2) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
+      for (int s = 0; s < NS; ++s)
 #pragma unroll
-      for (int n2 = 0; n2 < B; ++n2) out[s][n2] = ex[s * xs + l * SB + n2];
-      dft<B>(out[s]);
+        for (int r = 0; r < Q2; ++r) a3[s][r] = bufA[s * sl + spad(j + r * (L / Q2))];
+      butterfly<L, Q2, Q1, NS>(a3, j, tw);
+    }
+  } else {
+    if (j < L / Q2) {
+      C a2[NS][Q2];
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int r = 0; r < Q2; ++r) a2[s][r] = bufA[s * sl + spad(j + r * (L / Q2))];
+      butterfly<L, Q2, Q1, NS>(a2, j, tw);
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int r = 0; r < Q2; ++r) bufB[s * sl + spad(stockham_pos<Q2, Q1>(j, r))] = a2[s][r];
+    }
+    __syncthreads();
+    if (j < L / Q3) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int r = 0; r < Q3; ++r) a3[s][r] = bufB[s * sl + spad(j + r * (L / Q3))];
+      butterfly<L, Q3, Q1 * Q2, NS>(a3, j, tw);
     }
   }
   __syncthreads();

@@ -17,13 +17,46 @@ __host__ __device__ constexpr int row_kout(int ph) { return (ph == F_R1 || ph ==
 __host__ __device__ constexpr int col_kin(int ph) { return ph == F_C1 ? 1 : 2; }
 __host__ __device__ constexpr int col_kout(int ph) { return ph == A_C6 ? 1 : 2; }
 
+// Operands a row pass needs at one grid point, loaded before the transforms
+// so that their latency overlaps the FFT (row_load), then consumed by
+// row_point.  The meaning of v0..v4 depends on the phase.
+template <typename T>
+struct RowIn {
+  T v0, v1, v2, v3, v4;
+};
+
+template <typename T>
+__device__ __forceinline__ RowIn<T> row_load(const PropArgs<T>& a, const int ph, const int b, const int i,
+                                             const int j) {
+  const long long g = (long long)j * a.nx + i;
+  const long long gb = (long long)b * a.gstride + g;
+  RowIn<T> r;
+  r.v0 = r.v1 = r.v2 = r.v3 = r.v4 = (T)0;
+  if (ph == F_R1) {
+    r.v0 = a.rx[gb]; r.v1 = a.ry[gb]; r.v2 = a.Cc[g]; r.v3 = a.eta[g]; r.v4 = a.tau[g];
+  } else if (ph == F_R2 || ph == A_R5) {
+    r.v0 = a.vx[gb]; r.v1 = a.vy[gb]; r.v2 = a.dtrsx[g]; r.v3 = a.dtrsy[g];
+  } else if (ph == F_R3 || ph == F_R3L) {
+    r.v0 = a.rx[gb]; r.v1 = a.ry[gb]; r.v2 = a.rho0[g]; r.v3 = a.Cc[g];
+  } else if (ph == A_R1) {
+    r.v2 = a.Cc[g]; r.v3 = a.eta[g]; r.v4 = a.tau[g];
+  } else if (ph == A_R1L) {
+    r.v0 = a.rx[gb]; r.v1 = a.ry[gb]; r.v2 = a.rho0[g]; r.v3 = a.Cc[g];
+  } else if (ph == A_R3) {
+    r.v0 = a.rx[gb]; r.v1 = a.ry[gb]; r.v2 = a.rho0[g]; r.v3 = a.Cc[g]; r.v4 = a.pbuf[gb];
+  }
+  return r;
+}
+
 // Pointwise update of one grid point (i, j) of problem b in a row pass.
 // in0/in1: the incoming fields after the inverse transforms (already
-// normalised); scv: M^T w at this point (adjoint sensor source, A_R1*).
-// Writes the outgoing fields to out0/out1 (to be forward transformed).
+// normalised); scv: M^T w at this point (adjoint sensor source, A_R1*);
+// st: the operands from row_load.  Writes the outgoing fields to out0/out1
+// (to be forward transformed) and the updated state to global memory.
 template <typename T>
 __device__ __forceinline__ void row_point(const PropArgs<T>& a, const int ph, const int b, const int i, const int j,
-                                          const T in0, const T in1, const T scv, T& out0, T& out1, bool& bad) {
+                                          const T in0, const T in1, const T scv, const RowIn<T>& st, T& out0,
+                                          T& out1, bool& bad) {
   const long long g = (long long)j * a.nx + i;
   const long long gb = (long long)b * a.gstride;
   const bool interior = (i >= a.pml) && (i < a.pml + a.n0) && (j >= a.pml) && (j < a.pml + a.n1);
@@ -32,16 +65,16 @@ __device__ __forceinline__ void row_point(const PropArgs<T>& a, const int ph, co
   out1 = (T)0;
   if (ph == F_R1) {
     // eq. num-p: p = c^2 [ (I - eta Y_dis) sum rho_i + tau Y_abs u ]
-    const T r = a.rx[gb + g] + a.ry[gb + g];
-    const T p = a.Cc[g] * ((r - a.eta[g] * in0) + a.tau[g] * in1);
+    const T r = st.v0 + st.v1;
+    const T p = st.v2 * ((r - st.v3 * in0) + st.v4 * in1);
     a.pbuf[gb + g] = p;
     bad |= !isfinite(p);
     out0 = p;
   } else if (ph == F_R2) {
     // eq. num-vel: v_i <- A_i (A_i v_i - dt/rho_i d/dr_i^+ p)
     const T sx = a.asx[i], sy = a.asy[j];
-    const T vx = sx * (sx * a.vx[gb + g] - a.dtrsx[g] * in0);
-    const T vy = sy * (sy * a.vy[gb + g] - a.dtrsy[g] * in1);
+    const T vx = sx * (sx * st.v0 - st.v2 * in0);
+    const T vy = sy * (sy * st.v1 - st.v3 * in1);
     a.vx[gb + g] = vx;
     a.vy[gb + g] = vy;
     out0 = vx;
@@ -49,96 +82,128 @@ __device__ __forceinline__ void row_point(const PropArgs<T>& a, const int ph, co
   } else if (ph == F_R3 || ph == F_R3L) {
     // eq. num-rho with the additive source of eq. s1 (dt s_i = P0 / (2 d c^2))
     T q = (T)0;
-    if ((a.flags & kSource) && interior) q = a.p0[(long long)b * a.n0 * a.n1 + ii] / ((T)4 * a.Cc[g]);
-    const T ax = a.ax[i], ay = a.ay[j], r0 = a.rho0[g];
-    const T rx = ax * (ax * a.rx[gb + g] - a.dt * r0 * in0) + q;
-    const T ry = ay * (ay * a.ry[gb + g] - a.dt * r0 * in1) + q;
+    if ((a.flags & kSource) && interior) q = a.io->p0[(long long)b * a.n0 * a.n1 + ii] / ((T)4 * st.v3);
+    const T ax = a.ax[i], ay = a.ay[j], r0 = st.v2;
+    const T rx = ax * (ax * st.v0 - a.dt * r0 * in0) + q;
+    const T ry = ay * (ay * st.v1 - a.dt * r0 * in1) + q;
     a.rx[gb + g] = rx;
     a.ry[gb + g] = ry;
     if (ph == F_R3) {
       out0 = rx + ry;                            // sum_i rho_i
       out1 = ax * r0 * in0 + ay * r0 * in1;      // sum_i A_i rho0 d/dr_i^- v_i
     } else {
-      const T p = a.Cc[g] * (rx + ry);
+      const T p = st.v3 * (rx + ry);
       a.pbuf[gb + g] = p;
       bad |= !isfinite(p);
       out0 = p;
     }
   } else if (ph == A_R1) {
     // transpose of num-m and of the pressure update: C p-bar feeds Y_dis^T, Y_abs^T
-    const T Cp = a.Cc[g] * (in0 + scv);
+    const T Cp = st.v2 * (in0 + scv);
     a.pbuf[gb + g] = Cp;
-    out0 = a.eta[g] * Cp;
-    out1 = a.tau[g] * Cp;
+    out0 = st.v3 * Cp;
+    out1 = st.v4 * Cp;
   } else if (ph == A_R1L || ph == A_R3) {
     // transpose of the density update (and of the source injection)
     T Cp, ya = (T)0;
     if (ph == A_R1L) {
-      Cp = a.Cc[g] * (in0 + scv);
+      Cp = st.v3 * (in0 + scv);
     } else {
-      Cp = a.pbuf[gb + g];
+      Cp = st.v4;
       ya = in1;
     }
     const T rpart = (ph == A_R1L) ? Cp : Cp - in0;   // (I - Y_dis eta) C p-bar
-    const T ax = a.ax[i], ay = a.ay[j], r0 = a.rho0[g];
-    const T rtx = a.rx[gb + g] + rpart;
-    const T rty = a.ry[gb + g] + rpart;
+    const T ax = a.ax[i], ay = a.ay[j], r0 = st.v2;
+    const T rtx = st.v0 + rpart;
+    const T rty = st.v1 + rpart;
     out0 = r0 * ax * (ya - a.dt * rtx);
     out1 = r0 * ay * (ya - a.dt * rty);
     a.rx[gb + g] = ax * ax * rtx;
     a.ry[gb + g] = ay * ay * rty;
     bad |= !isfinite(rtx + rty);
     if (interior && (a.flags & (kAccWrite | kAccAdd))) {
-      T* dst = a.p0adj + (long long)b * a.n0 * a.n1 + ii;
-      const T val = (rtx + rty) / ((T)4 * a.Cc[g]);
+      T* dst = a.io->p0adj + (long long)b * a.n0 * a.n1 + ii;
+      const T val = (rtx + rty) / ((T)4 * st.v3);
       if (a.flags & kAccWrite) *dst = val;
       else *dst += val;
     }
   } else if (ph == A_R5) {
     // transpose of the velocity update
     const T sx = a.asx[i], sy = a.asy[j];
-    const T vtx = a.vx[gb + g] + in0;
-    const T vty = a.vy[gb + g] + in1;
+    const T vtx = st.v0 + in0;
+    const T vty = st.v1 + in1;
     a.vx[gb + g] = sx * sx * vtx;
     a.vy[gb + g] = sy * sy * vty;
-    out0 = sx * a.dtrsx[g] * vtx;
-    out1 = sy * a.dtrsy[g] * vty;
+    out0 = sx * st.v2 * vtx;
+    out1 = sy * st.v3 * vty;
   }
 }
 
-// Spectral symbol of a column pass at half-spectrum point (kx, ky):
-// o0/o1 from the y-transformed inputs X0/X1.
+// Operands of a column pass at one half-spectrum point, loaded early.
+template <typename T, typename C>
+struct ColIn {
+  T k1, k2;      // kappa (or |k|^(y-1)) and |k|^(y-2)
+  C sy;          // y shift-derivative factor
+};
+
+template <typename T, typename C>
+__device__ __forceinline__ ColIn<T, C> col_load(const PropArgs<T>& a, const int ph, const int kx, const int ky) {
+  const long long t = (long long)ky * a.nxh + kx;
+  ColIn<T, C> r;
+  r.k1 = (T)0;
+  r.k2 = (T)0;
+  r.sy = cmake<C>((T)0, (T)0);
+  if (ph == F_C3 || ph == A_C2) {
+    r.k1 = a.kp1[t];
+    r.k2 = a.kp2[t];
+  } else {
+    r.k1 = a.kap[t];
+    r.sy = (ph == F_C1 || ph == A_C6) ? a.shyp[ky] : a.shym[ky];
+  }
+  return r;
+}
+
+// Spectral symbol of a column pass from preloaded operands; sx is the x
+// shift-derivative factor of the column (shxp or shxm by phase).
+template <typename T, typename C>
+__device__ __forceinline__ void col_apply(const int ph, const ColIn<T, C>& st, const C sx, const C X0, const C X1,
+                                          C& o0, C& o1) {
+  if (ph == F_C1) {          // d/dr_x^+, d/dr_y^+ of p (eq. grr)
+    o0 = cscale(cmul(sx, X0), st.k1);
+    o1 = cscale(cmul(st.sy, X0), st.k1);
+  } else if (ph == F_C2) {   // d/dr_x^- v_x, d/dr_y^- v_y
+    o0 = cscale(cmul(sx, X0), st.k1);
+    o1 = cscale(cmul(st.sy, X1), st.k1);
+  } else if (ph == F_C3 || ph == A_C2) {   // Y_dis, Y_abs (real, even symbols)
+    o0 = cscale(X0, st.k1);
+    o1 = cscale(X1, st.k2);
+  } else if (ph == A_C4) {   // (d/dr_i^-)^T: conjugate symbols
+    o0 = cscale(cmul(cconj(sx), X0), st.k1);
+    o1 = cscale(cmul(cconj(st.sy), X1), st.k1);
+  } else {                   // A_C6: -sum_i (d/dr_i^+)^T
+    o0 = cscale(cadd(cmul(cconj(sx), X0), cmul(cconj(st.sy), X1)), -st.k1);
+    o1 = o0;
+  }
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ C col_sx(const PropArgs<T>& a, const int ph, const int kx) {
+  return (ph == F_C1 || ph == A_C6) ? a.shxp[kx] : a.shxm[kx];
+}
+
+// Spectral symbol of a column pass at half-spectrum point (kx, ky).
 template <typename T, typename C>
 __device__ __forceinline__ void col_point(const PropArgs<T>& a, const int ph, const int kx, const int ky, const C X0,
                                           const C X1, C& o0, C& o1) {
-  const long long t = (long long)ky * a.nxh + kx;
-  if (ph == F_C1) {          // d/dr_x^+, d/dr_y^+ of p (eq. grr)
-    const T k = a.kap[t];
-    o0 = cscale(cmul(a.shxp[kx], X0), k);
-    o1 = cscale(cmul(a.shyp[ky], X0), k);
-  } else if (ph == F_C2) {   // d/dr_x^- v_x, d/dr_y^- v_y
-    const T k = a.kap[t];
-    o0 = cscale(cmul(a.shxm[kx], X0), k);
-    o1 = cscale(cmul(a.shym[ky], X1), k);
-  } else if (ph == F_C3 || ph == A_C2) {   // Y_dis, Y_abs (real, even symbols)
-    o0 = cscale(X0, a.kp1[t]);
-    o1 = cscale(X1, a.kp2[t]);
-  } else if (ph == A_C4) {   // (d/dr_i^-)^T: conjugate symbols
-    const T k = a.kap[t];
-    o0 = cscale(cmul(cconj(a.shxm[kx]), X0), k);
-    o1 = cscale(cmul(cconj(a.shym[ky]), X1), k);
-  } else {                   // A_C6: -sum_i (d/dr_i^+)^T
-    const T k = a.kap[t];
-    o0 = cscale(cadd(cmul(cconj(a.shxp[kx]), X0), cmul(cconj(a.shyp[ky]), X1)), -k);
-    o1 = o0;
-  }
+  const ColIn<T, C> st = col_load<T, C>(a, ph, kx, ky);
+  col_apply<T, C>(ph, st, col_sx<T, C>(a, ph, kx), X0, X1, o0, o1);
 }
 
 // M^T w_n for the grid points of rows j0, j0 + 1 into sc[rr * nx + i]
 // (deterministic: each point sums its own entries).  Threads tid0..tid0+nth-1.
 template <typename T>
 __device__ __forceinline__ void sensor_scatter_rows(const PropArgs<T>& a, int b, int j0, T* sc, int tid, int nth) {
-  const T* wn = a.w + ((long long)b * a.nt + a.n) * a.ns;
+  const T* wn = a.io->w + ((long long)b * a.nt + a.n) * a.ns;
   for (int rr = 0; rr < 2; ++rr) {
     const int j = j0 + rr;
     for (int q = a.rowptr[j] + tid; q < a.rowptr[j + 1]; q += nth) {
@@ -153,7 +218,7 @@ __device__ __forceinline__ void sensor_scatter_rows(const PropArgs<T>& a, int b,
 template <typename T>
 __device__ __forceinline__ void sensor_gather(const PropArgs<T>& a, int b, int first, int stride) {
   const T* pb = a.pbuf + (long long)b * a.gstride;
-  T* dn = a.data + ((long long)b * a.nt + a.n) * a.ns;
+  T* dn = a.io->data + ((long long)b * a.nt + a.n) * a.ns;
   for (int s = first; s < a.ns; s += stride) {
     T acc = (T)0;
 #pragma unroll

@@ -18,6 +18,8 @@
 // a step touches the state fields once and the spectra twice per operator
 // application.  The batch index is blockIdx.y: many problems on the same
 // grid and medium share each launch.
+#include <type_traits>
+
 #include "pass_ops.cuh"
 
 namespace qpat {
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const PropArgs<T> a) {
       }
       const T scv = (PH == A_R1 || PH == A_R1L) ? sc[rr * nx + i] : (T)0;
       T out0, out1;
-      row_point<T>(a, PH, b, i, j0 + rr, in0, in1, scv, out0, out1, bad);
+      row_point<T>(a, PH, b, i, j0 + rr, in0, in1, scv, row_load<T>(a, PH, b, i, j0 + rr), out0, out1, bad);
       if (rr == 0) {
         oth[i].x = out0;
         if (KOUT > 1) oth[nx + i].x = out1;
@@ -221,8 +223,20 @@ static void set_col_attr() {
   cudaFuncSetAttribute(col_kernel<T, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
+#define QPAT_FAST_CASES(X) X(24) X(40) X(48) X(54) X(56) X(168) X(288) X(432) X(576) X(1024) X(1080)
+
 template <typename T>
-int prop_init_attributes() {
+int prop_init_attributes(int nx, int ny, int fast_rows, int fast_cols) {
+  if constexpr (std::is_same<T, float>::value) {
+    for (int L : {fast_rows ? nx : 0, fast_cols ? ny : 0}) {
+      switch (L) {
+#define QPAT_PREP_CASE(n) case n: prepare_fast_len<T, n>(); break;
+        QPAT_FAST_CASES(QPAT_PREP_CASE)
+#undef QPAT_PREP_CASE
+        default: break;
+      }
+    }
+  }
   set_row_attr<T, F_R1>(); set_row_attr<T, F_R2>(); set_row_attr<T, F_R3>(); set_row_attr<T, F_R3L>();
   set_row_attr<T, A_R1>(); set_row_attr<T, A_R1L>(); set_row_attr<T, A_R3>(); set_row_attr<T, A_R5>();
   set_col_attr<T, F_C1>(); set_col_attr<T, F_C2>(); set_col_attr<T, F_C3>();
@@ -230,20 +244,24 @@ int prop_init_attributes() {
   return 0;
 }
 
-#define QPAT_FAST_CASES(X) X(24) X(40) X(48) X(54) X(56) X(168) X(288) X(432) X(576)
-
-int fast_length_split(int L) {
+// Measured on GB300: the specialised passes win in FP32; in FP64 (slow FP64
+// pipes, twice the registers) the generic shared-memory passes are faster.
+bool fast_rows_supported(int L, int elt) {
+  if (elt != 4) return false;
   switch (L) {
-#define QPAT_SPLIT_CASE(n) case n: return fast_split_a(n);
-    QPAT_FAST_CASES(QPAT_SPLIT_CASE)
-#undef QPAT_SPLIT_CASE
-    default: return 0;
+#define QPAT_SUP_CASE(n) case n:
+    QPAT_FAST_CASES(QPAT_SUP_CASE)
+#undef QPAT_SUP_CASE
+    return true;
+    default: return false;
   }
 }
 
+bool fast_cols_supported(int L, int elt) { return fast_rows_supported(L, elt); }
+
 template <typename T>
 void launch_row(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
-  if (a.fx_ab) {
+  if constexpr (std::is_same<T, float>::value) if (a.fast_rows) {
     switch (a.nx) {
 #define QPAT_ROW_CASE(n) case n: launch_row_fast_len<T, n>(a, phase, batch, s); return;
       QPAT_FAST_CASES(QPAT_ROW_CASE)
@@ -268,7 +286,7 @@ void launch_row(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
 
 template <typename T>
 void launch_col(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
-  if (a.fy_ab) {
+  if constexpr (std::is_same<T, float>::value) if (a.fast_cols) {
     switch (a.ny) {
 #define QPAT_COL_CASE(n) case n: launch_col_fast_len<T, n>(a, phase, batch, s); return;
       QPAT_FAST_CASES(QPAT_COL_CASE)
@@ -290,6 +308,19 @@ void launch_col(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
 }
 
 template <typename T>
+__global__ void set_io_kernel(IoPtrs<T>* dst, const T* p0, T* data, const T* w, T* p0adj) {
+  dst->p0 = p0;
+  dst->data = data;
+  dst->w = w;
+  dst->p0adj = p0adj;
+}
+
+template <typename T>
+void launch_set_io(IoPtrs<T>* dst, const T* p0, T* data, const T* w, T* p0adj, cudaStream_t s) {
+  set_io_kernel<T><<<1, 1, 0, s>>>(dst, p0, data, w, p0adj);
+}
+
+template <typename T>
 void launch_gather(const PropArgs<T>& a, int batch, cudaStream_t s) {
   dim3 grid((a.ns + 255) / 256, batch);
   gather_kernel<T><<<grid, 256, 0, s>>>(a);
@@ -298,10 +329,11 @@ void launch_gather(const PropArgs<T>& a, int batch, cudaStream_t s) {
 #define QPAT_INST(T)                                                              \
   template size_t row_smem_bytes<T>(int);                                         \
   template size_t col_smem_bytes<T>(int, int);                                    \
-  template int prop_init_attributes<T>();                                         \
+  template int prop_init_attributes<T>(int, int, int, int);                                         \
   template void launch_row<T>(const PropArgs<T>&, int, int, cudaStream_t);        \
   template void launch_col<T>(const PropArgs<T>&, int, int, cudaStream_t);        \
-  template void launch_gather<T>(const PropArgs<T>&, int, cudaStream_t);
+  template void launch_gather<T>(const PropArgs<T>&, int, cudaStream_t);                \
+  template void launch_set_io<T>(IoPtrs<T>*, const T*, T*, const T*, T*, cudaStream_t);
 QPAT_INST(float)
 QPAT_INST(double)
 

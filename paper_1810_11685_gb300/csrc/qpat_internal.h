@@ -38,6 +38,14 @@ enum Phase : int {
 };
 
 template <typename T>
+struct IoPtrs {
+  const T* p0;            // [B][N] interior source (forward)
+  T* data;                // [B][nt][ns] (forward output)
+  const T* w;             // [B][nt][ns] (adjoint input)
+  T* p0adj;               // [B][N] (adjoint output)
+};
+
+template <typename T>
 struct PropArgs {
   typedef typename V2<T>::t C;
   int nx, ny, nxh, pitch, pml, n0, n1, ns, nt;
@@ -45,11 +53,8 @@ struct PropArgs {
   FFTPlan px, py;
   const C* twx;
   const C* twy;
-  // register-FFT twiddles W_L^(l k1) of the L = A * B splits (null: generic path)
-  const C* fx_ab;         // [A][B] for rows, L = nx
-  const C* fx_ba;         // [B][A]
-  const C* fy_ab;         // columns, L = ny
-  const C* fy_ba;
+  // 1: the row (x) / column (y) passes run the length-specialised kernels
+  int fast_rows, fast_cols;
   // medium diagonals on the full grid [ny][nx]
   const T* Cc;            // c^2
   const T* rho0;          // ambient density at nodes
@@ -85,11 +90,9 @@ struct PropArgs {
   C* spec;                // [B][2][ny][pitch]
   long long sstride;      // 2*ny*pitch
   T* pbuf;                // [B][ny][nx]
-  // per call
-  const T* p0;            // [B][N] interior source (forward)
-  T* data;                // [B][nt][ns] (forward output)
-  const T* w;             // [B][nt][ns] (adjoint input)
-  T* p0adj;               // [B][N] (adjoint output)
+  // per call: the caller's buffers, read through a device-resident struct so
+  // that a captured CUDA graph of the time loop serves every call
+  const IoPtrs<T>* io;
   int n;                  // sample index this launch reads or writes
   int flags;
   int* err;               // device flags word (bit 0: non-finite)
@@ -101,19 +104,25 @@ template <typename T>
 void launch_col(const PropArgs<T>& a, int phase, int batch, cudaStream_t s);
 template <typename T>
 void launch_gather(const PropArgs<T>& a, int batch, cudaStream_t s);
+template <typename T>
+void launch_set_io(IoPtrs<T>* dst, const T* p0, T* data, const T* w, T* p0adj, cudaStream_t s);
 // length-specialised passes (fast_kernels.cuh), one translation unit per length
 template <typename T, int L>
 void launch_row_fast_len(const PropArgs<T>& a, int ph, int batch, cudaStream_t s);
 template <typename T, int L>
 void launch_col_fast_len(const PropArgs<T>& a, int ph, int batch, cudaStream_t s);
-// A of the register-FFT split L = A * B, 0 if L has no specialised passes
-int fast_length_split(int L);
+template <typename T, int L>
+void prepare_fast_len();
+// Whether FFT extent L has length-specialised row / column passes for
+// elements of elt bytes (4: FP32, 8: FP64).
+bool fast_rows_supported(int L, int elt);
+bool fast_cols_supported(int L, int elt);
 template <typename T>
 size_t row_smem_bytes(int nx);
 template <typename T>
 size_t col_smem_bytes(int ny, int cb);
 template <typename T>
-int prop_init_attributes();
+int prop_init_attributes(int nx, int ny, int fast_rows, int fast_cols);
 
 // Table construction (tables.cu)
 template <typename T>
@@ -124,7 +133,6 @@ struct TableOut {
   T *kap, *kp1, *kp2;
   C *shxp, *shxm, *shyp, *shym;
   C *twx, *twy;
-  C *fx_ab, *fx_ba, *fy_ab, *fy_ba;   // optional (register-FFT lengths only)
 };
 template <typename T>
 cudaError_t build_tables(const TableOut<T>& o, const double* d_c, const double* d_rho, const double* d_alpha_db,

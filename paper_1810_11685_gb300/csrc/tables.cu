@@ -117,19 +117,6 @@ __global__ void twiddle_kernel(C* tw, int L) {
   tw[m].y = -s;
 }
 
-// W_L^(k1 l) at out[k1 * cols + l], k1 < rows, l < cols (register-FFT splits)
-template <typename C>
-__global__ void twiddle2_kernel(C* out, int L, int rows, int cols) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= rows * cols) return;
-  const int k1 = t / cols, l = t - k1 * cols;
-  const long long e = ((long long)k1 * l) % L;
-  double s, c;
-  sincospi(2.0 * (double)e / (double)L, &s, &c);
-  out[t].x = c;
-  out[t].y = -s;
-}
-
 template <typename T>
 cudaError_t build_tables(const TableOut<T>& o, const double* d_c, const double* d_rho, const double* d_alpha_db,
                          int nx, int ny, int nxh, int pml, double dx, double dt, double c_ref, double pml_alpha,
@@ -143,16 +130,6 @@ cudaError_t build_tables(const TableOut<T>& o, const double* d_c, const double* 
   shift_kernel<C><<<(ny + 127) / 128, 128, 0, s>>>(o.shyp, o.shym, ny, ny, dx);
   twiddle_kernel<C><<<(nx + 127) / 128, 128, 0, s>>>(o.twx, nx);
   twiddle_kernel<C><<<(ny + 127) / 128, 128, 0, s>>>(o.twy, ny);
-  if (o.fx_ab) {
-    const int A = fast_length_split(nx), B = nx / A;
-    twiddle2_kernel<C><<<(nx + 127) / 128, 128, 0, s>>>(o.fx_ab, nx, A, B);
-    twiddle2_kernel<C><<<(nx + 127) / 128, 128, 0, s>>>(o.fx_ba, nx, B, A);
-  }
-  if (o.fy_ab) {
-    const int A = fast_length_split(ny), B = ny / A;
-    twiddle2_kernel<C><<<(ny + 127) / 128, 128, 0, s>>>(o.fy_ab, ny, A, B);
-    twiddle2_kernel<C><<<(ny + 127) / 128, 128, 0, s>>>(o.fy_ba, ny, B, A);
-  }
   return cudaGetLastError();
 }
 
