@@ -37,13 +37,17 @@ __device__ __forceinline__ RowIn<T> row_load(const PropArgs<T>& a, const int ph,
   } else if (ph == F_R2 || ph == A_R5) {
     r.v0 = a.vx[gb]; r.v1 = a.vy[gb]; r.v2 = a.dtrsx[g]; r.v3 = a.dtrsy[g];
   } else if (ph == F_R3 || ph == F_R3L) {
-    r.v0 = a.rx[gb]; r.v1 = a.ry[gb]; r.v2 = a.rho0[g]; r.v3 = a.Cc[g];
+    // c^2 only enters through the source (F_R3) or the pressure (F_R3L)
+    r.v0 = a.rx[gb]; r.v1 = a.ry[gb]; r.v2 = a.rho0[g];
+    if (ph == F_R3L || (a.flags & kSource)) r.v3 = a.Cc[g];
   } else if (ph == A_R1) {
     r.v2 = a.Cc[g]; r.v3 = a.eta[g]; r.v4 = a.tau[g];
   } else if (ph == A_R1L) {
     r.v0 = a.rx[gb]; r.v1 = a.ry[gb]; r.v2 = a.rho0[g]; r.v3 = a.Cc[g];
   } else if (ph == A_R3) {
-    r.v0 = a.rx[gb]; r.v1 = a.ry[gb]; r.v2 = a.rho0[g]; r.v3 = a.Cc[g]; r.v4 = a.pbuf[gb];
+    // c^2 only enters through the source adjoint (accumulation steps)
+    r.v0 = a.rx[gb]; r.v1 = a.ry[gb]; r.v2 = a.rho0[g]; r.v4 = a.pbuf[gb];
+    if (a.flags & (kAccWrite | kAccAdd)) r.v3 = a.Cc[g];
   }
   return r;
 }
