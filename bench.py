@@ -206,9 +206,8 @@ def run_ours(args):
     import torch
     from paper_1810_11685_gb300.binding import context_from_workload
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1810_11685_gb300 import replicas
+    rank, world, local = replicas.world()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -258,12 +257,8 @@ def run_ours(args):
         dist.barrier()
     ctx.sync()
     launches = ctx.stats()["launches"] - launches0
-    t_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist is not None:
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * cells_per_step * args.steps / (t_ms / 1e3)
+    t_ms = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), device=dev)
+    value = replicas.throughput(cells_per_step * args.steps, world, t_ms / 1e3)
     clocks = clk.summary()
 
     extras = {}

@@ -157,6 +157,24 @@ qpat_status qpat_jvp(qpat_ctx* ctx, int batch, const double* mu, const double* p
 qpat_status qpat_vjp(qpat_ctx* ctx, int batch, const double* mu, const double* phi0,
                      const void* w, unsigned illum, double* g);
 
+/* Forward-state checkpointing of H_a.  The mu-gradient (qpat_vjp) needs no
+ * forward fields -- the transposed step T^* of Section 3.2.4 does not depend
+ * on the forward state -- so these calls serve callers that need the fields
+ * themselves (e.g. derivatives in c or rho) and let tests confirm that a
+ * forward resumed from any checkpoint reproduces the stored series exactly.
+ * A checkpoint holds, per problem, v_x, v_y, rho_x, rho_y, the sampling
+ * buffer and the two spectral work slots after loop iteration n with
+ * (n + 1) % K == 0 (Section 3.2.3 loop), m = (n + 1)/K - 1, 0 <= m < (nt-1)/K.
+ * qpat_ckpt_bytes: size of the checkpoint buffer for batch and K.
+ * qpat_acoustic_forward_ckpt: H_a as qpat_acoustic_forward, also filling
+ *   ckpt (device, caller-owned, qpat_ckpt_bytes bytes).
+ * qpat_acoustic_resume: restore checkpoint m and continue the loop, writing
+ *   samples (m + 1) K .. nt - 1 of data (other samples untouched). */
+qpat_status qpat_ckpt_bytes(const qpat_ctx* ctx, int batch, int K, long long* bytes);
+qpat_status qpat_acoustic_forward_ckpt(qpat_ctx* ctx, int batch, const void* p0, void* data, int K,
+                                       void* ckpt);
+qpat_status qpat_acoustic_resume(qpat_ctx* ctx, int batch, const void* ckpt, int K, int m, void* data);
+
 /* FP64 inner products <a_b, c_b> of two device prec vectors [batch][len]
  * with compensated (Neumaier) accumulation; out: host double [batch].
  * Synchronises. */

@@ -79,6 +79,9 @@ def load():
         "qpat_vjp": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
         "qpat_dot": [vp, i, ll, vp, vp, ctypes.POINTER(d)],
         "qpat_get_stats": [vp, ctypes.POINTER(ll)],
+        "qpat_ckpt_bytes": [vp, i, i, ctypes.POINTER(ll)],
+        "qpat_acoustic_forward_ckpt": [vp, i, vp, vp, i, vp],
+        "qpat_acoustic_resume": [vp, i, vp, i, i, vp],
         "qpat_profile": [vp, i],
         "qpat_profile_read": [vp, ctypes.POINTER(d), ctypes.POINTER(ll)],
     }
@@ -236,6 +239,30 @@ class Context:
         out = self._empty(B, self.n1, self.n0) if out is None else out
         self._stream()
         _check(self._ptr, self._lib.qpat_acoustic_adjoint(self._ptr, B, _ptr(data), _ptr(out)))
+        return out
+
+    def ckpt_bytes(self, batch, K):
+        n = ctypes.c_longlong()
+        _check(self._ptr, self._lib.qpat_ckpt_bytes(self._ptr, int(batch), int(K), ctypes.byref(n)))
+        return n.value
+
+    def acoustic_forward_ckpt(self, p0, K, out=None):
+        """H_a that also stores the forward state every K loop iterations;
+        returns (data, checkpoint buffer)."""
+        import torch
+        p0 = self._in(p0, self.dtype, (self.n1, self.n0))
+        B = p0.shape[0]
+        out = self._empty(B, self.nt, self.ns) if out is None else out
+        ck = torch.empty(self.ckpt_bytes(B, K), dtype=torch.uint8, device=self.device)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_acoustic_forward_ckpt(self._ptr, B, _ptr(p0), _ptr(out), int(K), _ptr(ck)))
+        return out, ck
+
+    def acoustic_resume(self, ckpt, K, m, batch, out=None):
+        """Continue H_a from checkpoint m: fills samples (m+1)K .. nt-1 of ``out``."""
+        out = self._empty(batch, self.nt, self.ns).zero_() if out is None else out
+        self._stream()
+        _check(self._ptr, self._lib.qpat_acoustic_resume(self._ptr, int(batch), _ptr(ckpt), int(K), int(m), _ptr(out)))
         return out
 
     def da_solve(self, mu, illum):

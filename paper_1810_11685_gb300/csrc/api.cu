@@ -294,19 +294,34 @@ void pass(qpat_ctx* c, const PropArgs<T>& a, int phase, int batch, bool is_row, 
 
 // H_a: launch sequence of the forward loop n = -1 .. Nt - 2 (Section 3.2.3),
 // enqueued on stream s; the caller's buffers are read through a.io.
+// Checkpointing (K > 0): after loop iteration n with (n + 1) % K == 0 the
+// full state is copied to checkpoint m = (n + 1)/K - 1 (store = true), or the
+// loop starts after checkpoint `resume_m` from its restored state, producing
+// samples (resume_m + 1) K .. Nt - 1 only.
 template <typename T>
-long long seq_forward(qpat_ctx* c, int batch, cudaStream_t s) {
+long long seq_forward(qpat_ctx* c, int batch, cudaStream_t s, int K = 0, bool store = false, int resume_m = -1) {
   PropArgs<T> a = args<T>(c);
   long long cnt = 0;
-  zero_state<T>(c, batch, s);
   const int nt = c->nt;
+  int n_first = 0;
+  if (resume_m >= 0) {
+    launch_ckpt_copy<T>(a, batch, resume_m, 0, s);
+    n_first = (resume_m + 1) * K;
+  } else {
+    zero_state<T>(c, batch, s);
+  }
+  auto checkpoint = [&](int n) {
+    if (store && K > 0 && (n + 1) % K == 0) launch_ckpt_copy<T>(a, batch, (n + 1) / K - 1, 1, s);
+  };
   if (!c->cfg.lossless) {
-    a.n = 0;
-    a.flags = kSkipInput | kSource;          // step n = -1 from zero fields
-    pass<T>(c, a, F_R3, batch, true, s, cnt);
-    a.flags = 0;
-    pass<T>(c, a, F_C3, batch, false, s, cnt);
-    for (int n = 0; n <= nt - 2; ++n) {
+    if (resume_m < 0) {
+      a.n = 0;
+      a.flags = kSkipInput | kSource;          // step n = -1 from zero fields
+      pass<T>(c, a, F_R3, batch, true, s, cnt);
+      a.flags = 0;
+      pass<T>(c, a, F_C3, batch, false, s, cnt);
+    }
+    for (int n = n_first; n <= nt - 2; ++n) {
       a.n = n;
       a.flags = 0;
       pass<T>(c, a, F_R1, batch, true, s, cnt);    // p_n
@@ -317,15 +332,18 @@ long long seq_forward(qpat_ctx* c, int batch, cudaStream_t s) {
       pass<T>(c, a, F_R3, batch, true, s, cnt);    // rho^(n+1)
       a.flags = 0;
       pass<T>(c, a, F_C3, batch, false, s, cnt);   // Y_dis, Y_abs
+      checkpoint(n);
     }
     a.n = nt - 1;
     a.flags = kSkipOutput;
     pass<T>(c, a, F_R1, batch, true, s, cnt);      // p_(Nt-1)
   } else {
-    a.n = 0;
-    a.flags = kSkipInput | kSource;
-    pass<T>(c, a, F_R3L, batch, true, s, cnt);     // p_0
-    for (int n = 0; n <= nt - 2; ++n) {
+    if (resume_m < 0) {
+      a.n = 0;
+      a.flags = kSkipInput | kSource;
+      pass<T>(c, a, F_R3L, batch, true, s, cnt);   // p_0
+    }
+    for (int n = n_first; n <= nt - 2; ++n) {
       a.n = n;
       a.flags = 0;
       pass<T>(c, a, F_C1, batch, false, s, cnt);
@@ -333,6 +351,7 @@ long long seq_forward(qpat_ctx* c, int batch, cudaStream_t s) {
       pass<T>(c, a, F_C2, batch, false, s, cnt);
       a.flags = (n == 0) ? kSource : 0;
       pass<T>(c, a, F_R3L, batch, true, s, cnt);   // p_(n+1)
+      checkpoint(n);
     }
     a.n = nt - 1;
   }
@@ -383,7 +402,7 @@ template <typename T>
 qpat_status run_prop(qpat_ctx* c, int dir, int batch, const T* p0, T* data, const T* w, T* p0adj) {
   PropArgs<T>& a = args<T>(c);
   IoPtrs<T>* io = const_cast<IoPtrs<T>*>(a.io);
-  launch_set_io<T>(io, p0, data, w, p0adj, c->stream);
+  launch_set_io<T>(io, p0, data, w, p0adj, nullptr, c->stream);
   QCK(cudaGetLastError());
   const bool direct = c->cfg.no_graphs || c->prof_phase >= 0;
   if (direct) {
@@ -408,6 +427,17 @@ qpat_status run_prop(qpat_ctx* c, int dir, int batch, const T* p0, T* data, cons
   }
   QCK(cudaGraphLaunch(it->second.first, c->stream));
   c->launches += it->second.second;
+  return QPAT_OK;
+}
+
+// Checkpointed forward (store) or resumed forward, launched directly.
+template <typename T>
+qpat_status run_ckpt(qpat_ctx* c, int batch, const T* p0, T* data, T* ckpt, int K, int resume_m) {
+  PropArgs<T>& a = args<T>(c);
+  IoPtrs<T>* io = const_cast<IoPtrs<T>*>(a.io);
+  launch_set_io<T>(io, p0, data, nullptr, nullptr, ckpt, c->stream);
+  c->launches += seq_forward<T>(c, batch, c->stream, K, resume_m < 0, resume_m);
+  QCK(cudaGetLastError());
   return QPAT_OK;
 }
 
@@ -680,6 +710,32 @@ qpat_status qpat_dot(qpat_ctx* c, int batch, long long len, const void* a, const
   QCK(cudaStreamSynchronize(c->stream));
   for (int i = 0; i < batch; ++i) out[i] = c->h_dot_out[i];
   return QPAT_OK;
+}
+
+qpat_status qpat_ckpt_bytes(const qpat_ctx* c, int batch, int K, long long* bytes) {
+  if (!c || !bytes || K < 1 || batch < 1) return QPAT_EINVAL;
+  const long long M = (c->nt - 1) / K;
+  const long long per = c->prec == QPAT_FP32 ? ckpt_elems<float>(c->pf) * 4 : ckpt_elems<double>(c->pd) * 8;
+  *bytes = M * batch * per;
+  return QPAT_OK;
+}
+
+qpat_status qpat_acoustic_forward_ckpt(qpat_ctx* c, int batch, const void* p0, void* data, int K, void* ckpt) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!p0 || !data || !ckpt || K < 1) return fail(c, QPAT_EINVAL, "bad checkpoint arguments");
+  return c->prec == QPAT_FP32 ? run_ckpt<float>(c, batch, (const float*)p0, (float*)data, (float*)ckpt, K, -1)
+                              : run_ckpt<double>(c, batch, (const double*)p0, (double*)data, (double*)ckpt, K, -1);
+}
+
+qpat_status qpat_acoustic_resume(qpat_ctx* c, int batch, const void* ckpt, int K, int m, void* data) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!data || !ckpt || K < 1 || m < 0 || m >= (c->nt - 1) / K)
+    return fail(c, QPAT_EINVAL, "bad resume arguments (checkpoint index out of range)");
+  return c->prec == QPAT_FP32
+             ? run_ckpt<float>(c, batch, nullptr, (float*)data, (float*)const_cast<void*>(ckpt), K, m)
+             : run_ckpt<double>(c, batch, nullptr, (double*)data, (double*)const_cast<void*>(ckpt), K, m);
 }
 
 qpat_status qpat_get_stats(const qpat_ctx* c, long long out[2]) {

@@ -308,16 +308,49 @@ void launch_col(const PropArgs<T>& a, int phase, int batch, cudaStream_t s) {
 }
 
 template <typename T>
-__global__ void set_io_kernel(IoPtrs<T>* dst, const T* p0, T* data, const T* w, T* p0adj) {
+__global__ void set_io_kernel(IoPtrs<T>* dst, const T* p0, T* data, const T* w, T* p0adj, T* ckpt) {
   dst->p0 = p0;
   dst->data = data;
   dst->w = w;
   dst->p0adj = p0adj;
+  dst->ckpt = ckpt;
 }
 
 template <typename T>
-void launch_set_io(IoPtrs<T>* dst, const T* p0, T* data, const T* w, T* p0adj, cudaStream_t s) {
-  set_io_kernel<T><<<1, 1, 0, s>>>(dst, p0, data, w, p0adj);
+void launch_set_io(IoPtrs<T>* dst, const T* p0, T* data, const T* w, T* p0adj, T* ckpt, cudaStream_t s) {
+  set_io_kernel<T><<<1, 1, 0, s>>>(dst, p0, data, w, p0adj, ckpt);
+}
+
+template <typename T>
+__host__ __device__ long long ckpt_elems(const PropArgs<T>& a) {
+  return 5 * a.gstride + 2 * a.sstride;     // 5 real grids + 2 slots of complex (2 T each)
+}
+
+// One forward-state checkpoint: v_x, v_y, rho_x, rho_y, the sampling buffer
+// and both spectral slots of every problem, at checkpoint index m.
+template <typename T>
+__global__ void ckpt_copy_kernel(const PropArgs<T> a, int batch, int m, int to_ckpt) {
+  const int b = blockIdx.y;
+  const long long per = ckpt_elems(a);
+  T* ck = a.io->ckpt + ((long long)m * batch + b) * per;
+  const long long G = a.gstride;
+  T* src[6] = {a.vx + b * G, a.vy + b * G, a.rx + b * G, a.ry + b * G, a.pbuf + b * G,
+               reinterpret_cast<T*>(a.spec + (long long)b * a.sstride)};
+  const long long len[6] = {G, G, G, G, G, 2 * a.sstride};
+  long long off = 0;
+  for (int f = 0; f < 6; ++f) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len[f];
+         t += (long long)gridDim.x * blockDim.x) {
+      if (to_ckpt) ck[off + t] = src[f][t];
+      else src[f][t] = ck[off + t];
+    }
+    off += len[f];
+  }
+}
+
+template <typename T>
+void launch_ckpt_copy(const PropArgs<T>& a, int batch, int m, int to_ckpt, cudaStream_t s) {
+  ckpt_copy_kernel<T><<<dim3(128, batch), 256, 0, s>>>(a, batch, m, to_ckpt);
 }
 
 template <typename T>
@@ -333,7 +366,9 @@ void launch_gather(const PropArgs<T>& a, int batch, cudaStream_t s) {
   template void launch_row<T>(const PropArgs<T>&, int, int, cudaStream_t);        \
   template void launch_col<T>(const PropArgs<T>&, int, int, cudaStream_t);        \
   template void launch_gather<T>(const PropArgs<T>&, int, cudaStream_t);                \
-  template void launch_set_io<T>(IoPtrs<T>*, const T*, T*, const T*, T*, cudaStream_t);
+  template void launch_set_io<T>(IoPtrs<T>*, const T*, T*, const T*, T*, T*, cudaStream_t);  \
+  template long long ckpt_elems<T>(const PropArgs<T>&);                                       \
+  template void launch_ckpt_copy<T>(const PropArgs<T>&, int, int, int, cudaStream_t);
 QPAT_INST(float)
 QPAT_INST(double)
 

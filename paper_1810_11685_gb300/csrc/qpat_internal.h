@@ -43,6 +43,7 @@ struct IoPtrs {
   T* data;                // [B][nt][ns] (forward output)
   const T* w;             // [B][nt][ns] (adjoint input)
   T* p0adj;               // [B][N] (adjoint output)
+  T* ckpt;                // forward-state checkpoints (optional)
 };
 
 template <typename T>
@@ -105,7 +106,14 @@ void launch_col(const PropArgs<T>& a, int phase, int batch, cudaStream_t s);
 template <typename T>
 void launch_gather(const PropArgs<T>& a, int batch, cudaStream_t s);
 template <typename T>
-void launch_set_io(IoPtrs<T>* dst, const T* p0, T* data, const T* w, T* p0adj, cudaStream_t s);
+void launch_set_io(IoPtrs<T>* dst, const T* p0, T* data, const T* w, T* p0adj, T* ckpt, cudaStream_t s);
+// Elements (of T) of one forward-state checkpoint of one problem: v_x, v_y,
+// rho_x, rho_y and the sampling buffer (5 grids) plus the two spectral slots.
+template <typename T>
+__host__ __device__ long long ckpt_elems(const PropArgs<T>& a);
+// store (to_ckpt = 1) or restore the state of all problems at checkpoint m
+template <typename T>
+void launch_ckpt_copy(const PropArgs<T>& a, int batch, int m, int to_ckpt, cudaStream_t s);
 // length-specialised passes (fast_kernels.cuh), one translation unit per length
 template <typename T, int L>
 void launch_row_fast_len(const PropArgs<T>& a, int ph, int batch, cudaStream_t s);

@@ -1,0 +1,102 @@
+"""Differentiation through the CUDA path: the torch.autograd.Function over
+P-hat = H_a H_o[mu] against the oracle's J^T w, against central finite
+differences of the GPU forward on random directions, in forward mode, and
+the forward-state checkpoints (resuming from any checkpoint reproduces the
+series bit for bit)."""
+import numpy as np
+import pytest
+
+import phantoms
+from oracle import qpat
+from gpu_helpers import make_pair, rel_l2, to_gpu, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def problem(n=24, pml=8, nt=40, seed=31):
+    return phantoms.small(n=n, pml=pml, nt=nt, n_sensors=12, seed=seed)
+
+
+def test_backward_matches_oracle_vjp():
+    from paper_1810_11685_gb300.autograd import qpat_data
+    w = problem()
+    ctx, S = make_pair(w, "fp64")
+    mu = phantoms.optical_absorption(w)
+    kappa = phantoms.optical_diffusion(w)
+    W = phantoms.random_field((w.nt, w.n_sensors), 3)
+    mu_g = to_gpu(mu, torch.float64).requires_grad_(True)
+    data = qpat_data(ctx, mu_g, 0b0001)
+    loss = (data[0] * to_gpu(W, torch.float64)).sum()
+    loss.backward()
+    assert rel_l2(to_np(mu_g.grad), qpat.vjp(S, mu, kappa, 0b0001, W)) <= 1e-9
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-4), ("fp32", 1e-3)])
+def test_gradient_against_central_differences(prec, tol):
+    """Gradient of 1/2 ||P-hat(mu) - d||^2 (eq. obj_couple) along 32 random
+    directions vs central differences of the GPU objective (FP64 objective
+    accumulation)."""
+    from paper_1810_11685_gb300.autograd import qpat_data
+    w = problem(seed=7)
+    ctx, _ = make_pair(w, prec)
+    mu = to_gpu(phantoms.optical_absorption(w), torch.float64)
+    d = ctx.forward(mu * 1.05, 0b0100)[0].double()
+
+    def objective(m):
+        r = qpat_data(ctx, m, 0b0100)[0].double() - d
+        return 0.5 * (r * r).sum()
+
+    m = mu.clone().requires_grad_(True)
+    objective(m).backward()
+    g = m.grad.clone()
+    rng = np.random.default_rng(5)
+    errs = []
+    for _ in range(32):
+        v = to_gpu(rng.standard_normal(w.interior_shape), torch.float64)
+        eps = 1e-3 * float(torch.linalg.norm(mu) / torch.linalg.norm(v))
+        fd = (objective(mu + eps * v) - objective(mu - eps * v)) / (2 * eps)
+        an = float((g * v).sum())
+        errs.append(abs(float(fd) - an) / max(abs(an), 1e-300))
+    assert np.median(errs) <= tol, errs
+
+
+def test_forward_mode_matches_jvp_and_oracle():
+    from paper_1810_11685_gb300.autograd import qpat_data
+    w = problem(seed=9)
+    ctx, S = make_pair(w, "fp64")
+    mu = phantoms.optical_absorption(w)
+    v = phantoms.random_field(w.interior_shape, 2)
+    import torch.autograd.forward_ad as fwAD
+    with fwAD.dual_level():
+        dual = fwAD.make_dual(to_gpu(mu, torch.float64), to_gpu(v, torch.float64))
+        out = qpat_data(ctx, dual, 0b0010)
+        tangent = fwAD.unpack_dual(out).tangent
+    ref = qpat.jvp(S, mu, phantoms.optical_diffusion(w), 0b0010, v)
+    assert rel_l2(to_np(tangent)[0], ref) <= 1e-9
+
+
+def test_acoustic_function_adjoint():
+    from paper_1810_11685_gb300.autograd import acoustic
+    w = problem(seed=11)
+    ctx, _ = make_pair(w, "fp64")
+    p0 = to_gpu(phantoms.random_field(w.interior_shape, 1), torch.float64).requires_grad_(True)
+    W = to_gpu(phantoms.random_field((w.nt, w.n_sensors), 2), torch.float64)
+    (acoustic(ctx, p0)[0] * W).sum().backward()
+    assert rel_l2(to_np(p0.grad), to_np(ctx.acoustic_adjoint(W))[0]) <= 1e-14
+
+
+@pytest.mark.parametrize("prec,lossless", [("fp32", False), ("fp64", False), ("fp32", True)])
+def test_checkpoint_resume_reproduces_series(prec, lossless):
+    w = phantoms.small(n=40, pml=8, nt=50, n_sensors=10, seed=12, lossless=lossless)
+    ctx, _ = make_pair(w, prec, max_batch=2)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    p0 = torch.stack([to_gpu(phantoms.smooth_p0(w, s), dt) for s in range(2)])
+    full = ctx.acoustic_forward(p0)
+    K = 7
+    data, ck = ctx.acoustic_forward_ckpt(p0, K)
+    assert torch.equal(data, full)
+    for m in range(0, (w.nt - 1) // K):
+        out = ctx.acoustic_resume(ck, K, m, batch=2)
+        first = (m + 1) * K
+        assert torch.equal(out[:, first:], full[:, first:]), m
