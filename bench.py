@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--batch", type=int, default=8, help="independent problems per step")
     p.add_argument("--nt", type=int, default=None, help="override Nt (default: workload's 2000)")
     p.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/roofline/cpu legs")
+    p.add_argument("--workload", default="c2", choices=["c2", "c4"],
+                   help="c2: the 576^2 forward+adjoint workload (default); c4: 48 Jacobian-vector "
+                        "products over 288^2/432^2/576^2 grids in one graph (diagnostic line)")
     return p.parse_args()
 
 
@@ -355,8 +358,48 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_c4(args):
+    """48 acoustic propagations of the Newton inner-loop mix: 16 problems on
+    each of the 256^2, 384^2 and 512^2 interiors (288^2, 432^2, 576^2 FFT
+    grids), Nt chosen so the background wave crosses the interior 1.5 times,
+    all in one CUDA graph (qpat_group_propagate)."""
+    import torch
+    from paper_1810_11685_gb300.binding import Group, context_from_workload
+    ws = phantoms.c4_workloads()
+    ctxs, p0s, cells = [], [], 0
+    for w in ws:
+        c, _, _ = phantoms.acoustic_medium(w)
+        nt = args.nt or phantoms.c4_nt(w, c)
+        ctx = context_from_workload(w, precision="fp32", max_batch=16, nt=nt)
+        ctx.autotune(batch=16, steps=20)
+        ctxs.append(ctx)
+        p0s.append(torch.as_tensor(phantoms.random_field((16,) + w.interior_shape, 7), dtype=torch.float32,
+                                   device="cuda"))
+        cells += 16 * w.grid * w.grid * nt
+    g = Group(ctxs)
+    for _ in range(max(3, args.warmup)):
+        g.acoustic_forward(p0s)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record()
+        g.acoustic_forward(p0s)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    line = {"metric": "jvp cell-steps/s (48 problems, 3 grids, one graph)", "value": cells * args.steps / (t_ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": t_ms / args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c4: 16 x 288^2 + 16 x 432^2 + 16 x 576^2 FFT grids, forward per problem",
+                       "nt": [c.nt for c in ctxs]}, "impl": "ours"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.impl == "ours" and args.workload == "c4":
+        run_c4(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -175,6 +175,31 @@ qpat_status qpat_acoustic_forward_ckpt(qpat_ctx* ctx, int batch, const void* p0,
                                        void* ckpt);
 qpat_status qpat_acoustic_resume(qpat_ctx* ctx, int batch, const void* ckpt, int K, int m, void* data);
 
+/* Groups: propagate several contexts (e.g. uneven grids of one Newton
+ * inner loop) concurrently in one CUDA graph, each context's time loop a
+ * parallel branch.  Contexts must live on one device and outlive the group.
+ * Group calls enqueue on `stream` and make it each member's stream.
+ * qpat_group_propagate: dir 0 = H_a (in: p0, out: data), dir 1 = H_a^* (in:
+ *   data, out: p0_adj), per member i with batches[i] problems (0 = skip);
+ *   the graph is captured on the first call with a given batches tuple.
+ * qpat_group_jvp: qpat_jvp for every member (diffusion solves per member,
+ *   synchronising), then one graph launch for all acoustic forwards. */
+typedef struct qpat_group qpat_group;
+qpat_status qpat_group_create(int n, qpat_ctx* const* ctxs, qpat_group** out);
+qpat_status qpat_group_destroy(qpat_group* group);
+qpat_status qpat_group_propagate(qpat_group* group, int dir, const int* batches, const void* const* in,
+                                 void* const* out, void* stream);
+qpat_status qpat_group_jvp(qpat_group* group, const int* batches, const double* const* mu,
+                           const double* const* phi0, const double* const* dmu, unsigned illum,
+                           void* const* dP, void* stream);
+
+/* Autotuner: time a `steps`-step forward + adjoint of `batch` problems with
+ * every supported choice of pass kernels (specialised or generic row passes,
+ * specialised or generic column passes) and keep the fastest for this
+ * context; *choice = bit 0 rows specialised, bit 1 columns specialised.
+ * Synchronises; allocates and frees temporary buffers. */
+qpat_status qpat_autotune(qpat_ctx* ctx, int batch, int steps, int* choice);
+
 /* FP64 inner products <a_b, c_b> of two device prec vectors [batch][len]
  * with compensated (Neumaier) accumulation; out: host double [batch].
  * Synchronises. */

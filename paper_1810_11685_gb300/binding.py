@@ -80,6 +80,11 @@ def load():
         "qpat_dot": [vp, i, ll, vp, vp, ctypes.POINTER(d)],
         "qpat_get_stats": [vp, ctypes.POINTER(ll)],
         "qpat_ckpt_bytes": [vp, i, i, ctypes.POINTER(ll)],
+        "qpat_group_create": [i, vp, ctypes.POINTER(vp)],
+        "qpat_group_destroy": [vp],
+        "qpat_group_propagate": [vp, i, vp, vp, vp, vp],
+        "qpat_group_jvp": [vp, vp, vp, vp, vp, ctypes.c_uint, vp, vp],
+        "qpat_autotune": [vp, i, i, ctypes.POINTER(i)],
         "qpat_acoustic_forward_ckpt": [vp, i, vp, vp, i, vp],
         "qpat_acoustic_resume": [vp, i, vp, i, i, vp],
         "qpat_profile": [vp, i],
@@ -265,6 +270,14 @@ class Context:
         _check(self._ptr, self._lib.qpat_acoustic_resume(self._ptr, int(batch), _ptr(ckpt), int(K), int(m), _ptr(out)))
         return out
 
+    def autotune(self, batch=1, steps=40):
+        """Pick specialised vs generic passes per axis by timing; returns
+        {"fast_rows": bool, "fast_cols": bool}."""
+        ch = ctypes.c_int()
+        self._stream()
+        _check(self._ptr, self._lib.qpat_autotune(self._ptr, int(batch), int(steps), ctypes.byref(ch)))
+        return {"fast_rows": bool(ch.value & 1), "fast_cols": bool(ch.value & 2)}
+
     def da_solve(self, mu, illum):
         import torch
         mu = self._in(mu, torch.float64, (self.n1, self.n0))
@@ -318,6 +331,69 @@ class Context:
         self._stream()
         _check(self._ptr, self._lib.qpat_dot(self._ptr, B, L, _ptr(a), _ptr(b), out))
         return list(out)
+
+
+class Group:
+    """Several contexts (e.g. the uneven grids of a Newton inner loop)
+    propagated concurrently in one captured CUDA graph (``qpat_group_*``)."""
+
+    def __init__(self, ctxs):
+        self._lib = load()
+        self.ctxs = list(ctxs)
+        arr = (ctypes.c_void_p * len(self.ctxs))(*[c._ptr.value for c in self.ctxs])
+        out = ctypes.c_void_p()
+        _check(None, self._lib.qpat_group_create(len(self.ctxs), arr, ctypes.byref(out)))
+        self._ptr = out
+
+    def close(self):
+        if getattr(self, "_ptr", None):
+            self._lib.qpat_group_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _run(self, dir_, ins, outs):
+        import torch
+        n = len(self.ctxs)
+        batches = (ctypes.c_int * n)(*[0 if t is None else t.shape[0] for t in ins])
+        pin = (ctypes.c_void_p * n)(*[_ptr(t) for t in ins])
+        pout = (ctypes.c_void_p * n)(*[_ptr(t) for t in outs])
+        st = self._lib.qpat_group_propagate(self._ptr, dir_, batches, pin, pout,
+                                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if st != 0:
+            raise QpatError(st, self._lib.qpat_last_error(self.ctxs[0]._ptr).decode())
+        return outs
+
+    def acoustic_forward(self, p0s):
+        """H_a of every member: p0s[i] is [B_i][n1][n0] (or None to skip)."""
+        ins = [None if p is None else c._in(p, c.dtype, (c.n1, c.n0)) for c, p in zip(self.ctxs, p0s)]
+        outs = [None if p is None else c._empty(p.shape[0], c.nt, c.ns) for c, p in zip(self.ctxs, ins)]
+        return self._run(0, ins, outs)
+
+    def acoustic_adjoint(self, datas):
+        ins = [None if d is None else c._in(d, c.dtype, (c.nt, c.ns)) for c, d in zip(self.ctxs, datas)]
+        outs = [None if d is None else c._empty(d.shape[0], c.n1, c.n0) for c, d in zip(self.ctxs, ins)]
+        return self._run(1, ins, outs)
+
+    def jvp(self, mus, dmus, illum, phi0s=None):
+        import torch
+        n = len(self.ctxs)
+        mus = [c._in(m, torch.float64, (c.n1, c.n0)) for c, m in zip(self.ctxs, mus)]
+        dmus = [c._in(d, torch.float64, (c.n1, c.n0)) for c, d in zip(self.ctxs, dmus)]
+        phis = [None] * n if phi0s is None else [c._in(p, torch.float64, (c.n1, c.n0)) for c, p in zip(self.ctxs, phi0s)]
+        outs = [c._empty(d.shape[0], c.nt, c.ns) for c, d in zip(self.ctxs, dmus)]
+        arr = lambda ts: (ctypes.c_void_p * n)(*[_ptr(t) for t in ts])
+        batches = (ctypes.c_int * n)(*[d.shape[0] for d in dmus])
+        st = self._lib.qpat_group_jvp(self._ptr, batches, arr(mus), arr(phis) if phi0s is not None else None,
+                                      arr(dmus), int(illum), arr(outs),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if st != 0:
+            raise QpatError(st, self._lib.qpat_last_error(self.ctxs[0]._ptr).decode())
+        return outs
 
 
 # C-ABI-named wrappers -------------------------------------------------------

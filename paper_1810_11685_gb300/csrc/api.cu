@@ -653,23 +653,38 @@ qpat_status qpat_forward(qpat_ctx* c, int batch, const double* mu, unsigned illu
   return qpat_acoustic_forward(c, batch, c->tw_p0, data);
 }
 
-qpat_status qpat_jvp(qpat_ctx* c, int batch, const double* mu, const double* phi0, const double* dmu, unsigned illum,
-                     void* dP) {
-  qpat_status st = check_batch(c, batch);
-  if (st != QPAT_OK) return st;
-  if (!mu || !dmu || !dP) return fail(c, QPAT_EINVAL, "null buffer");
+}  // extern "C"
+
+namespace {
+// J_o dmu into the context's heating buffer: dh = dmu o phi0 + mu o dphi with
+// A(mu) dphi = -h^2 dmu o phi0 (eq. dh_des).
+qpat_status jvp_heating(qpat_ctx* c, int batch, const double* mu, const double* phi0, const double* dmu,
+                        unsigned illum) {
   const int N = (int)c->N;
+  qpat_status st;
   if (!phi0) {
     st = qpat_da_solve(c, batch, mu, illum, c->d_phi);
     if (st != QPAT_OK) return st;
     phi0 = c->d_phi;
   }
-  // A dphi = -h^2 dmu o phi0 (eq. dh_des)
   QCK(da_hadamard(batch, N, -c->dx * c->dx, dmu, phi0, c->d_rhs, c->stream));
   st = solve_da(c, batch, mu, c->d_rhs, c->d_tmp);
   if (st != QPAT_OK) return st;
   if (c->prec == QPAT_FP32) QCK(da_heating_T<float>(batch, N, dmu, phi0, mu, c->d_tmp, (float*)c->tw_p0, c->stream));
   else QCK(da_heating_T<double>(batch, N, dmu, phi0, mu, c->d_tmp, (double*)c->tw_p0, c->stream));
+  return QPAT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qpat_status qpat_jvp(qpat_ctx* c, int batch, const double* mu, const double* phi0, const double* dmu, unsigned illum,
+                     void* dP) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!mu || !dmu || !dP) return fail(c, QPAT_EINVAL, "null buffer");
+  st = jvp_heating(c, batch, mu, phi0, dmu, illum);
+  if (st != QPAT_OK) return st;
   return qpat_acoustic_forward(c, batch, c->tw_p0, dP);
 }
 
@@ -736,6 +751,202 @@ qpat_status qpat_acoustic_resume(qpat_ctx* c, int batch, const void* ckpt, int K
   return c->prec == QPAT_FP32
              ? run_ckpt<float>(c, batch, nullptr, (float*)data, (float*)const_cast<void*>(ckpt), K, m)
              : run_ckpt<double>(c, batch, nullptr, (double*)data, (double*)const_cast<void*>(ckpt), K, m);
+}
+
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Groups: several contexts (e.g. different grids) propagated concurrently in
+// one CUDA graph, each context's time loop a parallel branch.
+// ---------------------------------------------------------------------------
+struct qpat_group {
+  std::vector<qpat_ctx*> ctxs;
+  cudaStream_t cap = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  std::map<std::vector<int>, std::pair<cudaGraphExec_t, long long>> graphs;
+};
+
+namespace {
+
+template <typename T>
+void set_io_for(qpat_ctx* c, int dir, const void* in, void* out, cudaStream_t s) {
+  PropArgs<T>& a = args<T>(c);
+  IoPtrs<T>* io = const_cast<IoPtrs<T>*>(a.io);
+  if (dir == 0) launch_set_io<T>(io, (const T*)in, (T*)out, nullptr, nullptr, nullptr, s);
+  else launch_set_io<T>(io, nullptr, nullptr, (const T*)in, (T*)out, nullptr, s);
+}
+
+long long seq_any(qpat_ctx* c, int dir, int batch, cudaStream_t s) {
+  if (c->prec == QPAT_FP32) return dir == 0 ? seq_forward<float>(c, batch, s) : seq_adjoint<float>(c, batch, s);
+  return dir == 0 ? seq_forward<double>(c, batch, s) : seq_adjoint<double>(c, batch, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+qpat_status qpat_group_create(int n, qpat_ctx* const* ctxs, qpat_group** out) {
+  if (!out || n < 1 || !ctxs) return QPAT_EINVAL;
+  *out = nullptr;
+  qpat_group* g = new qpat_group();
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) { delete g; return QPAT_EINVAL; }
+    g->ctxs.push_back(ctxs[i]);
+  }
+  if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) != cudaSuccess) {
+    delete g;
+    return QPAT_ECUDA;
+  }
+  g->join.resize(n);
+  for (int i = 0; i < n; ++i) {
+    if (cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming) != cudaSuccess) return QPAT_ECUDA;
+    if (!ctxs[i]->cap_stream && cudaStreamCreateWithFlags(&ctxs[i]->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return QPAT_ECUDA;
+  }
+  *out = g;
+  return QPAT_OK;
+}
+
+qpat_status qpat_group_destroy(qpat_group* g) {
+  if (!g) return QPAT_OK;
+  cudaStreamSynchronize(g->cap);
+  for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second.first);
+  for (cudaEvent_t e : g->join) cudaEventDestroy(e);
+  if (g->fork) cudaEventDestroy(g->fork);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  delete g;
+  return QPAT_OK;
+}
+
+qpat_status qpat_group_propagate(qpat_group* g, int dir, const int* batches, const void* const* in, void* const* out,
+                                 void* stream) {
+  if (!g || !batches || !in || !out || (dir != 0 && dir != 1)) return QPAT_EINVAL;
+  const int n = (int)g->ctxs.size();
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> key{dir};
+  for (int i = 0; i < n; ++i) {
+    qpat_ctx* c = g->ctxs[i];
+    if (batches[i] < 0 || batches[i] > c->maxb) return fail(c, QPAT_EINVAL, "group batch out of range");
+    if (batches[i] > 0 && (!in[i] || !out[i])) return fail(c, QPAT_EINVAL, "null group buffer");
+    if (c->prof_phase >= 0) return fail(c, QPAT_EINVAL, "profiling is not available in group calls");
+    key.push_back(batches[i]);
+  }
+  for (int i = 0; i < n; ++i) {
+    qpat_ctx* c = g->ctxs[i];
+    c->stream = s;
+    if (batches[i] == 0) continue;
+    if (c->prec == QPAT_FP32) set_io_for<float>(c, dir, in[i], out[i], s);
+    else set_io_for<double>(c, dir, in[i], out[i], s);
+  }
+  auto it = g->graphs.find(key);
+  if (it == g->graphs.end()) {
+    qpat_ctx* c0 = g->ctxs[0];
+    cudaError_t e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "group capture");
+    long long kernels = 0;
+    cudaEventRecord(g->fork, g->cap);
+    for (int i = 0; i < n; ++i) {
+      if (batches[i] == 0) continue;
+      qpat_ctx* c = g->ctxs[i];
+      cudaStreamWaitEvent(c->cap_stream, g->fork, 0);
+      kernels += seq_any(c, dir, batches[i], c->cap_stream);
+      cudaEventRecord(g->join[i], c->cap_stream);
+      cudaStreamWaitEvent(g->cap, g->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(g->cap, &graph);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "group capture end");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "group graph instantiation");
+    it = g->graphs.emplace(key, std::make_pair(ex, kernels)).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second.first, s);
+  if (e != cudaSuccess) return cuda_fail(g->ctxs[0], e, "group graph launch");
+  g->ctxs[0]->launches += it->second.second;
+  return QPAT_OK;
+}
+
+qpat_status qpat_group_jvp(qpat_group* g, const int* batches, const double* const* mu, const double* const* phi0,
+                           const double* const* dmu, unsigned illum, void* const* dP, void* stream) {
+  if (!g || !batches || !mu || !dmu || !dP) return QPAT_EINVAL;
+  const int n = (int)g->ctxs.size();
+  std::vector<const void*> in(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    qpat_ctx* c = g->ctxs[i];
+    c->stream = (cudaStream_t)stream;
+    if (batches[i] == 0) continue;
+    qpat_status st = check_batch(c, batches[i]);
+    if (st != QPAT_OK) return st;
+    st = jvp_heating(c, batches[i], mu[i], phi0 ? phi0[i] : nullptr, dmu[i], illum);
+    if (st != QPAT_OK) return st;
+    in[i] = c->tw_p0;
+  }
+  return qpat_group_propagate(g, 0, batches, in.data(), dP, stream);
+}
+
+qpat_status qpat_autotune(qpat_ctx* c, int batch, int steps, int* choice) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  const int elt = c->prec == QPAT_FP32 ? 4 : 8;
+  const bool rows_ok = !c->cfg.generic_fft && fast_rows_supported(c->nx, elt);
+  const bool cols_ok = !c->cfg.generic_fft && fast_cols_supported(c->ny, elt);
+  const int nt_saved = c->nt;
+  const int nt_try = std::max(2, std::min(steps, nt_saved));
+  const size_t esz = elt;
+  // The kernels address the sensor series with the context's full nt as
+  // the batch stride, so the tuning buffer has the full [batch][nt][ns]
+  // shape even though only the first nt_try samples are produced.
+  void *p0 = nullptr, *data = nullptr;
+  const size_t data_bytes = (size_t)batch * nt_saved * c->ns * esz;
+  QCK(cudaMalloc(&p0, (size_t)batch * c->N * esz));
+  QCK(cudaMalloc(&data, data_bytes));
+  QCK(cudaMemsetAsync(p0, 0, (size_t)batch * c->N * esz, c->stream));
+  QCK(cudaMemsetAsync(data, 0, data_bytes, c->stream));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_choice = 0;
+  c->nt = nt_try;
+  for (int cand = 0; cand < 4; ++cand) {
+    const int fr = cand & 1, fc = (cand >> 1) & 1;
+    if ((fr && !rows_ok) || (fc && !cols_ok)) continue;
+    c->pf.fast_rows = c->pd.fast_rows = fr;
+    c->pf.fast_cols = c->pd.fast_cols = fc;
+    float total = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {   // first repetition warms up
+      if (c->prec == QPAT_FP32) set_io_for<float>(c, 0, p0, data, c->stream);
+      else set_io_for<double>(c, 0, p0, data, c->stream);
+      cudaEventRecord(e0, c->stream);
+      seq_any(c, 0, batch, c->stream);
+      if (c->prec == QPAT_FP32) set_io_for<float>(c, 1, data, p0, c->stream);
+      else set_io_for<double>(c, 1, data, p0, c->stream);
+      seq_any(c, 1, batch, c->stream);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep == 1) total = ms;
+    }
+    if (total < best) { best = total; best_choice = cand; }
+  }
+  c->nt = nt_saved;
+  c->pf.fast_rows = c->pd.fast_rows = best_choice & 1;
+  c->pf.fast_cols = c->pd.fast_cols = (best_choice >> 1) & 1;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  c->graphs.clear();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(p0);
+  cudaFree(data);
+  QCK(cudaGetLastError());
+  if (choice) *choice = best_choice;
+  return QPAT_OK;
 }
 
 qpat_status qpat_get_stats(const qpat_ctx* c, long long out[2]) {
