@@ -16,8 +16,9 @@
  * the exact discrete transpose (Section 3.2.4, Lemma 2, eq. t41).
  *
  * Conventions (all entry points):
- *  - Grids are 2D.  Arrays are row-major with x fastest: a full-grid field
- *    is [ny][nx], an interior field is [n[1]][n[0]].  The FFT grid is the
+ *  - Grids are 2D, or 3D when qpat_config.n2 > 0.  Arrays are row-major with x
+ *    fastest: a full-grid field is [ny][nx] ([nz][ny][nx] in 3D), an interior
+ *    field is [n[1]][n[0]] ([n2][n[1]][n[0]]).  The FFT grid is the
  *    interior plus `pml` nodes on every side (the PML is added outside the
  *    stated grid, Section 3.2.2).  Node j along an axis of N nodes sits at
  *    x = (j - (N - 1)/2) * dx.
@@ -76,6 +77,9 @@ typedef struct {
                           length-specialised pass exists for the extent */
   int no_graphs;       /* 1: launch every pass directly instead of replaying a
                           CUDA graph of the time loop captured on first use */
+  int n2;              /* interior nodes along z: > 0 makes the problem 3D (grids
+                          [nz][ny][nx], sensors [ns][3], six illumination sides
+                          4: z low, 5: z high, gamma_d default 1/4) */
 } qpat_config;
 
 /* Medium, host memory, FP64, read during qpat_create only.

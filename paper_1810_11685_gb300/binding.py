@@ -39,7 +39,7 @@ class qpat_config(ctypes.Structure):
                 ("pml_alpha", ctypes.c_double), ("y", ctypes.c_double), ("lossless", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("gamma_d", ctypes.c_double),
                 ("pcg_max_iter", ctypes.c_int), ("pcg_tol", ctypes.c_double),
-                ("generic_fft", ctypes.c_int), ("no_graphs", ctypes.c_int)]
+                ("generic_fft", ctypes.c_int), ("no_graphs", ctypes.c_int), ("n2", ctypes.c_int)]
 
 
 class qpat_medium(ctypes.Structure):
@@ -136,11 +136,15 @@ class Context:
         c = _host(c)
         rho = _host(rho)
         kappa = _host(kappa)
-        sensors = _host(sensors).reshape(-1, 2)
-        self.ny, self.nx = c.shape
-        self.n0, self.n1 = kappa.shape[1], kappa.shape[0]
+        self.dim = c.ndim
+        sensors = _host(sensors).reshape(-1, self.dim)
+        self.grid_shape = c.shape
+        self.interior_shape = kappa.shape
+        self.ny, self.nx = c.shape[-2], c.shape[-1]
+        self.n0, self.n1 = kappa.shape[-1], kappa.shape[-2]
         cfg = qpat_config()
         cfg.n[0], cfg.n[1] = self.n0, self.n1
+        cfg.n2 = kappa.shape[0] if self.dim == 3 else 0
         cfg.pml, cfg.dx, cfg.dt, cfg.nt = int(pml), float(dx), float(dt), int(nt)
         cfg.c_ref, cfg.pml_alpha, cfg.y = float(c_ref), float(pml_alpha), float(y)
         cfg.lossless, cfg.max_batch = int(bool(lossless)), int(max_batch)
@@ -158,7 +162,7 @@ class Context:
         self.dtype = torch.float32 if precision == "fp32" else torch.float64
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nt, self.ns, self.max_batch = int(nt), sensors.shape[0], int(max_batch)
-        self.N = self.n0 * self.n1
+        self.N = int(np.prod(self.interior_shape))
         self.dx = float(dx)
         out = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -231,7 +235,7 @@ class Context:
 
     # -- entry points ----------------------------------------------------
     def acoustic_forward(self, p0, out=None):
-        p0 = self._in(p0, self.dtype, (self.n1, self.n0))
+        p0 = self._in(p0, self.dtype, self.interior_shape)
         B = p0.shape[0]
         out = self._empty(B, self.nt, self.ns) if out is None else out
         self._stream()
@@ -241,7 +245,7 @@ class Context:
     def acoustic_adjoint(self, data, out=None):
         data = self._in(data, self.dtype, (self.nt, self.ns))
         B = data.shape[0]
-        out = self._empty(B, self.n1, self.n0) if out is None else out
+        out = self._empty(B, *self.interior_shape) if out is None else out
         self._stream()
         _check(self._ptr, self._lib.qpat_acoustic_adjoint(self._ptr, B, _ptr(data), _ptr(out)))
         return out
@@ -255,7 +259,7 @@ class Context:
         """H_a that also stores the forward state every K loop iterations;
         returns (data, checkpoint buffer)."""
         import torch
-        p0 = self._in(p0, self.dtype, (self.n1, self.n0))
+        p0 = self._in(p0, self.dtype, self.interior_shape)
         B = p0.shape[0]
         out = self._empty(B, self.nt, self.ns) if out is None else out
         ck = torch.empty(self.ckpt_bytes(B, K), dtype=torch.uint8, device=self.device)
@@ -280,28 +284,28 @@ class Context:
 
     def da_solve(self, mu, illum):
         import torch
-        mu = self._in(mu, torch.float64, (self.n1, self.n0))
-        out = self._empty(mu.shape[0], self.n1, self.n0, dtype=torch.float64)
+        mu = self._in(mu, torch.float64, self.interior_shape)
+        out = self._empty(mu.shape[0], *self.interior_shape, dtype=torch.float64)
         self._stream()
         _check(self._ptr, self._lib.qpat_da_solve(self._ptr, mu.shape[0], _ptr(mu), int(illum), _ptr(out)))
         return out
 
     def forward(self, mu, illum, return_phi=False):
         import torch
-        mu = self._in(mu, torch.float64, (self.n1, self.n0))
+        mu = self._in(mu, torch.float64, self.interior_shape)
         B = mu.shape[0]
         out = self._empty(B, self.nt, self.ns)
-        phi = self._empty(B, self.n1, self.n0, dtype=torch.float64) if return_phi else None
+        phi = self._empty(B, *self.interior_shape, dtype=torch.float64) if return_phi else None
         self._stream()
         _check(self._ptr, self._lib.qpat_forward(self._ptr, B, _ptr(mu), int(illum), _ptr(out), _ptr(phi)))
         return (out, phi) if return_phi else out
 
     def jvp(self, mu, dmu, illum, phi0=None):
         import torch
-        mu = self._in(mu, torch.float64, (self.n1, self.n0))
-        dmu = self._in(dmu, torch.float64, (self.n1, self.n0))
+        mu = self._in(mu, torch.float64, self.interior_shape)
+        dmu = self._in(dmu, torch.float64, self.interior_shape)
         if phi0 is not None:
-            phi0 = self._in(phi0, torch.float64, (self.n1, self.n0))
+            phi0 = self._in(phi0, torch.float64, self.interior_shape)
         B = dmu.shape[0]
         out = self._empty(B, self.nt, self.ns)
         self._stream()
@@ -310,12 +314,12 @@ class Context:
 
     def vjp(self, mu, w, illum, phi0=None):
         import torch
-        mu = self._in(mu, torch.float64, (self.n1, self.n0))
+        mu = self._in(mu, torch.float64, self.interior_shape)
         w = self._in(w, self.dtype, (self.nt, self.ns))
         if phi0 is not None:
-            phi0 = self._in(phi0, torch.float64, (self.n1, self.n0))
+            phi0 = self._in(phi0, torch.float64, self.interior_shape)
         B = w.shape[0]
-        out = self._empty(B, self.n1, self.n0, dtype=torch.float64)
+        out = self._empty(B, *self.interior_shape, dtype=torch.float64)
         self._stream()
         _check(self._ptr, self._lib.qpat_vjp(self._ptr, B, _ptr(mu), _ptr(phi0), _ptr(w), int(illum), _ptr(out)))
         return out
@@ -370,21 +374,21 @@ class Group:
 
     def acoustic_forward(self, p0s):
         """H_a of every member: p0s[i] is [B_i][n1][n0] (or None to skip)."""
-        ins = [None if p is None else c._in(p, c.dtype, (c.n1, c.n0)) for c, p in zip(self.ctxs, p0s)]
+        ins = [None if p is None else c._in(p, c.dtype, c.interior_shape) for c, p in zip(self.ctxs, p0s)]
         outs = [None if p is None else c._empty(p.shape[0], c.nt, c.ns) for c, p in zip(self.ctxs, ins)]
         return self._run(0, ins, outs)
 
     def acoustic_adjoint(self, datas):
         ins = [None if d is None else c._in(d, c.dtype, (c.nt, c.ns)) for c, d in zip(self.ctxs, datas)]
-        outs = [None if d is None else c._empty(d.shape[0], c.n1, c.n0) for c, d in zip(self.ctxs, ins)]
+        outs = [None if d is None else c._empty(d.shape[0], *c.interior_shape) for c, d in zip(self.ctxs, ins)]
         return self._run(1, ins, outs)
 
     def jvp(self, mus, dmus, illum, phi0s=None):
         import torch
         n = len(self.ctxs)
-        mus = [c._in(m, torch.float64, (c.n1, c.n0)) for c, m in zip(self.ctxs, mus)]
-        dmus = [c._in(d, torch.float64, (c.n1, c.n0)) for c, d in zip(self.ctxs, dmus)]
-        phis = [None] * n if phi0s is None else [c._in(p, torch.float64, (c.n1, c.n0)) for c, p in zip(self.ctxs, phi0s)]
+        mus = [c._in(m, torch.float64, c.interior_shape) for c, m in zip(self.ctxs, mus)]
+        dmus = [c._in(d, torch.float64, c.interior_shape) for c, d in zip(self.ctxs, dmus)]
+        phis = [None] * n if phi0s is None else [c._in(p, torch.float64, c.interior_shape) for c, p in zip(self.ctxs, phi0s)]
         outs = [c._empty(d.shape[0], c.nt, c.ns) for c, d in zip(self.ctxs, dmus)]
         arr = lambda ts: (ctypes.c_void_p * n)(*[_ptr(t) for t in ts])
         batches = (ctypes.c_int * n)(*[d.shape[0] for d in dmus])

@@ -18,6 +18,7 @@
 
 #include "qpat.h"
 #include "qpat_internal.h"
+#include "prop3d.h"
 
 using namespace qpat;
 
@@ -25,7 +26,8 @@ struct qpat_ctx {
   int prec = QPAT_FP32;
   cudaStream_t stream = nullptr;
   qpat_config cfg{};
-  int nx = 0, ny = 0, nxh = 0, pitch = 0, n0 = 0, n1 = 0, pml = 0, ns = 0, nt = 0, maxb = 1;
+  int dim = 2;
+  int nx = 0, ny = 0, nz = 1, nxh = 0, pitch = 0, n0 = 0, n1 = 0, n2 = 1, pml = 0, ns = 0, nt = 0, maxb = 1;
   long long N = 0, G = 0;
   double dx = 0, dt = 0, c_ref = 0, c_max = 0;
   std::string err;
@@ -33,6 +35,8 @@ struct qpat_ctx {
   std::vector<void*> host_allocs;
   PropArgs<float> pf{};
   PropArgs<double> pd{};
+  Prop3<float> p3f{};
+  Prop3<double> p3d{};
   DAArgs da{};
   PCGWork pcg{};
   int* d_err = nullptr;
@@ -108,6 +112,169 @@ template <>
 PropArgs<float>& args<float>(qpat_ctx* c) { return c->pf; }
 template <>
 PropArgs<double>& args<double>(qpat_ctx* c) { return c->pd; }
+
+template <typename T>
+Prop3<T>& args3(qpat_ctx* c);
+template <>
+Prop3<float>& args3<float>(qpat_ctx* c) { return c->p3f; }
+template <>
+Prop3<double>& args3<double>(qpat_ctx* c) { return c->p3d; }
+
+// Sensor tables for a 2D or 3D node grid: the gather form (2^d corners per
+// sensor, multilinear weights) and the transposed scatter as a deterministic
+// per-row gather over the grid points the sensors touch; rows are indexed
+// k ny + j.
+template <typename T>
+qpat_status build_sensors(qpat_ctx* c, const double* pos, const int** d_sidx, const T** d_sw, const int** d_rowptr,
+                          const int** d_pcol, const int** d_pent, const int** d_esens, const T** d_ew) {
+  const int d = c->dim, nc = 1 << d;
+  const int Nax[3] = {c->nx, c->ny, c->nz};
+  std::vector<int> sidx((size_t)nc * c->ns);
+  std::vector<T> sw((size_t)nc * c->ns);
+  std::vector<std::tuple<int, int, int, double>> ent;   // row, col, sensor, weight
+  for (int s = 0; s < c->ns; ++s) {
+    int base[3] = {0, 0, 0};
+    double frac[3] = {0, 0, 0};
+    for (int ax = 0; ax < d; ++ax) {
+      const double g = pos[d * s + ax] / c->dx + (Nax[ax] - 1) / 2.0;
+      const int j0 = (int)floor(g);
+      const double f = g - j0;
+      if (!(g == g) || j0 < 0 || j0 > Nax[ax] - 1 || (j0 == Nax[ax] - 1 && f > 0))
+        return fail(c, QPAT_EINVAL, "sensor " + std::to_string(s) + " lies outside the grid");
+      base[ax] = j0;
+      frac[ax] = f;
+    }
+    for (int corner = 0; corner < nc; ++corner) {
+      double wgt = 1.0;
+      int idx[3] = {0, 0, 0};
+      for (int ax = 0; ax < d; ++ax) {
+        const int bit = (corner >> ax) & 1;
+        wgt *= bit ? frac[ax] : 1.0 - frac[ax];
+        idx[ax] = std::min(base[ax] + bit, Nax[ax] - 1);
+      }
+      const long long g = ((long long)idx[2] * c->ny + idx[1]) * c->nx + idx[0];
+      sidx[(size_t)nc * s + corner] = (int)g;
+      sw[(size_t)nc * s + corner] = (T)wgt;
+      if (wgt != 0.0) ent.emplace_back(idx[2] * c->ny + idx[1], idx[0], s, wgt);
+    }
+  }
+  std::sort(ent.begin(), ent.end());
+  const int nrows = c->nz * c->ny;
+  std::vector<int> rowptr(nrows + 1, 0), pcol, pent, esens;
+  std::vector<T> ew;
+  int prev_r = -1, prev_c = -1;
+  for (size_t e = 0; e < ent.size(); ++e) {
+    const int r = std::get<0>(ent[e]), col = std::get<1>(ent[e]);
+    if (r != prev_r || col != prev_c) {
+      pcol.push_back(col);
+      pent.push_back((int)e);
+      rowptr[r + 1] += 1;
+      prev_r = r;
+      prev_c = col;
+    }
+    esens.push_back(std::get<2>(ent[e]));
+    ew.push_back((T)std::get<3>(ent[e]));
+  }
+  pent.push_back((int)ent.size());
+  for (int r = 0; r < nrows; ++r) rowptr[r + 1] += rowptr[r];
+  int *a_sidx, *a_rowptr, *a_pcol, *a_pent, *a_esens;
+  T *a_sw, *a_ew;
+  QCK(dalloc(c, &a_sidx, sidx.size() * sizeof(int)));
+  QCK(dalloc(c, &a_sw, sw.size() * sizeof(T)));
+  QCK(dalloc(c, &a_rowptr, rowptr.size() * sizeof(int)));
+  QCK(dalloc(c, &a_pcol, std::max<size_t>(1, pcol.size()) * sizeof(int)));
+  QCK(dalloc(c, &a_pent, pent.size() * sizeof(int)));
+  QCK(dalloc(c, &a_esens, std::max<size_t>(1, esens.size()) * sizeof(int)));
+  QCK(dalloc(c, &a_ew, std::max<size_t>(1, ew.size()) * sizeof(T)));
+  QCK(cudaMemcpy(a_sidx, sidx.data(), sidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  QCK(cudaMemcpy(a_sw, sw.data(), sw.size() * sizeof(T), cudaMemcpyHostToDevice));
+  QCK(cudaMemcpy(a_rowptr, rowptr.data(), rowptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!pcol.empty()) QCK(cudaMemcpy(a_pcol, pcol.data(), pcol.size() * sizeof(int), cudaMemcpyHostToDevice));
+  QCK(cudaMemcpy(a_pent, pent.data(), pent.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!esens.empty()) QCK(cudaMemcpy(a_esens, esens.data(), esens.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!ew.empty()) QCK(cudaMemcpy(a_ew, ew.data(), ew.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *d_sidx = a_sidx; *d_sw = a_sw; *d_rowptr = a_rowptr; *d_pcol = a_pcol; *d_pent = a_pent; *d_esens = a_esens;
+  *d_ew = a_ew;
+  return QPAT_OK;
+}
+
+// 3D device tables + workspace for working precision T.
+template <typename T>
+qpat_status build_context3(qpat_ctx* c, const qpat_medium* med, const double* sensor_xy) {
+  typedef typename V2<T>::t C;
+  Prop3<T>& a = args3<T>(c);
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.nxh = c->nxh; a.pitch = c->pitch; a.pml = c->pml;
+  a.n0 = c->n0; a.n1 = c->n1; a.n2 = c->n2; a.ns = c->ns; a.nt = c->nt;
+  if (!factor_plan(c->nx, a.px) || !factor_plan(c->ny, a.py) || !factor_plan(c->nz, a.pz))
+    return fail(c, QPAT_EINVAL, "FFT extents must factor into 2, 3, 5 and 7");
+  a.cby = a.cbz = 1;
+  for (int cb : {8, 4, 2}) {
+    if (prop3_smem_col<T>(c->ny, cb) <= 100 * 1024 && cb * 4 <= c->nxh) { a.cby = cb; break; }
+  }
+  for (int cb : {8, 4, 2}) {
+    if (prop3_smem_col<T>(c->nz, cb) <= 100 * 1024 && cb * 4 <= c->nxh) { a.cbz = cb; break; }
+  }
+  if (prop3_smem_col<T>(c->ny, a.cby) > 227 * 1024 || prop3_smem_col<T>(c->nz, a.cbz) > 227 * 1024)
+    return fail(c, QPAT_EINVAL, "grid too large for the shared-memory FFT passes");
+  a.dt = (T)c->dt;
+  const long long G = c->G;
+  const int B = c->maxb;
+  Tables3<T> o{};
+  for (T** p : {&o.Cc, &o.rho0, &o.dtrsx, &o.dtrsy, &o.dtrsz, &o.tau, &o.eta}) QCK(dalloc(c, p, G * sizeof(T)));
+  QCK(dalloc(c, &o.ax, c->nx * sizeof(T)));
+  QCK(dalloc(c, &o.asx, c->nx * sizeof(T)));
+  QCK(dalloc(c, &o.ay, c->ny * sizeof(T)));
+  QCK(dalloc(c, &o.asy, c->ny * sizeof(T)));
+  QCK(dalloc(c, &o.az, c->nz * sizeof(T)));
+  QCK(dalloc(c, &o.asz, c->nz * sizeof(T)));
+  const long long KT = (long long)c->nz * c->ny * c->nxh;
+  for (T** p : {&o.kap, &o.kp1, &o.kp2}) QCK(dalloc(c, p, KT * sizeof(T)));
+  QCK(dalloc(c, &o.shxp, c->nxh * sizeof(C)));
+  QCK(dalloc(c, &o.shxm, c->nxh * sizeof(C)));
+  QCK(dalloc(c, &o.shyp, c->ny * sizeof(C)));
+  QCK(dalloc(c, &o.shym, c->ny * sizeof(C)));
+  QCK(dalloc(c, &o.shzp, c->nz * sizeof(C)));
+  QCK(dalloc(c, &o.shzm, c->nz * sizeof(C)));
+  QCK(dalloc(c, &o.twx, c->nx * sizeof(C)));
+  QCK(dalloc(c, &o.twy, c->ny * sizeof(C)));
+  QCK(dalloc(c, &o.twz, c->nz * sizeof(C)));
+  double *dc = nullptr, *drho = nullptr, *dal = nullptr;
+  QCK(cudaMalloc(&dc, G * sizeof(double)));
+  QCK(cudaMalloc(&drho, G * sizeof(double)));
+  QCK(cudaMalloc(&dal, G * sizeof(double)));
+  QCK(cudaMemcpyAsync(dc, med->c, G * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  QCK(cudaMemcpyAsync(drho, med->rho, G * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (!c->cfg.lossless) QCK(cudaMemcpyAsync(dal, med->alpha0_db, G * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  QCK(build_tables3<T>(o, dc, drho, dal, c->nx, c->ny, c->nz, c->nxh, c->pml, c->dx, c->dt, c->c_ref,
+                       c->cfg.pml_alpha, c->cfg.y, c->cfg.lossless, c->stream));
+  QCK(cudaStreamSynchronize(c->stream));
+  cudaFree(dc);
+  cudaFree(drho);
+  cudaFree(dal);
+  a.Cc = o.Cc; a.rho0 = o.rho0; a.dtrsx = o.dtrsx; a.dtrsy = o.dtrsy; a.dtrsz = o.dtrsz; a.tau = o.tau;
+  a.eta = o.eta; a.ax = o.ax; a.asx = o.asx; a.ay = o.ay; a.asy = o.asy; a.az = o.az; a.asz = o.asz;
+  a.kap = o.kap; a.kp1 = o.kp1; a.kp2 = o.kp2;
+  a.shxp = o.shxp; a.shxm = o.shxm; a.shyp = o.shyp; a.shym = o.shym; a.shzp = o.shzp; a.shzm = o.shzm;
+  a.twx = o.twx; a.twy = o.twy; a.twz = o.twz;
+  qpat_status st = build_sensors<T>(c, sensor_xy, &a.sidx, &a.sw, &a.rowptr, &a.pcol, &a.pent, &a.esens, &a.ew);
+  if (st != QPAT_OK) return st;
+  a.gstride = G;
+  a.slot = (long long)c->nz * c->ny * c->pitch;
+  a.sstride = 3 * a.slot;
+  for (T** p : {&a.vx, &a.vy, &a.vz, &a.rx, &a.ry, &a.rz, &a.pbuf}) QCK(dalloc(c, p, (size_t)B * G * sizeof(T)));
+  C* spec;
+  QCK(dalloc(c, &spec, (size_t)B * a.sstride * sizeof(C)));
+  QCK(cudaMemset(spec, 0, (size_t)B * a.sstride * sizeof(C)));
+  a.spec = spec;
+  QCK(dalloc(c, &c->tw_p0, (size_t)B * c->N * sizeof(T)));
+  QCK(dalloc(c, &c->tw_hbar, (size_t)B * c->N * sizeof(T)));
+  IoPtrs<T>* io = nullptr;
+  QCK(dalloc(c, &io, sizeof(IoPtrs<T>)));
+  a.io = io;
+  a.err = c->d_err;
+  prop3_init_attributes<T>();
+  return QPAT_OK;
+}
 
 // Device tables + workspace for working precision T.
 template <typename T>
@@ -392,6 +559,19 @@ long long seq_adjoint(qpat_ctx* c, int batch, cudaStream_t s) {
   return cnt;
 }
 
+// The launch sequence of H_a (dir 0) or H_a^* (dir 1) for the context's
+// dimension and precision, enqueued on s; returns the kernel count.
+long long seq_any(qpat_ctx* c, int dir, int batch, cudaStream_t s) {
+  const bool ll = c->cfg.lossless != 0;
+  if (c->dim == 3) {
+    if (c->prec == QPAT_FP32)
+      return dir == 0 ? seq3_forward<float>(c->p3f, batch, ll, s) : seq3_adjoint<float>(c->p3f, batch, ll, s);
+    return dir == 0 ? seq3_forward<double>(c->p3d, batch, ll, s) : seq3_adjoint<double>(c->p3d, batch, ll, s);
+  }
+  if (c->prec == QPAT_FP32) return dir == 0 ? seq_forward<float>(c, batch, s) : seq_adjoint<float>(c, batch, s);
+  return dir == 0 ? seq_forward<double>(c, batch, s) : seq_adjoint<double>(c, batch, s);
+}
+
 // Run H_a (dir 0) or H_a^* (dir 1) on the caller's buffers.  The launch
 // sequence is captured once per (direction, batch) into a CUDA graph on a
 // private stream and replayed on the context's stream; only a one-thread
@@ -400,13 +580,12 @@ long long seq_adjoint(qpat_ctx* c, int batch, cudaStream_t s) {
 // profiled, the sequence is launched directly.
 template <typename T>
 qpat_status run_prop(qpat_ctx* c, int dir, int batch, const T* p0, T* data, const T* w, T* p0adj) {
-  PropArgs<T>& a = args<T>(c);
-  IoPtrs<T>* io = const_cast<IoPtrs<T>*>(a.io);
+  IoPtrs<T>* io = const_cast<IoPtrs<T>*>(c->dim == 3 ? args3<T>(c).io : args<T>(c).io);
   launch_set_io<T>(io, p0, data, w, p0adj, nullptr, c->stream);
   QCK(cudaGetLastError());
   const bool direct = c->cfg.no_graphs || c->prof_phase >= 0;
   if (direct) {
-    c->launches += dir == 0 ? seq_forward<T>(c, batch, c->stream) : seq_adjoint<T>(c, batch, c->stream);
+    c->launches += seq_any(c, dir, batch, c->stream);
     QCK(cudaGetLastError());
     return QPAT_OK;
   }
@@ -415,7 +594,7 @@ qpat_status run_prop(qpat_ctx* c, int dir, int batch, const T* p0, T* data, cons
   if (it == c->graphs.end()) {
     if (!c->cap_stream) QCK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     QCK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const long long n = dir == 0 ? seq_forward<T>(c, batch, c->cap_stream) : seq_adjoint<T>(c, batch, c->cap_stream);
+    const long long n = seq_any(c, dir, batch, c->cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
@@ -485,22 +664,26 @@ qpat_status qpat_create(const qpat_config* cfg, const qpat_medium* med, const do
   if (cfg->nt < 2) return bad(QPAT_EINVAL, "nt must be at least 2");
   c->n0 = cfg->n[0];
   c->n1 = cfg->n[1];
+  c->dim = cfg->n2 > 0 ? 3 : 2;
+  c->n2 = c->dim == 3 ? cfg->n2 : 1;
   c->pml = cfg->pml;
   c->nx = c->n0 + 2 * c->pml;
   c->ny = c->n1 + 2 * c->pml;
-  if (c->nx % 2 || c->ny % 2) return bad(QPAT_EINVAL, "FFT grid extents must be even");
-  if (c->nx < 8 || c->ny < 8) return bad(QPAT_EINVAL, "FFT grid extents must be at least 8");
+  c->nz = c->dim == 3 ? c->n2 + 2 * c->pml : 1;
+  if (c->nx % 2 || c->ny % 2 || (c->dim == 3 && c->nz % 2)) return bad(QPAT_EINVAL, "FFT grid extents must be even");
+  if (c->nx < 8 || c->ny < 8 || (c->dim == 3 && c->nz < 8))
+    return bad(QPAT_EINVAL, "FFT grid extents must be at least 8");
   c->nxh = c->nx / 2 + 1;
   c->pitch = (c->nxh + 3) / 4 * 4;
-  c->N = (long long)c->n0 * c->n1;
-  c->G = (long long)c->nx * c->ny;
+  c->N = (long long)c->n0 * c->n1 * c->n2;
+  c->G = (long long)c->nx * c->ny * c->nz;
   c->ns = ns;
   c->nt = cfg->nt;
   c->dx = cfg->dx;
   c->dt = cfg->dt;
   c->maxb = cfg->max_batch > 0 ? cfg->max_batch : 1;
   if (!(c->cfg.pml_alpha > 0)) c->cfg.pml_alpha = 2.0;
-  if (!(c->cfg.gamma_d > 0)) c->cfg.gamma_d = 1.0 / M_PI;
+  if (!(c->cfg.gamma_d > 0)) c->cfg.gamma_d = c->dim == 3 ? 0.25 : 1.0 / M_PI;
   if (c->cfg.pcg_max_iter <= 0) c->cfg.pcg_max_iter = 20000;
   if (!(c->cfg.pcg_tol > 0)) c->cfg.pcg_tol = 1e-13;
   if (!c->cfg.lossless) {
@@ -519,8 +702,8 @@ qpat_status qpat_create(const qpat_config* cfg, const qpat_medium* med, const do
     if (!(med->kappa[g] > 0)) return bad(QPAT_EINVAL, "kappa must be positive and finite");
   c->c_max = cmax;
   c->c_ref = cfg->c_ref > 0 ? cfg->c_ref : cmax;
-  if (cmax * c->dt / c->dx > 2.0 / (M_PI * sqrt(2.0)))
-    return bad(QPAT_EUNSTABLE, "c_max dt / dx exceeds 2 / (pi sqrt 2)");
+  if (cmax * c->dt / c->dx > 2.0 / (M_PI * sqrt((double)c->dim)))
+    return bad(QPAT_EUNSTABLE, "c_max dt / dx exceeds 2 / (pi sqrt d)");
 
   cudaError_t e;
 #define QCKC(expr)                                                                  \
@@ -533,8 +716,11 @@ qpat_status qpat_create(const qpat_config* cfg, const qpat_medium* med, const do
   QCKC(cudaMemset(c->d_err, 0, sizeof(int)));
   QCKC(cudaMallocHost(&c->h_err, sizeof(int)));
   c->host_allocs.push_back(c->h_err);
-  qpat_status st = (prec == QPAT_FP32) ? build_context<float>(c, med, sensor_xy)
-                                       : build_context<double>(c, med, sensor_xy);
+  qpat_status st;
+  if (c->dim == 3)
+    st = (prec == QPAT_FP32) ? build_context3<float>(c, med, sensor_xy) : build_context3<double>(c, med, sensor_xy);
+  else
+    st = (prec == QPAT_FP32) ? build_context<float>(c, med, sensor_xy) : build_context<double>(c, med, sensor_xy);
   if (st != QPAT_OK) return bad(st, c->err);
 
   // diffusion solve
@@ -542,17 +728,21 @@ qpat_status qpat_create(const qpat_config* cfg, const qpat_medium* med, const do
   const long long N = c->N;
   c->da.n0 = c->n0;
   c->da.n1 = c->n1;
+  c->da.n2 = c->n2;
+  c->da.dim = c->dim;
   c->da.N = (int)N;
   c->da.h = c->dx;
+  c->da.hd = c->dim == 3 ? c->dx * c->dx * c->dx : c->dx * c->dx;
   c->da.gamma = c->cfg.gamma_d;
-  double *diag0, *cxf, *cyf, *bside, *dkappa;
+  double *diag0, *cxf, *cyf, *czf, *bside, *dkappa;
   QCKC(dalloc(c, &diag0, N * sizeof(double)));
   QCKC(dalloc(c, &cxf, N * sizeof(double)));
   QCKC(dalloc(c, &cyf, N * sizeof(double)));
-  QCKC(dalloc(c, &bside, 4 * N * sizeof(double)));
+  QCKC(dalloc(c, &czf, N * sizeof(double)));
+  QCKC(dalloc(c, &bside, 2 * c->dim * N * sizeof(double)));
   QCKC(dalloc(c, &dkappa, N * sizeof(double)));
   QCKC(cudaMemcpy(dkappa, med->kappa, N * sizeof(double), cudaMemcpyHostToDevice));
-  QCKC(da_setup(c->da, diag0, cxf, cyf, bside, dkappa, c->stream));
+  QCKC(da_setup(c->da, diag0, cxf, cyf, czf, bside, dkappa, c->stream));
   PCGWork& w = c->pcg;
   for (double** p : {&w.x, &w.r, &w.z, &w.p, &w.q, &w.dinv, &w.b}) QCKC(dalloc(c, p, B * N * sizeof(double)));
   QCKC(dalloc(c, &w.partial, (size_t)B * kPartials * 4 * sizeof(double)));
@@ -636,7 +826,8 @@ qpat_status qpat_da_solve(qpat_ctx* c, int batch, const double* mu, unsigned ill
   qpat_status st = check_batch(c, batch);
   if (st != QPAT_OK) return st;
   if (!mu || !phi) return fail(c, QPAT_EINVAL, "null buffer");
-  if (illum == 0 || illum > 15u) return fail(c, QPAT_EINVAL, "illumination mask must select sides 0..3");
+  if (illum == 0 || illum >= (1u << (2 * c->dim)))
+    return fail(c, QPAT_EINVAL, "illumination mask must select sides 0 .. 2d-1");
   return fluence(c, batch, mu, illum, phi);
 }
 
@@ -667,7 +858,7 @@ qpat_status jvp_heating(qpat_ctx* c, int batch, const double* mu, const double* 
     if (st != QPAT_OK) return st;
     phi0 = c->d_phi;
   }
-  QCK(da_hadamard(batch, N, -c->dx * c->dx, dmu, phi0, c->d_rhs, c->stream));
+  QCK(da_hadamard(batch, N, -c->da.hd, dmu, phi0, c->d_rhs, c->stream));
   st = solve_da(c, batch, mu, c->d_rhs, c->d_tmp);
   if (st != QPAT_OK) return st;
   if (c->prec == QPAT_FP32) QCK(da_heating_T<float>(batch, N, dmu, phi0, mu, c->d_tmp, (float*)c->tw_p0, c->stream));
@@ -702,7 +893,7 @@ qpat_status qpat_vjp(qpat_ctx* c, int batch, const double* mu, const double* phi
     phi0 = c->d_phi;
   }
   // A H~ = -h^2 mu o hbar (eq. system_adjoint); g = phi0 o (hbar + H~) (eq. prodtproj)
-  const double sc = -c->dx * c->dx;
+  const double sc = -c->da.hd;
   if (c->prec == QPAT_FP32) QCK(da_adjoint_rhs<float>(batch, N, sc, mu, (const float*)c->tw_hbar, c->d_rhs, c->stream));
   else QCK(da_adjoint_rhs<double>(batch, N, sc, mu, (const double*)c->tw_hbar, c->d_rhs, c->stream));
   st = solve_da(c, batch, mu, c->d_rhs, c->d_tmp);
@@ -739,6 +930,7 @@ qpat_status qpat_acoustic_forward_ckpt(qpat_ctx* c, int batch, const void* p0, v
   qpat_status st = check_batch(c, batch);
   if (st != QPAT_OK) return st;
   if (!p0 || !data || !ckpt || K < 1) return fail(c, QPAT_EINVAL, "bad checkpoint arguments");
+  if (c->dim != 2) return fail(c, QPAT_EINVAL, "checkpointing is implemented for 2D grids");
   return c->prec == QPAT_FP32 ? run_ckpt<float>(c, batch, (const float*)p0, (float*)data, (float*)ckpt, K, -1)
                               : run_ckpt<double>(c, batch, (const double*)p0, (double*)data, (double*)ckpt, K, -1);
 }
@@ -746,6 +938,7 @@ qpat_status qpat_acoustic_forward_ckpt(qpat_ctx* c, int batch, const void* p0, v
 qpat_status qpat_acoustic_resume(qpat_ctx* c, int batch, const void* ckpt, int K, int m, void* data) {
   qpat_status st = check_batch(c, batch);
   if (st != QPAT_OK) return st;
+  if (c->dim != 2) return fail(c, QPAT_EINVAL, "checkpointing is implemented for 2D grids");
   if (!data || !ckpt || K < 1 || m < 0 || m >= (c->nt - 1) / K)
     return fail(c, QPAT_EINVAL, "bad resume arguments (checkpoint index out of range)");
   return c->prec == QPAT_FP32
@@ -772,16 +965,11 @@ namespace {
 
 template <typename T>
 void set_io_for(qpat_ctx* c, int dir, const void* in, void* out, cudaStream_t s) {
-  PropArgs<T>& a = args<T>(c);
-  IoPtrs<T>* io = const_cast<IoPtrs<T>*>(a.io);
+  IoPtrs<T>* io = const_cast<IoPtrs<T>*>(c->dim == 3 ? args3<T>(c).io : args<T>(c).io);
   if (dir == 0) launch_set_io<T>(io, (const T*)in, (T*)out, nullptr, nullptr, nullptr, s);
   else launch_set_io<T>(io, nullptr, nullptr, (const T*)in, (T*)out, nullptr, s);
 }
 
-long long seq_any(qpat_ctx* c, int dir, int batch, cudaStream_t s) {
-  if (c->prec == QPAT_FP32) return dir == 0 ? seq_forward<float>(c, batch, s) : seq_adjoint<float>(c, batch, s);
-  return dir == 0 ? seq_forward<double>(c, batch, s) : seq_adjoint<double>(c, batch, s);
-}
 
 }  // namespace
 
@@ -893,8 +1081,8 @@ qpat_status qpat_autotune(qpat_ctx* c, int batch, int steps, int* choice) {
   qpat_status st = check_batch(c, batch);
   if (st != QPAT_OK) return st;
   const int elt = c->prec == QPAT_FP32 ? 4 : 8;
-  const bool rows_ok = !c->cfg.generic_fft && fast_rows_supported(c->nx, elt);
-  const bool cols_ok = !c->cfg.generic_fft && fast_cols_supported(c->ny, elt);
+  const bool rows_ok = c->dim == 2 && !c->cfg.generic_fft && fast_rows_supported(c->nx, elt);
+  const bool cols_ok = c->dim == 2 && !c->cfg.generic_fft && fast_cols_supported(c->ny, elt);
   const int nt_saved = c->nt;
   const int nt_try = std::max(2, std::min(steps, nt_saved));
   const size_t esz = elt;

@@ -18,36 +18,50 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
 
-__global__ void da_setup_kernel(int n0, int n1, double h, double gam, const double* kappa, double* diag0,
-                                double* cxf, double* cyf, double* bside) {
-  const int N = n0 * n1;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
-    const int i = g % n0, j = g / n0;
-    const double k = kappa[g];
+// Face, Robin and source coefficients of the finite-volume system for a
+// grid of n0 x n1 x n2 cells (n2 = 1 in 2D): an interior face carries
+// kappa_f h^(d-2), a boundary face adds 2 gamma kappa h^(d-1)/(gamma h + kappa)
+// to the diagonal and 2 kappa I h^(d-1)/(gamma h + kappa) to the right-hand side.
+__global__ void da_setup_kernel(int n0, int n1, int n2, int dim, double h, double gam, const double* kappa,
+                                double* diag0, double* cxf, double* cyf, double* czf, double* bside) {
+  const long long N = (long long)n0 * n1 * n2;
+  const double hf = (dim == 3) ? h : 1.0;           // h^(d-2)
+  const double hb = (dim == 3) ? h * h : h;         // h^(d-1)
+  const long long sy = n0, sz = (long long)n0 * n1;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(g % n0), j = (int)((g / n0) % n1), k = (int)(g / sz);
+    const double kc = kappa[g];
     double d = 0.0;
-    if (i > 0) d += harmonic(k, kappa[g - 1]);
-    if (i < n0 - 1) d += harmonic(k, kappa[g + 1]);
-    if (j > 0) d += harmonic(k, kappa[g - n0]);
-    if (j < n1 - 1) d += harmonic(k, kappa[g + n0]);
-    const double robin = 2.0 * gam * k * h / (gam * h + k);
-    const double src = 2.0 * k * h / (gam * h + k);
-    const bool on[4] = {i == 0, i == n0 - 1, j == 0, j == n1 - 1};
-    for (int s = 0; s < 4; ++s) {
+    if (i > 0) d += harmonic(kc, kappa[g - 1]) * hf;
+    if (i < n0 - 1) d += harmonic(kc, kappa[g + 1]) * hf;
+    if (j > 0) d += harmonic(kc, kappa[g - sy]) * hf;
+    if (j < n1 - 1) d += harmonic(kc, kappa[g + sy]) * hf;
+    if (dim == 3) {
+      if (k > 0) d += harmonic(kc, kappa[g - sz]) * hf;
+      if (k < n2 - 1) d += harmonic(kc, kappa[g + sz]) * hf;
+    }
+    const double robin = 2.0 * gam * kc * hb / (gam * h + kc);
+    const double src = 2.0 * kc * hb / (gam * h + kc);
+    const bool on[6] = {i == 0, i == n0 - 1, j == 0, j == n1 - 1, dim == 3 && k == 0, dim == 3 && k == n2 - 1};
+    for (int s = 0; s < 2 * dim; ++s) {
       if (on[s]) d += robin;
       bside[(long long)s * N + g] = on[s] ? src : 0.0;
     }
     diag0[g] = d;
-    cxf[g] = (i < n0 - 1) ? harmonic(k, kappa[g + 1]) : 0.0;
-    cyf[g] = (j < n1 - 1) ? harmonic(k, kappa[g + n0]) : 0.0;
+    cxf[g] = (i < n0 - 1) ? harmonic(kc, kappa[g + 1]) * hf : 0.0;
+    cyf[g] = (j < n1 - 1) ? harmonic(kc, kappa[g + sy]) * hf : 0.0;
+    if (dim == 3) czf[g] = (k < n2 - 1) ? harmonic(kc, kappa[g + sz]) * hf : 0.0;
   }
 }
 
-cudaError_t da_setup(DAArgs& a, double* d_diag0, double* d_cxf, double* d_cyf, double* d_bside,
+cudaError_t da_setup(DAArgs& a, double* d_diag0, double* d_cxf, double* d_cyf, double* d_czf, double* d_bside,
                      const double* d_kappa, cudaStream_t s) {
-  da_setup_kernel<<<256, kThreads, 0, s>>>(a.n0, a.n1, a.h, a.gamma, d_kappa, d_diag0, d_cxf, d_cyf, d_bside);
+  da_setup_kernel<<<256, kThreads, 0, s>>>(a.n0, a.n1, a.n2, a.dim, a.h, a.gamma, d_kappa, d_diag0, d_cxf, d_cyf,
+                                           d_czf, d_bside);
   a.diag0 = d_diag0;
   a.cxf = d_cxf;
   a.cyf = d_cyf;
+  a.czf = d_czf;
   a.bside = d_bside;
   return cudaGetLastError();
 }
@@ -56,7 +70,7 @@ __global__ void rhs_sides_kernel(DAArgs a, unsigned mask, double* rhs) {
   const int b = blockIdx.y;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
     double v = 0.0;
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < 2 * a.dim; ++s)
       if ((mask >> s) & 1u) v += a.bside[(long long)s * a.N + g];
     rhs[(long long)b * a.N + g] = v;
   }
@@ -67,13 +81,18 @@ cudaError_t da_rhs_from_sides(const DAArgs& a, unsigned mask, int batch, double*
   return cudaGetLastError();
 }
 
-__device__ __forceinline__ double apply_A(const DAArgs& a, const double* mu, const double* x, int g, double h2) {
-  const int i = g % a.n0, j = g / a.n0;
-  double y = (a.diag0[g] + mu[g] * h2) * x[g];
+__device__ __forceinline__ double apply_A(const DAArgs& a, const double* mu, const double* x, int g, double hd) {
+  const int sy = a.n0, sz = a.n0 * a.n1;
+  const int i = g % a.n0, j = (g / a.n0) % a.n1, k = g / sz;
+  double y = (a.diag0[g] + mu[g] * hd) * x[g];
   if (i > 0) y -= a.cxf[g - 1] * x[g - 1];
   if (i < a.n0 - 1) y -= a.cxf[g] * x[g + 1];
-  if (j > 0) y -= a.cyf[g - a.n0] * x[g - a.n0];
-  if (j < a.n1 - 1) y -= a.cyf[g] * x[g + a.n0];
+  if (j > 0) y -= a.cyf[g - sy] * x[g - sy];
+  if (j < a.n1 - 1) y -= a.cyf[g] * x[g + sy];
+  if (a.dim == 3) {
+    if (k > 0) y -= a.czf[g - sz] * x[g - sz];
+    if (k < a.n2 - 1) y -= a.czf[g] * x[g + sz];
+  }
   return y;
 }
 
@@ -103,7 +122,7 @@ __device__ __forceinline__ void block_sum3(double v0, double v1, double v2, doub
 __global__ void pcg_init_kernel(DAArgs a, const double* mu, const double* rhs, PCGWork w) {
   const int b = blockIdx.y;
   const long long o = (long long)b * a.N;
-  const double h2 = a.h * a.h;
+  const double h2 = a.hd;
   double rz = 0, rr = 0, bb = 0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
     const double di = 1.0 / (a.diag0[g] + mu[o + g] * h2);
@@ -143,7 +162,7 @@ __global__ void pcg_reduce_kernel(PCGWork w, int s0, int s1, int s2) {
 __global__ void pcg_spmv_kernel(DAArgs a, const double* mu, PCGWork w) {
   const int b = blockIdx.y;
   const long long o = (long long)b * a.N;
-  const double h2 = a.h * a.h;
+  const double h2 = a.hd;
   double pq = 0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
     const double q = apply_A(a, mu + o, w.p + o, g, h2);

@@ -149,14 +149,16 @@ cudaError_t build_tables(const TableOut<T>& o, const double* d_c, const double* 
 
 // FP64 helpers (da.cu)
 struct DAArgs {
-  int n0, n1, N;
+  int n0, n1, n2, N, dim;  // n2 = 1 in 2D
   double h, gamma;
+  double hd;               // h^dim, volume weight of the absorption term
   const double* diag0;     // face + Robin terms [N]
   const double* cxf;       // coefficient to the +x neighbour [N]
   const double* cyf;       // coefficient to the +y neighbour [N]
-  const double* bside;     // [4][N] right-hand side of a unit current on each side
+  const double* czf;       // coefficient to the +z neighbour [N] (3D)
+  const double* bside;     // [2 dim][N] right-hand side of a unit current on each side
 };
-cudaError_t da_setup(DAArgs& a, double* d_diag0, double* d_cxf, double* d_cyf, double* d_bside,
+cudaError_t da_setup(DAArgs& a, double* d_diag0, double* d_cxf, double* d_cyf, double* d_czf, double* d_bside,
                      const double* d_kappa, cudaStream_t s);
 
 struct PCGWork {

@@ -267,3 +267,36 @@ def test_pml_profile_and_absorption():
     acoustic.forward_full(S, P0, callback=lambda nn, v, r, p: last.__setitem__("p", p.copy()))
     e0 = np.sum(P0 ** 2)
     assert np.sum(last["p"] ** 2) < 1e-3 * e0
+
+
+def test_homogeneous_discrete_closed_form_3d():
+    """The 3D scheme, homogeneous lossless periodic: p_n = F^-1{P0 cos(n c |k| dt)}."""
+    n, dx, c = 12, 1e-4, 1500.0
+    shape = (n, n, n)
+    S = acoustic.make_setup(np.full(shape, c), np.full(shape, 1000.0), None, 1.5, dx, 0.3 * dx / c, 20, 0,
+                            np.zeros((1, 3)), lossless=True)
+    P0 = np.random.default_rng(4).standard_normal(shape)
+    fields = {}
+    acoustic.forward_full(S, P0, callback=lambda nn, v, r, p: fields.__setitem__(nn + 1, p.copy()))
+    k = acoustic.wavenumbers(n, dx)
+    K = np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
+    F0 = np.fft.fftn(P0)
+    np.testing.assert_allclose(fields[0], P0 / 2, atol=1e-13)
+    for m in range(1, 20):
+        np.testing.assert_allclose(fields[m], np.real(np.fft.ifftn(F0 * np.cos(m * c * K * S.dt))), atol=1e-11)
+
+
+def test_adjoint_brute_force_tiny_3d():
+    """3D H_a^* equals the transpose of the assembled 3D H_a (PML, absorption,
+    heterogeneity, trilinear sensors)."""
+    w = phantoms.small(n=4, pml=2, nt=5, n_sensors=3, seed=6, dim=3)
+    S = acoustic.setup_from_workload(w)
+    N = w.n ** 3
+    H = np.zeros((w.nt * 3, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        H[:, j] = acoustic.forward(S, e.reshape(w.interior_shape)).ravel()
+    Wd = np.random.default_rng(3).standard_normal((w.nt, 3))
+    np.testing.assert_allclose(acoustic.adjoint(S, Wd).ravel(), H.T @ Wd.ravel(), rtol=1e-11,
+                               atol=1e-13 * np.abs(H).max())
