@@ -48,7 +48,8 @@ def parse():
     p.add_argument("--batch", type=int, default=8, help="independent problems per step")
     p.add_argument("--nt", type=int, default=None, help="override Nt (default: workload's 2000)")
     p.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/roofline/cpu legs")
-    p.add_argument("--workload", default="c2", choices=["c2", "c4"],
+    p.add_argument("--n3", type=int, default=None, help="c5 only: interior nodes per axis (default 256)")
+    p.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
                    help="c2: the 576^2 forward+adjoint workload (default); c4: 48 Jacobian-vector "
                         "products over 288^2/432^2/576^2 grids in one graph (diagnostic line)")
     return p.parse_args()
@@ -395,10 +396,50 @@ def run_c4(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c5(args):
+    """3D workload: 256^3 interior, 16-cell PML (288^3 FFT grid), 128 x 128
+    planar sensors, forward + adjoint of one problem in FP32; Nt is shortened
+    (default 60 of the workload's 1500) and the rate reported per cell-step."""
+    import torch
+    from paper_1810_11685_gb300.binding import context_from_workload
+    w = phantoms.C5 if not args.n3 else phantoms.dataclasses.replace(phantoms.C5, n=args.n3)
+    nt = args.nt or 60
+    ctx = context_from_workload(w, precision="fp32", max_batch=1, nt=nt)
+    p0 = torch.as_tensor(phantoms.smooth_p0(w), dtype=torch.float32, device="cuda")
+    W = torch.randn(1, nt, w.n_sensors, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        ctx.acoustic_forward(p0)
+        ctx.acoustic_adjoint(W)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record()
+        ctx.acoustic_forward(p0)
+        ctx.acoustic_adjoint(W)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    G = w.grid ** 3
+    cells = G * nt * 2 * args.steps
+    value = cells / (t_ms / 1e3)
+    b_alg = 76
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic", "impl": "ours",
+            "config": {"workload": f"c5: 3D {w.n}^3 interior, {w.grid}^3 FFT grid, {w.n_sensors} sensors, "
+                                   f"fwd+adj, Nt shortened to {nt}", "nt": nt},
+            "step_b_alg": {"bytes_per_cell_step": b_alg, "achieved_gbs": value * b_alg / 1e9,
+                           "frac_of_hbm": value * b_alg / 1e9 / 6789.6}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "ours" and args.workload == "c4":
         run_c4(args)
+        return
+    if args.impl == "ours" and args.workload == "c5":
+        run_c5(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -80,6 +80,10 @@ typedef struct {
   int n2;              /* interior nodes along z: > 0 makes the problem 3D (grids
                           [nz][ny][nx], sensors [ns][3], six illumination sides
                           4: z low, 5: z high, gamma_d default 1/4) */
+  int da_jacobi;       /* 1: precondition the diffusion solve's conjugate gradients
+                          with the diagonal only; 0: with one geometric multigrid
+                          V-cycle (damped-Jacobi smoothing on grids halved while
+                          every extent is even), which needs far fewer iterations */
 } qpat_config;
 
 /* Medium, host memory, FP64, read during qpat_create only.
@@ -212,13 +216,14 @@ qpat_status qpat_dot(qpat_ctx* ctx, int batch, long long len, const void* a, con
 
 /* Instrumentation (no counterpart in the paper).
  * qpat_get_stats: out[0] = propagation kernels launched by this context so
- * far, out[1] = launches currently held by the phase profiler.
+ * far, out[1] = launches currently held by the phase profiler, out[2] =
+ * iterations of the last diffusion solve (-1: it hit the cap).
  * qpat_profile: from now on bracket every launch of pass `phase` (an
  * internal pass id, see paper_1810_11685_gb300/binding.py PHASES; -1 turns
  * profiling off) with CUDA events on the context's stream.
  * qpat_profile_read: synchronise, return the summed device time [ms] and the
  * number of profiled launches, and reset the profiler. */
-qpat_status qpat_get_stats(const qpat_ctx* ctx, long long out[2]);
+qpat_status qpat_get_stats(const qpat_ctx* ctx, long long out[3]);
 qpat_status qpat_profile(qpat_ctx* ctx, int phase);
 qpat_status qpat_profile_read(qpat_ctx* ctx, double* total_ms, long long* count);
 

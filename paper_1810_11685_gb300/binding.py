@@ -39,7 +39,8 @@ class qpat_config(ctypes.Structure):
                 ("pml_alpha", ctypes.c_double), ("y", ctypes.c_double), ("lossless", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("gamma_d", ctypes.c_double),
                 ("pcg_max_iter", ctypes.c_int), ("pcg_tol", ctypes.c_double),
-                ("generic_fft", ctypes.c_int), ("no_graphs", ctypes.c_int), ("n2", ctypes.c_int)]
+                ("generic_fft", ctypes.c_int), ("no_graphs", ctypes.c_int), ("n2", ctypes.c_int),
+                ("da_jacobi", ctypes.c_int)]
 
 
 class qpat_medium(ctypes.Structure):
@@ -130,7 +131,7 @@ class Context:
     def __init__(self, c, rho, alpha0_db, kappa, sensors, *, dx, dt, nt, pml, y=1.5, lossless=False,
                  precision="fp32", max_batch=1, c_ref=0.0, pml_alpha=0.0, gamma_d=0.0,
                  pcg_max_iter=0, pcg_tol=0.0, generic_fft=False, no_graphs=False,
-                 device=None):
+                 da_precond="multigrid", device=None):
         import torch
         lib = load()
         c = _host(c)
@@ -151,6 +152,9 @@ class Context:
         cfg.gamma_d, cfg.pcg_max_iter, cfg.pcg_tol = float(gamma_d), int(pcg_max_iter), float(pcg_tol)
         cfg.generic_fft = int(bool(generic_fft))
         cfg.no_graphs = int(bool(no_graphs))
+        if da_precond not in ("multigrid", "jacobi"):
+            raise ValueError(f"da_precond must be 'multigrid' or 'jacobi', not {da_precond!r}")
+        cfg.da_jacobi = int(da_precond == "jacobi")
         keep = [c, rho, kappa, sensors]
         al = None
         if not lossless:
@@ -217,9 +221,9 @@ class Context:
         _check(self._ptr, self._lib.qpat_sync(self._ptr))
 
     def stats(self):
-        arr = (ctypes.c_longlong * 2)()
+        arr = (ctypes.c_longlong * 3)()
         _check(self._ptr, self._lib.qpat_get_stats(self._ptr, arr))
-        return {"launches": arr[0], "profiled": arr[1]}
+        return {"launches": arr[0], "profiled": arr[1], "pcg_iterations": arr[2]}
 
     def profile(self, phase):
         """Bracket every launch of pass ``phase`` (name or id; None = off) with CUDA events."""

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <cstdio>
 #include <string>
 #include <tuple>
@@ -39,6 +40,7 @@ struct qpat_ctx {
   Prop3<double> p3d{};
   DAArgs da{};
   PCGWork pcg{};
+  std::unique_ptr<MGHierarchy> mg;
   int* d_err = nullptr;
   int* h_err = nullptr;
   void* tw_p0 = nullptr;       // [B][N] prec: heating handed to H_a
@@ -51,6 +53,7 @@ struct qpat_ctx {
   double* h_dot_out = nullptr;
   // launch accounting and per-phase event timing
   long long launches = 0;
+  long long last_pcg_iters = 0;
   int prof_phase = -1;
   cudaStream_t cap_stream = nullptr;
   std::map<int, std::pair<cudaGraphExec_t, long long>> graphs;   // (dir, batch) -> graph, kernels
@@ -86,6 +89,8 @@ cudaError_t dalloc(qpat_ctx* c, P** p, size_t bytes) {
   }
   return e;
 }
+
+cudaError_t dalloc_cb(void* owner, void** p, size_t bytes) { return dalloc((qpat_ctx*)owner, p, bytes); }
 
 bool factor_plan(int L, FFTPlan& p) {
   p.L = L;
@@ -630,6 +635,7 @@ qpat_status check_batch(qpat_ctx* c, int batch) {
 qpat_status solve_da(qpat_ctx* c, int batch, const double* mu, const double* rhs, double* x) {
   cudaError_t e = cudaSuccess;
   const int used = pcg_solve(c->da, mu, batch, rhs, x, c->pcg, c->cfg.pcg_max_iter, c->cfg.pcg_tol, c->stream, &e);
+  c->last_pcg_iters = used;
   if (e != cudaSuccess) return cuda_fail(c, e, "diffusion solve");
   if (used < 0) return fail(c, QPAT_ENOCONV, "diffusion solve reached its iteration cap");
   return QPAT_OK;
@@ -745,8 +751,16 @@ qpat_status qpat_create(const qpat_config* cfg, const qpat_medium* med, const do
   QCKC(da_setup(c->da, diag0, cxf, cyf, czf, bside, dkappa, c->stream));
   PCGWork& w = c->pcg;
   for (double** p : {&w.x, &w.r, &w.z, &w.p, &w.q, &w.dinv, &w.b}) QCKC(dalloc(c, p, B * N * sizeof(double)));
-  QCKC(dalloc(c, &w.partial, (size_t)B * kPartials * 4 * sizeof(double)));
+  QCKC(dalloc(c, &w.mu, B * N * sizeof(double)));
+  QCKC(dalloc(c, &w.partial, (size_t)B * kPCGBlocks * 4 * sizeof(double)));
   QCKC(dalloc(c, &w.scal, (size_t)B * 8 * sizeof(double)));
+  w.use_graphs = !c->cfg.no_graphs;
+  if (!c->cfg.da_jacobi) {
+    c->mg.reset(new MGHierarchy());
+    QCKC(mg_setup(*c->mg, c->da, dkappa, B, dalloc_cb, c, c->stream));
+    // a grid with an odd extent has no coarse level: diagonal preconditioning
+    w.mg = c->mg->nlev > 1 ? c->mg.get() : nullptr;
+  }
   QCKC(cudaMallocHost(&w.hostscal, (size_t)B * 8 * sizeof(double)));
   c->host_allocs.push_back(w.hostscal);
   QCKC(dalloc(c, &c->d_phi, B * N * sizeof(double)));
@@ -767,6 +781,8 @@ qpat_status qpat_destroy(qpat_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->pcg.chunk) cudaGraphExecDestroy(c->pcg.chunk);
+  if (c->pcg.cap) cudaStreamDestroy(c->pcg.cap);
   for (void* p : c->dev_allocs) cudaFree(p);
   for (void* p : c->host_allocs) cudaFreeHost(p);
   for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
@@ -1137,10 +1153,11 @@ qpat_status qpat_autotune(qpat_ctx* c, int batch, int steps, int* choice) {
   return QPAT_OK;
 }
 
-qpat_status qpat_get_stats(const qpat_ctx* c, long long out[2]) {
+qpat_status qpat_get_stats(const qpat_ctx* c, long long out[3]) {
   if (!c || !out) return QPAT_EINVAL;
   out[0] = c->launches;
   out[1] = (long long)c->prof_used / 2;
+  out[2] = c->last_pcg_iters;
   return QPAT_OK;
 }
 

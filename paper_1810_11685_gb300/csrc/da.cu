@@ -10,6 +10,8 @@
 // absorption adds mu h^2.  The matrix is symmetric positive definite and is
 // solved by Jacobi-preconditioned conjugate gradients with FP64 dot products
 // (deterministic two-level reductions), batched over problems.
+#include <algorithm>
+
 #include "qpat_internal.h"
 
 namespace qpat {
@@ -136,15 +138,15 @@ __global__ void pcg_init_kernel(DAArgs a, const double* mu, const double* rhs, P
     rr += r * r;
     bb += r * r;
   }
-  block_sum3(rz, rr, bb, w.partial + ((long long)b * kPartials + blockIdx.x) * 4);
+  block_sum3(rz, rr, bb, w.partial + ((long long)b * kPCGBlocks + blockIdx.x) * 4);
 }
 
 // Sum the partials of problem blockIdx.x into scal slots.
 __global__ void pcg_reduce_kernel(PCGWork w, int s0, int s1, int s2) {
   const int b = blockIdx.x;
-  const double* p = w.partial + (long long)b * kPartials * 4;
+  const double* p = w.partial + (long long)b * kPCGBlocks * 4;
   double v0 = 0, v1 = 0, v2 = 0;
-  for (int t = threadIdx.x; t < kPartials; t += blockDim.x) {
+  for (int t = threadIdx.x; t < kPCGBlocks; t += blockDim.x) {
     v0 += p[4 * t];
     v1 += p[4 * t + 1];
     v2 += p[4 * t + 2];
@@ -169,7 +171,7 @@ __global__ void pcg_spmv_kernel(DAArgs a, const double* mu, PCGWork w) {
     w.q[o + g] = q;
     pq += w.p[o + g] * q;
   }
-  block_sum3(pq, 0.0, 0.0, w.partial + ((long long)b * kPartials + blockIdx.x) * 4);
+  block_sum3(pq, 0.0, 0.0, w.partial + ((long long)b * kPCGBlocks + blockIdx.x) * 4);
 }
 
 __global__ void pcg_update_kernel(DAArgs a, PCGWork w, int parity) {
@@ -190,7 +192,7 @@ __global__ void pcg_update_kernel(DAArgs a, PCGWork w, int parity) {
     rz1 += r * z;
     rr += r * r;
   }
-  block_sum3(rz1, rr, 0.0, w.partial + ((long long)b * kPartials + blockIdx.x) * 4);
+  block_sum3(rz1, rr, 0.0, w.partial + ((long long)b * kPCGBlocks + blockIdx.x) * 4);
 }
 
 __global__ void pcg_pupdate_kernel(DAArgs a, PCGWork w, int parity) {
@@ -216,33 +218,313 @@ __global__ void copy_kernel(long long n, const double* in, double* out) {
     out[t] = in[t];
 }
 
-int pcg_solve(const DAArgs& a, const double* mu, int batch, const double* rhs, double* x, PCGWork& w,
-              int max_iter, double tol, cudaStream_t s, cudaError_t* err) {
-  const dim3 grid(kPartials, batch);
-  const double tol2 = tol * tol;
-  cudaMemsetAsync(w.scal, 0, sizeof(double) * 8 * batch, s);
-  pcg_init_kernel<<<grid, kThreads, 0, s>>>(a, mu, rhs, w);
-  pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, 0, 3, 4);
-  int it = 0;
-  int used = -1;
-  const int check_every = 16;
-  while (it < max_iter) {
-    const int parity = it & 1;
-    pcg_spmv_kernel<<<grid, kThreads, 0, s>>>(a, mu, w);
-    pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, 2, -1, -1);
+// ---- multigrid preconditioner ------------------------------------------------
+// Cell-centred geometric multigrid on the same finite-volume discretisation:
+// level l + 1 halves every axis of level l (while all are even and >= 4), its
+// operator is rediscretised at spacing 2h from the children's mean kappa and
+// mean mu, restriction sums the four (eight) children's residuals (R = P^T for
+// the piecewise-constant prolongation P), smoothing is damped Jacobi with the
+// same sweeps before and after the coarse correction, and the coarsest level
+// gets a fixed number of Jacobi sweeps from zero.  Every step is linear and
+// the V-cycle is symmetric, so it is a valid conjugate-gradient preconditioner.
+
+__global__ void coarsen_mean_kernel(const double* f, double* c, int fn0, int fn1, int fn2, int dim, long long fstride,
+                                    long long cstride) {
+  const int b = blockIdx.y;
+  const int cn0 = fn0 / 2, cn1 = fn1 / 2, cn2 = dim == 3 ? fn2 / 2 : 1;
+  const long long Nc = (long long)cn0 * cn1 * cn2;
+  const double inv = dim == 3 ? 0.125 : 0.25;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Nc; t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t % cn0), J = (int)((t / cn0) % cn1), K = (int)(t / ((long long)cn0 * cn1));
+    double acc = 0.0;
+    for (int dz = 0; dz < (dim == 3 ? 2 : 1); ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+          acc += f[(long long)b * fstride + ((long long)(dim == 3 ? 2 * K + dz : 0) * fn1 + 2 * J + dy) * fn0 + 2 * I + dx];
+    c[(long long)b * cstride + t] = acc * inv;
+  }
+}
+
+cudaError_t mg_setup(MGHierarchy& h, const DAArgs& fine, const double* d_kappa, int max_batch, DevAlloc alloc,
+                     void* owner, cudaStream_t s) {
+  h.nlev = 1;
+  h.lev[0].A = fine;
+  const double* kap = d_kappa;
+  while (h.nlev < kMaxLevels) {
+    const DAArgs& f = h.lev[h.nlev - 1].A;
+    const bool ok = f.n0 % 2 == 0 && f.n1 % 2 == 0 && f.n0 >= 4 && f.n1 >= 4 &&
+                    (f.dim == 2 || (f.n2 % 2 == 0 && f.n2 >= 4));
+    if (!ok) break;
+    DAArgs c = f;
+    c.n0 = f.n0 / 2;
+    c.n1 = f.n1 / 2;
+    c.n2 = f.dim == 3 ? f.n2 / 2 : 1;
+    c.N = c.n0 * c.n1 * c.n2;
+    c.h = 2.0 * f.h;
+    c.hd = f.dim == 3 ? c.h * c.h * c.h : c.h * c.h;
+    double *ck, *d0, *cx, *cy, *cz, *bs;
+    cudaError_t e;
+    if ((e = alloc(owner, (void**)&ck, c.N * sizeof(double))) != cudaSuccess) return e;
+    coarsen_mean_kernel<<<dim3(128, 1), kThreads, 0, s>>>(kap, ck, f.n0, f.n1, f.n2, f.dim, 0, 0);
+    for (double** p : {&d0, &cx, &cy, &cz})
+      if ((e = alloc(owner, (void**)p, c.N * sizeof(double))) != cudaSuccess) return e;
+    if ((e = alloc(owner, (void**)&bs, (size_t)2 * c.dim * c.N * sizeof(double))) != cudaSuccess) return e;
+    if ((e = da_setup(c, d0, cx, cy, cz, bs, ck, s)) != cudaSuccess) return e;
+    h.lev[h.nlev].A = c;
+    kap = ck;
+    ++h.nlev;
+  }
+  for (int l = 0; l < h.nlev; ++l) {
+    MGLevel& L = h.lev[l];
+    const size_t bytes = (size_t)max_batch * L.A.N * sizeof(double);
+    cudaError_t e;
+    if (l > 0 && (e = alloc(owner, (void**)&L.mu, bytes)) != cudaSuccess) return e;
+    if ((e = alloc(owner, (void**)&L.x2, bytes)) != cudaSuccess) return e;
+    if (l > 0 && (e = alloc(owner, (void**)&L.x, bytes)) != cudaSuccess) return e;
+    if (l > 0 && (e = alloc(owner, (void**)&L.b, bytes)) != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+// x_out = x_in + omega D^-1 (b - A x_in); x_in = 0 when first
+__global__ void mg_jacobi_kernel(DAArgs a, const double* mu, const double* xin, const double* b, double* xout,
+                                 double omega, int first) {
+  const long long o = (long long)blockIdx.y * a.N;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
+    const double d = a.diag0[g] + mu[o + g] * a.hd;
+    if (first) {
+      xout[o + g] = omega * b[o + g] / d;
+    } else {
+      const double ax = apply_A(a, mu + o, xin + o, g, a.hd);
+      xout[o + g] = xin[o + g] + omega * (b[o + g] - ax) / d;
+    }
+  }
+}
+
+// b_c[I] = sum over the children i of I of (b_f - A_f x_f)[i]
+__global__ void mg_restrict_kernel(DAArgs f, const double* mu, const double* x, const double* bf, double* bc,
+                                   int cn0, int cn1, int cn2) {
+  const long long Nc = (long long)cn0 * cn1 * cn2;
+  const long long of = (long long)blockIdx.y * f.N, oc = (long long)blockIdx.y * Nc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Nc; t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t % cn0), J = (int)((t / cn0) % cn1), K = (int)(t / ((long long)cn0 * cn1));
+    double acc = 0.0;
+    for (int dz = 0; dz < (f.dim == 3 ? 2 : 1); ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int g = ((f.dim == 3 ? 2 * K + dz : 0) * f.n1 + 2 * J + dy) * f.n0 + 2 * I + dx;
+          acc += bf[of + g] - apply_A(f, mu + of, x + of, g, f.hd);
+        }
+    bc[oc + t] = acc;
+  }
+}
+
+// x_f[i] += x_c[parent(i)]
+__global__ void mg_prolong_kernel(DAArgs f, const double* xc, double* xf, int cn0, int cn1, int cn2) {
+  const long long Nc = (long long)cn0 * cn1 * cn2;
+  const long long of = (long long)blockIdx.y * f.N, oc = (long long)blockIdx.y * Nc;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < f.N; g += gridDim.x * blockDim.x) {
+    const int i = g % f.n0, j = (g / f.n0) % f.n1, k = g / (f.n0 * f.n1);
+    const long long pc = ((long long)(f.dim == 3 ? k / 2 : 0) * cn1 + j / 2) * cn0 + i / 2;
+    xf[of + g] += xc[oc + pc];
+  }
+}
+
+// All sweeps of the coarsest level in one CTA per problem (the level has at
+// most kCoarseCells cells): x = 0, then `sweeps` damped-Jacobi sweeps, the
+// result left in x.
+constexpr int kCoarseCells = 4096;
+__global__ void mg_coarse_kernel(DAArgs a, const double* mu, const double* b, double* x, double* x2, double omega,
+                                 int sweeps) {
+  const long long o = (long long)blockIdx.x * a.N;
+  double* cur = x + o;
+  double* nxt = x2 + o;
+  for (int g = threadIdx.x; g < a.N; g += blockDim.x)
+    cur[g] = omega * b[o + g] / (a.diag0[g] + mu[o + g] * a.hd);
+  for (int it = 1; it < sweeps; ++it) {
+    __syncthreads();
+    for (int g = threadIdx.x; g < a.N; g += blockDim.x) {
+      const double d = a.diag0[g] + mu[o + g] * a.hd;
+      nxt[g] = cur[g] + omega * (b[o + g] - apply_A(a, mu + o, cur, g, a.hd)) / d;
+    }
+    double* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  __syncthreads();
+  if (cur != x + o)
+    for (int g = threadIdx.x; g < a.N; g += blockDim.x) x[o + g] = cur[g];
+}
+
+static dim3 mg_grid(int N, int batch) {
+  return dim3((unsigned)std::min(kPCGBlocks, (N + kThreads - 1) / kThreads), batch);
+}
+
+// z = V-cycle(r) for level l; x/x2/b of level 0 are bound by the caller.
+static void mg_vcycle(MGHierarchy& h, int l, int batch, cudaStream_t s) {
+  MGLevel& L = h.lev[l];
+  const dim3 g = mg_grid(L.A.N, batch);
+  if (l == h.nlev - 1 && L.A.N <= kCoarseCells) {
+    mg_coarse_kernel<<<batch, 1024, 0, s>>>(L.A, L.mu, L.b, L.x, L.x2, h.omega, h.coarse_sweeps);
+    return;
+  }
+  if (l == h.nlev - 1) {
+    mg_jacobi_kernel<<<g, kThreads, 0, s>>>(L.A, L.mu, L.x, L.b, L.x, h.omega, 1);
+    for (int it = 1; it < h.coarse_sweeps; ++it) {
+      mg_jacobi_kernel<<<g, kThreads, 0, s>>>(L.A, L.mu, L.x, L.b, L.x2, h.omega, 0);
+      mg_jacobi_kernel<<<g, kThreads, 0, s>>>(L.A, L.mu, L.x2, L.b, L.x, h.omega, 0);
+      ++it;
+    }
+    return;
+  }
+  MGLevel& Cl = h.lev[l + 1];
+  // pre-smoothing: nu sweeps from zero, result in x
+  mg_jacobi_kernel<<<g, kThreads, 0, s>>>(L.A, L.mu, L.x, L.b, L.x2, h.omega, 1);
+  mg_jacobi_kernel<<<g, kThreads, 0, s>>>(L.A, L.mu, L.x2, L.b, L.x, h.omega, 0);
+  mg_restrict_kernel<<<mg_grid(Cl.A.N, batch), kThreads, 0, s>>>(L.A, L.mu, L.x, L.b, Cl.b, Cl.A.n0, Cl.A.n1, Cl.A.n2);
+  mg_vcycle(h, l + 1, batch, s);
+  mg_prolong_kernel<<<g, kThreads, 0, s>>>(L.A, Cl.x, L.x, Cl.A.n0, Cl.A.n1, Cl.A.n2);
+  // post-smoothing: the same nu sweeps, result in x
+  mg_jacobi_kernel<<<g, kThreads, 0, s>>>(L.A, L.mu, L.x, L.b, L.x2, h.omega, 0);
+  mg_jacobi_kernel<<<g, kThreads, 0, s>>>(L.A, L.mu, L.x2, L.b, L.x, h.omega, 0);
+}
+
+__global__ void pcg_init_mg_kernel(DAArgs a, const double* rhs, PCGWork w) {
+  const int b = blockIdx.y;
+  const long long o = (long long)b * a.N;
+  double rr = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
+    const double r = rhs[o + g];
+    w.x[o + g] = 0.0;
+    w.r[o + g] = r;
+    rr += r * r;
+  }
+  block_sum3(0.0, rr, rr, w.partial + ((long long)b * kPCGBlocks + blockIdx.x) * 4);
+}
+
+// x += alpha p, r -= alpha q, partial r.r  (the preconditioner runs after)
+__global__ void pcg_update_mg_kernel(DAArgs a, PCGWork w, int parity) {
+  const int b = blockIdx.y;
+  const long long o = (long long)b * a.N;
+  const double* sc = w.scal + 8 * b;
+  const bool done = sc[5] != 0.0;
+  const double rz = sc[parity], pq = sc[2];
+  const double alpha = (done || pq == 0.0) ? 0.0 : rz / pq;
+  double rr = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
+    w.x[o + g] += alpha * w.p[o + g];
+    const double r = w.r[o + g] - alpha * w.q[o + g];
+    w.r[o + g] = r;
+    rr += r * r;
+  }
+  block_sum3(0.0, rr, 0.0, w.partial + ((long long)b * kPCGBlocks + blockIdx.x) * 4);
+}
+
+__global__ void pcg_dot_rz_kernel(DAArgs a, PCGWork w, int set_p) {
+  const int b = blockIdx.y;
+  const long long o = (long long)b * a.N;
+  double rz = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
+    rz += w.r[o + g] * w.z[o + g];
+    if (set_p) w.p[o + g] = w.z[o + g];
+  }
+  block_sum3(rz, 0.0, 0.0, w.partial + ((long long)b * kPCGBlocks + blockIdx.x) * 4);
+}
+
+// One conjugate-gradient iteration of every problem in the batch (parity =
+// iteration number mod 2 selects the slot holding the current r.z).
+static void pcg_iteration(const DAArgs& a, const double* mu, int batch, PCGWork& w, int parity, cudaStream_t s) {
+  const dim3 grid(kPCGBlocks, batch);
+  MGHierarchy* mg = w.mg;
+  pcg_spmv_kernel<<<grid, kThreads, 0, s>>>(a, mu, w);
+  pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, 2, -1, -1);
+  if (mg && mg->nlev > 0) {
+    pcg_update_mg_kernel<<<grid, kThreads, 0, s>>>(a, w, parity);
+    pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, -1, 3, -1);
+    mg_vcycle(*mg, 0, batch, s);
+    pcg_dot_rz_kernel<<<grid, kThreads, 0, s>>>(a, w, 0);
+    pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, parity ^ 1, -1, -1);
+  } else {
     pcg_update_kernel<<<grid, kThreads, 0, s>>>(a, w, parity);
     pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, parity ^ 1, 3, -1);
-    pcg_pupdate_kernel<<<grid, kThreads, 0, s>>>(a, w, parity);
-    pcg_mark_done_kernel<<<(batch + 127) / 128, 128, 0, s>>>(w, batch, tol2);
-    ++it;
-    if (it % check_every == 0 || it == max_iter) {
-      cudaMemcpyAsync(w.hostscal, w.scal, sizeof(double) * 8 * batch, cudaMemcpyDeviceToHost, s);
-      cudaError_t e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) { *err = e; return -1; }
-      bool all = true;
-      for (int b = 0; b < batch; ++b) all = all && (w.hostscal[8 * b + 5] != 0.0);
-      if (all) { used = it; break; }
+  }
+  pcg_pupdate_kernel<<<grid, kThreads, 0, s>>>(a, w, parity);
+}
+
+int pcg_solve(const DAArgs& a, const double* mu_in, int batch, const double* rhs, double* x, PCGWork& w,
+              int max_iter, double tol, cudaStream_t s, cudaError_t* err) {
+  const dim3 grid(kPCGBlocks, batch);
+  const double tol2 = tol * tol;
+  MGHierarchy* mg = w.mg;
+  const bool multigrid = mg && mg->nlev > 0;
+  // the iterations read mu from a buffer of their own, so that a captured
+  // chunk of them stays valid for every call
+  copy_kernel<<<256, kThreads, 0, s>>>((long long)batch * a.N, mu_in, w.mu);
+  const double* mu = w.mu;
+  cudaMemsetAsync(w.scal, 0, sizeof(double) * 8 * batch, s);
+  if (multigrid) {
+    // level 0 of the hierarchy works on the PCG vectors: the V-cycle maps r to z
+    MGLevel& L0 = mg->lev[0];
+    L0.A = a;
+    L0.mu = w.mu;
+    L0.b = w.r;
+    L0.x = w.z;
+    for (int l = 1; l < mg->nlev; ++l) {
+      const DAArgs& f = mg->lev[l - 1].A;
+      coarsen_mean_kernel<<<dim3(128, batch), kThreads, 0, s>>>(mg->lev[l - 1].mu, mg->lev[l].mu, f.n0, f.n1, f.n2,
+                                                                 f.dim, f.N, mg->lev[l].A.N);
     }
+    pcg_init_mg_kernel<<<grid, kThreads, 0, s>>>(a, rhs, w);
+    pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, -1, 3, 4);
+    mg_vcycle(*mg, 0, batch, s);
+    pcg_dot_rz_kernel<<<grid, kThreads, 0, s>>>(a, w, 1);
+    pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, 0, -1, -1);
+  } else {
+    pcg_init_kernel<<<grid, kThreads, 0, s>>>(a, mu, rhs, w);
+    pcg_reduce_kernel<<<batch, kThreads, 0, s>>>(w, 0, 3, 4);
+  }
+  *err = cudaGetLastError();
+  if (*err != cudaSuccess) return -1;
+  // the host looks at the convergence flags after every chunk of iterations
+  // (an even number, so that every chunk starts at parity 0)
+  const int chunk = multigrid ? kPCGChunk : 4 * kPCGChunk;
+  if (w.use_graphs && w.chunk_batch != batch) {
+    if (w.chunk) cudaGraphExecDestroy(w.chunk);
+    w.chunk = nullptr;
+    w.chunk_batch = 0;
+    if (!w.cap && (*err = cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking)) != cudaSuccess) return -1;
+    if ((*err = cudaStreamBeginCapture(w.cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return -1;
+    for (int k = 0; k < chunk; ++k) {
+      pcg_iteration(a, mu, batch, w, k & 1, w.cap);
+      pcg_mark_done_kernel<<<(batch + 127) / 128, 128, 0, w.cap>>>(w, batch, tol2);
+    }
+    cudaGraph_t g = nullptr;
+    *err = cudaStreamEndCapture(w.cap, &g);
+    if (*err != cudaSuccess) return -1;
+    *err = cudaGraphInstantiate(&w.chunk, g, 0);
+    cudaGraphDestroy(g);
+    if (*err != cudaSuccess) { w.chunk = nullptr; return -1; }
+    w.chunk_batch = batch;
+  }
+  int it = 0;
+  int used = -1;
+  while (it < max_iter) {
+    const int len = std::min(chunk, max_iter - it);
+    if (w.use_graphs && len == chunk) {
+      if ((*err = cudaGraphLaunch(w.chunk, s)) != cudaSuccess) return -1;
+    } else {
+      for (int k = 0; k < len; ++k) {
+        pcg_iteration(a, mu, batch, w, k & 1, s);
+        pcg_mark_done_kernel<<<(batch + 127) / 128, 128, 0, s>>>(w, batch, tol2);
+      }
+    }
+    it += len;
+    cudaMemcpyAsync(w.hostscal, w.scal, sizeof(double) * 8 * batch, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { *err = e; return -1; }
+    bool all = true;
+    for (int b = 0; b < batch; ++b) all = all && (w.hostscal[8 * b + 5] != 0.0);
+    if (all) { used = it; break; }
   }
   copy_kernel<<<256, kThreads, 0, s>>>((long long)batch * a.N, w.x, x);
   *err = cudaGetLastError();

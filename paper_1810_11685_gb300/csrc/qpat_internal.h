@@ -161,12 +161,41 @@ struct DAArgs {
 cudaError_t da_setup(DAArgs& a, double* d_diag0, double* d_cxf, double* d_cyf, double* d_czf, double* d_bside,
                      const double* d_kappa, cudaStream_t s);
 
+// One level of the multigrid preconditioner: the finite-volume operator
+// rediscretised at spacing 2^l h (A), the absorption averaged to the level,
+// and work vectors, all [B][N_l].
+struct MGLevel {
+  DAArgs A;
+  double *mu, *x, *x2, *b;
+};
+constexpr int kMaxLevels = 16;
+struct MGHierarchy {
+  int nlev = 0;            // 0: Jacobi preconditioner
+  MGLevel lev[kMaxLevels];
+  int coarse_sweeps = 41;  // sweeps on the coarsest level (two before and two
+                           // after the coarse correction on the others)
+  double omega = 0.8;      // Jacobi damping
+};
+
 struct PCGWork {
   double *x, *r, *z, *p, *q, *dinv, *b;   // [B][N]
   double *partial;                         // [B][kPartials][4]
   double *scal;                            // [B][8]
   double *hostscal;                        // pinned [B][8]
+  MGHierarchy* mg;                         // null: Jacobi preconditioner
+  double* mu;                              // [B][N] copy of the absorption of the current solve
+  // CUDA graph of kPCGChunk iterations (fixed pointers: mu is staged in `mu`)
+  bool use_graphs;
+  cudaStream_t cap;
+  cudaGraphExec_t chunk;
+  int chunk_batch;
 };
+constexpr int kPCGChunk = 4;
+// Build the coarse levels of `fine` (kappa on the fine grid) for up to
+// max_batch problems; allocations go through `alloc` (owned by the caller).
+typedef cudaError_t (*DevAlloc)(void* owner, void** p, size_t bytes);
+cudaError_t mg_setup(MGHierarchy& h, const DAArgs& fine, const double* d_kappa, int max_batch, DevAlloc alloc,
+                     void* owner, cudaStream_t s);
 // Solve A(mu_b) x_b = rhs_b for a batch; x holds the result.  Returns the
 // number of iterations used, or -1 if the cap was reached.
 int pcg_solve(const DAArgs& a, const double* mu, int batch, const double* rhs, double* x, PCGWork& w,
@@ -193,5 +222,7 @@ template <typename T>
 cudaError_t dot_compensated(int batch, long long len, const T* a, const T* b, double* d_partial, double* d_out,
                             cudaStream_t s);
 constexpr int kPartials = 256;
+// CTAs per problem of the conjugate-gradient and multigrid kernels (eight per SM)
+constexpr int kPCGBlocks = 1216;
 
 }  // namespace qpat
