@@ -278,6 +278,10 @@ qpat_status build_context3(qpat_ctx* c, const qpat_medium* med, const double* se
   a.io = io;
   a.err = c->d_err;
   prop3_init_attributes<T>();
+  a.fast_x = !c->cfg.generic_fft && fast3_supported(c->nx, (int)sizeof(T));
+  a.fast_y = !c->cfg.generic_fft && fast3_supported(c->ny, (int)sizeof(T));
+  a.fast_z = !c->cfg.generic_fft && fast3_supported(c->nz, (int)sizeof(T));
+  prop3_init_fast<T>(a);
   return QPAT_OK;
 }
 

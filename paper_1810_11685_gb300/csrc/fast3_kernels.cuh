@@ -1,0 +1,349 @@
+// Length-specialised 3D propagation passes on the compile-time Stockham FFTs
+// of fft_reg.cuh (the 3D counterpart of fast_kernels.cuh).
+//
+// x row pass (one thread group per pair of y-rows (k, j0), (k, j0 + 1)):
+//   load up to three incoming half spectra into registers, Hermitian-extend
+//   and pack the two rows into one complex sequence -> inverse x-FFT via
+//   conj(FFT(conj .)) with the reversed plan -> pointwise update of one
+//   equation (row3_point) on the registers -> forward x-FFT -> split into the
+//   two rows' half spectra through shared memory -> store.
+// y pass (one thread group per (z, kx) line, CBW adjacent kx per CTA so that a
+//   warp's accesses are contiguous): forward y-FFT of K slots, or the inverse
+//   as conj(FFT(conj .)).
+// z pass (one thread group per (ky, kx) line): forward z-FFT, k-space symbol
+//   (z3_apply), inverse z-FFT with the reversed plan, store.
+#pragma once
+#include "fast_kernels.cuh"
+#include "pass3_ops.cuh"
+
+namespace qpat {
+
+template <typename T, int L, int PH>
+__global__ void __launch_bounds__(SGeom<L>::RP * SGeom<L>::TPT)
+row3_fast(const Prop3<T> a) {
+  constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH);
+  constexpr int NSX = (KIN > KOUT ? KIN : KOUT);
+  typedef typename V2<T>::t C;
+  typedef SGeom<L> G;
+  constexpr int TPT = G::TPT, SL = G::SL, RP = G::RP;
+  constexpr int Q1 = G::Q1, QL = G::QL, P1 = G::P1;
+  constexpr bool SCATTER = (PH == A_R1 || PH == A_R1L);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = threadIdx.x / TPT;
+  const int j = threadIdx.x - m * TPT;
+  C* tws = reinterpret_cast<C*>(smem_raw);                       // W_L^m table
+  C* bufA = tws + L + m * 2 * NSX * SL;
+  C* bufB = bufA + NSX * SL;
+  T* sc = reinterpret_cast<T*>(tws + L + RP * 2 * NSX * SL) + m * 2 * L;
+  const int b = blockIdx.z, k = blockIdx.y;
+  const int jp = blockIdx.x * RP + m;
+  const bool valid = jp < (a.ny >> 1);
+  const int j0 = valid ? 2 * jp : 0;
+  C* spec = a.spec + (long long)b * a.sstride + ((long long)k * a.ny + j0) * a.pitch;
+  const bool skip_in = (a.flags & kSkipInput) != 0;
+
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
+
+  // 1. inverse x-transform of the incoming half spectra (reversed plan)
+  C y[KIN][Q1];
+  if (!skip_in) {
+    C v[KIN][P1];
+    if (j < L / P1) {
+#pragma unroll
+      for (int s = 0; s < KIN; ++s) {
+        const C* r0 = spec + s * a.slot;
+        const C* r1 = r0 + a.pitch;
+#pragma unroll
+        for (int r = 0; r < P1; ++r) {
+          const int n = j + r * (L / P1);
+          C P, Q;
+          if (2 * n <= L) {
+            P = r0[n];
+            Q = r1[n];
+            if (n == 0 || 2 * n == L) { P.y = (T)0; Q.y = (T)0; }
+          } else {
+            P = cconj(r0[L - n]);
+            Q = cconj(r1[L - n]);
+          }
+          v[s][r] = cmake<C>(P.x - Q.y, -(P.y + Q.x));   // conj(P + i Q)
+        }
+      }
+    }
+    fft_stockham<L, G::P1, G::P2, G::P3, KIN>(v, y, bufA, bufB, SL, j, tws);
+  } else {
+#pragma unroll
+    for (int s = 0; s < KIN; ++s)
+#pragma unroll
+      for (int r = 0; r < Q1; ++r) y[s][r] = cmake<C>((T)0, (T)0);
+  }
+
+  // adjoint sensor source M^T w_n on the two rows
+  if (SCATTER) {
+    for (int i = j; i < 2 * L; i += TPT) sc[i] = (T)0;
+    __syncthreads();
+    if (valid) sensor_scatter_rows3<T>(a, b, k * a.ny + j0, sc, j, TPT);
+    __syncthreads();
+  }
+
+  // 2. pointwise update on grid points i = j + r L/Q1 of both rows;
+  //    y = FFT(conj Z) = conj(z): row j0 is Re, row j0+1 is -Im
+  C o[KOUT][Q1];
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < Q1; ++r) {
+    T u[2][3] = {{(T)0, (T)0, (T)0}, {(T)0, (T)0, (T)0}};
+    if (j < L / Q1 && valid) {
+      const int i = j + r * (L / Q1);
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        T in[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+        for (int s = 0; s < KIN; ++s) in[s] = rr ? -y[s][r].y : y[s][r].x;
+        const T scv = SCATTER ? sc[rr * L + i] : (T)0;
+        row3_point<T>(a, PH, b, i, j0 + rr, k, in, scv, u[rr], bad);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s) o[s][r] = cmake<C>(u[0][s], u[1][s]);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.err, 1);
+  if (a.flags & kSkipOutput) return;
+
+  // 3. forward x-transform of the packed outgoing rows, split, store
+  C X[KOUT][QL];
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KOUT>(o, X, bufA, bufB, SL, j, tws);
+  if (j < L / QL) {
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s)
+#pragma unroll
+      for (int r = 0; r < QL; ++r) bufA[s * SL + spad(j + r * (L / QL))] = X[s][r];
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s) {
+      C* w0 = spec + s * a.slot;
+      C* w1 = w0 + a.pitch;
+      for (int q = j; 2 * q <= L; q += TPT) {
+        const C Z = bufA[s * SL + spad(q)];
+        const C Zm = cconj(bufA[s * SL + spad(q == 0 ? 0 : L - q)]);
+        w0[q] = cscale(cadd(Z, Zm), (T)0.5);
+        w1[q] = cscale(cmul_mi(csub(Z, Zm)), (T)0.5);
+      }
+    }
+  }
+}
+
+// y pass over the (z = blockIdx.y, kx) lines of problem blockIdx.z.
+template <typename T, int L, int K, int INV>
+__global__ void __launch_bounds__(SGeom<L>::CBW * SGeom<L>::TPT)
+ypass3_fast(const Prop3<T> a, const int gather) {
+  typedef typename V2<T>::t C;
+  typedef SGeom<L> G;
+  constexpr int SL = G::SL, CBW = G::CBW, Q1 = G::Q1, QL = G::QL;
+  constexpr int CS = col_stride<L, K, CBW>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = threadIdx.x % CBW;
+  const int j = threadIdx.x / CBW;
+  C* tws = reinterpret_cast<C*>(smem_raw);
+  C* bufA = tws + L + c * CS;
+  C* bufB = bufA + K * SL;
+  const int b = blockIdx.z, k = blockIdx.y;
+  const int kx = blockIdx.x * CBW + c;
+  const bool valid = kx < a.nxh;
+  C* spec = a.spec + (long long)b * a.sstride + (long long)k * a.ny * a.pitch + (valid ? kx : 0);
+  if (gather) {
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    gather3<T>(a, b, blk * blockDim.x + threadIdx.x, gridDim.x * gridDim.y * blockDim.x);
+  }
+  C v[K][Q1];
+  if (j < L / Q1) {
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+      for (int r = 0; r < Q1; ++r) {
+        const C z = spec[s * a.slot + (long long)(j + r * (L / Q1)) * a.pitch];
+        v[s][r] = INV ? cconj(z) : z;
+      }
+  }
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twy[t];
+  C X[K][QL];
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, K>(v, X, bufA, bufB, SL, j, tws);
+  if (j < L / QL && valid) {
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+      for (int r = 0; r < QL; ++r)
+        spec[s * a.slot + (long long)(j + r * (L / QL)) * a.pitch] = INV ? cconj(X[s][r]) : X[s][r];
+  }
+}
+
+// z pass over the (ky = blockIdx.y, kx) lines of problem blockIdx.z.
+template <typename T, int L, int PH>
+__global__ void __launch_bounds__(SGeom<L>::CBW * SGeom<L>::TPT)
+zpass3_fast(const Prop3<T> a) {
+  constexpr int KIN = z3_kin(PH), KOUT = z3_kout(PH);
+  constexpr int NSX = (KIN > KOUT ? KIN : KOUT);
+  typedef typename V2<T>::t C;
+  typedef SGeom<L> G;
+  constexpr int SL = G::SL, CBW = G::CBW, Q1 = G::Q1, QL = G::QL;
+  constexpr int CS = col_stride<L, NSX, CBW>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = threadIdx.x % CBW;
+  const int j = threadIdx.x / CBW;
+  C* tws = reinterpret_cast<C*>(smem_raw);
+  C* bufA = tws + L + c * CS;
+  C* bufB = bufA + NSX * SL;
+  const int b = blockIdx.z, ky = blockIdx.y;
+  const int kx = blockIdx.x * CBW + c;
+  const bool valid = kx < a.nxh;
+  const int kxs = valid ? kx : 0;
+  const long long zs = (long long)a.ny * a.pitch;
+  C* spec = a.spec + (long long)b * a.sstride + (long long)ky * a.pitch + kxs;
+
+  C v[KIN][Q1];
+  if (j < L / Q1) {
+#pragma unroll
+    for (int s = 0; s < KIN; ++s)
+#pragma unroll
+      for (int r = 0; r < Q1; ++r) v[s][r] = spec[s * a.slot + (long long)(j + r * (L / Q1)) * zs];
+  }
+  // twiddles and the symbol operands of this thread's points before the transforms
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twz[t];
+  Z3In<T, C> st[QL];
+#pragma unroll
+  for (int r = 0; r < QL; ++r)
+    st[r] = (j < L / QL && valid) ? z3_load<T, C>(a, PH, kx, ky, j + r * (L / QL)) : Z3In<T, C>{};
+  const C sx = z3_sx<T, C>(a, PH, kxs), sy = z3_sy<T, C>(a, PH, ky);
+  C X[KIN][QL];
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KIN>(v, X, bufA, bufB, SL, j, tws);
+  C o[KOUT][QL];
+#pragma unroll
+  for (int r = 0; r < QL; ++r) {
+    C xin[3], out[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) xin[s] = (s < KIN) ? X[s < KIN ? s : 0][r] : cmake<C>((T)0, (T)0);
+    if (j < L / QL && valid) z3_apply<T, C>(PH, st[r], sx, sy, xin, out);
+    else out[0] = out[1] = out[2] = cmake<C>((T)0, (T)0);
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s) o[s][r] = cconj(out[s]);
+  }
+  C Y[KOUT][Q1];
+  fft_stockham<L, G::P1, G::P2, G::P3, KOUT>(o, Y, bufA, bufB, SL, j, tws);
+  if (j < L / Q1 && valid) {
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s)
+#pragma unroll
+      for (int r = 0; r < Q1; ++r) spec[s * a.slot + (long long)(j + r * (L / Q1)) * zs] = cconj(Y[s][r]);
+  }
+}
+
+template <typename T, int L, int PH>
+constexpr size_t row3_fast_smem() {
+  typedef typename V2<T>::t C;
+  constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT);
+  constexpr bool SCATTER = (PH == A_R1 || PH == A_R1L);
+  return (L + SGeom<L>::RP * 2 * NSX * SGeom<L>::SL) * sizeof(C) + (SCATTER ? SGeom<L>::RP * 2 * L * sizeof(T) : 0);
+}
+template <typename T, int L, int NSX>
+constexpr size_t line3_fast_smem() {
+  typedef typename V2<T>::t C;
+  return ((size_t)L + (size_t)SGeom<L>::CBW * col_stride<L, NSX, SGeom<L>::CBW>()) * sizeof(C);
+}
+
+template <typename T, int L, int PH>
+void set_row3_fast_attr() {
+  cudaFuncSetAttribute(row3_fast<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)row3_fast_smem<T, L, PH>());
+}
+template <typename T, int L, int PH>
+void set_z3_fast_attr() {
+  constexpr int NSX = z3_kin(PH) > z3_kout(PH) ? z3_kin(PH) : z3_kout(PH);
+  cudaFuncSetAttribute(zpass3_fast<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)line3_fast_smem<T, L, NSX>());
+}
+template <typename T, int L, int K, int INV>
+void set_y3_fast_attr() {
+  cudaFuncSetAttribute(ypass3_fast<T, L, K, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)line3_fast_smem<T, L, K>());
+}
+
+// Dynamic shared-memory limits of all 3D pass kernels of length L; called at
+// context creation, outside any stream capture.
+template <typename T, int L>
+void prepare3_fast_len() {
+  set_row3_fast_attr<T, L, F_R1>(); set_row3_fast_attr<T, L, F_R2>(); set_row3_fast_attr<T, L, F_R3>();
+  set_row3_fast_attr<T, L, F_R3L>(); set_row3_fast_attr<T, L, A_R1>(); set_row3_fast_attr<T, L, A_R1L>();
+  set_row3_fast_attr<T, L, A_R3>(); set_row3_fast_attr<T, L, A_R5>();
+  set_z3_fast_attr<T, L, F_C1>(); set_z3_fast_attr<T, L, F_C2>(); set_z3_fast_attr<T, L, F_C3>();
+  set_z3_fast_attr<T, L, A_C2>(); set_z3_fast_attr<T, L, A_C4>(); set_z3_fast_attr<T, L, A_C6>();
+  set_y3_fast_attr<T, L, 1, 0>(); set_y3_fast_attr<T, L, 2, 0>(); set_y3_fast_attr<T, L, 3, 0>();
+  set_y3_fast_attr<T, L, 1, 1>(); set_y3_fast_attr<T, L, 2, 1>(); set_y3_fast_attr<T, L, 3, 1>();
+}
+
+template <typename T, int L, int PH>
+void run_row3_fast(const Prop3<T>& a, int batch, cudaStream_t s) {
+  typedef SGeom<L> G;
+  const dim3 grid((a.ny / 2 + G::RP - 1) / G::RP, a.nz, batch);
+  row3_fast<T, L, PH><<<grid, G::RP * G::TPT, row3_fast_smem<T, L, PH>(), s>>>(a);
+}
+template <typename T, int L, int PH>
+void run_z3_fast(const Prop3<T>& a, int batch, cudaStream_t s) {
+  typedef SGeom<L> G;
+  constexpr int NSX = z3_kin(PH) > z3_kout(PH) ? z3_kin(PH) : z3_kout(PH);
+  const dim3 grid((a.nxh + G::CBW - 1) / G::CBW, a.ny, batch);
+  zpass3_fast<T, L, PH><<<grid, G::CBW * G::TPT, line3_fast_smem<T, L, NSX>(), s>>>(a);
+}
+template <typename T, int L, int K, int INV>
+void run_y3_fast(const Prop3<T>& a, int gather, int batch, cudaStream_t s) {
+  typedef SGeom<L> G;
+  const dim3 grid((a.nxh + G::CBW - 1) / G::CBW, a.nz, batch);
+  ypass3_fast<T, L, K, INV><<<grid, G::CBW * G::TPT, line3_fast_smem<T, L, K>(), s>>>(a, gather);
+}
+
+template <typename T, int L>
+void launch_row3_fast_len(const Prop3<T>& a, int ph, int batch, cudaStream_t s) {
+  switch (ph) {
+    case F_R1: run_row3_fast<T, L, F_R1>(a, batch, s); break;
+    case F_R2: run_row3_fast<T, L, F_R2>(a, batch, s); break;
+    case F_R3: run_row3_fast<T, L, F_R3>(a, batch, s); break;
+    case F_R3L: run_row3_fast<T, L, F_R3L>(a, batch, s); break;
+    case A_R1: run_row3_fast<T, L, A_R1>(a, batch, s); break;
+    case A_R1L: run_row3_fast<T, L, A_R1L>(a, batch, s); break;
+    case A_R3: run_row3_fast<T, L, A_R3>(a, batch, s); break;
+    case A_R5: run_row3_fast<T, L, A_R5>(a, batch, s); break;
+    default: break;
+  }
+}
+template <typename T, int L>
+void launch_z3_fast_len(const Prop3<T>& a, int ph, int batch, cudaStream_t s) {
+  switch (ph) {
+    case F_C1: run_z3_fast<T, L, F_C1>(a, batch, s); break;
+    case F_C2: run_z3_fast<T, L, F_C2>(a, batch, s); break;
+    case F_C3: run_z3_fast<T, L, F_C3>(a, batch, s); break;
+    case A_C2: run_z3_fast<T, L, A_C2>(a, batch, s); break;
+    case A_C4: run_z3_fast<T, L, A_C4>(a, batch, s); break;
+    case A_C6: run_z3_fast<T, L, A_C6>(a, batch, s); break;
+    default: break;
+  }
+}
+template <typename T, int L>
+void launch_y3_fast_len(const Prop3<T>& a, int K, int inv, int gather, int batch, cudaStream_t s) {
+  if (!inv) {
+    if (K == 1) run_y3_fast<T, L, 1, 0>(a, gather, batch, s);
+    else if (K == 2) run_y3_fast<T, L, 2, 0>(a, gather, batch, s);
+    else run_y3_fast<T, L, 3, 0>(a, gather, batch, s);
+  } else {
+    if (K == 1) run_y3_fast<T, L, 1, 1>(a, gather, batch, s);
+    else if (K == 2) run_y3_fast<T, L, 2, 1>(a, gather, batch, s);
+    else run_y3_fast<T, L, 3, 1>(a, gather, batch, s);
+  }
+}
+
+#define QPAT_FAST3_LENGTH(L)                                                                                   \
+  template void prepare3_fast_len<float, L>();                                                                 \
+  template void launch_row3_fast_len<float, L>(const Prop3<float>&, int, int, cudaStream_t);                 \
+  template void launch_y3_fast_len<float, L>(const Prop3<float>&, int, int, int, int, cudaStream_t);         \
+  template void launch_z3_fast_len<float, L>(const Prop3<float>&, int, int, cudaStream_t);
+
+}  // namespace qpat

@@ -59,6 +59,8 @@ struct Prop3 {
   int n;
   int flags;
   int* err;
+  // length-specialised passes per axis (FP32, supported extents)
+  bool fast_x, fast_y, fast_z;
 };
 
 template <typename T>
@@ -81,6 +83,21 @@ template <typename T>
 size_t prop3_smem_col(int n, int cb);
 // Forward / adjoint launch sequences of the 3D loop; return the number of
 // kernels enqueued.
+// Length-specialised 3D passes (fast3_kernels.cuh; one translation unit per
+// group of extents).  FP32 only, like the 2D ones.
+#define QPAT_FAST3_CASES(X) X(24) X(48) X(288)
+bool fast3_supported(int L, int elt);
+template <typename T, int L>
+void prepare3_fast_len();
+template <typename T, int L>
+void launch_row3_fast_len(const Prop3<T>& a, int ph, int batch, cudaStream_t s);
+template <typename T, int L>
+void launch_y3_fast_len(const Prop3<T>& a, int K, int inv, int gather, int batch, cudaStream_t s);
+template <typename T, int L>
+void launch_z3_fast_len(const Prop3<T>& a, int ph, int batch, cudaStream_t s);
+template <typename T>
+void prop3_init_fast(const Prop3<T>& a);
+
 template <typename T>
 long long seq3_forward(Prop3<T> a, int batch, bool lossless, cudaStream_t s);
 template <typename T>

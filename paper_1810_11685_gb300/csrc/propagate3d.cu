@@ -16,116 +16,11 @@
 #include <math.h>
 
 #include <initializer_list>
+#include <type_traits>
 
-#include "prop3d.h"
+#include "pass3_ops.cuh"
 
 namespace qpat {
-
-__host__ __device__ constexpr int r3_kin(int ph) {
-  return (ph == F_R1) ? 2 : (ph == A_R1 || ph == A_R1L) ? 1 : (ph == A_R3) ? 2 : 3;
-}
-__host__ __device__ constexpr int r3_kout(int ph) {
-  return (ph == F_R1 || ph == F_R3L) ? 1 : (ph == F_R3 || ph == A_R1) ? 2 : 3;
-}
-__host__ __device__ constexpr int z3_kin(int ph) { return ph == F_C1 ? 1 : (ph == F_C3 || ph == A_C2) ? 2 : 3; }
-__host__ __device__ constexpr int z3_kout(int ph) { return ph == A_C6 ? 1 : (ph == F_C3 || ph == A_C2) ? 2 : 3; }
-
-constexpr int k3Threads = 256;
-
-// ---- pointwise update of one grid point (i, j, k) -------------------------
-template <typename T>
-__device__ __forceinline__ void row3_point(const Prop3<T>& a, const int ph, const int b, const int i, const int j,
-                                           const int k, const T* in, const T scv, T* out, bool& bad) {
-  const long long g = ((long long)k * a.ny + j) * a.nx + i;
-  const long long gb = (long long)b * a.gstride + g;
-  const bool interior = i >= a.pml && i < a.pml + a.n0 && j >= a.pml && j < a.pml + a.n1 && k >= a.pml &&
-                        k < a.pml + a.n2;
-  const long long ii = interior ? ((long long)(k - a.pml) * a.n1 + (j - a.pml)) * a.n0 + (i - a.pml) : 0;
-  const long long N = (long long)a.n0 * a.n1 * a.n2;
-  out[0] = out[1] = out[2] = (T)0;
-  if (ph == F_R1) {
-    // eq. num-p with sum_i rho_i over three components
-    const T r = a.rx[gb] + a.ry[gb] + a.rz[gb];
-    const T p = a.Cc[g] * ((r - a.eta[g] * in[0]) + a.tau[g] * in[1]);
-    a.pbuf[gb] = p;
-    bad |= !isfinite(p);
-    out[0] = p;
-  } else if (ph == F_R2) {
-    // eq. num-vel per axis
-    const T sx = a.asx[i], sy = a.asy[j], sz = a.asz[k];
-    const T vx = sx * (sx * a.vx[gb] - a.dtrsx[g] * in[0]);
-    const T vy = sy * (sy * a.vy[gb] - a.dtrsy[g] * in[1]);
-    const T vz = sz * (sz * a.vz[gb] - a.dtrsz[g] * in[2]);
-    a.vx[gb] = vx;
-    a.vy[gb] = vy;
-    a.vz[gb] = vz;
-    out[0] = vx;
-    out[1] = vy;
-    out[2] = vz;
-  } else if (ph == F_R3 || ph == F_R3L) {
-    // eq. num-rho with the additive source of eq. s1, dt s_i = P0 / (2 d c^2), d = 3
-    T q = (T)0;
-    if ((a.flags & kSource) && interior) q = a.io->p0[(long long)b * N + ii] / ((T)6 * a.Cc[g]);
-    const T ax = a.ax[i], ay = a.ay[j], az = a.az[k], r0 = a.rho0[g];
-    const T rx = ax * (ax * a.rx[gb] - a.dt * r0 * in[0]) + q;
-    const T ry = ay * (ay * a.ry[gb] - a.dt * r0 * in[1]) + q;
-    const T rz = az * (az * a.rz[gb] - a.dt * r0 * in[2]) + q;
-    a.rx[gb] = rx;
-    a.ry[gb] = ry;
-    a.rz[gb] = rz;
-    if (ph == F_R3) {
-      out[0] = rx + ry + rz;
-      out[1] = r0 * (ax * in[0] + ay * in[1] + az * in[2]);
-    } else {
-      const T p = a.Cc[g] * (rx + ry + rz);
-      a.pbuf[gb] = p;
-      bad |= !isfinite(p);
-      out[0] = p;
-    }
-  } else if (ph == A_R1) {
-    const T Cp = a.Cc[g] * (in[0] + scv);
-    a.pbuf[gb] = Cp;
-    out[0] = a.eta[g] * Cp;
-    out[1] = a.tau[g] * Cp;
-  } else if (ph == A_R1L || ph == A_R3) {
-    T Cp, ya = (T)0;
-    if (ph == A_R1L) {
-      Cp = a.Cc[g] * (in[0] + scv);
-    } else {
-      Cp = a.pbuf[gb];
-      ya = in[1];
-    }
-    const T rpart = (ph == A_R1L) ? Cp : Cp - in[0];
-    const T A[3] = {a.ax[i], a.ay[j], a.az[k]};
-    T* R[3] = {a.rx, a.ry, a.rz};
-    const T r0 = a.rho0[g];
-    T sum = (T)0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T rt = R[c][gb] + rpart;
-      out[c] = r0 * A[c] * (ya - a.dt * rt);
-      R[c][gb] = A[c] * A[c] * rt;
-      sum += rt;
-    }
-    bad |= !isfinite(sum);
-    if (interior && (a.flags & (kAccWrite | kAccAdd))) {
-      T* dst = a.io->p0adj + (long long)b * N + ii;
-      const T val = sum / ((T)6 * a.Cc[g]);
-      if (a.flags & kAccWrite) *dst = val;
-      else *dst += val;
-    }
-  } else if (ph == A_R5) {
-    const T S[3] = {a.asx[i], a.asy[j], a.asz[k]};
-    const T D[3] = {a.dtrsx[g], a.dtrsy[g], a.dtrsz[g]};
-    T* V[3] = {a.vx, a.vy, a.vz};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T vt = V[c][gb] + in[c];
-      V[c][gb] = S[c] * S[c] * vt;
-      out[c] = S[c] * D[c] * vt;
-    }
-  }
-}
 
 // ---- x row pass: rows (k, j0) and (k, j0+1) of problem blockIdx.z ----------
 template <typename T, int PH>
@@ -216,19 +111,6 @@ __global__ void __launch_bounds__(k3Threads) row3_kernel(const Prop3<T> a) {
   }
 }
 
-// eq. num-m, trilinear: samples of p_n for problem b
-template <typename T>
-__device__ __forceinline__ void gather3(const Prop3<T>& a, int b, int first, int stride) {
-  const T* pb = a.pbuf + (long long)b * a.gstride;
-  T* dn = a.io->data + ((long long)b * a.nt + a.n) * a.ns;
-  for (int s = first; s < a.ns; s += stride) {
-    T acc = (T)0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc += a.sw[8 * s + c] * pb[a.sidx[8 * s + c]];
-    dn[s] = acc;
-  }
-}
-
 // ---- y pass: forward (INV = 0) or inverse (INV = 1) y-FFT of K slots -------
 template <typename T, int K, int INV>
 __global__ void __launch_bounds__(k3Threads) ypass3_kernel(const Prop3<T> a, const int gather) {
@@ -294,32 +176,8 @@ __global__ void __launch_bounds__(k3Threads) zpass3_kernel(const Prop3<T> a) {
       X[s] = (s < KIN) ? res[(s * cb + c) * S + kz] : cmake<C>((T)0, (T)0);
       o[s] = cmake<C>((T)0, (T)0);
     }
-    if (kx < nxh) {
-      const long long t = ((long long)kz * a.ny + ky) * nxh + kx;
-      if (PH == F_C1) {          // d/dr_i^+ of p, i = x, y, z (eq. grr)
-        const T kk = a.kap[t];
-        o[0] = cscale(cmul(a.shxp[kx], X[0]), kk);
-        o[1] = cscale(cmul(a.shyp[ky], X[0]), kk);
-        o[2] = cscale(cmul(a.shzp[kz], X[0]), kk);
-      } else if (PH == F_C2) {   // d/dr_i^- v_i
-        const T kk = a.kap[t];
-        o[0] = cscale(cmul(a.shxm[kx], X[0]), kk);
-        o[1] = cscale(cmul(a.shym[ky], X[1]), kk);
-        o[2] = cscale(cmul(a.shzm[kz], X[2]), kk);
-      } else if (PH == F_C3 || PH == A_C2) {   // Y_dis, Y_abs
-        o[0] = cscale(X[0], a.kp1[t]);
-        o[1] = cscale(X[1], a.kp2[t]);
-      } else if (PH == A_C4) {   // (d/dr_i^-)^T
-        const T kk = a.kap[t];
-        o[0] = cscale(cmul(cconj(a.shxm[kx]), X[0]), kk);
-        o[1] = cscale(cmul(cconj(a.shym[ky]), X[1]), kk);
-        o[2] = cscale(cmul(cconj(a.shzm[kz]), X[2]), kk);
-      } else {                   // A_C6: -sum_i (d/dr_i^+)^T
-        const T kk = a.kap[t];
-        o[0] = cscale(cadd(cadd(cmul(cconj(a.shxp[kx]), X[0]), cmul(cconj(a.shyp[ky]), X[1])),
-                           cmul(cconj(a.shzp[kz]), X[2])), -kk);
-      }
-    }
+    if (kx < nxh) z3_apply<T, C>(PH, z3_load<T, C>(a, PH, kx, ky, kz), z3_sx<T, C>(a, PH, kx),
+                                 z3_sy<T, C>(a, PH, ky), X, o);
 #pragma unroll
     for (int s = 0; s < KOUT; ++s) oth[(s * cb + c) * S + kz] = cconj(o[s]);
   }
@@ -489,8 +347,41 @@ void prop3_init_attributes() {
   set3_y_attr<T, 1, 1>(); set3_y_attr<T, 2, 1>(); set3_y_attr<T, 3, 1>();
 }
 
+bool fast3_supported(int L, int elt) {
+  if (elt != 4) return false;
+  switch (L) {
+#define QPAT_SUP3_CASE(n) case n:
+    QPAT_FAST3_CASES(QPAT_SUP3_CASE)
+#undef QPAT_SUP3_CASE
+    return true;
+    default: return false;
+  }
+}
+
+template <typename T>
+void prop3_init_fast(const Prop3<T>& a) {
+  if constexpr (std::is_same<T, float>::value) {
+    for (int L : {a.fast_x ? a.nx : 0, a.fast_y ? a.ny : 0, a.fast_z ? a.nz : 0}) {
+      switch (L) {
+#define QPAT_PREP3_CASE(n) case n: prepare3_fast_len<T, n>(); break;
+        QPAT_FAST3_CASES(QPAT_PREP3_CASE)
+#undef QPAT_PREP3_CASE
+        default: break;
+      }
+    }
+  }
+}
+
 template <typename T>
 void row3(const Prop3<T>& a, int ph, int batch, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) if (a.fast_x) {
+    switch (a.nx) {
+#define QPAT_ROW3_CASE(n) case n: launch_row3_fast_len<T, n>(a, ph, batch, s); return;
+      QPAT_FAST3_CASES(QPAT_ROW3_CASE)
+#undef QPAT_ROW3_CASE
+      default: break;
+    }
+  }
   const dim3 grid(a.ny / 2, a.nz, batch);
   const size_t sm = prop3_smem_row<T>(a.nx);
   switch (ph) {
@@ -508,6 +399,14 @@ void row3(const Prop3<T>& a, int ph, int batch, cudaStream_t s) {
 
 template <typename T>
 void ypass3(const Prop3<T>& a, int K, int inv, int gather, int batch, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) if (a.fast_y) {
+    switch (a.ny) {
+#define QPAT_Y3_CASE(n) case n: launch_y3_fast_len<T, n>(a, K, inv, gather, batch, s); return;
+      QPAT_FAST3_CASES(QPAT_Y3_CASE)
+#undef QPAT_Y3_CASE
+      default: break;
+    }
+  }
   const dim3 grid((a.nxh + a.cby - 1) / a.cby, a.nz, batch);
   const size_t sm = prop3_smem_col<T>(a.ny, a.cby);
   if (!inv) {
@@ -523,6 +422,14 @@ void ypass3(const Prop3<T>& a, int K, int inv, int gather, int batch, cudaStream
 
 template <typename T>
 void zpass3(const Prop3<T>& a, int ph, int batch, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) if (a.fast_z) {
+    switch (a.nz) {
+#define QPAT_Z3_CASE(n) case n: launch_z3_fast_len<T, n>(a, ph, batch, s); return;
+      QPAT_FAST3_CASES(QPAT_Z3_CASE)
+#undef QPAT_Z3_CASE
+      default: break;
+    }
+  }
   const dim3 grid((a.nxh + a.cbz - 1) / a.cbz, a.ny, batch);
   const size_t sm = prop3_smem_col<T>(a.nz, a.cbz);
   switch (ph) {
@@ -632,6 +539,7 @@ long long seq3_adjoint(Prop3<T> a, int batch, bool lossless, cudaStream_t s) {
                                         int, int, int, int, double, double, double, double, double, int,       \
                                         cudaStream_t);                                                         \
   template void prop3_init_attributes<T>();                                                                    \
+  template void prop3_init_fast<T>(const Prop3<T>&);                                                           \
   template size_t prop3_smem_col<T>(int, int);                                                                 \
   template long long seq3_forward<T>(Prop3<T>, int, bool, cudaStream_t);                                       \
   template long long seq3_adjoint<T>(Prop3<T>, int, bool, cudaStream_t);

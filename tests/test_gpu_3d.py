@@ -83,3 +83,48 @@ def test_jvp_vjp_3d():
                   qpat.jvp(S, mu, kappa, 0b100000, v)) <= 1e-9
     assert rel_l2(to_np(ctx.vjp(mu_g, to_gpu(W, torch.float64), 0b100000))[0],
                   qpat.vjp(S, mu, kappa, 0b100000, W)) <= 1e-9
+
+
+@pytest.mark.parametrize("generic", [False, True])
+def test_fp32_3d_48_specialised_and_generic(generic):
+    # 48^3: the compile-time Stockham 3D passes (and, with generic_fft, the
+    # runtime-radix ones) against the oracle, two problems in one batch
+    w = phantoms.small(n=40, pml=4, nt=24, n_sensors=12, seed=8, dim=3)
+    ctx, S = make_pair(w, "fp32", max_batch=2, generic_fft=generic)
+    p0 = np.stack([phantoms.smooth_p0(w, 2), phantoms.random_field(w.interior_shape, 9)])
+    got = to_np(ctx.acoustic_forward(to_gpu(p0, torch.float32)))
+    for b in range(2):
+        assert rel_l2(got[b], acoustic.forward(S, p0[b])) <= 2e-4
+    W = np.stack([phantoms.random_field((w.nt, w.n_sensors), 13), phantoms.random_field((w.nt, w.n_sensors), 14)])
+    got = to_np(ctx.acoustic_adjoint(to_gpu(W, torch.float32)))
+    for b in range(2):
+        assert rel_l2(got[b], acoustic.adjoint(S, W[b])) <= 2e-4
+
+
+def test_fp32_3d_full_size_against_fp64_and_dot():
+    # the 256^3-interior workload on its 288^3 FFT grid, in the launch
+    # configuration the bench uses (FP32, specialised passes), for a shortened
+    # loop: against the FP64 GPU path (itself pinned to the oracle above), and
+    # the adjoint dot test <H p0, w> = <p0, H^* w> with w = H p0 + noise, so
+    # that the inner product has no cancellation to amplify FP32 rounding
+    import dataclasses
+    w = dataclasses.replace(phantoms.C5, nt=16)
+    ctx32, _ = make_pair(w, "fp32", nt=16)
+    # white noise: in 16 steps only sources near the sensor plane reach it, so
+    # a smooth central p0 would leave the sensors with rounding-level tails
+    p0 = phantoms.random_field(w.interior_shape, 7)
+    p0g = to_gpu(p0, torch.float32)
+    d32 = ctx32.acoustic_forward(p0g)
+    noise = to_gpu(phantoms.random_field((w.nt, w.n_sensors), 21), torch.float32)
+    W = (d32[0] + 0.1 * d32.abs().max() * noise).contiguous()
+    a32 = ctx32.acoustic_adjoint(W)
+    lhs = ctx32.dot(d32, W.unsqueeze(0))[0]
+    rhs = ctx32.dot(p0g.reshape(1, -1), a32.reshape(1, -1))[0]
+    d32, a32 = to_np(d32)[0], to_np(a32)[0]
+    del ctx32
+    torch.cuda.empty_cache()
+    ctx64, _ = make_pair(w, "fp64", nt=16)
+    d64 = to_np(ctx64.acoustic_forward(to_gpu(p0, torch.float64)))[0]
+    a64 = to_np(ctx64.acoustic_adjoint(W.double()))[0]
+    errs = (abs(lhs - rhs) / abs(lhs), rel_l2(d32, d64), rel_l2(a32, a64))
+    assert errs[0] <= 1e-5 and errs[1] <= 2e-4 and errs[2] <= 2e-4, errs
