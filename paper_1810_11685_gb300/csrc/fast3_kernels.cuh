@@ -2,9 +2,11 @@
 // of fft_reg.cuh (the 3D counterpart of fast_kernels.cuh).
 //
 // x row pass (one thread group per pair of y-rows (k, j0), (k, j0 + 1)):
-//   load up to three incoming half spectra into registers, Hermitian-extend
-//   and pack the two rows into one complex sequence -> inverse x-FFT via
-//   conj(FFT(conj .)) with the reversed plan -> pointwise update of one
+//   start asynchronous copies (cp.async) of the two rows of every state and
+//   medium field the update reads into shared memory; load up to three
+//   incoming half spectra into registers, Hermitian-extend and pack the two
+//   rows into one complex sequence -> inverse x-FFT via conj(FFT(conj .))
+//   with the reversed plan -> wait for the copies -> pointwise update of one
 //   equation (row3_point) on the registers -> forward x-FFT -> split into the
 //   two rows' half spectra through shared memory -> store.
 // y pass (one thread group per (z, kx) line, CBW adjacent kx per CTA so that a
@@ -18,23 +20,48 @@
 
 namespace qpat {
 
+// Row pairs per CTA of the 3D row pass (about 96 threads: the staged operands
+// take shared memory that would otherwise hold more row pairs).
+template <int L>
+constexpr int rp3() { return (96 / SGeom<L>::TPT) > 0 ? (96 / SGeom<L>::TPT) : 1; }
+
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// Operand loader reading the staged rows: field f of row rr at point i.
+template <typename T, int PH, int L>
+struct R3Staged {
+  const T* st;
+  int rr, i;
+  __device__ __forceinline__ T operator()(int f) const { return st[(r3_slot(PH, f) * 2 + rr) * L + i]; }
+};
+
 template <typename T, int L, int PH>
-__global__ void __launch_bounds__(SGeom<L>::RP * SGeom<L>::TPT)
+__global__ void __launch_bounds__(rp3<L>() * SGeom<L>::TPT)
 row3_fast(const Prop3<T> a) {
   constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH);
   constexpr int NSX = (KIN > KOUT ? KIN : KOUT);
+  constexpr int NF = r3_nfields(PH);
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
-  constexpr int TPT = G::TPT, SL = G::SL, RP = G::RP;
+  constexpr int TPT = G::TPT, SL = G::SL, RP = rp3<L>();
   constexpr int Q1 = G::Q1, QL = G::QL, P1 = G::P1;
   constexpr bool SCATTER = (PH == A_R1 || PH == A_R1L);
+  static_assert((L * sizeof(T)) % 16 == 0, "staged rows are copied in 16-byte pieces");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = threadIdx.x / TPT;
   const int j = threadIdx.x - m * TPT;
   C* tws = reinterpret_cast<C*>(smem_raw);                       // W_L^m table
   C* bufA = tws + L + m * 2 * NSX * SL;
   C* bufB = bufA + NSX * SL;
-  T* sc = reinterpret_cast<T*>(tws + L + RP * 2 * NSX * SL) + m * 2 * L;
+  T* stage = reinterpret_cast<T*>(tws + L + RP * 2 * NSX * SL) + m * NF * 2 * L;
+  T* sc = reinterpret_cast<T*>(tws + L + RP * 2 * NSX * SL) + RP * NF * 2 * L + m * 2 * L;
   const int b = blockIdx.z, k = blockIdx.y;
   const int jp = blockIdx.x * RP + m;
   const bool valid = jp < (a.ny >> 1);
@@ -42,6 +69,17 @@ row3_fast(const Prop3<T> a) {
   C* spec = a.spec + (long long)b * a.sstride + ((long long)k * a.ny + j0) * a.pitch;
   const bool skip_in = (a.flags & kSkipInput) != 0;
 
+  // the update's operands of both rows, copied while the spectra load and the
+  // inverse transform runs
+  if (valid) {
+    constexpr int CH = L * (int)sizeof(T) / 16;                  // 16-byte pieces per row
+    for (int q = j; q < NF * 2 * CH; q += TPT) {
+      const int f = q / (2 * CH), rr = (q / CH) & 1, piece = q % CH;
+      const T* src = r3_row<T>(a, r3_field(PH, f), b, (long long)k * a.ny + j0 + rr);
+      cp_async16(stage + (f * 2 + rr) * L + piece * (16 / (int)sizeof(T)),
+                 src + piece * (16 / (int)sizeof(T)));
+    }
+  }
   for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
 
   // 1. inverse x-transform of the incoming half spectra (reversed plan)
@@ -82,8 +120,9 @@ row3_fast(const Prop3<T> a) {
     for (int i = j; i < 2 * L; i += TPT) sc[i] = (T)0;
     __syncthreads();
     if (valid) sensor_scatter_rows3<T>(a, b, k * a.ny + j0, sc, j, TPT);
-    __syncthreads();
   }
+  cp_async_wait_all();
+  __syncthreads();
 
   // 2. pointwise update on grid points i = j + r L/Q1 of both rows;
   //    y = FFT(conj Z) = conj(z): row j0 is Re, row j0+1 is -Im
@@ -100,7 +139,8 @@ row3_fast(const Prop3<T> a) {
 #pragma unroll
         for (int s = 0; s < KIN; ++s) in[s] = rr ? -y[s][r].y : y[s][r].x;
         const T scv = SCATTER ? sc[rr * L + i] : (T)0;
-        row3_point<T>(a, PH, b, i, j0 + rr, k, in, scv, u[rr], bad);
+        const R3Staged<T, PH, L> ld{stage, rr, i};
+        row3_point<T>(a, PH, b, i, j0 + rr, k, in, scv, ld, u[rr], bad);
       }
     }
 #pragma unroll
@@ -241,9 +281,10 @@ zpass3_fast(const Prop3<T> a) {
 template <typename T, int L, int PH>
 constexpr size_t row3_fast_smem() {
   typedef typename V2<T>::t C;
-  constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT);
+  constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT), RP = rp3<L>();
   constexpr bool SCATTER = (PH == A_R1 || PH == A_R1L);
-  return (L + SGeom<L>::RP * 2 * NSX * SGeom<L>::SL) * sizeof(C) + (SCATTER ? SGeom<L>::RP * 2 * L * sizeof(T) : 0);
+  return (L + RP * 2 * NSX * SGeom<L>::SL) * sizeof(C) + (size_t)RP * r3_nfields(PH) * 2 * L * sizeof(T) +
+         (SCATTER ? RP * 2 * L * sizeof(T) : 0);
 }
 template <typename T, int L, int NSX>
 constexpr size_t line3_fast_smem() {
@@ -283,9 +324,9 @@ void prepare3_fast_len() {
 
 template <typename T, int L, int PH>
 void run_row3_fast(const Prop3<T>& a, int batch, cudaStream_t s) {
-  typedef SGeom<L> G;
-  const dim3 grid((a.ny / 2 + G::RP - 1) / G::RP, a.nz, batch);
-  row3_fast<T, L, PH><<<grid, G::RP * G::TPT, row3_fast_smem<T, L, PH>(), s>>>(a);
+  constexpr int RP = rp3<L>();
+  const dim3 grid((a.ny / 2 + RP - 1) / RP, a.nz, batch);
+  row3_fast<T, L, PH><<<grid, RP * SGeom<L>::TPT, row3_fast_smem<T, L, PH>(), s>>>(a);
 }
 template <typename T, int L, int PH>
 void run_z3_fast(const Prop3<T>& a, int batch, cudaStream_t s) {

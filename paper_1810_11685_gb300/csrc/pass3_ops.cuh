@@ -16,10 +16,86 @@ __host__ __device__ constexpr int z3_kout(int ph) { return ph == A_C6 ? 1 : (ph 
 
 constexpr int k3Threads = 256;
 
-// ---- pointwise update of one grid point (i, j, k) -------------------------
+// ---- operands of the pointwise updates --------------------------------------
+// Per-point fields a row pass reads: state of problem b (v_i, rho_i, the
+// sampling buffer) and medium diagonals shared by the batch.
+enum R3Field : int { FVX, FVY, FVZ, FRX, FRY, FRZ, FPB, MCC, MRHO, MDX, MDY, MDZ, META, MTAU, kR3Fields };
+
+// Fields read by the update of phase ph, in staging order (-1: unused slot).
+__host__ __device__ constexpr int r3_field(int ph, int slot) {
+  switch (ph) {
+    case F_R1: { const int f[6] = {FRX, FRY, FRZ, MCC, META, MTAU}; return f[slot]; }
+    case F_R2: case A_R5: { const int f[6] = {FVX, FVY, FVZ, MDX, MDY, MDZ}; return f[slot]; }
+    case F_R3: case F_R3L: case A_R1L: { const int f[6] = {FRX, FRY, FRZ, MRHO, MCC, -1}; return f[slot]; }
+    case A_R1: { const int f[6] = {MCC, META, MTAU, -1, -1, -1}; return f[slot]; }
+    case A_R3: { const int f[6] = {FRX, FRY, FRZ, MRHO, FPB, MCC}; return f[slot]; }
+    default: return -1;
+  }
+}
+__host__ __device__ constexpr int r3_nfields(int ph) {
+  int n = 0;
+  for (int s = 0; s < 6; ++s) n += r3_field(ph, s) >= 0 ? 1 : 0;
+  return n;
+}
+__host__ __device__ constexpr int r3_slot(int ph, int field) {
+  for (int s = 0; s < 6; ++s)
+    if (r3_field(ph, s) == field) return s;
+  return -1;
+}
+
+// Row-start pointer of field f for grid row r = k ny + j of problem b.
 template <typename T>
+__device__ __forceinline__ const T* r3_row(const Prop3<T>& a, int f, int b, long long r) {
+  const long long o = r * a.nx, ob = (long long)b * a.gstride + o;
+  switch (f) {
+    case FVX: return a.vx + ob;
+    case FVY: return a.vy + ob;
+    case FVZ: return a.vz + ob;
+    case FRX: return a.rx + ob;
+    case FRY: return a.ry + ob;
+    case FRZ: return a.rz + ob;
+    case FPB: return a.pbuf + ob;
+    case MCC: return a.Cc + o;
+    case MRHO: return a.rho0 + o;
+    case MDX: return a.dtrsx + o;
+    case MDY: return a.dtrsy + o;
+    case MDZ: return a.dtrsz + o;
+    case META: return a.eta + o;
+    default: return a.tau + o;
+  }
+}
+
+// Operand loader reading global memory at grid point g of problem b.
+template <typename T>
+struct R3Global {
+  const Prop3<T>& a;
+  long long g, gb;
+  __device__ __forceinline__ T operator()(int f) const {
+    switch (f) {
+      case FVX: return a.vx[gb];
+      case FVY: return a.vy[gb];
+      case FVZ: return a.vz[gb];
+      case FRX: return a.rx[gb];
+      case FRY: return a.ry[gb];
+      case FRZ: return a.rz[gb];
+      case FPB: return a.pbuf[gb];
+      case MCC: return a.Cc[g];
+      case MRHO: return a.rho0[g];
+      case MDX: return a.dtrsx[g];
+      case MDY: return a.dtrsy[g];
+      case MDZ: return a.dtrsz[g];
+      case META: return a.eta[g];
+      default: return a.tau[g];
+    }
+  }
+};
+
+// ---- pointwise update of one grid point (i, j, k) -------------------------
+// ld(f) returns field f at this point (from global memory or a staged copy);
+// results go to global memory and to out[] (the fields to be transformed).
+template <typename T, class Ld>
 __device__ __forceinline__ void row3_point(const Prop3<T>& a, const int ph, const int b, const int i, const int j,
-                                           const int k, const T* in, const T scv, T* out, bool& bad) {
+                                           const int k, const T* in, const T scv, const Ld& ld, T* out, bool& bad) {
   const long long g = ((long long)k * a.ny + j) * a.nx + i;
   const long long gb = (long long)b * a.gstride + g;
   const bool interior = i >= a.pml && i < a.pml + a.n0 && j >= a.pml && j < a.pml + a.n1 && k >= a.pml &&
@@ -29,17 +105,17 @@ __device__ __forceinline__ void row3_point(const Prop3<T>& a, const int ph, cons
   out[0] = out[1] = out[2] = (T)0;
   if (ph == F_R1) {
     // eq. num-p with sum_i rho_i over three components
-    const T r = a.rx[gb] + a.ry[gb] + a.rz[gb];
-    const T p = a.Cc[g] * ((r - a.eta[g] * in[0]) + a.tau[g] * in[1]);
+    const T r = ld(FRX) + ld(FRY) + ld(FRZ);
+    const T p = ld(MCC) * ((r - ld(META) * in[0]) + ld(MTAU) * in[1]);
     a.pbuf[gb] = p;
     bad |= !isfinite(p);
     out[0] = p;
   } else if (ph == F_R2) {
     // eq. num-vel per axis
     const T sx = a.asx[i], sy = a.asy[j], sz = a.asz[k];
-    const T vx = sx * (sx * a.vx[gb] - a.dtrsx[g] * in[0]);
-    const T vy = sy * (sy * a.vy[gb] - a.dtrsy[g] * in[1]);
-    const T vz = sz * (sz * a.vz[gb] - a.dtrsz[g] * in[2]);
+    const T vx = sx * (sx * ld(FVX) - ld(MDX) * in[0]);
+    const T vy = sy * (sy * ld(FVY) - ld(MDY) * in[1]);
+    const T vz = sz * (sz * ld(FVZ) - ld(MDZ) * in[2]);
     a.vx[gb] = vx;
     a.vy[gb] = vy;
     a.vz[gb] = vz;
@@ -49,11 +125,11 @@ __device__ __forceinline__ void row3_point(const Prop3<T>& a, const int ph, cons
   } else if (ph == F_R3 || ph == F_R3L) {
     // eq. num-rho with the additive source of eq. s1, dt s_i = P0 / (2 d c^2), d = 3
     T q = (T)0;
-    if ((a.flags & kSource) && interior) q = a.io->p0[(long long)b * N + ii] / ((T)6 * a.Cc[g]);
-    const T ax = a.ax[i], ay = a.ay[j], az = a.az[k], r0 = a.rho0[g];
-    const T rx = ax * (ax * a.rx[gb] - a.dt * r0 * in[0]) + q;
-    const T ry = ay * (ay * a.ry[gb] - a.dt * r0 * in[1]) + q;
-    const T rz = az * (az * a.rz[gb] - a.dt * r0 * in[2]) + q;
+    if ((a.flags & kSource) && interior) q = a.io->p0[(long long)b * N + ii] / ((T)6 * ld(MCC));
+    const T ax = a.ax[i], ay = a.ay[j], az = a.az[k], r0 = ld(MRHO);
+    const T rx = ax * (ax * ld(FRX) - a.dt * r0 * in[0]) + q;
+    const T ry = ay * (ay * ld(FRY) - a.dt * r0 * in[1]) + q;
+    const T rz = az * (az * ld(FRZ) - a.dt * r0 * in[2]) + q;
     a.rx[gb] = rx;
     a.ry[gb] = ry;
     a.rz[gb] = rz;
@@ -61,32 +137,33 @@ __device__ __forceinline__ void row3_point(const Prop3<T>& a, const int ph, cons
       out[0] = rx + ry + rz;
       out[1] = r0 * (ax * in[0] + ay * in[1] + az * in[2]);
     } else {
-      const T p = a.Cc[g] * (rx + ry + rz);
+      const T p = ld(MCC) * (rx + ry + rz);
       a.pbuf[gb] = p;
       bad |= !isfinite(p);
       out[0] = p;
     }
   } else if (ph == A_R1) {
-    const T Cp = a.Cc[g] * (in[0] + scv);
+    const T Cp = ld(MCC) * (in[0] + scv);
     a.pbuf[gb] = Cp;
-    out[0] = a.eta[g] * Cp;
-    out[1] = a.tau[g] * Cp;
+    out[0] = ld(META) * Cp;
+    out[1] = ld(MTAU) * Cp;
   } else if (ph == A_R1L || ph == A_R3) {
     T Cp, ya = (T)0;
     if (ph == A_R1L) {
-      Cp = a.Cc[g] * (in[0] + scv);
+      Cp = ld(MCC) * (in[0] + scv);
     } else {
-      Cp = a.pbuf[gb];
+      Cp = ld(FPB);
       ya = in[1];
     }
     const T rpart = (ph == A_R1L) ? Cp : Cp - in[0];
     const T A[3] = {a.ax[i], a.ay[j], a.az[k]};
+    const T Rin[3] = {ld(FRX), ld(FRY), ld(FRZ)};
     T* R[3] = {a.rx, a.ry, a.rz};
-    const T r0 = a.rho0[g];
+    const T r0 = ld(MRHO);
     T sum = (T)0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const T rt = R[c][gb] + rpart;
+      const T rt = Rin[c] + rpart;
       out[c] = r0 * A[c] * (ya - a.dt * rt);
       R[c][gb] = A[c] * A[c] * rt;
       sum += rt;
@@ -94,17 +171,18 @@ __device__ __forceinline__ void row3_point(const Prop3<T>& a, const int ph, cons
     bad |= !isfinite(sum);
     if (interior && (a.flags & (kAccWrite | kAccAdd))) {
       T* dst = a.io->p0adj + (long long)b * N + ii;
-      const T val = sum / ((T)6 * a.Cc[g]);
+      const T val = sum / ((T)6 * ld(MCC));
       if (a.flags & kAccWrite) *dst = val;
       else *dst += val;
     }
   } else if (ph == A_R5) {
     const T S[3] = {a.asx[i], a.asy[j], a.asz[k]};
-    const T D[3] = {a.dtrsx[g], a.dtrsy[g], a.dtrsz[g]};
+    const T D[3] = {ld(MDX), ld(MDY), ld(MDZ)};
+    const T Vin[3] = {ld(FVX), ld(FVY), ld(FVZ)};
     T* V[3] = {a.vx, a.vy, a.vz};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const T vt = V[c][gb] + in[c];
+      const T vt = Vin[c] + in[c];
       V[c][gb] = S[c] * S[c] * vt;
       out[c] = S[c] * D[c] * vt;
     }

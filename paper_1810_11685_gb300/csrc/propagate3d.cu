@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(k3Threads) row3_kernel(const Prop3<T> a) {
       }
       const T scv = (PH == A_R1 || PH == A_R1L) ? sc[rr * nx + i] : (T)0;
       T out[3];
-      row3_point<T>(a, PH, b, i, j0 + rr, k, in, scv, out, bad);
+      const long long g = ((long long)k * a.ny + j0 + rr) * a.nx + i;
+      const R3Global<T> ld{a, g, (long long)b * a.gstride + g};
+      row3_point<T>(a, PH, b, i, j0 + rr, k, in, scv, ld, out, bad);
 #pragma unroll
       for (int s = 0; s < KOUT; ++s) {
         if (rr == 0) oth[s * nx + i].x = out[s];
