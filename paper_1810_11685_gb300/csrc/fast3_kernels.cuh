@@ -25,15 +25,6 @@ namespace qpat {
 template <int L>
 constexpr int rp3() { return (96 / SGeom<L>::TPT) > 0 ? (96 / SGeom<L>::TPT) : 1; }
 
-// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 // Operand loader reading the staged rows: field f of row rr at point i.
 template <typename T, int PH, int L>
 struct R3Staged {

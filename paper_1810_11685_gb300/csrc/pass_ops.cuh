@@ -52,6 +52,16 @@ __device__ __forceinline__ RowIn<T> row_load(const PropArgs<T>& a, const int ph,
   return r;
 }
 
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+// Commit this thread's outstanding cp.async copies and wait for all of them.
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Pointwise update of one grid point (i, j) of problem b in a row pass.
 // in0/in1: the incoming fields after the inverse transforms (already
 // normalised); scv: M^T w at this point (adjoint sensor source, A_R1*);
