@@ -20,10 +20,11 @@
 
 namespace qpat {
 
-// Row pairs per CTA of the 3D row pass (about 96 threads: the staged operands
-// take shared memory that would otherwise hold more row pairs).
+// Row pairs per CTA of the 3D row pass: about 48 threads, i.e. one row pair
+// at extent 288 (measured on GB300 at 288^3: 48 threads 8.7e9, 96 threads
+// 8.3e9, 144 threads 8.0e9 forward+adjoint cell-steps/s).
 template <int L>
-constexpr int rp3() { return (96 / SGeom<L>::TPT) > 0 ? (96 / SGeom<L>::TPT) : 1; }
+constexpr int rp3() { return (48 / SGeom<L>::TPT) > 0 ? (48 / SGeom<L>::TPT) : 1; }
 
 // Operand loader reading the staged rows: field f of row rr at point i.
 template <typename T, int PH, int L>
