@@ -26,6 +26,11 @@ namespace qpat {
 template <int L>
 constexpr int rp3() { return (48 / SGeom<L>::TPT) > 0 ? (48 / SGeom<L>::TPT) : 1; }
 
+// Spectral lines per CTA of the 3D y and z passes (adjacent kx; measured on
+// GB300 at 288^3: 8 lines 9.3e9, 4 lines 8.7e9, 2 lines 6.3e9 cell-steps/s).
+template <int L>
+constexpr int cbw3() { return 8; }
+
 // Operand loader reading the staged rows: field f of row rr at point i.
 template <typename T, int PH, int L>
 struct R3Staged {
@@ -168,11 +173,11 @@ row3_fast(const Prop3<T> a) {
 
 // y pass over the (z = blockIdx.y, kx) lines of problem blockIdx.z.
 template <typename T, int L, int K, int INV>
-__global__ void __launch_bounds__(SGeom<L>::CBW * SGeom<L>::TPT)
+__global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT)
 ypass3_fast(const Prop3<T> a, const int gather) {
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
-  constexpr int SL = G::SL, CBW = G::CBW, Q1 = G::Q1, QL = G::QL;
+  constexpr int SL = G::SL, CBW = cbw3<L>(), Q1 = G::Q1, QL = G::QL;
   constexpr int CS = col_stride<L, K, CBW>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % CBW;
@@ -212,13 +217,13 @@ ypass3_fast(const Prop3<T> a, const int gather) {
 
 // z pass over the (ky = blockIdx.y, kx) lines of problem blockIdx.z.
 template <typename T, int L, int PH>
-__global__ void __launch_bounds__(SGeom<L>::CBW * SGeom<L>::TPT)
+__global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT)
 zpass3_fast(const Prop3<T> a) {
   constexpr int KIN = z3_kin(PH), KOUT = z3_kout(PH);
   constexpr int NSX = (KIN > KOUT ? KIN : KOUT);
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
-  constexpr int SL = G::SL, CBW = G::CBW, Q1 = G::Q1, QL = G::QL;
+  constexpr int SL = G::SL, CBW = cbw3<L>(), Q1 = G::Q1, QL = G::QL;
   constexpr int CS = col_stride<L, NSX, CBW>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % CBW;
@@ -281,7 +286,7 @@ constexpr size_t row3_fast_smem() {
 template <typename T, int L, int NSX>
 constexpr size_t line3_fast_smem() {
   typedef typename V2<T>::t C;
-  return ((size_t)L + (size_t)SGeom<L>::CBW * col_stride<L, NSX, SGeom<L>::CBW>()) * sizeof(C);
+  return ((size_t)L + (size_t)cbw3<L>() * col_stride<L, NSX, cbw3<L>()>()) * sizeof(C);
 }
 
 template <typename T, int L, int PH>
@@ -324,14 +329,16 @@ template <typename T, int L, int PH>
 void run_z3_fast(const Prop3<T>& a, int batch, cudaStream_t s) {
   typedef SGeom<L> G;
   constexpr int NSX = z3_kin(PH) > z3_kout(PH) ? z3_kin(PH) : z3_kout(PH);
-  const dim3 grid((a.nxh + G::CBW - 1) / G::CBW, a.ny, batch);
-  zpass3_fast<T, L, PH><<<grid, G::CBW * G::TPT, line3_fast_smem<T, L, NSX>(), s>>>(a);
+  constexpr int CBW = cbw3<L>();
+  const dim3 grid((a.nxh + CBW - 1) / CBW, a.ny, batch);
+  zpass3_fast<T, L, PH><<<grid, CBW * G::TPT, line3_fast_smem<T, L, NSX>(), s>>>(a);
 }
 template <typename T, int L, int K, int INV>
 void run_y3_fast(const Prop3<T>& a, int gather, int batch, cudaStream_t s) {
   typedef SGeom<L> G;
-  const dim3 grid((a.nxh + G::CBW - 1) / G::CBW, a.nz, batch);
-  ypass3_fast<T, L, K, INV><<<grid, G::CBW * G::TPT, line3_fast_smem<T, L, K>(), s>>>(a, gather);
+  constexpr int CBW = cbw3<L>();
+  const dim3 grid((a.nxh + CBW - 1) / CBW, a.nz, batch);
+  ypass3_fast<T, L, K, INV><<<grid, CBW * G::TPT, line3_fast_smem<T, L, K>(), s>>>(a, gather);
 }
 
 template <typename T, int L>
