@@ -70,12 +70,15 @@ row3_fast(const Prop3<T> a) {
   // inverse transform runs
   if (valid) {
     constexpr int CH = L * (int)sizeof(T) / 16;                  // 16-byte pieces per row
-    for (int q = j; q < NF * 2 * CH; q += TPT) {
-      const int f = q / (2 * CH), rr = (q / CH) & 1, piece = q % CH;
-      const T* src = r3_row<T>(a, r3_field(PH, f), b, (long long)k * a.ny + j0 + rr);
-      cp_async16(stage + (f * 2 + rr) * L + piece * (16 / (int)sizeof(T)),
-                 src + piece * (16 / (int)sizeof(T)));
-    }
+    constexpr int PW = 16 / (int)sizeof(T);                      // elements per piece
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const T* src = r3_row<T>(a, r3_field(PH, f), b, (long long)k * a.ny + j0 + rr);
+        T* dst = stage + (f * 2 + rr) * L;
+        for (int piece = j; piece < CH; piece += TPT) cp_async16(dst + piece * PW, src + piece * PW);
+      }
   }
   for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
 
