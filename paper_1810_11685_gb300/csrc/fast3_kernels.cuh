@@ -26,10 +26,27 @@ namespace qpat {
 template <int L>
 constexpr int rp3() { return (48 / SGeom<L>::TPT) > 0 ? (48 / SGeom<L>::TPT) : 1; }
 
+// The y and z passes run their Stockham stages in one shared buffer per line
+// (measured on GB300 at 288^3, 8 lines per CTA: 1.08e10 against 1.00e10
+// cell-steps/s with two buffers).
+constexpr bool kLine3OneBuf = true;
+constexpr int kLine3Bufs = kLine3OneBuf ? 1 : 2;
+
 // Spectral lines per CTA of the 3D y and z passes (adjacent kx; measured on
 // GB300 at 288^3: 8 lines 9.3e9, 4 lines 8.7e9, 2 lines 6.3e9 cell-steps/s).
 template <int L>
 constexpr int cbw3() { return 8; }
+
+// The row pass runs its Stockham stages in one shared buffer per row pair
+// (288^3: 1.11e10 against 1.09e10 cell-steps/s with two buffers).
+constexpr bool kRow3OneBuf = true;
+
+// Complex values of the row pass's shared memory before its staging area:
+// twiddles and Stockham buffers, rounded up to a 16-byte boundary.
+template <int L, int NSX>
+constexpr int row3_stage_offset() {
+  return (L + rp3<L>() * (kRow3OneBuf ? 1 : 2) * NSX * SGeom<L>::SL + 1) & ~1;
+}
 
 // Operand loader reading the staged rows: field f of row rr at point i.
 template <typename T, int PH, int L>
@@ -55,10 +72,13 @@ row3_fast(const Prop3<T> a) {
   const int m = threadIdx.x / TPT;
   const int j = threadIdx.x - m * TPT;
   C* tws = reinterpret_cast<C*>(smem_raw);                       // W_L^m table
-  C* bufA = tws + L + m * 2 * NSX * SL;
-  C* bufB = bufA + NSX * SL;
-  T* stage = reinterpret_cast<T*>(tws + L + RP * 2 * NSX * SL) + m * NF * 2 * L;
-  T* sc = reinterpret_cast<T*>(tws + L + RP * 2 * NSX * SL) + RP * NF * 2 * L + m * 2 * L;
+  constexpr int NB = kRow3OneBuf ? 1 : 2;
+  // the staging area starts on a 16-byte boundary (cp.async destinations)
+  constexpr int STAGE_OFF = row3_stage_offset<L, NSX>();
+  C* bufA = tws + L + m * NB * NSX * SL;
+  C* bufB = kRow3OneBuf ? bufA : bufA + NSX * SL;
+  T* stage = reinterpret_cast<T*>(tws + STAGE_OFF) + m * NF * 2 * L;
+  T* sc = reinterpret_cast<T*>(tws + STAGE_OFF) + RP * NF * 2 * L + m * 2 * L;
   const int b = blockIdx.z, k = blockIdx.y;
   const int jp = blockIdx.x * RP + m;
   const bool valid = jp < (a.ny >> 1);
@@ -107,7 +127,7 @@ row3_fast(const Prop3<T> a) {
         }
       }
     }
-    fft_stockham<L, G::P1, G::P2, G::P3, KIN>(v, y, bufA, bufB, SL, j, tws);
+    fft_stockham<L, G::P1, G::P2, G::P3, KIN, kRow3OneBuf>(v, y, bufA, bufB, SL, j, tws);
   } else {
 #pragma unroll
     for (int s = 0; s < KIN; ++s)
@@ -151,7 +171,7 @@ row3_fast(const Prop3<T> a) {
 
   // 3. forward x-transform of the packed outgoing rows, split, store
   C X[KOUT][QL];
-  fft_stockham<L, G::Q1, G::Q2, G::Q3, KOUT>(o, X, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KOUT, kRow3OneBuf>(o, X, bufA, bufB, SL, j, tws);
   if (j < L / QL) {
 #pragma unroll
     for (int s = 0; s < KOUT; ++s)
@@ -174,6 +194,13 @@ row3_fast(const Prop3<T> a) {
   }
 }
 
+// Per-line shared-memory stride of the y and z passes (col_stride with the
+// number of Stockham buffers in use).
+template <int L, int NSX, int CBW>
+__host__ __device__ constexpr int line3_stride() {
+  return kLine3Bufs * NSX * SGeom<L>::SL + ((16 / CBW - (kLine3Bufs * NSX * SGeom<L>::SL) % 16) + 16) % 16;
+}
+
 // y pass over the (z = blockIdx.y, kx) lines of problem blockIdx.z.
 template <typename T, int L, int K, int INV>
 __global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT)
@@ -181,13 +208,13 @@ ypass3_fast(const Prop3<T> a, const int gather) {
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
   constexpr int SL = G::SL, CBW = cbw3<L>(), Q1 = G::Q1, QL = G::QL;
-  constexpr int CS = col_stride<L, K, CBW>();
+  constexpr int CS = line3_stride<L, K, CBW>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % CBW;
   const int j = threadIdx.x / CBW;
   C* tws = reinterpret_cast<C*>(smem_raw);
   C* bufA = tws + L + c * CS;
-  C* bufB = bufA + K * SL;
+  C* bufB = kLine3OneBuf ? bufA : bufA + K * SL;
   const int b = blockIdx.z, k = blockIdx.y;
   const int kx = blockIdx.x * CBW + c;
   const bool valid = kx < a.nxh;
@@ -208,7 +235,7 @@ ypass3_fast(const Prop3<T> a, const int gather) {
   }
   for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twy[t];
   C X[K][QL];
-  fft_stockham<L, G::Q1, G::Q2, G::Q3, K>(v, X, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, K, kLine3OneBuf>(v, X, bufA, bufB, SL, j, tws);
   if (j < L / QL && valid) {
 #pragma unroll
     for (int s = 0; s < K; ++s)
@@ -227,13 +254,13 @@ zpass3_fast(const Prop3<T> a) {
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
   constexpr int SL = G::SL, CBW = cbw3<L>(), Q1 = G::Q1, QL = G::QL;
-  constexpr int CS = col_stride<L, NSX, CBW>();
+  constexpr int CS = line3_stride<L, NSX, CBW>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % CBW;
   const int j = threadIdx.x / CBW;
   C* tws = reinterpret_cast<C*>(smem_raw);
   C* bufA = tws + L + c * CS;
-  C* bufB = bufA + NSX * SL;
+  C* bufB = kLine3OneBuf ? bufA : bufA + NSX * SL;
   const int b = blockIdx.z, ky = blockIdx.y;
   const int kx = blockIdx.x * CBW + c;
   const bool valid = kx < a.nxh;
@@ -256,7 +283,7 @@ zpass3_fast(const Prop3<T> a) {
     st[r] = (j < L / QL && valid) ? z3_load<T, C>(a, PH, kx, ky, j + r * (L / QL)) : Z3In<T, C>{};
   const C sx = z3_sx<T, C>(a, PH, kxs), sy = z3_sy<T, C>(a, PH, ky);
   C X[KIN][QL];
-  fft_stockham<L, G::Q1, G::Q2, G::Q3, KIN>(v, X, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KIN, kLine3OneBuf>(v, X, bufA, bufB, SL, j, tws);
   C o[KOUT][QL];
 #pragma unroll
   for (int r = 0; r < QL; ++r) {
@@ -269,7 +296,7 @@ zpass3_fast(const Prop3<T> a) {
     for (int s = 0; s < KOUT; ++s) o[s][r] = cconj(out[s]);
   }
   C Y[KOUT][Q1];
-  fft_stockham<L, G::P1, G::P2, G::P3, KOUT>(o, Y, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::P1, G::P2, G::P3, KOUT, kLine3OneBuf>(o, Y, bufA, bufB, SL, j, tws);
   if (j < L / Q1 && valid) {
 #pragma unroll
     for (int s = 0; s < KOUT; ++s)
@@ -283,13 +310,13 @@ constexpr size_t row3_fast_smem() {
   typedef typename V2<T>::t C;
   constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT), RP = rp3<L>();
   constexpr bool SCATTER = (PH == A_R1 || PH == A_R1L);
-  return (L + RP * 2 * NSX * SGeom<L>::SL) * sizeof(C) + (size_t)RP * r3_nfields(PH) * 2 * L * sizeof(T) +
+  return (size_t)row3_stage_offset<L, NSX>() * sizeof(C) + (size_t)RP * r3_nfields(PH) * 2 * L * sizeof(T) +
          (SCATTER ? RP * 2 * L * sizeof(T) : 0);
 }
 template <typename T, int L, int NSX>
 constexpr size_t line3_fast_smem() {
   typedef typename V2<T>::t C;
-  return ((size_t)L + (size_t)cbw3<L>() * col_stride<L, NSX, cbw3<L>()>()) * sizeof(C);
+  return ((size_t)L + (size_t)cbw3<L>() * line3_stride<L, NSX, cbw3<L>()>()) * sizeof(C);
 }
 
 template <typename T, int L, int PH>

@@ -149,7 +149,10 @@ __device__ __forceinline__ int stockham_pos(int j, int r) {
 // out: a3[s][r] = X_s[j + r L/Qlast] for j < L/Qlast
 // bufA, bufB: NS * spad_size(L) complex each, sequences `sl` apart.
 // Every thread of the CTA must call it (it synchronises the CTA).
-template <int L, int Q1, int Q2, int Q3, int NS, typename C>
+// ONEBUF: bufB may alias bufA; the middle stage of a three-stage plan then
+// waits for every thread's reads before its writes (one more barrier, half
+// the shared memory).
+template <int L, int Q1, int Q2, int Q3, int NS, bool ONEBUF = false, typename C>
 __device__ __forceinline__ void fft_stockham(C (&a1)[NS][Q1], C (&a3)[NS][(Q3 > 1 ? Q3 : Q2)], C* bufA, C* bufB,
                                              int sl, int j, const C* __restrict__ tw) {
   static_assert(Q1 * Q2 * Q3 == L, "radices must multiply to L");
@@ -168,6 +171,30 @@ __device__ __forceinline__ void fft_stockham(C (&a1)[NS][Q1], C (&a3)[NS][(Q3 > 
 #pragma unroll
         for (int r = 0; r < Q2; ++r) a3[s][r] = bufA[s * sl + spad(j + r * (L / Q2))];
       butterfly<L, Q2, Q1, NS>(a3, j, tw);
+    }
+  } else if constexpr (ONEBUF) {
+    C a2[NS][Q2];
+    if (j < L / Q2) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int r = 0; r < Q2; ++r) a2[s][r] = bufA[s * sl + spad(j + r * (L / Q2))];
+      butterfly<L, Q2, Q1, NS>(a2, j, tw);
+    }
+    __syncthreads();
+    if (j < L / Q2) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int r = 0; r < Q2; ++r) bufB[s * sl + spad(stockham_pos<Q2, Q1>(j, r))] = a2[s][r];
+    }
+    __syncthreads();
+    if (j < L / Q3) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int r = 0; r < Q3; ++r) a3[s][r] = bufB[s * sl + spad(j + r * (L / Q3))];
+      butterfly<L, Q3, Q1 * Q2, NS>(a3, j, tw);
     }
   } else {
     if (j < L / Q2) {
