@@ -176,6 +176,237 @@ row_fast(const PropArgs<T> a) {
   }
 }
 
+// ---- row pass with the pointwise operands staged in shared memory ----------
+// The same pass as row_fast, but the state and medium rows that the update
+// reads are copied into shared memory with cp.async (issued before the
+// spectra loads, waited on just before the update) instead of being held in
+// registers across the inverse transform.  Used for extents whose rows are a
+// whole number of 16-byte pieces.
+
+// Field of the medium or state staged for RowIn member v (0..4) of phase ph,
+// -1 if the update does not read it.
+enum RowField : int { RFVX, RFVY, RFRX, RFRY, RFPB, RFCC, RFRHO, RFDX, RFDY, RFETA, RFTAU };
+__host__ __device__ constexpr int row_field(int ph, int v) {
+  switch (ph) {
+    case F_R1: { const int f[5] = {RFRX, RFRY, RFCC, RFETA, RFTAU}; return f[v]; }
+    case F_R2: case A_R5: { const int f[5] = {RFVX, RFVY, RFDX, RFDY, -1}; return f[v]; }
+    case F_R3: case F_R3L: case A_R1L: { const int f[5] = {RFRX, RFRY, RFRHO, RFCC, -1}; return f[v]; }
+    case A_R1: { const int f[5] = {-1, -1, RFCC, RFETA, RFTAU}; return f[v]; }
+    case A_R3: { const int f[5] = {RFRX, RFRY, RFRHO, RFCC, RFPB}; return f[v]; }
+    default: return -1;
+  }
+}
+// Staging slot of RowIn member v (its rank among the members the phase reads).
+__host__ __device__ constexpr int row_stage_slot(int ph, int v) {
+  int n = 0;
+  for (int u = 0; u < v; ++u) n += row_field(ph, u) >= 0 ? 1 : 0;
+  return n;
+}
+__host__ __device__ constexpr int row_nfields(int ph) { return row_stage_slot(ph, 5); }
+
+// Row-start pointer of field f for grid row j of problem b.
+template <typename T>
+__device__ __forceinline__ const T* row_field_ptr(const PropArgs<T>& a, int f, int b, int j) {
+  const long long o = (long long)j * a.nx, ob = (long long)b * a.gstride + o;
+  switch (f) {
+    case RFVX: return a.vx + ob;
+    case RFVY: return a.vy + ob;
+    case RFRX: return a.rx + ob;
+    case RFRY: return a.ry + ob;
+    case RFPB: return a.pbuf + ob;
+    case RFCC: return a.Cc + o;
+    case RFRHO: return a.rho0 + o;
+    case RFDX: return a.dtrsx + o;
+    case RFDY: return a.dtrsy + o;
+    case RFETA: return a.eta + o;
+    default: return a.tau + o;
+  }
+}
+
+// c^2 is read by F_R3 and A_R3 only at the source steps.
+__device__ __forceinline__ bool row_field_needed(int ph, int f, int flags) {
+  if (f != RFCC) return true;
+  if (ph == F_R3) return (flags & kSource) != 0;
+  if (ph == A_R3) return (flags & (kAccWrite | kAccAdd)) != 0;
+  return true;
+}
+
+#ifndef QPAT_ROW_STAGED
+#define QPAT_ROW_STAGED 1
+#endif
+template <int L>
+__host__ __device__ constexpr bool row_staged() { return QPAT_ROW_STAGED && L % 4 == 0 && L >= 96; }
+
+// Row pairs per CTA of the staged row pass.
+#ifndef QPAT_ROWST_RP
+#define QPAT_ROWST_RP 1
+#endif
+template <int L>
+__host__ __device__ constexpr int rp_st() { return QPAT_ROWST_RP; }
+
+#ifndef QPAT_ROWST_ONEBUF
+#define QPAT_ROWST_ONEBUF 1
+#endif
+constexpr bool kRowStOneBuf = QPAT_ROWST_ONEBUF != 0;
+
+// Complex values before the staging area (twiddles and Stockham buffers),
+// rounded up to a 16-byte boundary.
+template <int L, int NSX>
+__host__ __device__ constexpr int row_st_offset() {
+  return (L + rp_st<L>() * (kRowStOneBuf ? 1 : 2) * NSX * SGeom<L>::SL + 1) & ~1;
+}
+
+template <typename T, int L, int PH>
+__global__ void __launch_bounds__(rp_st<L>() * SGeom<L>::TPT)
+row_fast_st(const PropArgs<T> a) {
+  constexpr int ph = PH, KIN = row_kin(PH), KOUT = row_kout(PH);
+  constexpr int NSX = (KIN > KOUT ? KIN : KOUT), NF = row_nfields(PH);
+  typedef typename V2<T>::t C;
+  typedef SGeom<L> G;
+  constexpr int TPT = G::TPT, SL = G::SL, RP = rp_st<L>();
+  constexpr int Q1 = G::Q1, QL = G::QL, P1 = G::P1;
+  constexpr int NB = kRowStOneBuf ? 1 : 2;
+  static_assert((L * sizeof(T)) % 16 == 0, "staged rows are copied in 16-byte pieces");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = threadIdx.x / TPT;
+  const int j = threadIdx.x - m * TPT;
+  C* tws = reinterpret_cast<C*>(smem_raw);                       // W_L^m table
+  C* bufA = tws + L + m * NB * NSX * SL;
+  C* bufB = kRowStOneBuf ? bufA : bufA + NSX * SL;
+  constexpr int OFF = row_st_offset<L, NSX>();
+  T* stage = reinterpret_cast<T*>(tws + OFF) + m * NF * 2 * L;
+  T* sc = reinterpret_cast<T*>(tws + OFF) + RP * NF * 2 * L + m * 2 * L;
+  const int b = blockIdx.y;
+  const int jp = blockIdx.x * RP + m;
+  const bool valid = jp < (a.ny >> 1);
+  const int j0 = valid ? 2 * jp : 0;
+  C* spec = a.spec + (long long)b * a.sstride;
+  const long long slot = (long long)a.ny * a.pitch;
+  const bool skip_in = (a.flags & kSkipInput) != 0;
+
+  // the update's operands of both rows, copied while the spectra load and the
+  // inverse transform runs
+  if (valid) {
+    constexpr int CH = L * (int)sizeof(T) / 16;                  // 16-byte pieces per row
+    constexpr int PW = 16 / (int)sizeof(T);                      // elements per piece
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int f = row_field(ph, v);
+      if (f < 0 || !row_field_needed(ph, f, a.flags)) continue;
+      const int sl = row_stage_slot(ph, v);
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const T* src = row_field_ptr<T>(a, f, b, j0 + rr);
+        T* dst = stage + (sl * 2 + rr) * L;
+        for (int piece = j; piece < CH; piece += TPT) cp_async16(dst + piece * PW, src + piece * PW);
+      }
+    }
+  }
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
+
+  // 1. inverse x-transform of the incoming half spectra (reversed plan)
+  C y[KIN][Q1];
+  if (!skip_in) {
+    C v[KIN][P1];
+    if (j < L / P1) {
+#pragma unroll
+      for (int s = 0; s < KIN; ++s) {
+        const C* r0 = spec + s * slot + (long long)j0 * a.pitch;
+        const C* r1 = r0 + a.pitch;
+#pragma unroll
+        for (int r = 0; r < P1; ++r) {
+          const int n = j + r * (L / P1);
+          C P, Q;
+          if (2 * n <= L) {
+            P = r0[n];
+            Q = r1[n];
+            if (n == 0 || 2 * n == L) { P.y = (T)0; Q.y = (T)0; }
+          } else {
+            P = cconj(r0[L - n]);
+            Q = cconj(r1[L - n]);
+          }
+          v[s][r] = cmake<C>(P.x - Q.y, -(P.y + Q.x));   // conj(P + i Q)
+        }
+      }
+    }
+    fft_stockham<L, G::P1, G::P2, G::P3, KIN, kRowStOneBuf>(v, y, bufA, bufB, SL, j, tws);
+  } else {
+#pragma unroll
+    for (int s = 0; s < KIN; ++s)
+#pragma unroll
+      for (int r = 0; r < Q1; ++r) y[s][r] = cmake<C>((T)0, (T)0);
+  }
+
+  // adjoint sensor source M^T w_n on the two rows (A_R1, A_R1L)
+  if (KIN == 1) {
+    for (int i = j; i < 2 * L; i += TPT) sc[i] = (T)0;
+    __syncthreads();
+    if (valid) sensor_scatter_rows<T>(a, b, j0, sc, j, TPT);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // 2. pointwise update on grid points i = j + r L/Q1 of both rows;
+  //    y = FFT(conj Z) = conj(z): row j0 is Re, row j0+1 is -Im
+  C o[KOUT][Q1];
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < Q1; ++r) {
+    T u0[2] = {(T)0, (T)0}, u1[2] = {(T)0, (T)0};
+    if (j < L / Q1 && valid) {
+      const int i = j + r * (L / Q1);
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        T sv[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          sv[v] = row_field(ph, v) >= 0 ? stage[(row_stage_slot(ph, v) * 2 + rr) * L + i] : (T)0;
+        const RowIn<T> st{sv[0], sv[1], sv[2], sv[3], sv[4]};
+        const T in0 = rr ? -y[0][r].y : y[0][r].x;
+        const T in1 = (KIN > 1) ? (rr ? -y[KIN - 1][r].y : y[KIN - 1][r].x) : (T)0;
+        const T scv = (KIN == 1) ? sc[rr * L + i] : (T)0;
+        row_point<T>(a, ph, b, i, j0 + rr, in0, in1, scv, st, u0[rr], u1[rr], bad);
+      }
+    }
+    o[0][r] = cmake<C>(u0[0], u0[1]);
+    if (KOUT > 1) o[KOUT - 1][r] = cmake<C>(u1[0], u1[1]);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.err, 1);
+  if (a.flags & kSkipOutput) return;
+
+  // 3. forward x-transform of the packed outgoing rows, split, store
+  C X[KOUT][QL];
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KOUT, kRowStOneBuf>(o, X, bufA, bufB, SL, j, tws);
+  if (j < L / QL) {
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s)
+#pragma unroll
+      for (int r = 0; r < QL; ++r) bufA[s * SL + spad(j + r * (L / QL))] = X[s][r];
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s) {
+      C* w0 = spec + s * slot + (long long)j0 * a.pitch;
+      C* w1 = w0 + a.pitch;
+      for (int k = j; 2 * k <= L; k += TPT) {
+        const C Z = bufA[s * SL + spad(k)];
+        const C Zm = cconj(bufA[s * SL + spad(k == 0 ? 0 : L - k)]);
+        w0[k] = cscale(cadd(Z, Zm), (T)0.5);
+        w1[k] = cscale(cmul_mi(csub(Z, Zm)), (T)0.5);
+      }
+    }
+  }
+}
+
+template <typename T, int L, int PH>
+constexpr size_t row_fast_st_smem() {
+  typedef typename V2<T>::t C;
+  constexpr int KIN = row_kin(PH), KOUT = row_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT);
+  return row_st_offset<L, NSX>() * sizeof(C) + (size_t)rp_st<L>() * (row_nfields(PH) * 2 * L) * sizeof(T) +
+         (KIN == 1 ? (size_t)rp_st<L>() * 2 * L * sizeof(T) : 0);
+}
+
 // Per-column shared-memory stride: congruent to 16/CBW complex values mod 16
 // so that the CBW columns of a half warp fall on distinct banks.
 template <int L, int NSX, int CBW>
@@ -259,7 +490,12 @@ constexpr size_t col_fast_smem() {
 
 template <typename T, int L, int PH>
 void set_row_fast_attr() {
-  cudaFuncSetAttribute(row_fast<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fast_smem<T, L, PH>());
+  if constexpr (row_staged<L>())
+    cudaFuncSetAttribute(row_fast_st<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)row_fast_st_smem<T, L, PH>());
+  else
+    cudaFuncSetAttribute(row_fast<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)row_fast_smem<T, L, PH>());
 }
 template <typename T, int L, int PH>
 void set_col_fast_attr() {
@@ -280,8 +516,14 @@ void prepare_fast_len() {
 template <typename T, int L, int PH>
 void run_row_fast(const PropArgs<T>& a, int batch, cudaStream_t s) {
   typedef SGeom<L> G;
-  dim3 grid((a.ny / 2 + G::RP - 1) / G::RP, batch);
-  row_fast<T, L, PH><<<grid, G::RP * G::TPT, row_fast_smem<T, L, PH>(), s>>>(a);
+  if constexpr (row_staged<L>()) {
+    constexpr int RP = rp_st<L>();
+    dim3 grid((a.ny / 2 + RP - 1) / RP, batch);
+    row_fast_st<T, L, PH><<<grid, RP * G::TPT, row_fast_st_smem<T, L, PH>(), s>>>(a);
+  } else {
+    dim3 grid((a.ny / 2 + G::RP - 1) / G::RP, batch);
+    row_fast<T, L, PH><<<grid, G::RP * G::TPT, row_fast_smem<T, L, PH>(), s>>>(a);
+  }
 }
 
 template <typename T, int L, int PH>
