@@ -57,7 +57,7 @@ struct R3Staged {
 };
 
 template <typename T, int L, int PH>
-__global__ void __launch_bounds__(rp3<L>() * SGeom<L>::TPT)
+__global__ void __launch_bounds__(rp3<L>() * SGeom<L>::TPT, 8)
 row3_fast(const Prop3<T> a) {
   constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH);
   constexpr int NSX = (KIN > KOUT ? KIN : KOUT);
@@ -203,7 +203,7 @@ __host__ __device__ constexpr int line3_stride() {
 
 // y pass over the (z = blockIdx.y, kx) lines of problem blockIdx.z.
 template <typename T, int L, int K, int INV>
-__global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT)
+__global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT, 2)
 ypass3_fast(const Prop3<T> a, const int gather) {
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
@@ -247,7 +247,7 @@ ypass3_fast(const Prop3<T> a, const int gather) {
 
 // z pass over the (ky = blockIdx.y, kx) lines of problem blockIdx.z.
 template <typename T, int L, int PH>
-__global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT)
+__global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT, 2)
 zpass3_fast(const Prop3<T> a) {
   constexpr int KIN = z3_kin(PH), KOUT = z3_kout(PH);
   constexpr int NSX = (KIN > KOUT ? KIN : KOUT);
