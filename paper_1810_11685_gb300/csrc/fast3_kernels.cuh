@@ -31,11 +31,20 @@ constexpr int rp3() { return (48 / SGeom<L>::TPT) > 0 ? (48 / SGeom<L>::TPT) : 1
 // cell-steps/s with two buffers).
 constexpr bool kLine3OneBuf = true;
 constexpr int kLine3Bufs = kLine3OneBuf ? 1 : 2;
+#ifndef QPAT_LINE3_PAIRS
+#define QPAT_LINE3_PAIRS 1
+#endif
+constexpr bool kLine3Pairs = QPAT_LINE3_PAIRS != 0;
 
 // Spectral lines per CTA of the 3D y and z passes (adjacent kx; measured on
 // GB300 at 288^3: 8 lines 9.3e9, 4 lines 8.7e9, 2 lines 6.3e9 cell-steps/s).
 template <int L>
 constexpr int cbw3() { return 8; }
+
+#ifndef QPAT_ROW3_DESC
+#define QPAT_ROW3_DESC 1
+#endif
+constexpr bool kRow3Descending = QPAT_ROW3_DESC != 0;
 
 // The row pass runs its Stockham stages in one shared buffer per row pair
 // (288^3: 1.11e10 against 1.09e10 cell-steps/s with two buffers).
@@ -79,7 +88,10 @@ row3_fast(const Prop3<T> a) {
   C* bufB = kRow3OneBuf ? bufA : bufA + NSX * SL;
   T* stage = reinterpret_cast<T*>(tws + STAGE_OFF) + m * NF * 2 * L;
   T* sc = reinterpret_cast<T*>(tws + STAGE_OFF) + RP * NF * 2 * L + m * 2 * L;
-  const int b = blockIdx.z, k = blockIdx.y;
+  // planes in descending z: the y pass before this one wrote the high planes
+  // last, so they are read while still in L2, and the y pass after this one
+  // (ascending) starts on the planes written last here
+  const int b = blockIdx.z, k = kRow3Descending ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
   const int jp = blockIdx.x * RP + m;
   const bool valid = jp < (a.ny >> 1);
   const int j0 = valid ? 2 * jp : 0;
@@ -235,7 +247,7 @@ ypass3_fast(const Prop3<T> a, const int gather) {
   }
   for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twy[t];
   C X[K][QL];
-  fft_stockham<L, G::Q1, G::Q2, G::Q3, K, kLine3OneBuf>(v, X, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, K, kLine3OneBuf, kLine3Pairs>(v, X, bufA, bufB, SL, j, tws);
   if (j < L / QL && valid) {
 #pragma unroll
     for (int s = 0; s < K; ++s)
@@ -283,7 +295,7 @@ zpass3_fast(const Prop3<T> a) {
     st[r] = (j < L / QL && valid) ? z3_load<T, C>(a, PH, kx, ky, j + r * (L / QL)) : Z3In<T, C>{};
   const C sx = z3_sx<T, C>(a, PH, kxs), sy = z3_sy<T, C>(a, PH, ky);
   C X[KIN][QL];
-  fft_stockham<L, G::Q1, G::Q2, G::Q3, KIN, kLine3OneBuf>(v, X, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KIN, kLine3OneBuf, kLine3Pairs>(v, X, bufA, bufB, SL, j, tws);
   C o[KOUT][QL];
 #pragma unroll
   for (int r = 0; r < QL; ++r) {
@@ -296,7 +308,7 @@ zpass3_fast(const Prop3<T> a) {
     for (int s = 0; s < KOUT; ++s) o[s][r] = cconj(out[s]);
   }
   C Y[KOUT][Q1];
-  fft_stockham<L, G::P1, G::P2, G::P3, KOUT, kLine3OneBuf>(o, Y, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::P1, G::P2, G::P3, KOUT, kLine3OneBuf, kLine3Pairs>(o, Y, bufA, bufB, SL, j, tws);
   if (j < L / Q1 && valid) {
 #pragma unroll
     for (int s = 0; s < KOUT; ++s)

@@ -414,6 +414,11 @@ __host__ __device__ constexpr int col_stride() {
   return 2 * NSX * SGeom<L>::SL + ((16 / CBW - (2 * NSX * SGeom<L>::SL) % 16) + 16) % 16;
 }
 
+#ifndef QPAT_COL_PAIRS
+#define QPAT_COL_PAIRS 1
+#endif
+constexpr bool kColPairs = QPAT_COL_PAIRS != 0;
+
 template <typename T, int L, int PH>
 __global__ void __launch_bounds__(SGeom<L>::CBW * SGeom<L>::TPT)
 col_fast(const PropArgs<T> a) {
@@ -454,7 +459,7 @@ col_fast(const PropArgs<T> a) {
     cst[r] = (j < L / QL && valid) ? col_load<T, C>(a, ph, kx, j + r * (L / QL)) : ColIn<T, C>{};
   const C sx = col_sx<T, C>(a, ph, kxs);
   C X[KIN][QL];
-  fft_stockham<L, G::Q1, G::Q2, G::Q3, KIN>(v, X, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KIN, false, kColPairs>(v, X, bufA, bufB, SL, j, tws);
   // thread j < L/QL holds X[ky = j + r L/QL]
   C o[KOUT][QL];
 #pragma unroll
@@ -465,7 +470,7 @@ col_fast(const PropArgs<T> a) {
     if (KOUT > 1) o[KOUT - 1][r] = cconj(o1);
   }
   C Y[KOUT][Q1];
-  fft_stockham<L, G::P1, G::P2, G::P3, KOUT>(o, Y, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::P1, G::P2, G::P3, KOUT, false, kColPairs>(o, Y, bufA, bufB, SL, j, tws);
   if (j < L / Q1 && valid) {
 #pragma unroll
     for (int s = 0; s < KOUT; ++s)

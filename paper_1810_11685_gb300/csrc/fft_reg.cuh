@@ -321,11 +321,11 @@ __device__ __forceinline__ void fft_stockham_pairs(float2 (&a1)[NS][Q1], float2 
 // ONEBUF: bufB may alias bufA; the middle stage of a three-stage plan then
 // waits for every thread's reads before its writes (one more barrier, half
 // the shared memory).
-template <int L, int Q1, int Q2, int Q3, int NS, bool ONEBUF = false, typename C>
+template <int L, int Q1, int Q2, int Q3, int NS, bool ONEBUF = false, bool PAIRS = true, typename C>
 __device__ __forceinline__ void fft_stockham(C (&a1)[NS][Q1], C (&a3)[NS][(Q3 > 1 ? Q3 : Q2)], C* bufA, C* bufB,
                                              int sl, int j, const C* __restrict__ tw) {
   static_assert(Q1 * Q2 * Q3 == L, "radices must multiply to L");
-  if constexpr (QPAT_FFT_PAIRS && NS >= 2 && std::is_same<C, float2>::value) {
+  if constexpr (PAIRS && QPAT_FFT_PAIRS && NS >= 2 && std::is_same<C, float2>::value) {
     fft_stockham_pairs<L, Q1, Q2, Q3, NS, ONEBUF>(a1, a3, bufA, bufB, sl, j, tw);
     return;
   }
