@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--batch", type=int, default=8, help="independent problems per step")
+    p.add_argument("--batch", type=int, default=12, help="independent problems per step")
     p.add_argument("--nt", type=int, default=None, help="override Nt (default: workload's 2000)")
     p.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/roofline/cpu legs")
     p.add_argument("--n3", type=int, default=None, help="c5 only: interior nodes per axis (default 256)")
@@ -316,7 +316,8 @@ def run_ours(args):
         traffic = None
         try:
             tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
-            if tr.get("source_hash") == source_hash() and top in tr.get("per_launch", {}):
+            if (tr.get("source_hash") == source_hash() and tr.get("batch") == B
+                    and top in tr.get("per_launch", {})):
                 traffic = tr["per_launch"][top]
         except Exception:
             pass

@@ -48,7 +48,10 @@ struct SGeom {
   // columns per CTA: 8 adjacent columns make each warp access 64 contiguous
   // bytes per row (measured on GB300: 576^2 batch 8 1.92e10 against 1.82e10
   // cell-steps/s with 4 columns; 288^2..576^2 jvp mix 1.9e10 against 1.7e10)
-  static constexpr int CBW = 8;
+#ifndef QPAT_COL_CBW
+#define QPAT_COL_CBW 8
+#endif
+  static constexpr int CBW = QPAT_COL_CBW;
 };
 
 template <typename T, int L, int PH>
@@ -251,9 +254,17 @@ constexpr bool kRowStOneBuf = QPAT_ROWST_ONEBUF != 0;
 
 // Complex values before the staging area (twiddles and Stockham buffers),
 // rounded up to a 16-byte boundary.
+// The staged row pass reads the stage twiddles W_L^m straight from global
+// memory (L1) instead of a per-CTA shared copy.
+#ifndef QPAT_ROWST_TWG
+#define QPAT_ROWST_TWG 1
+#endif
+constexpr bool kRowStTwGlobal = QPAT_ROWST_TWG != 0;
+constexpr int kRowStTwSmem(int L) { return kRowStTwGlobal ? 0 : L; }
+
 template <int L, int NSX>
 __host__ __device__ constexpr int row_st_offset() {
-  return (L + rp_st<L>() * (kRowStOneBuf ? 1 : 2) * NSX * SGeom<L>::SL + 1) & ~1;
+  return (kRowStTwSmem(L) + rp_st<L>() * (kRowStOneBuf ? 1 : 2) * NSX * SGeom<L>::SL + 1) & ~1;
 }
 
 template <typename T, int L, int PH>
@@ -270,12 +281,14 @@ row_fast_st(const PropArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = threadIdx.x / TPT;
   const int j = threadIdx.x - m * TPT;
-  C* tws = reinterpret_cast<C*>(smem_raw);                       // W_L^m table
-  C* bufA = tws + L + m * NB * NSX * SL;
+  C* const sbase = reinterpret_cast<C*>(smem_raw);
+  C* tws = sbase;                                                // W_L^m table
+  const C* tw = kRowStTwGlobal ? a.twx : tws;
+  C* bufA = sbase + kRowStTwSmem(L) + m * NB * NSX * SL;
   C* bufB = kRowStOneBuf ? bufA : bufA + NSX * SL;
   constexpr int OFF = row_st_offset<L, NSX>();
-  T* stage = reinterpret_cast<T*>(tws + OFF) + m * NF * 2 * L;
-  T* sc = reinterpret_cast<T*>(tws + OFF) + RP * NF * 2 * L + m * 2 * L;
+  T* stage = reinterpret_cast<T*>(sbase + OFF) + m * NF * 2 * L;
+  T* sc = reinterpret_cast<T*>(sbase + OFF) + RP * NF * 2 * L + m * 2 * L;
   const int b = blockIdx.y;
   const int jp = blockIdx.x * RP + m;
   const bool valid = jp < (a.ny >> 1);
@@ -302,7 +315,8 @@ row_fast_st(const PropArgs<T> a) {
       }
     }
   }
-  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
+  if constexpr (!kRowStTwGlobal)
+    for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
 
   // 1. inverse x-transform of the incoming half spectra (reversed plan)
   C y[KIN][Q1];
@@ -329,7 +343,7 @@ row_fast_st(const PropArgs<T> a) {
         }
       }
     }
-    fft_stockham<L, G::P1, G::P2, G::P3, KIN, kRowStOneBuf>(v, y, bufA, bufB, SL, j, tws);
+    fft_stockham<L, G::P1, G::P2, G::P3, KIN, kRowStOneBuf>(v, y, bufA, bufB, SL, j, tw);
   } else {
 #pragma unroll
     for (int s = 0; s < KIN; ++s)
@@ -376,7 +390,7 @@ row_fast_st(const PropArgs<T> a) {
 
   // 3. forward x-transform of the packed outgoing rows, split, store
   C X[KOUT][QL];
-  fft_stockham<L, G::Q1, G::Q2, G::Q3, KOUT, kRowStOneBuf>(o, X, bufA, bufB, SL, j, tws);
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KOUT, kRowStOneBuf>(o, X, bufA, bufB, SL, j, tw);
   if (j < L / QL) {
 #pragma unroll
     for (int s = 0; s < KOUT; ++s)
