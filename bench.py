@@ -186,12 +186,23 @@ def measured_hbm_peak(fallback=6800.0):
         return fallback
 
 
-def source_hash():
+def source_hash(files=None):
+    """Hash of the library sources (all of csrc/, or the named files)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1810_11685_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+        if files is None or f in files:
+            h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+# the sources the 2D FP32 pass kernels of the bench workload are built from
+PASS_SOURCES = ("fast_576.cu", "fast_kernels.cuh", "fft_reg.cuh", "fft_smem.cuh", "pass_ops.cuh",
+                "qpat_internal.h", "propagate.cu")
+
+
+def pass_hash():
+    return source_hash(PASS_SOURCES)
 
 
 def pass_bytes(phase, w, batch, elt=4):
@@ -316,7 +327,7 @@ def run_ours(args):
         traffic = None
         try:
             tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
-            if (tr.get("source_hash") == source_hash() and tr.get("batch") == B
+            if (tr.get("pass_hash") == pass_hash() and tr.get("batch") == B
                     and top in tr.get("per_launch", {})):
                 traffic = tr["per_launch"][top]
         except Exception:
@@ -356,7 +367,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(w, B, nt, {"parallelism": f"replicas x{world}, no collective"}),
                 "clocks": clocks, "gpu_launches": int(launches), "impl": "ours",
-                "source_hash": source_hash()}
+                "source_hash": source_hash(), "pass_hash": pass_hash()}
         line.update(extras)
         print(json.dumps(line), flush=True)
     ctx.close()
