@@ -16,6 +16,9 @@ Modules
   with its Frechet derivative and adjoint in mu (Lemma 1).
 - ``qpat``: the composite maps H = H_a H_o, J and J^* (Section 3.2.2,
   eqs. com_des and J_des).
+- ``ld``: the inexact-Newton lagged-diffusivity reconstruction of mu with the
+  TV priorconditioner (Section 5.2.1, Algorithms 4 and 5; Section 5, eqs. gr,
+  apj, tvm, m, m1).
 
 Every function is pinned by tests in ``tests/test_oracle_*.py`` against
 closed forms, invariants, brute force or the paper's printed values; none is

@@ -1,0 +1,197 @@
+"""FP64 oracle of the inexact-Newton lagged-diffusivity (LD) reconstruction.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The unknown is the absorption mu on the interior grid; kappa stays fixed (the
+mu-derivative only, as in ``optics``).  Written out from Sections 4 and 5:
+
+* logarithmic scaling Xbar = log(mu / mu0) (eq. logscale), so that
+  d mu / d Xbar = diag(mu);
+* data misfit eps = 1/2 sum_q ||H_q[mu] - P_q||^2 (eq. varr);
+* gradient  grad eps = sum_q diag(mu) J_q^* (H_q[mu] - P_q) (eq. gr);
+* Gauss-Newton Hessian  H d = sum_q diag(mu) J_q^* J_q diag(mu) d (eq. apj);
+* TV prior (eqs. tvm, dd, jm, m, m1): one row of D per interior face l
+  between cells j1, j2 with entries +a, -a (a = the face length in 2D, the
+  face area in 3D, here measured in mm as in Section 6), C = diag(((D Xbar)^2
+  + beta)^(-1/2)), M[Xbar] = D^T C D, and M_gamma = M + gamma I;
+* Algorithm 4 (PCG on the priorconditioned normal equation, eq. pre) with
+  M_gamma^k = M_gamma[Xbar^k] lagged at the subproblem's start point, and its
+  stopping rule (i_max; after i_m iterations the relative reduction of r^T z
+  over the last i_m iterations against Tol_in);
+* Algorithm 5 (outer loop, step alpha = 1, stop when the relative decrease of
+  eps falls to Tol_out, or after k_max linearisations).
+
+Library primitives: scipy's sparse direct solve for M_gamma z = r, and the
+composite maps of ``oracle.qpat``.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Callable, List, Sequence
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import acoustic, optics
+
+
+@dataclasses.dataclass
+class LDParams:
+    """Parameters of Algorithms 4 and 5 (Section 6 values for the 2D phantom
+    as defaults: i_max = 30, i_m = 5, Tol_in = 0, gamma = 1e-6, beta = 2e-5,
+    Tol_out = 1e-3)."""
+    k_max: int = 10
+    i_max: int = 30
+    i_m: int = 5
+    tol_in: float = 0.0
+    tol_out: float = 1e-3
+    gamma: float = 1e-6
+    beta: float = 2e-5
+    edge: float = 0.1          # a: face length (2D) / area (3D) of an interior face
+
+
+# ---- TV prior ----------------------------------------------------------------
+def tv_difference(shape, edge):
+    """D: one row per interior face, +edge at the lower cell and -edge at the
+    upper cell of the face (cells x fastest), faces of axis x first."""
+    dim = len(shape)
+    N = int(np.prod(shape))
+    idx = np.arange(N).reshape(shape)
+    rows, cols, vals = [], [], []
+    r0 = 0
+    for i in range(dim):
+        a = dim - 1 - i
+        lo = [slice(None)] * dim
+        hi = [slice(None)] * dim
+        lo[a] = slice(0, shape[a] - 1)
+        hi[a] = slice(1, shape[a])
+        ia, ib = idx[tuple(lo)].ravel(), idx[tuple(hi)].ravel()
+        r = r0 + np.arange(ia.size)
+        rows += [r, r]
+        cols += [ia, ib]
+        vals += [np.full(ia.size, edge), np.full(ia.size, -edge)]
+        r0 += ia.size
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(r0, N))
+
+
+def tv_functional(xbar, edge, beta):
+    """J_beta[Xbar] = sum_l sqrt((D Xbar)_l^2 + beta): the smoothed TV whose
+    gradient is M[Xbar] Xbar (eq. jm)."""
+    D = tv_difference(xbar.shape, edge)
+    g = D @ xbar.ravel()
+    return float(np.sum(np.sqrt(g * g + beta)))
+
+
+def tv_matrix(xbar, edge, beta):
+    """M[Xbar] = D^T C[Xbar] D (eqs. m, m1)."""
+    D = tv_difference(xbar.shape, edge)
+    g = D @ xbar.ravel()
+    C = sp.diags(1.0 / np.sqrt(g * g + beta))
+    return (D.T @ C @ D).tocsr()
+
+
+def m_gamma(xbar, edge, beta, gamma):
+    M = tv_matrix(xbar, edge, beta)
+    return (M + gamma * sp.identity(M.shape[0], format="csr")).tocsc()
+
+
+# ---- data misfit, gradient and Gauss-Newton Hessian -----------------------------
+class Problem:
+    """Direct-QPAT misfit over illuminations ``illums`` (side masks) for the
+    data ``P`` [nq][Nt][Ns], with the FP64 oracle maps."""
+
+    def __init__(self, S, kappa, illums: Sequence[int], P, mu0):
+        self.S, self.kappa = S, np.asarray(kappa, dtype=np.float64)
+        self.illums = list(illums)
+        self.P = [np.asarray(p, dtype=np.float64) for p in P]
+        self.mu0 = np.asarray(mu0, dtype=np.float64)
+
+    def mu(self, xbar):
+        return self.mu0 * np.exp(xbar)
+
+    def forward(self, mu, q):
+        h = optics.heating(mu, self.kappa, self.S.dx, self.illums[q])
+        return acoustic.forward(self.S, h)
+
+    def J(self, mu, q, dmu):
+        dh = optics.jvp(mu, self.kappa, self.S.dx, self.illums[q], dmu)
+        return acoustic.forward(self.S, dh)
+
+    def JT(self, mu, q, W):
+        hbar = acoustic.adjoint(self.S, W)
+        return optics.vjp(mu, self.kappa, self.S.dx, self.illums[q], hbar)
+
+    def residuals(self, xbar):
+        mu = self.mu(xbar)
+        return [self.forward(mu, q) - self.P[q] for q in range(len(self.illums))]
+
+    def misfit(self, xbar):
+        """eps (eq. varr)."""
+        return 0.5 * sum(float(np.sum(r * r)) for r in self.residuals(xbar))
+
+    def gradient(self, xbar, res=None):
+        """grad eps = sum_q diag(mu) J_q^* (H_q - P_q) (eq. gr)."""
+        mu = self.mu(xbar)
+        res = self.residuals(xbar) if res is None else res
+        return sum(mu * self.JT(mu, q, res[q]) for q in range(len(self.illums)))
+
+    def gn_product(self, xbar, d):
+        """H d = sum_q diag(mu) J_q^* J_q diag(mu) d (eq. apj)."""
+        mu = self.mu(xbar)
+        return sum(mu * self.JT(mu, q, self.J(mu, q, mu * d)) for q in range(len(self.illums)))
+
+
+# ---- Algorithm 4 ---------------------------------------------------------------
+def pcg(apply_H: Callable, rhs, solve_M: Callable, i_max, i_m, tol_in):
+    """Algorithm 4: PCG for H d = rhs preconditioned by M (solve_M(r) = M^-1 r),
+    starting from d = 0.  Stops when i reaches i_max, or when i >= i_m and
+    1 - (r_i^T z_i) / (r_{i-i_m}^T z_{i-i_m}) <= tol_in, or when r_i^T z_i = 0
+    (the exact solution has been reached; the step would divide 0 by 0).
+    Returns (d, i, the sequence r_i^T z_i)."""
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    z = solve_M(r)
+    d = z.copy()
+    rz = [float(r.ravel() @ z.ravel())]
+    i = 0
+    while i < i_max and rz[i] != 0.0 and (i < i_m or 1.0 - rz[i] / rz[i - i_m] > tol_in):
+        Hd = apply_H(d)
+        alpha = rz[i] / float(d.ravel() @ Hd.ravel())
+        x = x + alpha * d
+        r = r - alpha * Hd
+        z = solve_M(r)
+        rz.append(float(r.ravel() @ z.ravel()))
+        beta = rz[i + 1] / rz[i]
+        d = z + beta * d
+        i += 1
+    return x, i, rz
+
+
+# ---- Algorithm 5 ---------------------------------------------------------------
+def ld_newton(prob: Problem, prm: LDParams):
+    """Algorithm 5: returns (mu*, Xbar*, eps history, inner iterations per
+    outer iteration).  eps history holds eps^0, eps^1, ...: the misfit at each
+    linearisation point, the last at the returned mu*."""
+    shape = prob.mu0.shape
+    xbar = np.zeros(shape)
+    eps_hist: List[float] = []
+    inner: List[int] = []
+    k = 0
+    while True:
+        res = prob.residuals(xbar)
+        eps = 0.5 * sum(float(np.sum(r * r)) for r in res)
+        eps_hist.append(eps)
+        if k > 0 and not (1.0 - eps_hist[k] / eps_hist[k - 1] > prm.tol_out):
+            break
+        if k >= prm.k_max:
+            break
+        g = prob.gradient(xbar, res)
+        Mg = m_gamma(xbar, prm.edge, prm.beta, prm.gamma)
+        lu = spla.splu(Mg)
+        d, i, _ = pcg(lambda v: prob.gn_product(xbar, v.reshape(shape)).ravel(), -g.ravel(),
+                      lambda r: lu.solve(r), prm.i_max, prm.i_m, prm.tol_in)
+        inner.append(i)
+        xbar = xbar + d.reshape(shape)
+        k += 1
+    return prob.mu(xbar), xbar, eps_hist, inner
