@@ -49,9 +49,10 @@ def parse():
     p.add_argument("--nt", type=int, default=None, help="override Nt (default: workload's 2000)")
     p.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/roofline/cpu legs")
     p.add_argument("--n3", type=int, default=None, help="c5 only: interior nodes per axis (default 256)")
-    p.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "ld"],
                    help="c2: the 576^2 forward+adjoint workload (default); c4: 48 Jacobian-vector "
-                        "products over 288^2/432^2/576^2 grids in one graph (diagnostic line)")
+                        "products over 288^2/432^2/576^2 grids in one graph; c5: the 3D 256^3 workload; "
+                        "ld: the inexact-Newton LD reconstruction (diagnostic lines)")
     return p.parse_args()
 
 
@@ -450,6 +451,49 @@ def run_c5(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ld(args):
+    """Inexact-Newton LD reconstruction (Algorithms 4 and 5, qpat_ld_solve) on
+    the 128^2 interior of the 2D circle-sensor workload (168^2 FFT grid, 600
+    samples, 128 sensors), four illuminated sides, FP32 propagation: synthetic
+    data from a seeded mu with three discs, initial guess the background."""
+    import torch
+    from paper_1810_11685_gb300.binding import context_from_workload
+    w = phantoms.C1
+    nt = args.nt or w.nt
+    ctx = context_from_workload(w, precision="fp32", nt=nt, max_batch=4)
+    mu_true = torch.as_tensor(phantoms.optical_absorption(w), device="cuda")
+    illums = (1, 2, 4, 8)
+    data = torch.stack([ctx.forward(mu_true, q)[0] for q in illums])
+    mu0 = torch.full(w.interior_shape, w.mu_bg, dtype=torch.float64, device="cuda")
+    kw = dict(k_max=3, i_max=4, i_m=4, tol_in=0.0, tol_out=0.0)
+    ctx.ld_solve(data, illums, mu0, k_max=1, i_max=2)      # warm-up (graphs, multigrid)
+    torch.cuda.synchronize()
+    times, res = [], None
+    for _ in range(max(1, args.steps)):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        res = ctx.ld_solve(data, illums, mu0, **kw)
+        e.record()
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e) / 1e3)
+    mu, eps, inner, info = res
+    t = statistics.median(times)
+    G = w.grid * w.grid
+    cells = info["products"] * G * nt
+    err0 = float(torch.linalg.norm(mu0 - mu_true) / torch.linalg.norm(mu_true))
+    err = float(torch.linalg.norm(mu - mu_true) / torch.linalg.norm(mu_true))
+    line = {"metric": "LD reconstruction: propagation cell-steps/s inside qpat_ld_solve", "value": cells / t,
+            "unit": UNIT, "n_gpus": 1, "steps": len(times), "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": f"2d {w.n}x{w.n} interior, {w.grid}x{w.grid} FFT grid, Nt={nt}, "
+                                   f"{w.n_sensors} sensors, 4 illuminations, LD k_max=3 i_max=i_m=4",
+                       "nt": nt},
+            "seconds_per_solve": t, "outer": info["outer"], "inner": inner, "products": info["products"],
+            "tv_cg_iterations": info["tv_iters"], "seconds_per_outer": t / max(1, info["outer"]),
+            "eps": eps, "rel_error_mu": {"initial": err0, "final": err}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "ours" and args.workload == "c4":
@@ -457,6 +501,9 @@ def main():
         return
     if args.impl == "ours" and args.workload == "c5":
         run_c5(args)
+        return
+    if args.impl == "ours" and args.workload == "ld":
+        run_ld(args)
         return
     if args.impl == "reference":
         run_reference(args)

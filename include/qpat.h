@@ -214,6 +214,65 @@ qpat_status qpat_autotune(qpat_ctx* ctx, int batch, int steps, int* choice);
 qpat_status qpat_dot(qpat_ctx* ctx, int batch, long long len, const void* a, const void* b,
                      double* out);
 
+/* Reconstruction of mu by the inexact-Newton lagged-diffusivity method with
+ * TV priorconditioning (Section 5.2.1, Algorithms 4 and 5), kappa fixed.
+ *  - Unknown Xbar = log(mu / mu0) (eq. logscale); misfit
+ *    eps = 1/2 sum_q ||H_q[mu] - P_q||^2 over the illuminations q (eq. varr).
+ *  - Outer iteration k (Algorithm 5): gradient g = sum_q mu o J_q^*(H_q - P_q)
+ *    (eq. gr); M_gamma = D^T C D + gamma I frozen at Xbar^k (eqs. m, m1:
+ *    D has +a/-a per interior face, C = ((D Xbar)^2 + beta)^(-1/2));
+ *    Algorithm 4 (PCG, start 0) on H d = -g with H d = sum_q mu o J_q^* J_q
+ *    (mu o d) (eq. apj) and preconditioner M_gamma; Xbar += d (alpha = 1).
+ *    Stops when k = k_max or 1 - eps^k / eps^(k-1) <= tol_out.
+ *  - M_gamma z = r is solved exactly along constants (M 1 = 0, so
+ *    M_gamma 1 = gamma 1) and by conjugate gradients on the mean-free part
+ *    (diagonal preconditioner, mean removed), to a relative residual tv_tol.
+ * The acoustic halves of the nq illuminations run as one batch, so the
+ * context's max_batch must be at least nq.
+ * nq illuminations illum[q] (host, side masks as in qpat_da_solve); data:
+ * device prec [nq][nt][ns] measured series P_q; mu: device double [N], mu0 on
+ * entry (the initial guess, also the scale of Xbar), the reconstruction on
+ * return.  eps_hist (host double [k_max + 1]) and inner_hist (host int
+ * [k_max]) are optional: eps^0, eps^1, ... and the PCG iterations per outer
+ * iteration.  info (optional) receives the counts below.
+ * Allocates and frees its workspace (about (17 + nq) N doubles, 2 nq nt ns
+ * and 2 nq N prec values, and the face weights); synchronises (the Krylov
+ * scalars are read on the host every iteration).  mu0 must be positive (log scaling); this is
+ * not checked.  Errors: EINVAL (nq < 1 or > max_batch, bad masks), ENOCONV
+ * (a diffusion solve), ENOMEM, ECUDA. */
+typedef struct {
+  int k_max;         /* outer linearisations; <= 0: 10 */
+  int i_max;         /* PCG iterations per linearisation; <= 0: 30 */
+  int i_m;           /* window of the inner stopping rule; <= 0: 5 */
+  double tol_in;     /* Tol_in; < 0: 0 */
+  double tol_out;    /* Tol_out; < 0: 1e-3 */
+  double gamma;      /* <= 0: 1e-6 */
+  double beta;       /* <= 0: 2e-5 */
+  double tv_edge;    /* a: face length (2D) / area (3D) in the length unit of beta;
+                        <= 0: dx in mm (2D), (dx in mm)^2 (3D) */
+  int tv_max_iter;   /* CG iterations per M_gamma solve; <= 0: 20000 */
+  double tv_tol;     /* relative residual of the M_gamma solve; <= 0: 1e-12 */
+} qpat_ld_params;
+
+typedef struct {
+  int outer;              /* linearisations performed */
+  int inner_total;        /* PCG iterations, all outer iterations */
+  long long tv_iters;     /* CG iterations of all M_gamma solves */
+  long long products;     /* applications of J_q or J_q^* (one propagation each) */
+  double eps_first;       /* eps at mu0 */
+  double eps_last;        /* eps at the returned mu */
+} qpat_ld_info;
+
+qpat_status qpat_ld_solve(qpat_ctx* ctx, int nq, const unsigned* illum, const void* data, double* mu,
+                          const qpat_ld_params* prm, qpat_ld_info* info, double* eps_hist,
+                          int* inner_hist);
+
+/* M_gamma u of the TV priorconditioner at Xbar (the operator qpat_ld_solve
+ * builds; exposed for testing and for callers that run their own Krylov
+ * loop).  xbar, u, out: device double [N].  Synchronises. */
+qpat_status qpat_tv_apply(qpat_ctx* ctx, const double* xbar, double edge, double beta, double gamma,
+                          const double* u, double* out);
+
 /* Instrumentation (no counterpart in the paper).
  * qpat_get_stats: out[0] = propagation kernels launched by this context so
  * far, out[1] = launches currently held by the phase profiler, out[2] =

@@ -48,6 +48,18 @@ class qpat_medium(ctypes.Structure):
                 ("kappa", ctypes.c_void_p)]
 
 
+class qpat_ld_params(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int), ("i_max", ctypes.c_int), ("i_m", ctypes.c_int),
+                ("tol_in", ctypes.c_double), ("tol_out", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("beta", ctypes.c_double), ("tv_edge", ctypes.c_double), ("tv_max_iter", ctypes.c_int),
+                ("tv_tol", ctypes.c_double)]
+
+
+class qpat_ld_info(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int), ("inner_total", ctypes.c_int), ("tv_iters", ctypes.c_longlong),
+                ("products", ctypes.c_longlong), ("eps_first", ctypes.c_double), ("eps_last", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -90,6 +102,9 @@ def load():
         "qpat_acoustic_resume": [vp, i, vp, i, i, vp],
         "qpat_profile": [vp, i],
         "qpat_profile_read": [vp, ctypes.POINTER(d), ctypes.POINTER(ll)],
+        "qpat_ld_solve": [vp, i, vp, vp, vp, ctypes.POINTER(qpat_ld_params), ctypes.POINTER(qpat_ld_info),
+                          ctypes.POINTER(d), ctypes.POINTER(i)],
+        "qpat_tv_apply": [vp, vp, d, d, d, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -328,6 +343,40 @@ class Context:
         _check(self._ptr, self._lib.qpat_vjp(self._ptr, B, _ptr(mu), _ptr(phi0), _ptr(w), int(illum), _ptr(out)))
         return out
 
+    def ld_solve(self, data, illums, mu0, k_max=10, i_max=30, i_m=5, tol_in=0.0, tol_out=1e-3, gamma=1e-6,
+                 beta=2e-5, tv_edge=0.0, tv_max_iter=0, tv_tol=0.0):
+        """qpat_ld_solve: returns (mu, eps history, inner iterations per outer
+        iteration, info dict).  data: [nq][nt][ns] in the context precision;
+        mu0: FP64 interior field (the initial guess)."""
+        import torch
+        nq = len(illums)
+        data = data.contiguous()
+        if data.dtype != self.dtype or tuple(data.shape) != (nq, self.nt, self.ns) or data.device.type != "cuda":
+            raise TypeError("data must be a CUDA tensor [nq][nt][ns] of the context precision")
+        mu = self._in(mu0, torch.float64, self.interior_shape).clone()
+        prm = qpat_ld_params(k_max, i_max, i_m, tol_in, tol_out, gamma, beta, tv_edge, tv_max_iter, tv_tol)
+        info = qpat_ld_info()
+        eps = (ctypes.c_double * (max(k_max, 1) + 1))()
+        inner = (ctypes.c_int * max(k_max, 1))()
+        ill = (ctypes.c_uint * nq)(*[int(q) for q in illums])
+        self._stream()
+        _check(self._ptr, self._lib.qpat_ld_solve(self._ptr, nq, ill, _ptr(data), _ptr(mu), ctypes.byref(prm),
+                                                  ctypes.byref(info), eps, inner))
+        k = info.outer
+        out = {f: getattr(info, f) for f, _ in qpat_ld_info._fields_}
+        return mu[0], list(eps)[:k + 1], list(inner)[:k], out
+
+    def tv_apply(self, xbar, u, edge, beta, gamma):
+        """qpat_tv_apply: M_gamma[xbar] u (FP64 interior fields)."""
+        import torch
+        xbar = self._in(xbar, torch.float64, self.interior_shape)
+        u = self._in(u, torch.float64, self.interior_shape)
+        out = torch.empty_like(u)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_tv_apply(self._ptr, _ptr(xbar), float(edge), float(beta), float(gamma),
+                                                  _ptr(u), _ptr(out)))
+        return out[0]
+
     def dot(self, a, b):
         a = a.contiguous()
         b = b.contiguous()
@@ -457,6 +506,14 @@ def qpat_dot_noalloc(a, b, out=None):
     if st != 0:
         raise QpatError(st, lib.qpat_noalloc_last_error().decode())
     return out
+
+
+def qpat_ld_solve(ctx: Context, data, illums, mu0, **params):
+    return ctx.ld_solve(data, illums, mu0, **params)
+
+
+def qpat_tv_apply(ctx: Context, xbar, edge, beta, gamma, u):
+    return ctx.tv_apply(xbar, u, edge, beta, gamma)
 
 
 def qpat_sync(ctx: Context):

@@ -61,6 +61,28 @@ struct qpat_ctx {
   size_t prof_used = 0;
 };
 
+namespace qpat {
+bool ctx_view(const qpat_ctx* c, CtxView* v) {
+  if (!c || !v) return false;
+  v->prec = c->prec;
+  v->dim = c->dim;
+  v->n0 = c->n0;
+  v->n1 = c->n1;
+  v->n2 = c->dim == 3 ? c->n2 : 1;
+  v->nt = c->nt;
+  v->ns = c->ns;
+  v->maxb = c->maxb;
+  v->N = c->N;
+  v->dx = c->dx;
+  v->stream = c->stream;
+  return true;
+}
+int ctx_fail(qpat_ctx* c, int st, const char* msg) {
+  if (c) c->err = msg;
+  return st;
+}
+}  // namespace qpat
+
 namespace {
 
 qpat_status fail(qpat_ctx* c, qpat_status st, const std::string& msg) {
@@ -922,6 +944,48 @@ qpat_status qpat_vjp(qpat_ctx* c, int batch, const double* mu, const double* phi
   else QCK(da_adjoint_out<double>(batch, N, phi0, (const double*)c->tw_hbar, c->d_tmp, g, c->stream));
   return QPAT_OK;
 }
+
+}  // extern "C"
+
+// Optical halves of the composite maps for one problem, with caller buffers,
+// so that a caller holding several illuminations can batch their acoustic
+// propagations (declared in qpat_internal.h).
+namespace qpat {
+
+int optics_forward(qpat_ctx* c, const double* mu, unsigned illum, double* phi, void* h) {
+  qpat_status st = qpat_da_solve(c, 1, mu, illum, phi);
+  if (st != QPAT_OK) return st;
+  const int N = (int)c->N;
+  if (c->prec == QPAT_FP32) QCK(da_heating_T<float>(1, N, mu, phi, nullptr, nullptr, (float*)h, c->stream));
+  else QCK(da_heating_T<double>(1, N, mu, phi, nullptr, nullptr, (double*)h, c->stream));
+  return QPAT_OK;
+}
+
+int optics_jvp(qpat_ctx* c, const double* mu, const double* phi0, const double* dmu, void* dh) {
+  const int N = (int)c->N;
+  QCK(da_hadamard(1, N, -c->da.hd, dmu, phi0, c->d_rhs, c->stream));
+  qpat_status st = solve_da(c, 1, mu, c->d_rhs, c->d_tmp);
+  if (st != QPAT_OK) return st;
+  if (c->prec == QPAT_FP32) QCK(da_heating_T<float>(1, N, dmu, phi0, mu, c->d_tmp, (float*)dh, c->stream));
+  else QCK(da_heating_T<double>(1, N, dmu, phi0, mu, c->d_tmp, (double*)dh, c->stream));
+  return QPAT_OK;
+}
+
+int optics_vjp(qpat_ctx* c, const double* mu, const double* phi0, const void* hbar, double* g) {
+  const int N = (int)c->N;
+  const double sc = -c->da.hd;
+  if (c->prec == QPAT_FP32) QCK(da_adjoint_rhs<float>(1, N, sc, mu, (const float*)hbar, c->d_rhs, c->stream));
+  else QCK(da_adjoint_rhs<double>(1, N, sc, mu, (const double*)hbar, c->d_rhs, c->stream));
+  qpat_status st = solve_da(c, 1, mu, c->d_rhs, c->d_tmp);
+  if (st != QPAT_OK) return st;
+  if (c->prec == QPAT_FP32) QCK(da_adjoint_out<float>(1, N, phi0, (const float*)hbar, c->d_tmp, g, c->stream));
+  else QCK(da_adjoint_out<double>(1, N, phi0, (const double*)hbar, c->d_tmp, g, c->stream));
+  return QPAT_OK;
+}
+
+}  // namespace qpat
+
+extern "C" {
 
 qpat_status qpat_dot(qpat_ctx* c, int batch, long long len, const void* a, const void* b, double* out) {
   qpat_status st = check_batch(c, batch);

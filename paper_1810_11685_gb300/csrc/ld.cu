@@ -1,0 +1,427 @@
+// Inexact-Newton lagged-diffusivity reconstruction of mu with TV
+// priorconditioning (Section 5.2.1, Algorithms 4 and 5).
+//
+// Each application of H, J or J^* runs the optical half (the diffusion solve
+// and the heating map) per illumination and the acoustic half H_a or H_a^*
+// for all illuminations as one batch of the propagation kernels.  The kernels
+// below do the vector work on the interior grid in FP64: the log scaling
+// mu = mu0 exp(Xbar), the residuals,
+// the TV face weights C = ((D Xbar)^2 + beta)^(-1/2) and M_gamma u =
+// D^T C D u + gamma u (eqs. m, m1), and the Krylov vector updates.  Inner
+// products are the library's compensated FP64 reductions; the Krylov
+// scalars go to the host, which runs the iteration control of Algorithms 4
+// and 5.
+#include <math.h>
+
+#include <string>
+#include <vector>
+
+#include "qpat.h"
+#include "qpat_internal.h"
+
+using namespace qpat;
+
+namespace {
+
+constexpr int kT = 256;
+
+inline int blocks_for(long long n) {
+  long long b = (n + kT - 1) / kT;
+  return (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+}
+
+__global__ void exp_scale_kernel(long long n, const double* mu0, const double* xbar, double* mu) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    mu[i] = mu0[i] * exp(xbar[i]);
+}
+
+template <typename T>
+__global__ void resid_kernel(long long n, const T* h, const T* p, T* r) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = h[i] - p[i];
+}
+
+// y = a x + b y
+__global__ void axpby_kernel(long long n, double a, const double* x, double b, double* y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+// out = u o v (acc = 0) or out += u o v (acc = 1)
+__global__ void hadamard_kernel(long long n, const double* u, const double* v, double* out, int acc) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (acc ? out[i] : 0.0) + u[i] * v[i];
+}
+
+// out = u / d
+__global__ void divide_kernel(long long n, const double* u, const double* d, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = u[i] / d[i];
+}
+
+// y = a + y (a a constant), or y = a when set
+__global__ void add_const_kernel(long long n, double a, double* y, int set) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = set ? a : y[i] + a;
+}
+
+struct TVGrid {
+  int n0, n1, n2;
+  double edge, beta, gamma;
+  double* wx;   // faces (i, i+1): [n2][n1][n0 - 1]
+  double* wy;   // faces (j, j+1): [n2][n1 - 1][n0]
+  double* wz;   // faces (k, k+1): [n2 - 1][n1][n0]
+};
+
+// Face weight a^2 C_l of M = D^T C D: the row of D for face l holds +a, -a,
+// so (D Xbar)_l = a (Xbar_j1 - Xbar_j2) and M couples the two cells with
+// a^2 / sqrt((D Xbar)_l^2 + beta) (eq. m1).
+__device__ __forceinline__ double tv_face(double a, double beta, double x1, double x2) {
+  const double g = a * (x1 - x2);
+  return a * a / sqrt(g * g + beta);
+}
+
+__global__ void tv_weights_kernel(TVGrid t, const double* xbar) {
+  const long long N = (long long)t.n0 * t.n1 * t.n2;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % t.n0);
+    const int j = (int)((c / t.n0) % t.n1);
+    const int k = (int)(c / ((long long)t.n0 * t.n1));
+    if (i + 1 < t.n0) t.wx[((long long)k * t.n1 + j) * (t.n0 - 1) + i] = tv_face(t.edge, t.beta, xbar[c], xbar[c + 1]);
+    if (j + 1 < t.n1) t.wy[((long long)k * (t.n1 - 1) + j) * t.n0 + i] = tv_face(t.edge, t.beta, xbar[c], xbar[c + t.n0]);
+    if (k + 1 < t.n2)
+      t.wz[((long long)k * t.n1 + j) * t.n0 + i] = tv_face(t.edge, t.beta, xbar[c], xbar[c + (long long)t.n0 * t.n1]);
+  }
+}
+
+// out = M_gamma u (diag_only: out = the diagonal of M_gamma)
+__global__ void tv_apply_kernel(TVGrid t, const double* u, double* out, int diag_only) {
+  const long long N = (long long)t.n0 * t.n1 * t.n2;
+  const long long sxy = (long long)t.n0 * t.n1;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % t.n0);
+    const int j = (int)((c / t.n0) % t.n1);
+    const int k = (int)(c / sxy);
+    const double uc = diag_only ? 1.0 : u[c];
+    double acc = t.gamma * uc, w;
+    if (i > 0) { w = t.wx[((long long)k * t.n1 + j) * (t.n0 - 1) + i - 1]; acc += w * (uc - (diag_only ? 0.0 : u[c - 1])); }
+    if (i + 1 < t.n0) { w = t.wx[((long long)k * t.n1 + j) * (t.n0 - 1) + i]; acc += w * (uc - (diag_only ? 0.0 : u[c + 1])); }
+    if (j > 0) { w = t.wy[((long long)k * (t.n1 - 1) + j - 1) * t.n0 + i]; acc += w * (uc - (diag_only ? 0.0 : u[c - t.n0])); }
+    if (j + 1 < t.n1) { w = t.wy[((long long)k * (t.n1 - 1) + j) * t.n0 + i]; acc += w * (uc - (diag_only ? 0.0 : u[c + t.n0])); }
+    if (k > 0) { w = t.wz[((long long)(k - 1) * t.n1 + j) * t.n0 + i]; acc += w * (uc - (diag_only ? 0.0 : u[c - sxy])); }
+    if (k + 1 < t.n2) { w = t.wz[((long long)k * t.n1 + j) * t.n0 + i]; acc += w * (uc - (diag_only ? 0.0 : u[c + sxy])); }
+    out[c] = acc;
+  }
+}
+
+// Device workspace of one reconstruction, freed on every exit path.
+struct Work {
+  std::vector<void*> ptrs;
+  cudaError_t err = cudaSuccess;
+  template <typename P>
+  P* get(size_t count) {
+    void* v = nullptr;
+    if (err == cudaSuccess) err = cudaMalloc(&v, (count ? count : 1) * sizeof(P));
+    if (err != cudaSuccess) return nullptr;
+    ptrs.push_back(v);
+    return (P*)v;
+  }
+  ~Work() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+struct Ld {
+  qpat_ctx* c;
+  CtxView v;
+  long long N = 0, M = 0;       // interior cells, samples per series
+  size_t elt = 8;
+  double* partial = nullptr;
+  double* dout = nullptr;
+  long long products = 0, tv_iters = 0;
+  TVGrid tv{};
+
+  qpat_status cuda(cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return QPAT_OK;
+    return (qpat_status)ctx_fail(c, e == cudaErrorMemoryAllocation ? QPAT_ENOMEM : QPAT_ECUDA,
+                                 (std::string(where) + ": " + cudaGetErrorString(e)).c_str());
+  }
+  // FP64 inner product of two FP64 vectors of length n (host result)
+  qpat_status dot(const double* a, const double* b, long long n, double* out) {
+    qpat_status st = cuda(dot_compensated<double>(1, n, a, b, partial, dout, v.stream), "dot");
+    if (st != QPAT_OK) return st;
+    st = cuda(cudaMemcpyAsync(out, dout, sizeof(double), cudaMemcpyDeviceToHost, v.stream), "dot copy");
+    if (st != QPAT_OK) return st;
+    return cuda(cudaStreamSynchronize(v.stream), "dot sync");
+  }
+  qpat_status dot_data(const void* a, const void* b, long long n, double* out) {
+    qpat_status st;
+    if (v.prec == QPAT_FP32)
+      st = cuda(dot_compensated<float>(1, n, (const float*)a, (const float*)b, partial, dout, v.stream), "dot");
+    else
+      st = cuda(dot_compensated<double>(1, n, (const double*)a, (const double*)b, partial, dout, v.stream), "dot");
+    if (st != QPAT_OK) return st;
+    st = cuda(cudaMemcpyAsync(out, dout, sizeof(double), cudaMemcpyDeviceToHost, v.stream), "dot copy");
+    if (st != QPAT_OK) return st;
+    return cuda(cudaStreamSynchronize(v.stream), "dot sync");
+  }
+  void axpby(double a, const double* x, double b, double* y) {
+    axpby_kernel<<<blocks_for(N), kT, 0, v.stream>>>(N, a, x, b, y);
+  }
+
+  qpat_status tv_weights(const double* xbar) {
+    tv_weights_kernel<<<blocks_for(N), kT, 0, v.stream>>>(tv, xbar);
+    return cuda(cudaGetLastError(), "tv_weights_kernel");
+  }
+  void tv_apply(const double* u, double* out) { tv_apply_kernel<<<blocks_for(N), kT, 0, v.stream>>>(tv, u, out, 0); }
+
+  // mean of an [N] vector (ones: a vector of ones)
+  qpat_status mean(const double* u, const double* ones, double* out) {
+    qpat_status st = dot(u, ones, N, out);
+    *out /= (double)N;
+    return st;
+  }
+
+  // M_gamma z = r.  M annihilates constants (M 1 = 0), so M_gamma 1 = gamma 1
+  // and the mean-free part is invariant: z = (mean r / gamma) 1 + y with
+  // M_gamma y = r - mean(r) 1 solved by conjugate gradients on mean-free
+  // vectors, preconditioned with the diagonal followed by removal of the mean
+  // (symmetric positive definite on that subspace).  Without the split the
+  // constant mode, of eigenvalue gamma, would dominate the conditioning.
+  // rr, pp, ap, zz, dg: work vectors [N]; y accumulates in z.
+  qpat_status tv_solve(const double* r, double* z, double* rr, double* pp, double* ap, double* zz, double* dg,
+                       const double* ones, int max_iter, double tol) {
+    tv_apply_kernel<<<blocks_for(N), kT, 0, v.stream>>>(tv, nullptr, dg, 1);
+    qpat_status st = cuda(cudaMemsetAsync(z, 0, N * sizeof(double), v.stream), "memset");
+    if (st != QPAT_OK) return st;
+    st = cuda(cudaMemcpyAsync(rr, r, N * sizeof(double), cudaMemcpyDeviceToDevice, v.stream), "copy");
+    if (st != QPAT_OK) return st;
+    double m_r, m;
+    if ((st = mean(rr, ones, &m_r)) != QPAT_OK) return st;
+    add_const_kernel<<<blocks_for(N), kT, 0, v.stream>>>(N, -m_r, rr, 0);
+    auto precondition = [&]() -> qpat_status {
+      divide_kernel<<<blocks_for(N), kT, 0, v.stream>>>(N, rr, dg, zz);
+      qpat_status e = mean(zz, ones, &m);
+      add_const_kernel<<<blocks_for(N), kT, 0, v.stream>>>(N, -m, zz, 0);
+      return e;
+    };
+    if ((st = precondition()) != QPAT_OK) return st;
+    st = cuda(cudaMemcpyAsync(pp, zz, N * sizeof(double), cudaMemcpyDeviceToDevice, v.stream), "copy");
+    if (st != QPAT_OK) return st;
+    double rz0, rz;
+    if ((st = dot(rr, zz, N, &rz0)) != QPAT_OK) return st;
+    rz = rz0;
+    for (int it = 0; rz0 > 0.0 && it < max_iter; ++it) {
+      if (sqrt(rz / rz0) <= tol) break;
+      tv_apply(pp, ap);
+      double pap;
+      if ((st = dot(pp, ap, N, &pap)) != QPAT_OK) return st;
+      const double alpha = rz / pap;
+      axpby(alpha, pp, 1.0, z);
+      axpby(-alpha, ap, 1.0, rr);
+      if ((st = precondition()) != QPAT_OK) return st;
+      double rzn;
+      if ((st = dot(rr, zz, N, &rzn)) != QPAT_OK) return st;
+      axpby(1.0, zz, rzn / rz, pp);
+      rz = rzn;
+      ++tv_iters;
+    }
+    // the cap bounds the work; the result is then the last iterate
+    add_const_kernel<<<blocks_for(N), kT, 0, v.stream>>>(N, m_r / tv.gamma, z, 0);
+    return cuda(cudaGetLastError(), "tv_solve");
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+qpat_status qpat_tv_apply(qpat_ctx* c, const double* xbar, double edge, double beta, double gamma, const double* u,
+                          double* out) {
+  Ld L;
+  L.c = c;
+  if (!ctx_view(c, &L.v)) return QPAT_EINVAL;
+  if (!xbar || !u || !out || !(edge > 0) || !(beta > 0) || gamma < 0)
+    return (qpat_status)ctx_fail(c, QPAT_EINVAL, "qpat_tv_apply: bad arguments");
+  L.N = L.v.N;
+  Work w;
+  L.tv = TVGrid{L.v.n0, L.v.n1, L.v.n2, edge, beta, gamma, nullptr, nullptr, nullptr};
+  L.tv.wx = w.get<double>((size_t)L.v.n2 * L.v.n1 * (L.v.n0 - 1));
+  L.tv.wy = w.get<double>((size_t)L.v.n2 * (L.v.n1 - 1) * L.v.n0);
+  L.tv.wz = w.get<double>((size_t)(L.v.n2 > 1 ? L.v.n2 - 1 : 1) * L.v.n1 * L.v.n0);
+  if (w.err != cudaSuccess) return L.cuda(w.err, "qpat_tv_apply workspace");
+  qpat_status st = L.tv_weights(xbar);
+  if (st != QPAT_OK) return st;
+  L.tv_apply(u, out);
+  st = L.cuda(cudaGetLastError(), "tv_apply_kernel");
+  if (st != QPAT_OK) return st;
+  return L.cuda(cudaStreamSynchronize(L.v.stream), "qpat_tv_apply sync");
+}
+
+qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void* data, double* mu,
+                          const qpat_ld_params* prm_in, qpat_ld_info* info, double* eps_hist, int* inner_hist) {
+  Ld L;
+  L.c = c;
+  if (!ctx_view(c, &L.v)) return QPAT_EINVAL;
+  if (nq < 1 || !illum || !data || !mu) return (qpat_status)ctx_fail(c, QPAT_EINVAL, "qpat_ld_solve: bad arguments");
+  if (nq > L.v.maxb)
+    return (qpat_status)ctx_fail(c, QPAT_EINVAL, "qpat_ld_solve: the context's max_batch must be >= nq");
+  const unsigned all = (1u << (2 * L.v.dim)) - 1;
+  for (int q = 0; q < nq; ++q)
+    if (illum[q] == 0 || (illum[q] & ~all))
+      return (qpat_status)ctx_fail(c, QPAT_EINVAL, "qpat_ld_solve: illumination mask must select sides 0 .. 2d-1");
+  qpat_ld_params p{};
+  if (prm_in) p = *prm_in;
+  if (p.k_max <= 0) p.k_max = 10;
+  if (p.i_max <= 0) p.i_max = 30;
+  if (p.i_m <= 0) p.i_m = 5;
+  if (p.tol_in < 0) p.tol_in = 0;
+  if (p.tol_out < 0) p.tol_out = 1e-3;
+  if (p.gamma <= 0) p.gamma = 1e-6;
+  if (p.beta <= 0) p.beta = 2e-5;
+  if (p.tv_edge <= 0) p.tv_edge = L.v.dim == 3 ? (L.v.dx * 1e3) * (L.v.dx * 1e3) : L.v.dx * 1e3;
+  if (p.tv_max_iter <= 0) p.tv_max_iter = 20000;
+  if (p.tv_tol <= 0) p.tv_tol = 1e-12;
+
+  const long long N = L.v.N;
+  L.N = N;
+  L.M = (long long)L.v.nt * L.v.ns;
+  L.elt = L.v.prec == QPAT_FP32 ? sizeof(float) : sizeof(double);
+  cudaStream_t s = L.v.stream;
+  Work w;
+  double* mu0 = w.get<double>(N);
+  double* xbar = w.get<double>(N);
+  double* phi = w.get<double>((size_t)nq * N);   // fluence of every illumination at mu^k
+  double* g = w.get<double>(N);
+  double* r = w.get<double>(N);
+  double* z = w.get<double>(N);
+  double* d = w.get<double>(N);
+  double* x = w.get<double>(N);
+  double* hd = w.get<double>(N);
+  double* t1 = w.get<double>(N);
+  double* t2 = w.get<double>(N);
+  double* c_rr = w.get<double>(N);
+  double* c_pp = w.get<double>(N);
+  double* c_ap = w.get<double>(N);
+  double* c_zz = w.get<double>(N);
+  double* c_dg = w.get<double>(N);
+  double* ones = w.get<double>(N);
+  char* res = w.get<char>((size_t)nq * L.M * L.elt);   // residual series H_q - P_q
+  char* jv = w.get<char>((size_t)nq * L.M * L.elt);    // J_q of the current direction
+  char* hq = w.get<char>((size_t)nq * N * L.elt);      // heating (or its derivative) per q
+  char* hb = w.get<char>((size_t)nq * N * L.elt);      // H_a^* of a series per q
+  L.partial = w.get<double>((size_t)kPartials * 4);
+  L.dout = w.get<double>(1);
+  L.tv = TVGrid{L.v.n0, L.v.n1, L.v.n2, p.tv_edge, p.beta, p.gamma, nullptr, nullptr, nullptr};
+  L.tv.wx = w.get<double>((size_t)L.v.n2 * L.v.n1 * (L.v.n0 - 1));
+  L.tv.wy = w.get<double>((size_t)L.v.n2 * (L.v.n1 - 1) * L.v.n0);
+  L.tv.wz = w.get<double>((size_t)(L.v.n2 > 1 ? L.v.n2 - 1 : 1) * L.v.n1 * L.v.n0);
+  if (w.err != cudaSuccess) return L.cuda(w.err, "qpat_ld_solve workspace");
+
+  qpat_status st;
+  if ((st = L.cuda(cudaMemcpyAsync(mu0, mu, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
+    return st;
+  if ((st = L.cuda(cudaMemsetAsync(xbar, 0, N * sizeof(double), s), "memset")) != QPAT_OK) return st;
+  add_const_kernel<<<blocks_for(N), kT, 0, s>>>(N, 1.0, ones, 1);
+
+  auto phi_q = [&](int q) { return phi + (size_t)q * N; };
+  auto hq_q = [&](int q) -> void* { return hq + (size_t)q * N * L.elt; };
+  auto hb_q = [&](int q) -> const void* { return hb + (size_t)q * N * L.elt; };
+
+  // sum_q mu o J_o,q^*(hbar_q) into out; the acoustic halves of all
+  // illuminations run as one batch
+  auto optical_adjoint_sum = [&](double* out) -> qpat_status {
+    for (int q = 0; q < nq; ++q) {
+      qpat_status e = (qpat_status)optics_vjp(c, mu, phi_q(q), hb_q(q), t2);
+      if (e != QPAT_OK) return e;
+      hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu, t2, out, q > 0);
+    }
+    return L.cuda(cudaGetLastError(), "optical adjoint");
+  };
+
+  // H d = sum_q mu o J_q^*(J_q(mu o d)) into hd (eq. apj); t1, t2 scratch
+  auto gn_product = [&](const double* dd) -> qpat_status {
+    hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu, dd, t1, 0);
+    for (int q = 0; q < nq; ++q) {
+      qpat_status e = (qpat_status)optics_jvp(c, mu, phi_q(q), t1, hq_q(q));
+      if (e != QPAT_OK) return e;
+    }
+    qpat_status e = qpat_acoustic_forward(c, nq, hq, jv);
+    if (e != QPAT_OK) return e;
+    if ((e = qpat_acoustic_adjoint(c, nq, jv, hb)) != QPAT_OK) return e;
+    L.products += 2 * nq;
+    return optical_adjoint_sum(hd);
+  };
+
+  std::vector<double> eps;
+  int inner_total = 0;
+  int k = 0;
+  for (;;) {
+    // linearisation point mu^k = mu0 exp(Xbar^k): residuals, eps^k, fluences
+    exp_scale_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu0, xbar, mu);
+    for (int q = 0; q < nq; ++q)
+      if ((st = (qpat_status)optics_forward(c, mu, illum[q], phi_q(q), hq_q(q))) != QPAT_OK) return st;
+    if ((st = qpat_acoustic_forward(c, nq, hq, res)) != QPAT_OK) return st;
+    L.products += nq;
+    const long long MS = (long long)nq * L.M;
+    if (L.v.prec == QPAT_FP32)
+      resid_kernel<float><<<blocks_for(MS), kT, 0, s>>>(MS, (const float*)res, (const float*)data, (float*)res);
+    else
+      resid_kernel<double><<<blocks_for(MS), kT, 0, s>>>(MS, (const double*)res, (const double*)data, (double*)res);
+    double e2;
+    if ((st = L.dot_data(res, res, MS, &e2)) != QPAT_OK) return st;
+    eps.push_back(0.5 * e2);
+    if (k > 0 && !(1.0 - eps[k] / eps[k - 1] > p.tol_out)) break;
+    if (k >= p.k_max) break;
+
+    // gradient g = sum_q mu o J_q^*(H_q - P_q) (eq. gr)
+    if ((st = qpat_acoustic_adjoint(c, nq, res, hb)) != QPAT_OK) return st;
+    L.products += nq;
+    if ((st = optical_adjoint_sum(g)) != QPAT_OK) return st;
+    // M_gamma^k frozen at Xbar^k (lagged diffusivity)
+    if ((st = L.tv_weights(xbar)) != QPAT_OK) return st;
+
+    // Algorithm 4: PCG on H d = -g, preconditioner M_gamma, from 0
+    if ((st = L.cuda(cudaMemsetAsync(x, 0, N * sizeof(double), s), "memset")) != QPAT_OK) return st;
+    if ((st = L.cuda(cudaMemsetAsync(r, 0, N * sizeof(double), s), "memset")) != QPAT_OK) return st;
+    L.axpby(-1.0, g, 1.0, r);   // r_0 = -grad eps
+    if ((st = L.tv_solve(r, z, c_rr, c_pp, c_ap, c_zz, c_dg, ones, p.tv_max_iter, p.tv_tol)) != QPAT_OK) return st;
+    if ((st = L.cuda(cudaMemcpyAsync(d, z, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
+      return st;
+    std::vector<double> rz(1);
+    if ((st = L.dot(r, z, N, &rz[0])) != QPAT_OK) return st;
+    int i = 0;
+    while (i < p.i_max && rz[i] != 0.0 && (i < p.i_m || 1.0 - rz[i] / rz[i - p.i_m] > p.tol_in)) {
+      if ((st = gn_product(d)) != QPAT_OK) return st;
+      double dhd;
+      if ((st = L.dot(d, hd, N, &dhd)) != QPAT_OK) return st;
+      const double alpha = rz[i] / dhd;
+      L.axpby(alpha, d, 1.0, x);
+      L.axpby(-alpha, hd, 1.0, r);
+      if ((st = L.tv_solve(r, z, c_rr, c_pp, c_ap, c_zz, c_dg, ones, p.tv_max_iter, p.tv_tol)) != QPAT_OK) return st;
+      double rzn;
+      if ((st = L.dot(r, z, N, &rzn)) != QPAT_OK) return st;
+      rz.push_back(rzn);
+      L.axpby(1.0, z, rz[i + 1] / rz[i], d);
+      ++i;
+    }
+    if (inner_hist) inner_hist[k] = i;
+    inner_total += i;
+    L.axpby(1.0, x, 1.0, xbar);   // Xbar^{k+1} = Xbar^k + d^k (alpha^k = 1)
+    ++k;
+  }
+  if ((st = L.cuda(cudaStreamSynchronize(s), "qpat_ld_solve sync")) != QPAT_OK) return st;
+  if (eps_hist)
+    for (size_t j = 0; j < eps.size(); ++j) eps_hist[j] = eps[j];
+  if (info) {
+    info->outer = k;
+    info->inner_total = inner_total;
+    info->tv_iters = L.tv_iters;
+    info->products = L.products;
+    info->eps_first = eps.front();
+    info->eps_last = eps.back();
+  }
+  return QPAT_OK;
+}
+
+}  // extern "C"

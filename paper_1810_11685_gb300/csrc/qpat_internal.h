@@ -6,6 +6,8 @@
 
 #include "fft_smem.cuh"
 
+struct qpat_ctx;
+
 namespace qpat {
 
 // Flags of one propagation kernel launch.
@@ -222,6 +224,25 @@ template <typename T>
 cudaError_t dot_compensated(int batch, long long len, const T* a, const T* b, double* d_partial, double* d_out,
                             cudaStream_t s);
 constexpr int kPartials = 256;
+
+// What code outside api.cu needs to know about a context (the reconstruction
+// loop in ld.cu is a client of the public entry points).
+struct CtxView {
+  int prec, dim, n0, n1, n2, nt, ns, maxb;
+  long long N;
+  double dx;
+  cudaStream_t stream;
+};
+bool ctx_view(const struct ::qpat_ctx* c, CtxView* v);
+// Record msg as the context's last error and return st.
+int ctx_fail(struct ::qpat_ctx* c, int st, const char* msg);
+// Optical halves of the composite maps for one problem (return qpat_status):
+// optics_forward: phi = fluence of mu, h = mu o phi (prec [N]);
+// optics_jvp: dh = dmu o phi0 + mu o dphi, A dphi = -h^d dmu o phi0;
+// optics_vjp: g = phi0 o (hbar + H~), A H~ = -h^d mu o hbar (hbar prec [N]).
+int optics_forward(struct ::qpat_ctx* c, const double* mu, unsigned illum, double* phi, void* h);
+int optics_jvp(struct ::qpat_ctx* c, const double* mu, const double* phi0, const double* dmu, void* dh);
+int optics_vjp(struct ::qpat_ctx* c, const double* mu, const double* phi0, const void* hbar, double* g);
 // CTAs per problem of the conjugate-gradient and multigrid kernels (eight per SM)
 constexpr int kPCGBlocks = 1216;
 
