@@ -140,3 +140,98 @@ def vjp(mu, kappa, h, sides_mask, hbar, phi0=None):
         phi0 = solve(A, b).reshape(mu.shape)
     ht = solve(A, -(h ** dim) * (mu * hbar).ravel()).reshape(mu.shape)
     return phi0 * (hbar + ht)
+
+
+# ---- derivatives in kappa (Lemma 1, delta-kappa rows) -------------------------
+def _dharmonic_da(a, b):
+    """d/da of the harmonic mean 2ab/(a+b)."""
+    return 2.0 * b * b / (a + b) ** 2
+
+
+def kappa_source(mu, kappa, h, sides_mask, phi0, dkappa, gamma=None):
+    """delta-b - delta-A Phi0 for the perturbation dkappa of the cell values
+    of kappa: the right-hand side of A delta-Phi in the discrete counterpart of
+    eq. dPhi.  Written out face by face like ``assemble``: an interior face
+    between cells a, b carries t = kappa_f h^(d-2) with the harmonic mean
+    kappa_f, so delta-t = h^(d-2) (d kappa_f/d kappa_a dkappa_a + d kappa_f /
+    d kappa_b dkappa_b) and delta-A Phi0 gains delta-t (Phi_a - Phi_b) at a
+    and the opposite at b; a boundary face of cell c adds
+    2 gamma kappa_c h^(d-1)/(gamma h + kappa_c) to the diagonal and
+    2 kappa_c I h^(d-1)/(gamma h + kappa_c) to the right-hand side, both
+    differentiated in kappa_c."""
+    mu = np.asarray(mu, dtype=np.float64)
+    kappa = np.asarray(kappa, dtype=np.float64)
+    shape = mu.shape
+    dim = mu.ndim
+    gam = gamma_d(dim) if gamma is None else gamma
+    out = np.zeros(shape)
+    currents = boundary_current(shape, sides_mask)
+    for i in range(dim):
+        a = dim - 1 - i
+        lo = [slice(None)] * dim
+        hi = [slice(None)] * dim
+        lo[a] = slice(0, shape[a] - 1)
+        hi[a] = slice(1, shape[a])
+        lo, hi = tuple(lo), tuple(hi)
+        ka, kb = kappa[lo], kappa[hi]
+        dt = (_dharmonic_da(ka, kb) * dkappa[lo] + _dharmonic_da(kb, ka) * dkappa[hi]) * h ** (dim - 2)
+        flux = dt * (phi0[lo] - phi0[hi])
+        out[lo] -= flux
+        out[hi] += flux
+        for side in (0, 1):
+            sl = [slice(None)] * dim
+            sl[a] = 0 if side == 0 else shape[a] - 1
+            sl = tuple(sl)
+            kc = kappa[sl]
+            q = gam * h / (gam * h + kc) ** 2 * h ** (dim - 1)    # d/dkappa of kappa h^(d-1)/(gamma h + kappa)
+            I = np.asarray(currents[2 * i + side], dtype=np.float64)
+            out[sl] += 2.0 * q * dkappa[sl] * (I - gam * phi0[sl])
+    return out
+
+
+def jvp_kappa(mu, kappa, h, sides_mask, dkappa, phi0=None):
+    """J_o dkappa = mu o delta-Phi with A delta-Phi = delta-b - delta-A Phi0
+    (Lemma 1, eqs. fr and dPhi, delta-mu = 0)."""
+    A, b = assemble(mu, kappa, h, boundary_current(mu.shape, sides_mask))
+    if phi0 is None:
+        phi0 = solve(A, b).reshape(mu.shape)
+    rhs = kappa_source(mu, kappa, h, sides_mask, phi0, np.asarray(dkappa, dtype=np.float64))
+    return mu * solve(A, rhs.ravel()).reshape(mu.shape)
+
+
+def vjp_kappa(mu, kappa, h, sides_mask, hbar, phi0=None):
+    """J_o^T hbar in kappa: with psi = A^-1 (mu o hbar) (A is symmetric),
+    <J_o dkappa, hbar> = <delta-b - delta-A Phi0, psi>, read off cell by cell
+    (the discrete counterpart of the grad-phi0 . grad-h~ row of eq.
+    opt_adjoint with its boundary term)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    kappa = np.asarray(kappa, dtype=np.float64)
+    shape = mu.shape
+    dim = mu.ndim
+    gam = gamma_d(dim)
+    A, b = assemble(mu, kappa, h, boundary_current(shape, sides_mask))
+    if phi0 is None:
+        phi0 = solve(A, b).reshape(shape)
+    psi = solve(A, (mu * hbar).ravel()).reshape(shape)
+    g = np.zeros(shape)
+    currents = boundary_current(shape, sides_mask)
+    for i in range(dim):
+        a = dim - 1 - i
+        lo = [slice(None)] * dim
+        hi = [slice(None)] * dim
+        lo[a] = slice(0, shape[a] - 1)
+        hi[a] = slice(1, shape[a])
+        lo, hi = tuple(lo), tuple(hi)
+        ka, kb = kappa[lo], kappa[hi]
+        w = -(phi0[lo] - phi0[hi]) * (psi[lo] - psi[hi]) * h ** (dim - 2)
+        g[lo] += _dharmonic_da(ka, kb) * w
+        g[hi] += _dharmonic_da(kb, ka) * w
+        for side in (0, 1):
+            sl = [slice(None)] * dim
+            sl[a] = 0 if side == 0 else shape[a] - 1
+            sl = tuple(sl)
+            kc = kappa[sl]
+            q = gam * h / (gam * h + kc) ** 2 * h ** (dim - 1)
+            I = np.asarray(currents[2 * i + side], dtype=np.float64)
+            g[sl] += 2.0 * q * (I - gam * phi0[sl]) * psi[sl]
+    return g

@@ -137,3 +137,51 @@ def test_vjp_is_transpose_of_jvp_brute_force():
     w = rng.standard_normal((n, n))
     np.testing.assert_allclose(optics.vjp(mu, kappa, h, 0b1000, w).ravel(), J.T @ w.ravel(),
                                rtol=1e-10, atol=1e-14)
+
+
+# ---- kappa derivatives (Lemma 1, delta-kappa rows) -------------------------------
+@pytest.mark.parametrize("dim,mask", [(2, 0b0001), (2, 0b0110), (3, 0b010001)])
+def test_kappa_jvp_matches_central_differences(dim, mask):
+    rng = np.random.default_rng(11 + dim)
+    n = 9 if dim == 2 else 6
+    shape = (n,) * dim
+    h = 1e-4
+    mu = rng.uniform(5, 50, size=shape)
+    kappa = rng.uniform(3e-4, 6e-4, size=shape)
+    for k in range(3):
+        v = rng.standard_normal(shape) * kappa
+        t = 1e-6
+        fd = (optics.heating(mu, kappa + t * v, h, mask) - optics.heating(mu, kappa - t * v, h, mask)) / (2 * t)
+        jv = optics.jvp_kappa(mu, kappa, h, mask, v)
+        assert np.linalg.norm(fd - jv) <= 1e-6 * np.linalg.norm(jv)
+
+
+def test_kappa_vjp_is_transpose_brute_force():
+    rng = np.random.default_rng(13)
+    n, h = 5, 1e-4
+    mu = rng.uniform(5, 50, size=(n, n))
+    kappa = rng.uniform(3e-4, 6e-4, size=(n, n))
+    J = np.zeros((n * n, n * n))
+    for j in range(n * n):
+        e = np.zeros(n * n)
+        e[j] = 1
+        J[:, j] = optics.jvp_kappa(mu, kappa, h, 0b0101, e.reshape(n, n)).ravel()
+    w = rng.standard_normal((n, n))
+    np.testing.assert_allclose(optics.vjp_kappa(mu, kappa, h, 0b0101, w).ravel(), J.T @ w.ravel(),
+                               rtol=1e-10, atol=1e-14 * np.abs(J).max())
+
+
+def test_kappa_derivative_of_a_homogeneous_scaling():
+    """Scaling kappa and mu together by s with h fixed maps Phi to a problem
+    whose heating changes only through the Robin terms; a check independent
+    of the face formulas: d/ds heating(s mu, s kappa) at s = 1 equals
+    J_mu mu + J_kappa kappa."""
+    rng = np.random.default_rng(14)
+    n, h = 8, 1e-4
+    mu = rng.uniform(5, 50, size=(n, n))
+    kappa = rng.uniform(3e-4, 6e-4, size=(n, n))
+    t = 1e-6
+    fd = (optics.heating((1 + t) * mu, (1 + t) * kappa, h, 0b0011)
+          - optics.heating((1 - t) * mu, (1 - t) * kappa, h, 0b0011)) / (2 * t)
+    both = optics.jvp(mu, kappa, h, 0b0011, mu) + optics.jvp_kappa(mu, kappa, h, 0b0011, kappa)
+    assert np.linalg.norm(fd - both) <= 1e-6 * np.linalg.norm(both)
