@@ -165,6 +165,24 @@ qpat_status qpat_jvp(qpat_ctx* ctx, int batch, const double* mu, const double* p
 qpat_status qpat_vjp(qpat_ctx* ctx, int batch, const double* mu, const double* phi0,
                      const void* w, unsigned illum, double* g);
 
+/* Derivatives in kappa (Lemma 1, delta-kappa rows), on the finite-volume
+ * system: A(kappa, mu) phi = b(kappa) with harmonic-mean face coefficients and
+ * Robin terms, differentiated face by face.
+ * qpat_set_kappa: replace the context's kappa (device double [N], > 0; read
+ *   during the call) and rebuild the diffusion operator and its multigrid
+ *   levels in place.  Synchronises.
+ * qpat_jvp_kappa: dP-hat = H_a(mu o dphi), A dphi = delta-b - delta-A phi0
+ *   (eqs. fr, dPhi with delta-mu = 0); dkappa: device double [batch][N].
+ * qpat_vjp_kappa: g = <delta-b - delta-A phi0, psi> per cell with
+ *   A psi = mu o H_a^*(w) (the discrete counterpart of the grad phi0 . grad h~
+ *   row of eq. opt_adjoint with its boundary term); g: device double
+ *   [batch][N].  phi0 as in qpat_jvp (NULL: solved here). */
+qpat_status qpat_set_kappa(qpat_ctx* ctx, const double* kappa);
+qpat_status qpat_jvp_kappa(qpat_ctx* ctx, int batch, const double* mu, const double* phi0,
+                           const double* dkappa, unsigned illum, void* dP);
+qpat_status qpat_vjp_kappa(qpat_ctx* ctx, int batch, const double* mu, const double* phi0,
+                           const void* w, unsigned illum, double* g);
+
 /* Forward-state checkpointing of H_a.  The mu-gradient (qpat_vjp) needs no
  * forward fields -- the transposed step T^* of Section 3.2.4 does not depend
  * on the forward state -- so these calls serve callers that need the fields

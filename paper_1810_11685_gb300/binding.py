@@ -105,6 +105,9 @@ def load():
         "qpat_ld_solve": [vp, i, vp, vp, vp, ctypes.POINTER(qpat_ld_params), ctypes.POINTER(qpat_ld_info),
                           ctypes.POINTER(d), ctypes.POINTER(i)],
         "qpat_tv_apply": [vp, vp, d, d, d, vp, vp],
+        "qpat_set_kappa": [vp, vp],
+        "qpat_jvp_kappa": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
+        "qpat_vjp_kappa": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -377,6 +380,41 @@ class Context:
                                                   _ptr(u), _ptr(out)))
         return out[0]
 
+    def set_kappa(self, kappa):
+        """qpat_set_kappa: new optical diffusion (FP64 interior field)."""
+        import torch
+        kappa = self._in(kappa, torch.float64, self.interior_shape)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_set_kappa(self._ptr, _ptr(kappa)))
+
+    def jvp_kappa(self, mu, dkappa, illum, phi0=None):
+        """qpat_jvp_kappa: H_a J_o dkappa."""
+        import torch
+        mu = self._in(mu, torch.float64, self.interior_shape)
+        dkappa = self._in(dkappa, torch.float64, self.interior_shape)
+        if phi0 is not None:
+            phi0 = self._in(phi0, torch.float64, self.interior_shape)
+        B = dkappa.shape[0]
+        out = self._empty(B, self.nt, self.ns)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_jvp_kappa(self._ptr, B, _ptr(mu), _ptr(phi0), _ptr(dkappa), int(illum),
+                                                   _ptr(out)))
+        return out
+
+    def vjp_kappa(self, mu, w, illum, phi0=None):
+        """qpat_vjp_kappa: J_o^* H_a^*(w) in kappa."""
+        import torch
+        mu = self._in(mu, torch.float64, self.interior_shape)
+        w = self._in(w, self.dtype, (self.nt, self.ns))
+        if phi0 is not None:
+            phi0 = self._in(phi0, torch.float64, self.interior_shape)
+        B = w.shape[0]
+        out = self._empty(B, *self.interior_shape, dtype=torch.float64)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_vjp_kappa(self._ptr, B, _ptr(mu), _ptr(phi0), _ptr(w), int(illum),
+                                                   _ptr(out)))
+        return out
+
     def dot(self, a, b):
         a = a.contiguous()
         b = b.contiguous()
@@ -514,6 +552,18 @@ def qpat_ld_solve(ctx: Context, data, illums, mu0, **params):
 
 def qpat_tv_apply(ctx: Context, xbar, edge, beta, gamma, u):
     return ctx.tv_apply(xbar, u, edge, beta, gamma)
+
+
+def qpat_set_kappa(ctx: Context, kappa):
+    ctx.set_kappa(kappa)
+
+
+def qpat_jvp_kappa(ctx: Context, mu, dkappa, illum, phi0=None):
+    return ctx.jvp_kappa(mu, dkappa, illum, phi0)
+
+
+def qpat_vjp_kappa(ctx: Context, mu, w, illum, phi0=None):
+    return ctx.vjp_kappa(mu, w, illum, phi0)
 
 
 def qpat_sync(ctx: Context):

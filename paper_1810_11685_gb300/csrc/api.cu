@@ -45,6 +45,7 @@ struct qpat_ctx {
   int* h_err = nullptr;
   void* tw_p0 = nullptr;       // [B][N] prec: heating handed to H_a
   void* tw_hbar = nullptr;     // [B][N] prec: H_a^* output
+  double* d_kappa = nullptr;   // [N] optical diffusion (qpat_set_kappa replaces it)
   double* d_phi = nullptr;     // [B][N]
   double* d_rhs = nullptr;     // [B][N]
   double* d_tmp = nullptr;     // [B][N]
@@ -774,6 +775,7 @@ qpat_status qpat_create(const qpat_config* cfg, const qpat_medium* med, const do
   QCKC(dalloc(c, &bside, 2 * c->dim * N * sizeof(double)));
   QCKC(dalloc(c, &dkappa, N * sizeof(double)));
   QCKC(cudaMemcpy(dkappa, med->kappa, N * sizeof(double), cudaMemcpyHostToDevice));
+  c->d_kappa = dkappa;
   QCKC(da_setup(c->da, diag0, cxf, cyf, czf, bside, dkappa, c->stream));
   PCGWork& w = c->pcg;
   for (double** p : {&w.x, &w.r, &w.z, &w.p, &w.q, &w.dinv, &w.b}) QCKC(dalloc(c, p, B * N * sizeof(double)));
@@ -942,6 +944,65 @@ qpat_status qpat_vjp(qpat_ctx* c, int batch, const double* mu, const double* phi
   if (st != QPAT_OK) return st;
   if (c->prec == QPAT_FP32) QCK(da_adjoint_out<float>(batch, N, phi0, (const float*)c->tw_hbar, c->d_tmp, g, c->stream));
   else QCK(da_adjoint_out<double>(batch, N, phi0, (const double*)c->tw_hbar, c->d_tmp, g, c->stream));
+  return QPAT_OK;
+}
+
+// kappa derivatives (Lemma 1, delta-kappa rows) ---------------------------------
+
+qpat_status qpat_set_kappa(qpat_ctx* c, const double* kappa) {
+  if (!c) return QPAT_EINVAL;
+  if (!kappa) return fail(c, QPAT_EINVAL, "null buffer");
+  QCK(cudaMemcpyAsync(c->d_kappa, kappa, (size_t)c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  QCK(da_setup(c->da, const_cast<double*>(c->da.diag0), const_cast<double*>(c->da.cxf),
+               const_cast<double*>(c->da.cyf), const_cast<double*>(c->da.czf), const_cast<double*>(c->da.bside),
+               c->d_kappa, c->stream));
+  if (c->mg) {
+    c->mg->lev[0].A = c->da;
+    QCK(mg_rekappa(*c->mg, c->stream));
+  }
+  QCK(cudaStreamSynchronize(c->stream));
+  return QPAT_OK;
+}
+
+qpat_status qpat_jvp_kappa(qpat_ctx* c, int batch, const double* mu, const double* phi0, const double* dkappa,
+                           unsigned illum, void* dP) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!mu || !dkappa || !dP) return fail(c, QPAT_EINVAL, "null buffer");
+  const int N = (int)c->N;
+  if (!phi0) {
+    st = qpat_da_solve(c, batch, mu, illum, c->d_phi);
+    if (st != QPAT_OK) return st;
+    phi0 = c->d_phi;
+  }
+  // A dphi = delta-b - delta-A phi0 (eq. dPhi), dh = mu o dphi (eq. fr)
+  QCK(da_kappa_source(c->da, c->d_kappa, batch, phi0, dkappa, illum, c->d_rhs, c->stream));
+  st = solve_da(c, batch, mu, c->d_rhs, c->d_tmp);
+  if (st != QPAT_OK) return st;
+  if (c->prec == QPAT_FP32) QCK(da_heating_T<float>(batch, N, mu, c->d_tmp, nullptr, nullptr, (float*)c->tw_p0, c->stream));
+  else QCK(da_heating_T<double>(batch, N, mu, c->d_tmp, nullptr, nullptr, (double*)c->tw_p0, c->stream));
+  return qpat_acoustic_forward(c, batch, c->tw_p0, dP);
+}
+
+qpat_status qpat_vjp_kappa(qpat_ctx* c, int batch, const double* mu, const double* phi0, const void* w,
+                           unsigned illum, double* g) {
+  qpat_status st = check_batch(c, batch);
+  if (st != QPAT_OK) return st;
+  if (!mu || !w || !g) return fail(c, QPAT_EINVAL, "null buffer");
+  const int N = (int)c->N;
+  st = qpat_acoustic_adjoint(c, batch, w, c->tw_hbar);
+  if (st != QPAT_OK) return st;
+  if (!phi0) {
+    st = qpat_da_solve(c, batch, mu, illum, c->d_phi);
+    if (st != QPAT_OK) return st;
+    phi0 = c->d_phi;
+  }
+  // psi = A^-1 (mu o hbar); g = <delta-b - delta-A phi0, psi> per cell
+  if (c->prec == QPAT_FP32) QCK(da_adjoint_rhs<float>(batch, N, 1.0, mu, (const float*)c->tw_hbar, c->d_rhs, c->stream));
+  else QCK(da_adjoint_rhs<double>(batch, N, 1.0, mu, (const double*)c->tw_hbar, c->d_rhs, c->stream));
+  st = solve_da(c, batch, mu, c->d_rhs, c->d_tmp);
+  if (st != QPAT_OK) return st;
+  QCK(da_kappa_grad(c->da, c->d_kappa, batch, phi0, c->d_tmp, illum, g, c->stream));
   return QPAT_OK;
 }
 

@@ -249,6 +249,7 @@ cudaError_t mg_setup(MGHierarchy& h, const DAArgs& fine, const double* d_kappa, 
                      void* owner, cudaStream_t s) {
   h.nlev = 1;
   h.lev[0].A = fine;
+  h.lev[0].kappa = const_cast<double*>(d_kappa);
   const double* kap = d_kappa;
   while (h.nlev < kMaxLevels) {
     const DAArgs& f = h.lev[h.nlev - 1].A;
@@ -271,6 +272,7 @@ cudaError_t mg_setup(MGHierarchy& h, const DAArgs& fine, const double* d_kappa, 
     if ((e = alloc(owner, (void**)&bs, (size_t)2 * c.dim * c.N * sizeof(double))) != cudaSuccess) return e;
     if ((e = da_setup(c, d0, cx, cy, cz, bs, ck, s)) != cudaSuccess) return e;
     h.lev[h.nlev].A = c;
+    h.lev[h.nlev].kappa = ck;
     kap = ck;
     ++h.nlev;
   }
@@ -282,6 +284,20 @@ cudaError_t mg_setup(MGHierarchy& h, const DAArgs& fine, const double* d_kappa, 
     if ((e = alloc(owner, (void**)&L.x2, bytes)) != cudaSuccess) return e;
     if (l > 0 && (e = alloc(owner, (void**)&L.x, bytes)) != cudaSuccess) return e;
     if (l > 0 && (e = alloc(owner, (void**)&L.b, bytes)) != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t mg_rekappa(MGHierarchy& h, cudaStream_t s) {
+  for (int l = 1; l < h.nlev; ++l) {
+    const DAArgs& f = h.lev[l - 1].A;
+    DAArgs& c = h.lev[l].A;
+    coarsen_mean_kernel<<<dim3(128, 1), kThreads, 0, s>>>(h.lev[l - 1].kappa, h.lev[l].kappa, f.n0, f.n1, f.n2, f.dim,
+                                                          0, 0);
+    cudaError_t e = da_setup(c, const_cast<double*>(c.diag0), const_cast<double*>(c.cxf),
+                             const_cast<double*>(c.cyf), const_cast<double*>(c.czf), const_cast<double*>(c.bside),
+                             h.lev[l].kappa, s);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -594,6 +610,67 @@ template <typename T>
 cudaError_t da_adjoint_rhs(int batch, int N, double scale, const double* mu, const T* hbar, double* out,
                            cudaStream_t s) {
   adjoint_rhs_kernel<T><<<512, kThreads, 0, s>>>((long long)batch * N, scale, mu, hbar, out);
+  return cudaGetLastError();
+}
+
+// ---- derivatives in kappa --------------------------------------------------
+// d/da of the harmonic mean 2ab/(a+b)
+__device__ __forceinline__ double dharmonic(double a, double b) { return 2.0 * b * b / ((a + b) * (a + b)); }
+
+// Per cell c: the faces to its neighbours (axis, direction) and its boundary
+// sides.  mode 0: out = delta-b - delta-A phi for dkappa (gather form: the
+// face (c, nb) changes its coefficient by hf (dh(k_c, k_nb) dk_c +
+// dh(k_nb, k_c) dk_nb) and contributes -delta-t (phi_c - phi_nb); a boundary
+// side s adds 2 q dk_c (I_s - gamma phi_c) with q = d/dk of k h^(d-1)/(gamma h
+// + k)).  mode 1: out = the kappa gradient sum over faces of
+// -dh(k_c, k_nb) hf (phi_c - phi_nb)(psi_c - psi_nb) plus 2 q (I_s - gamma
+// phi_c) psi_c per boundary side.
+__global__ void kappa_deriv_kernel(DAArgs a, const double* kappa, const double* phi, const double* v, unsigned mask,
+                                   double* out, int mode) {
+  const long long o = (long long)blockIdx.y * a.N;
+  const double hf = (a.dim == 3) ? a.h : 1.0;
+  const double hb = (a.dim == 3) ? a.h * a.h : a.h;
+  const int sy = a.n0, sz = a.n0 * a.n1;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.N; g += gridDim.x * blockDim.x) {
+    const int i = g % a.n0, j = (g / a.n0) % a.n1, k = g / sz;
+    const double kc = kappa[g], pc = phi[o + g], vc = v[o + g];
+    double acc = 0.0;
+    const int nbs[6] = {i > 0 ? g - 1 : -1, i < a.n0 - 1 ? g + 1 : -1, j > 0 ? g - sy : -1,
+                        j < a.n1 - 1 ? g + sy : -1, (a.dim == 3 && k > 0) ? g - sz : -1,
+                        (a.dim == 3 && k < a.n2 - 1) ? g + sz : -1};
+    for (int f = 0; f < 6; ++f) {
+      const int nb = nbs[f];
+      if (nb < 0) continue;
+      const double kn = kappa[nb];
+      if (mode == 0) {
+        const double dt = hf * (dharmonic(kc, kn) * vc + dharmonic(kn, kc) * v[o + nb]);
+        acc -= dt * (pc - phi[o + nb]);
+      } else {
+        acc -= dharmonic(kc, kn) * hf * (pc - phi[o + nb]) * (vc - v[o + nb]);
+      }
+    }
+    const double gh = a.gamma * a.h;
+    const double q = gh * hb / ((gh + kc) * (gh + kc));
+    const bool on[6] = {i == 0, i == a.n0 - 1, j == 0, j == a.n1 - 1, a.dim == 3 && k == 0,
+                        a.dim == 3 && k == a.n2 - 1};
+    for (int s = 0; s < 2 * a.dim; ++s) {
+      if (!on[s]) continue;
+      const double I = ((mask >> s) & 1u) ? 1.0 : 0.0;
+      acc += 2.0 * q * (I - a.gamma * pc) * vc;
+    }
+    out[o + g] = acc;
+  }
+}
+
+cudaError_t da_kappa_source(const DAArgs& a, const double* kappa, int batch, const double* phi, const double* dkappa,
+                            unsigned mask, double* out, cudaStream_t s) {
+  kappa_deriv_kernel<<<dim3(128, batch), kThreads, 0, s>>>(a, kappa, phi, dkappa, mask, out, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t da_kappa_grad(const DAArgs& a, const double* kappa, int batch, const double* phi, const double* psi,
+                          unsigned mask, double* out, cudaStream_t s) {
+  kappa_deriv_kernel<<<dim3(128, batch), kThreads, 0, s>>>(a, kappa, phi, psi, mask, out, 1);
   return cudaGetLastError();
 }
 

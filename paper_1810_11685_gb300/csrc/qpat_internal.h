@@ -169,6 +169,7 @@ cudaError_t da_setup(DAArgs& a, double* d_diag0, double* d_cxf, double* d_cyf, d
 struct MGLevel {
   DAArgs A;
   double *mu, *x, *x2, *b;
+  double* kappa;           // the level's kappa (the fine level: the context's)
 };
 constexpr int kMaxLevels = 16;
 struct MGHierarchy {
@@ -203,6 +204,17 @@ cudaError_t mg_setup(MGHierarchy& h, const DAArgs& fine, const double* d_kappa, 
 int pcg_solve(const DAArgs& a, const double* mu, int batch, const double* rhs, double* x, PCGWork& w,
               int max_iter, double tol, cudaStream_t s, cudaError_t* err);
 cudaError_t da_rhs_from_sides(const DAArgs& a, unsigned mask, int batch, double* rhs, cudaStream_t s);
+// Rebuild every coarse level's operator from the fine level's kappa, in the
+// same buffers (captured graphs stay valid).
+cudaError_t mg_rekappa(MGHierarchy& h, cudaStream_t s);
+// delta-b - delta-A phi of the system for the kappa perturbation dkappa_b
+// (illumination mask), [B][N] (Lemma 1, delta-kappa rows).
+cudaError_t da_kappa_source(const DAArgs& a, const double* kappa, int batch, const double* phi, const double* dkappa,
+                            unsigned mask, double* out, cudaStream_t s);
+// Its transpose read against psi_b: the kappa gradient <delta-b - delta-A phi,
+// psi> per cell, [B][N].
+cudaError_t da_kappa_grad(const DAArgs& a, const double* kappa, int batch, const double* phi, const double* psi,
+                          unsigned mask, double* out, cudaStream_t s);
 // out_b = alpha * (u_b o v_b)   (all [B][N] FP64)
 cudaError_t da_hadamard(int batch, int N, double alpha, const double* u, const double* v, double* out,
                         cudaStream_t s);
