@@ -2,8 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-The unknown is the absorption mu on the interior grid; kappa stays fixed (the
-mu-derivative only, as in ``optics``).  Written out from Sections 4 and 5:
+The unknown is the absorption mu on the interior grid with kappa fixed
+(``Problem``), or both kappa and mu (``JointProblem``, the simultaneous
+reconstruction of Section 6, using the kappa derivatives of ``optics``).
+Written out from Sections 4 and 5:
 
 * logarithmic scaling Xbar = log(mu / mu0) (eq. logscale), so that
   d mu / d Xbar = diag(mu);
@@ -97,6 +99,57 @@ def m_gamma(xbar, edge, beta, gamma):
 
 
 # ---- data misfit, gradient and Gauss-Newton Hessian -----------------------------
+class JointProblem:
+    """The simultaneous reconstruction of kappa and mu (Sections 5 and 6):
+    Xbar = [kappa-bar, mu-bar] (eq. scaling), each log-scaled against its
+    initial guess (eq. logscale), so d X / d Xbar = diag(kappa, mu); J_q
+    acts on both blocks (Lemma 1, eq. fr), and D is block diagonal (eq. dd)."""
+
+    def __init__(self, S, illums: Sequence[int], P, mu0, kappa0):
+        self.S = S
+        self.illums = list(illums)
+        self.P = [np.asarray(p, dtype=np.float64) for p in P]
+        self.mu0 = np.asarray(mu0, dtype=np.float64)
+        self.kappa0 = np.asarray(kappa0, dtype=np.float64)
+        self.shape = (2,) + self.mu0.shape
+
+    def coeffs(self, xbar):
+        """(kappa, mu) at Xbar."""
+        return self.kappa0 * np.exp(xbar[0]), self.mu0 * np.exp(xbar[1])
+
+    def forward(self, kappa, mu, q):
+        return acoustic.forward(self.S, optics.heating(mu, kappa, self.S.dx, self.illums[q]))
+
+    def residuals(self, xbar):
+        kappa, mu = self.coeffs(xbar)
+        return [self.forward(kappa, mu, q) - self.P[q] for q in range(len(self.illums))]
+
+    def misfit(self, xbar):
+        return 0.5 * sum(float(np.sum(r * r)) for r in self.residuals(xbar))
+
+    def _JT(self, kappa, mu, q, W):
+        hbar = acoustic.adjoint(self.S, W)
+        gk = optics.vjp_kappa(mu, kappa, self.S.dx, self.illums[q], hbar)
+        gm = optics.vjp(mu, kappa, self.S.dx, self.illums[q], hbar)
+        return np.stack([kappa * gk, mu * gm])
+
+    def gradient(self, xbar, res=None):
+        """eq. gr with d X / d Xbar = diag(kappa, mu)."""
+        kappa, mu = self.coeffs(xbar)
+        res = self.residuals(xbar) if res is None else res
+        return sum(self._JT(kappa, mu, q, res[q]) for q in range(len(self.illums)))
+
+    def gn_product(self, xbar, d):
+        """eq. apj on both blocks."""
+        kappa, mu = self.coeffs(xbar)
+        out = np.zeros(self.shape)
+        for q, m in enumerate(self.illums):
+            dh = (optics.jvp_kappa(mu, kappa, self.S.dx, m, kappa * d[0])
+                  + optics.jvp(mu, kappa, self.S.dx, m, mu * d[1]))
+            out += self._JT(kappa, mu, q, acoustic.forward(self.S, dh))
+        return out
+
+
 class Problem:
     """Direct-QPAT misfit over illuminations ``illums`` (side masks) for the
     data ``P`` [nq][Nt][Ns], with the FP64 oracle maps."""
@@ -169,11 +222,14 @@ def pcg(apply_H: Callable, rhs, solve_M: Callable, i_max, i_m, tol_in):
 
 
 # ---- Algorithm 5 ---------------------------------------------------------------
-def ld_newton(prob: Problem, prm: LDParams):
+def ld_newton(prob, prm: LDParams):
     """Algorithm 5: returns (mu*, Xbar*, eps history, inner iterations per
-    outer iteration).  eps history holds eps^0, eps^1, ...: the misfit at each
-    linearisation point, the last at the returned mu*."""
-    shape = prob.mu0.shape
+    outer iteration) for a ``Problem`` (mu only), or ((kappa*, mu*), Xbar*,
+    ...) for a ``JointProblem``, where M_gamma acts block by block.  eps
+    history holds eps^0, eps^1, ...: the misfit at each linearisation point,
+    the last at the returned coefficients."""
+    joint = isinstance(prob, JointProblem)
+    shape = prob.shape if joint else prob.mu0.shape
     xbar = np.zeros(shape)
     eps_hist: List[float] = []
     inner: List[int] = []
@@ -187,11 +243,20 @@ def ld_newton(prob: Problem, prm: LDParams):
         if k >= prm.k_max:
             break
         g = prob.gradient(xbar, res)
-        Mg = m_gamma(xbar, prm.edge, prm.beta, prm.gamma)
-        lu = spla.splu(Mg)
+        if joint:
+            lus = [spla.splu(m_gamma(xbar[b], prm.edge, prm.beta, prm.gamma)) for b in range(2)]
+            n = xbar[0].size
+
+            def solve_M(r):
+                return np.concatenate([lus[0].solve(r[:n]), lus[1].solve(r[n:])])
+        else:
+            lu = spla.splu(m_gamma(xbar, prm.edge, prm.beta, prm.gamma))
+
+            def solve_M(r):
+                return lu.solve(r)
         d, i, _ = pcg(lambda v: prob.gn_product(xbar, v.reshape(shape)).ravel(), -g.ravel(),
-                      lambda r: lu.solve(r), prm.i_max, prm.i_m, prm.tol_in)
+                      solve_M, prm.i_max, prm.i_m, prm.tol_in)
         inner.append(i)
         xbar = xbar + d.reshape(shape)
         k += 1
-    return prob.mu(xbar), xbar, eps_hist, inner
+    return (prob.coeffs(xbar) if joint else prob.mu(xbar)), xbar, eps_hist, inner

@@ -123,3 +123,54 @@ def test_ld_newton_decreases_the_misfit_and_the_error():
     assert eps[-1] < 0.2 * eps[0]
     assert np.linalg.norm(mu - mu_true) < np.linalg.norm(prob.mu0 - mu_true)
     assert np.allclose(mu, prob.mu0 * np.exp(xbar))
+
+
+def _joint_problem(n=8, nt=30, illums=(1, 4, 2, 8), seed=3):
+    w = phantoms.small(n=n, pml=4, nt=nt, n_sensors=12, seed=seed)
+    S = acoustic.setup_from_workload(w)
+    rng = np.random.default_rng(seed)
+    kappa_true = phantoms.optical_diffusion(w) * np.exp(0.3 * rng.standard_normal(w.interior_shape))
+    mu_true = phantoms.optical_absorption(w)
+    P = [acoustic.forward(S, optics.heating(mu_true, kappa_true, S.dx, q)) for q in illums]
+    mu0 = np.full(w.interior_shape, w.mu_bg)
+    kappa0 = phantoms.optical_diffusion(w)
+    return ld.JointProblem(S, illums, P, mu0, kappa0), (kappa_true, mu_true), w
+
+
+def test_joint_gradient_matches_central_differences():
+    prob, _, w = _joint_problem(illums=(1, 4))
+    rng = np.random.default_rng(6)
+    xbar = 0.2 * rng.normal(size=prob.shape)
+    g = prob.gradient(xbar)
+    t = 1e-4
+    for k in range(3):
+        v = rng.normal(size=prob.shape)
+        fd = (prob.misfit(xbar + t * v) - prob.misfit(xbar - t * v)) / (2 * t)
+        assert abs(fd - np.sum(g * v)) <= 1e-6 * abs(fd)
+
+
+def test_joint_gauss_newton_product_is_the_gram_form():
+    prob, _, w = _joint_problem(illums=(1, 4))
+    rng = np.random.default_rng(7)
+    xbar = 0.2 * rng.normal(size=prob.shape)
+    v, u = rng.normal(size=prob.shape), rng.normal(size=prob.shape)
+    Hv, Hu = prob.gn_product(xbar, v), prob.gn_product(xbar, u)
+    assert abs(np.sum(Hv * u) - np.sum(v * Hu)) <= 1e-12 * abs(np.sum(Hv * u))
+    t = 1e-5
+
+    def jsv(d, q):
+        kp, mp = prob.coeffs(xbar + t * d)
+        km, mm = prob.coeffs(xbar - t * d)
+        return (prob.forward(kp, mp, q) - prob.forward(km, mm, q)) / (2 * t)
+
+    gram = sum(np.sum(jsv(v, q) * jsv(u, q)) for q in range(2))
+    assert abs(gram - np.sum(Hv * u)) <= 1e-6 * abs(gram)
+
+
+def test_joint_ld_newton_decreases_the_misfit():
+    prob, (kappa_true, mu_true), w = _joint_problem()
+    prm = ld.LDParams(k_max=3, i_max=4, i_m=4, tol_in=0.0, tol_out=0.0, edge=w.dx / phantoms.MM)
+    (kappa, mu), xbar, eps, inner = ld.ld_newton(prob, prm)
+    assert len(eps) == 4 and inner == [4, 4, 4]
+    assert all(eps[k + 1] < eps[k] for k in range(3))
+    assert np.allclose(mu, prob.mu0 * np.exp(xbar[1])) and np.allclose(kappa, prob.kappa0 * np.exp(xbar[0]))
