@@ -232,9 +232,17 @@ qpat_status qpat_autotune(qpat_ctx* ctx, int batch, int steps, int* choice);
 qpat_status qpat_dot(qpat_ctx* ctx, int batch, long long len, const void* a, const void* b,
                      double* out);
 
-/* Reconstruction of mu by the inexact-Newton lagged-diffusivity method with
- * TV priorconditioning (Section 5.2.1, Algorithms 4 and 5), kappa fixed.
- *  - Unknown Xbar = log(mu / mu0) (eq. logscale); misfit
+/* Reconstruction of mu, or of kappa and mu together, by the inexact-Newton
+ * lagged-diffusivity method with TV priorconditioning (Section 5.2.1,
+ * Algorithms 4 and 5).
+ *  - kappa == NULL: the unknown is mu, kappa stays the context's.  Otherwise
+ *    the unknown is [kappa, mu] (eq. scaling): kappa is a device double [N],
+ *    kappa0 on entry and the reconstruction on return; the derivatives in
+ *    kappa are those of qpat_jvp_kappa / qpat_vjp_kappa, M_gamma and D are
+ *    block diagonal (eq. dd), and the context's kappa is replaced
+ *    (qpat_set_kappa) at every linearisation point, so it holds the
+ *    reconstructed kappa on return.
+ *  - Unknown Xbar = log(X / X0) per block (eq. logscale); misfit
  *    eps = 1/2 sum_q ||H_q[mu] - P_q||^2 over the illuminations q (eq. varr).
  *  - Outer iteration k (Algorithm 5): gradient g = sum_q mu o J_q^*(H_q - P_q)
  *    (eq. gr); M_gamma = D^T C D + gamma I frozen at Xbar^k (eqs. m, m1:
@@ -253,7 +261,7 @@ qpat_status qpat_dot(qpat_ctx* ctx, int batch, long long len, const void* a, con
  * return.  eps_hist (host double [k_max + 1]) and inner_hist (host int
  * [k_max]) are optional: eps^0, eps^1, ... and the PCG iterations per outer
  * iteration.  info (optional) receives the counts below.
- * Allocates and frees its workspace (about (17 + nq) N doubles, 2 nq nt ns
+ * Allocates and frees its workspace (about (20 + nq) N doubles, 2 nq nt ns
  * and 2 nq N prec values, and the face weights); synchronises (the Krylov
  * scalars are read on the host every iteration).  mu0 must be positive (log scaling); this is
  * not checked.  Errors: EINVAL (nq < 1 or > max_batch, bad masks), ENOCONV
@@ -282,7 +290,7 @@ typedef struct {
 } qpat_ld_info;
 
 qpat_status qpat_ld_solve(qpat_ctx* ctx, int nq, const unsigned* illum, const void* data, double* mu,
-                          const qpat_ld_params* prm, qpat_ld_info* info, double* eps_hist,
+                          double* kappa, const qpat_ld_params* prm, qpat_ld_info* info, double* eps_hist,
                           int* inner_hist);
 
 /* M_gamma u of the TV priorconditioner at Xbar (the operator qpat_ld_solve

@@ -102,7 +102,7 @@ def load():
         "qpat_acoustic_resume": [vp, i, vp, i, i, vp],
         "qpat_profile": [vp, i],
         "qpat_profile_read": [vp, ctypes.POINTER(d), ctypes.POINTER(ll)],
-        "qpat_ld_solve": [vp, i, vp, vp, vp, ctypes.POINTER(qpat_ld_params), ctypes.POINTER(qpat_ld_info),
+        "qpat_ld_solve": [vp, i, vp, vp, vp, vp, ctypes.POINTER(qpat_ld_params), ctypes.POINTER(qpat_ld_info),
                           ctypes.POINTER(d), ctypes.POINTER(i)],
         "qpat_tv_apply": [vp, vp, d, d, d, vp, vp],
         "qpat_set_kappa": [vp, vp],
@@ -346,28 +346,31 @@ class Context:
         _check(self._ptr, self._lib.qpat_vjp(self._ptr, B, _ptr(mu), _ptr(phi0), _ptr(w), int(illum), _ptr(out)))
         return out
 
-    def ld_solve(self, data, illums, mu0, k_max=10, i_max=30, i_m=5, tol_in=0.0, tol_out=1e-3, gamma=1e-6,
-                 beta=2e-5, tv_edge=0.0, tv_max_iter=0, tv_tol=0.0):
+    def ld_solve(self, data, illums, mu0, kappa0=None, k_max=10, i_max=30, i_m=5, tol_in=0.0, tol_out=1e-3,
+                 gamma=1e-6, beta=2e-5, tv_edge=0.0, tv_max_iter=0, tv_tol=0.0):
         """qpat_ld_solve: returns (mu, eps history, inner iterations per outer
-        iteration, info dict).  data: [nq][nt][ns] in the context precision;
-        mu0: FP64 interior field (the initial guess)."""
+        iteration, info dict), or ((kappa, mu), ...) when kappa0 is given
+        (simultaneous reconstruction).  data: [nq][nt][ns] in the context
+        precision; mu0, kappa0: FP64 interior fields (initial guesses)."""
         import torch
         nq = len(illums)
         data = data.contiguous()
         if data.dtype != self.dtype or tuple(data.shape) != (nq, self.nt, self.ns) or data.device.type != "cuda":
             raise TypeError("data must be a CUDA tensor [nq][nt][ns] of the context precision")
         mu = self._in(mu0, torch.float64, self.interior_shape).clone()
+        kappa = None if kappa0 is None else self._in(kappa0, torch.float64, self.interior_shape).clone()
         prm = qpat_ld_params(k_max, i_max, i_m, tol_in, tol_out, gamma, beta, tv_edge, tv_max_iter, tv_tol)
         info = qpat_ld_info()
         eps = (ctypes.c_double * (max(k_max, 1) + 1))()
         inner = (ctypes.c_int * max(k_max, 1))()
         ill = (ctypes.c_uint * nq)(*[int(q) for q in illums])
         self._stream()
-        _check(self._ptr, self._lib.qpat_ld_solve(self._ptr, nq, ill, _ptr(data), _ptr(mu), ctypes.byref(prm),
-                                                  ctypes.byref(info), eps, inner))
+        _check(self._ptr, self._lib.qpat_ld_solve(self._ptr, nq, ill, _ptr(data), _ptr(mu), _ptr(kappa),
+                                                  ctypes.byref(prm), ctypes.byref(info), eps, inner))
         k = info.outer
         out = {f: getattr(info, f) for f, _ in qpat_ld_info._fields_}
-        return mu[0], list(eps)[:k + 1], list(inner)[:k], out
+        coeffs = mu[0] if kappa is None else (kappa[0], mu[0])
+        return coeffs, list(eps)[:k + 1], list(inner)[:k], out
 
     def tv_apply(self, xbar, u, edge, beta, gamma):
         """qpat_tv_apply: M_gamma[xbar] u (FP64 interior fields)."""
@@ -546,8 +549,8 @@ def qpat_dot_noalloc(a, b, out=None):
     return out
 
 
-def qpat_ld_solve(ctx: Context, data, illums, mu0, **params):
-    return ctx.ld_solve(data, illums, mu0, **params)
+def qpat_ld_solve(ctx: Context, data, illums, mu0, kappa0=None, **params):
+    return ctx.ld_solve(data, illums, mu0, kappa0, **params)
 
 
 def qpat_tv_apply(ctx: Context, xbar, edge, beta, gamma, u):

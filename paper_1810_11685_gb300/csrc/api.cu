@@ -1002,7 +1002,7 @@ qpat_status qpat_vjp_kappa(qpat_ctx* c, int batch, const double* mu, const doubl
   else QCK(da_adjoint_rhs<double>(batch, N, 1.0, mu, (const double*)c->tw_hbar, c->d_rhs, c->stream));
   st = solve_da(c, batch, mu, c->d_rhs, c->d_tmp);
   if (st != QPAT_OK) return st;
-  QCK(da_kappa_grad(c->da, c->d_kappa, batch, phi0, c->d_tmp, illum, g, c->stream));
+  QCK(da_kappa_grad(c->da, c->d_kappa, batch, phi0, c->d_tmp, illum, 1.0, g, c->stream));
   return QPAT_OK;
 }
 
@@ -1022,25 +1022,41 @@ int optics_forward(qpat_ctx* c, const double* mu, unsigned illum, double* phi, v
   return QPAT_OK;
 }
 
-int optics_jvp(qpat_ctx* c, const double* mu, const double* phi0, const double* dmu, void* dh) {
+int optics_jvp2(qpat_ctx* c, const double* mu, const double* phi0, const double* dmu, const double* dkappa,
+                unsigned illum, void* dh) {
   const int N = (int)c->N;
-  QCK(da_hadamard(1, N, -c->da.hd, dmu, phi0, c->d_rhs, c->stream));
+  // right-hand side of A dphi: -h^d dmu o phi0 (delta-mu) + delta-b - delta-A phi0 (delta-kappa)
+  if (dkappa) QCK(da_kappa_source(c->da, c->d_kappa, 1, phi0, dkappa, illum, c->d_rhs, c->stream));
+  else QCK(cudaMemsetAsync(c->d_rhs, 0, (size_t)N * sizeof(double), c->stream));
+  if (dmu) {
+    QCK(da_hadamard(1, N, -c->da.hd, dmu, phi0, c->d_tmp, c->stream));
+    QCK(da_axpy(N, 1.0, c->d_tmp, c->d_rhs, c->stream));
+  }
   qpat_status st = solve_da(c, 1, mu, c->d_rhs, c->d_tmp);
   if (st != QPAT_OK) return st;
-  if (c->prec == QPAT_FP32) QCK(da_heating_T<float>(1, N, dmu, phi0, mu, c->d_tmp, (float*)dh, c->stream));
-  else QCK(da_heating_T<double>(1, N, dmu, phi0, mu, c->d_tmp, (double*)dh, c->stream));
+  // dh = dmu o phi0 + mu o dphi
+  const double* a1 = dmu ? dmu : mu;
+  const double* b1 = dmu ? phi0 : c->d_tmp;
+  const double* a2 = dmu ? mu : nullptr;
+  if (c->prec == QPAT_FP32) QCK(da_heating_T<float>(1, N, a1, b1, a2, c->d_tmp, (float*)dh, c->stream));
+  else QCK(da_heating_T<double>(1, N, a1, b1, a2, c->d_tmp, (double*)dh, c->stream));
   return QPAT_OK;
 }
 
-int optics_vjp(qpat_ctx* c, const double* mu, const double* phi0, const void* hbar, double* g) {
+int optics_vjp2(qpat_ctx* c, const double* mu, const double* phi0, const void* hbar, unsigned illum, double* g_mu,
+                double* g_kappa) {
   const int N = (int)c->N;
   const double sc = -c->da.hd;
+  // A H~ = -h^d mu o hbar; psi = A^-1 (mu o hbar) = -H~ / h^d
   if (c->prec == QPAT_FP32) QCK(da_adjoint_rhs<float>(1, N, sc, mu, (const float*)hbar, c->d_rhs, c->stream));
   else QCK(da_adjoint_rhs<double>(1, N, sc, mu, (const double*)hbar, c->d_rhs, c->stream));
   qpat_status st = solve_da(c, 1, mu, c->d_rhs, c->d_tmp);
   if (st != QPAT_OK) return st;
-  if (c->prec == QPAT_FP32) QCK(da_adjoint_out<float>(1, N, phi0, (const float*)hbar, c->d_tmp, g, c->stream));
-  else QCK(da_adjoint_out<double>(1, N, phi0, (const double*)hbar, c->d_tmp, g, c->stream));
+  if (g_mu) {
+    if (c->prec == QPAT_FP32) QCK(da_adjoint_out<float>(1, N, phi0, (const float*)hbar, c->d_tmp, g_mu, c->stream));
+    else QCK(da_adjoint_out<double>(1, N, phi0, (const double*)hbar, c->d_tmp, g_mu, c->stream));
+  }
+  if (g_kappa) QCK(da_kappa_grad(c->da, c->d_kappa, 1, phi0, c->d_tmp, illum, -1.0 / c->da.hd, g_kappa, c->stream));
   return QPAT_OK;
 }
 

@@ -626,7 +626,7 @@ __device__ __forceinline__ double dharmonic(double a, double b) { return 2.0 * b
 // -dh(k_c, k_nb) hf (phi_c - phi_nb)(psi_c - psi_nb) plus 2 q (I_s - gamma
 // phi_c) psi_c per boundary side.
 __global__ void kappa_deriv_kernel(DAArgs a, const double* kappa, const double* phi, const double* v, unsigned mask,
-                                   double* out, int mode) {
+                                   double* out, int mode, double scale) {
   const long long o = (long long)blockIdx.y * a.N;
   const double hf = (a.dim == 3) ? a.h : 1.0;
   const double hb = (a.dim == 3) ? a.h * a.h : a.h;
@@ -658,19 +658,29 @@ __global__ void kappa_deriv_kernel(DAArgs a, const double* kappa, const double* 
       const double I = ((mask >> s) & 1u) ? 1.0 : 0.0;
       acc += 2.0 * q * (I - a.gamma * pc) * vc;
     }
-    out[o + g] = acc;
+    out[o + g] = scale * acc;
   }
 }
 
 cudaError_t da_kappa_source(const DAArgs& a, const double* kappa, int batch, const double* phi, const double* dkappa,
                             unsigned mask, double* out, cudaStream_t s) {
-  kappa_deriv_kernel<<<dim3(128, batch), kThreads, 0, s>>>(a, kappa, phi, dkappa, mask, out, 0);
+  kappa_deriv_kernel<<<dim3(128, batch), kThreads, 0, s>>>(a, kappa, phi, dkappa, mask, out, 0, 1.0);
   return cudaGetLastError();
 }
 
 cudaError_t da_kappa_grad(const DAArgs& a, const double* kappa, int batch, const double* phi, const double* psi,
-                          unsigned mask, double* out, cudaStream_t s) {
-  kappa_deriv_kernel<<<dim3(128, batch), kThreads, 0, s>>>(a, kappa, phi, psi, mask, out, 1);
+                          unsigned mask, double scale, double* out, cudaStream_t s) {
+  kappa_deriv_kernel<<<dim3(128, batch), kThreads, 0, s>>>(a, kappa, phi, psi, mask, out, 1, scale);
+  return cudaGetLastError();
+}
+
+__global__ void axpy_kernel(long long n, double alpha, const double* x, double* y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] += alpha * x[t];
+}
+
+cudaError_t da_axpy(long long n, double alpha, const double* x, double* y, cudaStream_t s) {
+  axpy_kernel<<<512, kThreads, 0, s>>>(n, alpha, x, y);
   return cudaGetLastError();
 }
 

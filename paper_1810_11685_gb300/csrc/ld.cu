@@ -259,7 +259,8 @@ qpat_status qpat_tv_apply(qpat_ctx* c, const double* xbar, double edge, double b
 }
 
 qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void* data, double* mu,
-                          const qpat_ld_params* prm_in, qpat_ld_info* info, double* eps_hist, int* inner_hist) {
+                          double* kappa, const qpat_ld_params* prm_in, qpat_ld_info* info, double* eps_hist,
+                          int* inner_hist) {
   Ld L;
   L.c = c;
   if (!ctx_view(c, &L.v)) return QPAT_EINVAL;
@@ -283,23 +284,29 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   if (p.tv_max_iter <= 0) p.tv_max_iter = 20000;
   if (p.tv_tol <= 0) p.tv_tol = 1e-12;
 
-  const long long N = L.v.N;
+  // unknowns: [kappa-bar | mu-bar] (joint) or mu-bar, each block N cells
+  const bool joint = kappa != nullptr;
+  const int U = joint ? 2 : 1;
+  const long long N = L.v.N, NU = U * N;
   L.N = N;
   L.M = (long long)L.v.nt * L.v.ns;
   L.elt = L.v.prec == QPAT_FP32 ? sizeof(float) : sizeof(double);
   cudaStream_t s = L.v.stream;
   Work w;
   double* mu0 = w.get<double>(N);
-  double* xbar = w.get<double>(N);
-  double* phi = w.get<double>((size_t)nq * N);   // fluence of every illumination at mu^k
-  double* g = w.get<double>(N);
-  double* r = w.get<double>(N);
-  double* z = w.get<double>(N);
-  double* d = w.get<double>(N);
-  double* x = w.get<double>(N);
-  double* hd = w.get<double>(N);
+  double* kap0 = joint ? w.get<double>(N) : nullptr;
+  double* xbar = w.get<double>(NU);
+  double* phi = w.get<double>((size_t)nq * N);   // fluence of every illumination at the linearisation point
+  double* g = w.get<double>(NU);
+  double* r = w.get<double>(NU);
+  double* z = w.get<double>(NU);
+  double* d = w.get<double>(NU);
+  double* x = w.get<double>(NU);
+  double* hd = w.get<double>(NU);
   double* t1 = w.get<double>(N);
   double* t2 = w.get<double>(N);
+  double* t3 = w.get<double>(N);
+  double* t4 = w.get<double>(N);
   double* c_rr = w.get<double>(N);
   double* c_pp = w.get<double>(N);
   double* c_ap = w.get<double>(N);
@@ -312,38 +319,48 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   char* hb = w.get<char>((size_t)nq * N * L.elt);      // H_a^* of a series per q
   L.partial = w.get<double>((size_t)kPartials * 4);
   L.dout = w.get<double>(1);
-  L.tv = TVGrid{L.v.n0, L.v.n1, L.v.n2, p.tv_edge, p.beta, p.gamma, nullptr, nullptr, nullptr};
-  L.tv.wx = w.get<double>((size_t)L.v.n2 * L.v.n1 * (L.v.n0 - 1));
-  L.tv.wy = w.get<double>((size_t)L.v.n2 * (L.v.n1 - 1) * L.v.n0);
-  L.tv.wz = w.get<double>((size_t)(L.v.n2 > 1 ? L.v.n2 - 1 : 1) * L.v.n1 * L.v.n0);
+  TVGrid tvb[2];                                       // TV operator of each unknown block
+  for (int u = 0; u < U; ++u) {
+    tvb[u] = TVGrid{L.v.n0, L.v.n1, L.v.n2, p.tv_edge, p.beta, p.gamma, nullptr, nullptr, nullptr};
+    tvb[u].wx = w.get<double>((size_t)L.v.n2 * L.v.n1 * (L.v.n0 - 1));
+    tvb[u].wy = w.get<double>((size_t)L.v.n2 * (L.v.n1 - 1) * L.v.n0);
+    tvb[u].wz = w.get<double>((size_t)(L.v.n2 > 1 ? L.v.n2 - 1 : 1) * L.v.n1 * L.v.n0);
+  }
   if (w.err != cudaSuccess) return L.cuda(w.err, "qpat_ld_solve workspace");
 
   qpat_status st;
   if ((st = L.cuda(cudaMemcpyAsync(mu0, mu, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
     return st;
-  if ((st = L.cuda(cudaMemsetAsync(xbar, 0, N * sizeof(double), s), "memset")) != QPAT_OK) return st;
+  if (joint &&
+      (st = L.cuda(cudaMemcpyAsync(kap0, kappa, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
+    return st;
+  if ((st = L.cuda(cudaMemsetAsync(xbar, 0, NU * sizeof(double), s), "memset")) != QPAT_OK) return st;
   add_const_kernel<<<blocks_for(N), kT, 0, s>>>(N, 1.0, ones, 1);
 
   auto phi_q = [&](int q) { return phi + (size_t)q * N; };
   auto hq_q = [&](int q) -> void* { return hq + (size_t)q * N * L.elt; };
   auto hb_q = [&](int q) -> const void* { return hb + (size_t)q * N * L.elt; };
+  auto blk_mu = [&](double* v) { return v + (joint ? N : 0); };   // mu-bar block
+  auto blk_k = [&](double* v) { return v; };                        // kappa-bar block (joint)
 
-  // sum_q mu o J_o,q^*(hbar_q) into out; the acoustic halves of all
-  // illuminations run as one batch
+  // out = sum_q dX/dXbar o J_o,q^*(hbar_q), block by block (eq. gr / apj);
+  // the acoustic halves of all illuminations have run as one batch
   auto optical_adjoint_sum = [&](double* out) -> qpat_status {
     for (int q = 0; q < nq; ++q) {
-      qpat_status e = (qpat_status)optics_vjp(c, mu, phi_q(q), hb_q(q), t2);
+      qpat_status e = (qpat_status)optics_vjp2(c, mu, phi_q(q), hb_q(q), illum[q], t2, joint ? t3 : nullptr);
       if (e != QPAT_OK) return e;
-      hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu, t2, out, q > 0);
+      hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu, t2, blk_mu(out), q > 0);
+      if (joint) hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, kappa, t3, blk_k(out), q > 0);
     }
     return L.cuda(cudaGetLastError(), "optical adjoint");
   };
 
-  // H d = sum_q mu o J_q^*(J_q(mu o d)) into hd (eq. apj); t1, t2 scratch
-  auto gn_product = [&](const double* dd) -> qpat_status {
-    hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu, dd, t1, 0);
+  // H d = sum_q S J_q^* J_q S d into hd (eq. apj), S = dX/dXbar
+  auto gn_product = [&](double* dd) -> qpat_status {
+    hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu, blk_mu(dd), t1, 0);
+    if (joint) hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, kappa, blk_k(dd), t4, 0);
     for (int q = 0; q < nq; ++q) {
-      qpat_status e = (qpat_status)optics_jvp(c, mu, phi_q(q), t1, hq_q(q));
+      qpat_status e = (qpat_status)optics_jvp2(c, mu, phi_q(q), t1, joint ? t4 : nullptr, illum[q], hq_q(q));
       if (e != QPAT_OK) return e;
     }
     qpat_status e = qpat_acoustic_forward(c, nq, hq, jv);
@@ -353,12 +370,29 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
     return optical_adjoint_sum(hd);
   };
 
+  // z = M_gamma^-1 r, block by block (D is block diagonal, eq. dd)
+  auto precond = [&](double* rv, double* zv) -> qpat_status {
+    for (int u = 0; u < U; ++u) {
+      L.tv = tvb[u];
+      qpat_status e = L.tv_solve(rv + u * N, zv + u * N, c_rr, c_pp, c_ap, c_zz, c_dg, ones, p.tv_max_iter, p.tv_tol);
+      if (e != QPAT_OK) return e;
+    }
+    return QPAT_OK;
+  };
+  auto axpby_u = [&](double a, const double* xv, double b, double* yv) {
+    axpby_kernel<<<blocks_for(NU), kT, 0, s>>>(NU, a, xv, b, yv);
+  };
+
   std::vector<double> eps;
   int inner_total = 0;
   int k = 0;
   for (;;) {
-    // linearisation point mu^k = mu0 exp(Xbar^k): residuals, eps^k, fluences
-    exp_scale_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu0, xbar, mu);
+    // linearisation point X^k = X0 exp(Xbar^k): coefficients, residuals, eps^k, fluences
+    exp_scale_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu0, blk_mu(xbar), mu);
+    if (joint) {
+      exp_scale_kernel<<<blocks_for(N), kT, 0, s>>>(N, kap0, blk_k(xbar), kappa);
+      if ((st = qpat_set_kappa(c, kappa)) != QPAT_OK) return st;
+    }
     for (int q = 0; q < nq; ++q)
       if ((st = (qpat_status)optics_forward(c, mu, illum[q], phi_q(q), hq_q(q))) != QPAT_OK) return st;
     if ((st = qpat_acoustic_forward(c, nq, hq, res)) != QPAT_OK) return st;
@@ -374,40 +408,43 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
     if (k > 0 && !(1.0 - eps[k] / eps[k - 1] > p.tol_out)) break;
     if (k >= p.k_max) break;
 
-    // gradient g = sum_q mu o J_q^*(H_q - P_q) (eq. gr)
+    // gradient (eq. gr)
     if ((st = qpat_acoustic_adjoint(c, nq, res, hb)) != QPAT_OK) return st;
     L.products += nq;
     if ((st = optical_adjoint_sum(g)) != QPAT_OK) return st;
-    // M_gamma^k frozen at Xbar^k (lagged diffusivity)
-    if ((st = L.tv_weights(xbar)) != QPAT_OK) return st;
+    // M_gamma^k frozen at Xbar^k (lagged diffusivity), one per block
+    for (int u = 0; u < U; ++u) {
+      L.tv = tvb[u];
+      if ((st = L.tv_weights(xbar + u * N)) != QPAT_OK) return st;
+    }
 
     // Algorithm 4: PCG on H d = -g, preconditioner M_gamma, from 0
-    if ((st = L.cuda(cudaMemsetAsync(x, 0, N * sizeof(double), s), "memset")) != QPAT_OK) return st;
-    if ((st = L.cuda(cudaMemsetAsync(r, 0, N * sizeof(double), s), "memset")) != QPAT_OK) return st;
-    L.axpby(-1.0, g, 1.0, r);   // r_0 = -grad eps
-    if ((st = L.tv_solve(r, z, c_rr, c_pp, c_ap, c_zz, c_dg, ones, p.tv_max_iter, p.tv_tol)) != QPAT_OK) return st;
-    if ((st = L.cuda(cudaMemcpyAsync(d, z, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
+    if ((st = L.cuda(cudaMemsetAsync(x, 0, NU * sizeof(double), s), "memset")) != QPAT_OK) return st;
+    if ((st = L.cuda(cudaMemsetAsync(r, 0, NU * sizeof(double), s), "memset")) != QPAT_OK) return st;
+    axpby_u(-1.0, g, 1.0, r);   // r_0 = -grad eps
+    if ((st = precond(r, z)) != QPAT_OK) return st;
+    if ((st = L.cuda(cudaMemcpyAsync(d, z, NU * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
       return st;
     std::vector<double> rz(1);
-    if ((st = L.dot(r, z, N, &rz[0])) != QPAT_OK) return st;
+    if ((st = L.dot(r, z, NU, &rz[0])) != QPAT_OK) return st;
     int i = 0;
     while (i < p.i_max && rz[i] != 0.0 && (i < p.i_m || 1.0 - rz[i] / rz[i - p.i_m] > p.tol_in)) {
       if ((st = gn_product(d)) != QPAT_OK) return st;
       double dhd;
-      if ((st = L.dot(d, hd, N, &dhd)) != QPAT_OK) return st;
+      if ((st = L.dot(d, hd, NU, &dhd)) != QPAT_OK) return st;
       const double alpha = rz[i] / dhd;
-      L.axpby(alpha, d, 1.0, x);
-      L.axpby(-alpha, hd, 1.0, r);
-      if ((st = L.tv_solve(r, z, c_rr, c_pp, c_ap, c_zz, c_dg, ones, p.tv_max_iter, p.tv_tol)) != QPAT_OK) return st;
+      axpby_u(alpha, d, 1.0, x);
+      axpby_u(-alpha, hd, 1.0, r);
+      if ((st = precond(r, z)) != QPAT_OK) return st;
       double rzn;
-      if ((st = L.dot(r, z, N, &rzn)) != QPAT_OK) return st;
+      if ((st = L.dot(r, z, NU, &rzn)) != QPAT_OK) return st;
       rz.push_back(rzn);
-      L.axpby(1.0, z, rz[i + 1] / rz[i], d);
+      axpby_u(1.0, z, rz[i + 1] / rz[i], d);
       ++i;
     }
     if (inner_hist) inner_hist[k] = i;
     inner_total += i;
-    L.axpby(1.0, x, 1.0, xbar);   // Xbar^{k+1} = Xbar^k + d^k (alpha^k = 1)
+    axpby_u(1.0, x, 1.0, xbar);   // Xbar^{k+1} = Xbar^k + d^k (alpha^k = 1)
     ++k;
   }
   if ((st = L.cuda(cudaStreamSynchronize(s), "qpat_ld_solve sync")) != QPAT_OK) return st;

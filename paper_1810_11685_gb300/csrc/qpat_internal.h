@@ -214,7 +214,9 @@ cudaError_t da_kappa_source(const DAArgs& a, const double* kappa, int batch, con
 // Its transpose read against psi_b: the kappa gradient <delta-b - delta-A phi,
 // psi> per cell, [B][N].
 cudaError_t da_kappa_grad(const DAArgs& a, const double* kappa, int batch, const double* phi, const double* psi,
-                          unsigned mask, double* out, cudaStream_t s);
+                          unsigned mask, double scale, double* out, cudaStream_t s);
+// y += alpha x
+cudaError_t da_axpy(long long n, double alpha, const double* x, double* y, cudaStream_t s);
 // out_b = alpha * (u_b o v_b)   (all [B][N] FP64)
 cudaError_t da_hadamard(int batch, int N, double alpha, const double* u, const double* v, double* out,
                         cudaStream_t s);
@@ -250,11 +252,13 @@ bool ctx_view(const struct ::qpat_ctx* c, CtxView* v);
 int ctx_fail(struct ::qpat_ctx* c, int st, const char* msg);
 // Optical halves of the composite maps for one problem (return qpat_status):
 // optics_forward: phi = fluence of mu, h = mu o phi (prec [N]);
-// optics_jvp: dh = dmu o phi0 + mu o dphi, A dphi = -h^d dmu o phi0;
-// optics_vjp: g = phi0 o (hbar + H~), A H~ = -h^d mu o hbar (hbar prec [N]).
 int optics_forward(struct ::qpat_ctx* c, const double* mu, unsigned illum, double* phi, void* h);
-int optics_jvp(struct ::qpat_ctx* c, const double* mu, const double* phi0, const double* dmu, void* dh);
-int optics_vjp(struct ::qpat_ctx* c, const double* mu, const double* phi0, const void* hbar, double* g);
+// dh = J_o (dmu, dkappa): either may be NULL (Lemma 1, eq. fr)
+int optics_jvp2(struct ::qpat_ctx* c, const double* mu, const double* phi0, const double* dmu,
+                const double* dkappa, unsigned illum, void* dh);
+// g_mu, g_kappa = J_o^*(hbar) in mu and in kappa: either may be NULL (eq. opt_adjoint)
+int optics_vjp2(struct ::qpat_ctx* c, const double* mu, const double* phi0, const void* hbar, unsigned illum,
+                double* g_mu, double* g_kappa);
 // CTAs per problem of the conjugate-gradient and multigrid kernels (eight per SM)
 constexpr int kPCGBlocks = 1216;
 

@@ -109,3 +109,52 @@ def test_ld_stops_on_tol_out_and_rejects_bad_masks():
     small = context_from_workload(w, precision="fp64", max_batch=1)
     with pytest.raises(QpatError):
         small.ld_solve(data, ILLUMS, torch.as_tensor(mu0, device="cuda"), k_max=1)
+
+
+JOINT_ILLUMS = (1, 4, 2, 8)
+
+
+def _run_joint(prec, k_max=2, i_max=4, i_m=4, gamma=1e-2):
+    from paper_1810_11685_gb300.binding import context_from_workload
+    w = phantoms.small(n=8, pml=4, nt=30, n_sensors=12, seed=3)
+    S = acoustic.setup_from_workload(w)
+    rng = np.random.default_rng(3)
+    kappa_true = phantoms.optical_diffusion(w) * np.exp(0.3 * rng.standard_normal(w.interior_shape))
+    mu_true = phantoms.optical_absorption(w)
+    P = np.stack([acoustic.forward(S, optics.heating(mu_true, kappa_true, S.dx, q)) for q in JOINT_ILLUMS])
+    mu0 = np.full(w.interior_shape, w.mu_bg)
+    kappa0 = phantoms.optical_diffusion(w)
+    edge = w.dx / phantoms.MM
+    prm = ld.LDParams(k_max=k_max, i_max=i_max, i_m=i_m, tol_in=0.0, tol_out=0.0, gamma=gamma, edge=edge)
+    (k_ref, m_ref), _, eps_ref, inner_ref = ld.ld_newton(ld.JointProblem(S, JOINT_ILLUMS, P, mu0, kappa0), prm)
+    ctx = context_from_workload(w, precision=prec, max_batch=len(JOINT_ILLUMS))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    (kap, mu), eps, inner, info = ctx.ld_solve(torch.as_tensor(P, dtype=dt, device="cuda"), JOINT_ILLUMS,
+                                               torch.as_tensor(mu0, device="cuda"),
+                                               torch.as_tensor(kappa0, device="cuda"), k_max=k_max,
+                                               i_max=i_max, i_m=i_m, tol_in=0.0, tol_out=0.0, gamma=gamma,
+                                               tv_edge=edge)
+    return (kap.cpu().numpy(), mu.cpu().numpy()), eps, inner, info, (k_ref, m_ref), eps_ref, inner_ref, \
+        (kappa0, mu0), ctx
+
+
+def test_joint_ld_fp64_matches_oracle():
+    (kap, mu), eps, inner, info, (k_ref, m_ref), eps_ref, inner_ref, (kappa0, mu0), ctx = _run_joint("fp64")
+    assert inner == inner_ref == [4, 4]
+    assert eps_ref[2] < eps_ref[1] < eps_ref[0]
+    # the same bounds as the mu-only reconstruction: the kappa derivatives
+    # add one stencil kernel per product and no iterative step
+    assert np.allclose(eps, eps_ref, rtol=1e-9, atol=0)
+    assert np.linalg.norm(mu - m_ref) <= 1e-8 * np.linalg.norm(m_ref - mu0)
+    assert np.linalg.norm(kap - k_ref) <= 1e-8 * np.linalg.norm(k_ref - kappa0)
+    # the context holds the reconstructed kappa: its fluence is the oracle's at (kappa, mu)
+    phi = ctx.da_solve(torch.as_tensor(mu, device="cuda"), 1)[0].cpu().numpy()
+    assert np.linalg.norm(phi - optics.fluence(mu, kap, ctx.dx, 1)) <= 1e-9 * np.linalg.norm(phi)
+
+
+def test_joint_ld_fp32_tracks_oracle():
+    (kap, mu), eps, inner, info, (k_ref, m_ref), eps_ref, inner_ref, (kappa0, mu0), _ = _run_joint("fp32")
+    assert inner == inner_ref
+    assert np.allclose(eps, eps_ref, rtol=1e-3, atol=0)
+    assert np.linalg.norm(mu - m_ref) <= 1e-2 * np.linalg.norm(m_ref - mu0)
+    assert np.linalg.norm(kap - k_ref) <= 1e-2 * np.linalg.norm(k_ref - kappa0)
