@@ -499,6 +499,7 @@ def run_ld(args):
                                    f"k_max=3, i_max=i_m=4", "nt": nt},
             "seconds_per_solve": t, "outer": info["outer"], "inner": inner, "products": info["products"],
             "tv_cg_iterations": info["tv_iters"], "seconds_per_outer": t / max(1, info["outer"]),
+            "seconds_by_phase": info["seconds"],
             "eps": eps,
             "rel_error": {"mu_initial": rel(mu0, mu_true), "mu_final": rel(mu, mu_true),
                           "kappa_initial": rel(kappa0, kappa_true), "kappa_final": rel(kappa, kappa_true)}}

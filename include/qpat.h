@@ -287,6 +287,8 @@ typedef struct {
   long long products;     /* applications of J_q or J_q^* (one propagation each) */
   double eps_first;       /* eps at mu0 */
   double eps_last;        /* eps at the returned mu */
+  double seconds[3];      /* host wall time in the acoustic propagations, the optical
+                             (diffusion) halves, and the M_gamma solves */
 } qpat_ld_info;
 
 qpat_status qpat_ld_solve(qpat_ctx* ctx, int nq, const unsigned* illum, const void* data, double* mu,

@@ -57,7 +57,8 @@ class qpat_ld_params(ctypes.Structure):
 
 class qpat_ld_info(ctypes.Structure):
     _fields_ = [("outer", ctypes.c_int), ("inner_total", ctypes.c_int), ("tv_iters", ctypes.c_longlong),
-                ("products", ctypes.c_longlong), ("eps_first", ctypes.c_double), ("eps_last", ctypes.c_double)]
+                ("products", ctypes.c_longlong), ("eps_first", ctypes.c_double), ("eps_last", ctypes.c_double),
+                ("seconds", ctypes.c_double * 3)]
 
 
 _lib = None
@@ -369,6 +370,7 @@ class Context:
                                                   ctypes.byref(prm), ctypes.byref(info), eps, inner))
         k = info.outer
         out = {f: getattr(info, f) for f, _ in qpat_ld_info._fields_}
+        out["seconds"] = {"acoustic": info.seconds[0], "optical": info.seconds[1], "tv": info.seconds[2]}
         coeffs = mu[0] if kappa is None else (kappa[0], mu[0])
         return coeffs, list(eps)[:k + 1], list(inner)[:k], out
 

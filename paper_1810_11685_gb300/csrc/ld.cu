@@ -13,6 +13,7 @@
 // and 5.
 #include <math.h>
 
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -65,6 +66,37 @@ __global__ void add_const_kernel(long long n, double a, double* y, int set) {
     y[i] = set ? a : y[i] + a;
 }
 
+// Conjugate-gradient steps of the M_gamma solve with the Krylov scalars in
+// device memory: sc[0] = r^T z, sc[1] = p^T A p, sc[2] = the new r^T z,
+// sc[3] = sum of the preconditioned residual (for the mean removal).  A zero
+// denominator (an exactly converged iteration) gives a zero step.
+__global__ void cg_update_kernel(long long n, const double* sc, const double* pp, const double* ap, double* z,
+                                 double* rr, double* zz, const double* dg) {
+  const double alpha = sc[1] != 0.0 ? sc[0] / sc[1] : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    z[i] += alpha * pp[i];
+    const double r = rr[i] - alpha * ap[i];
+    rr[i] = r;
+    zz[i] = r / dg[i];
+  }
+}
+
+__global__ void cg_demean_kernel(long long n, const double* sc, double* zz) {
+  const double m = sc[3] / (double)n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    zz[i] -= m;
+}
+
+__global__ void cg_direction_kernel(long long n, const double* sc, const double* zz, double* pp) {
+  const double beta = sc[0] != 0.0 ? sc[2] / sc[0] : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    pp[i] = zz[i] + beta * pp[i];
+}
+
+__global__ void cg_rotate_kernel(double* sc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc[0] = sc[2];
+}
+
 struct TVGrid {
   int n0, n1, n2;
   double edge, beta, gamma;
@@ -114,6 +146,108 @@ __global__ void tv_apply_kernel(TVGrid t, const double* u, double* out, int diag
   }
 }
 
+// ---- the whole M_gamma solve in one CTA (grids up to kOneCtaMax cells) -------
+constexpr int kCgThreads = 1024;
+constexpr long long kOneCtaMax = 1LL << 18;
+
+// Deterministic block sum (fixed tree order) of one value per thread; every
+// thread gets the result.
+__device__ __forceinline__ double cta_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[32] = v;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+__device__ __forceinline__ double tv_row(const TVGrid& t, const double* u, long long c, int diag_only) {
+  const long long sxy = (long long)t.n0 * t.n1;
+  const int i = (int)(c % t.n0);
+  const int j = (int)((c / t.n0) % t.n1);
+  const int k = (int)(c / sxy);
+  const double uc = diag_only ? 1.0 : u[c];
+  double acc = t.gamma * uc, w;
+  if (i > 0) { w = t.wx[((long long)k * t.n1 + j) * (t.n0 - 1) + i - 1]; acc += w * (uc - (diag_only ? 0.0 : u[c - 1])); }
+  if (i + 1 < t.n0) { w = t.wx[((long long)k * t.n1 + j) * (t.n0 - 1) + i]; acc += w * (uc - (diag_only ? 0.0 : u[c + 1])); }
+  if (j > 0) { w = t.wy[((long long)k * (t.n1 - 1) + j - 1) * t.n0 + i]; acc += w * (uc - (diag_only ? 0.0 : u[c - t.n0])); }
+  if (j + 1 < t.n1) { w = t.wy[((long long)k * (t.n1 - 1) + j) * t.n0 + i]; acc += w * (uc - (diag_only ? 0.0 : u[c + t.n0])); }
+  if (k > 0) { w = t.wz[((long long)(k - 1) * t.n1 + j) * t.n0 + i]; acc += w * (uc - (diag_only ? 0.0 : u[c - sxy])); }
+  if (k + 1 < t.n2) { w = t.wz[((long long)k * t.n1 + j) * t.n0 + i]; acc += w * (uc - (diag_only ? 0.0 : u[c + sxy])); }
+  return acc;
+}
+
+// z = M_gamma^-1 r: exact along constants, conjugate gradients on the
+// mean-free part with the diagonal preconditioner followed by removal of the
+// mean (the same iteration as the multi-kernel path), in one CTA; stats[0]
+// receives the number of iterations.
+__global__ void __launch_bounds__(kCgThreads) tv_cg_kernel(TVGrid t, const double* r, double* z, double* rr,
+                                                            double* pp, double* ap, double* zz, double* dg,
+                                                            int max_iter, double tol, int* stats) {
+  __shared__ double sh[33];
+  const long long N = (long long)t.n0 * t.n1 * t.n2;
+  const int T = blockDim.x, tid = threadIdx.x;
+  double s = 0.0;
+  for (long long c = tid; c < N; c += T) s += r[c];
+  const double m_r = cta_sum(s, sh) / (double)N;
+  s = 0.0;
+  for (long long c = tid; c < N; c += T) {
+    dg[c] = tv_row(t, nullptr, c, 1);
+    const double v = r[c] - m_r;
+    rr[c] = v;
+    zz[c] = v / dg[c];
+    z[c] = 0.0;
+    s += zz[c];
+  }
+  const double m0 = cta_sum(s, sh) / (double)N;
+  s = 0.0;
+  for (long long c = tid; c < N; c += T) {
+    zz[c] -= m0;
+    pp[c] = zz[c];
+    s += rr[c] * zz[c];
+  }
+  const double rz0 = cta_sum(s, sh);
+  double rz = rz0;
+  int it = 0;
+  for (; rz0 > 0.0 && it < max_iter && sqrt(fabs(rz) / rz0) > tol; ++it) {
+    s = 0.0;
+    for (long long c = tid; c < N; c += T) {
+      const double a = tv_row(t, pp, c, 0);
+      ap[c] = a;
+      s += pp[c] * a;
+    }
+    const double pap = cta_sum(s, sh);
+    const double alpha = pap != 0.0 ? rz / pap : 0.0;
+    s = 0.0;
+    for (long long c = tid; c < N; c += T) {
+      z[c] += alpha * pp[c];
+      const double v = rr[c] - alpha * ap[c];
+      rr[c] = v;
+      zz[c] = v / dg[c];
+      s += zz[c];
+    }
+    const double m = cta_sum(s, sh) / (double)N;
+    s = 0.0;
+    for (long long c = tid; c < N; c += T) {
+      zz[c] -= m;
+      s += rr[c] * zz[c];
+    }
+    const double rzn = cta_sum(s, sh);
+    const double beta = rz != 0.0 ? rzn / rz : 0.0;
+    for (long long c = tid; c < N; c += T) pp[c] = zz[c] + beta * pp[c];
+    rz = rzn;
+    __syncthreads();
+  }
+  for (long long c = tid; c < N; c += T) z[c] += m_r / t.gamma;
+  if (tid == 0) stats[0] = it;
+}
+
 // Device workspace of one reconstruction, freed on every exit path.
 struct Work {
   std::vector<void*> ptrs;
@@ -131,8 +265,24 @@ struct Work {
   }
 };
 
+// Host wall time of a phase, the stream drained at both ends.
+struct PhaseTimer {
+  double* acc;
+  cudaStream_t s;
+  std::chrono::steady_clock::time_point t0;
+  PhaseTimer(double* a, cudaStream_t st) : acc(a), s(st) {
+    cudaStreamSynchronize(s);
+    t0 = std::chrono::steady_clock::now();
+  }
+  ~PhaseTimer() {
+    cudaStreamSynchronize(s);
+    *acc += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
 struct Ld {
   qpat_ctx* c;
+  double sec[3] = {0, 0, 0};    // acoustic, optical, M_gamma solves
   CtxView v;
   long long N = 0, M = 0;       // interior cells, samples per series
   size_t elt = 8;
@@ -182,6 +332,12 @@ struct Ld {
     return st;
   }
 
+  // device Krylov scalars of the M_gamma solves and a pinned host copy
+  double* sc = nullptr;
+  double* hsc = nullptr;
+  int* cg_stats = nullptr;
+  int* hstats = nullptr;
+
   // M_gamma z = r.  M annihilates constants (M 1 = 0), so M_gamma 1 = gamma 1
   // and the mean-free part is invariant: z = (mean r / gamma) 1 + y with
   // M_gamma y = r - mean(r) 1 solved by conjugate gradients on mean-free
@@ -191,6 +347,15 @@ struct Ld {
   // rr, pp, ap, zz, dg: work vectors [N]; y accumulates in z.
   qpat_status tv_solve(const double* r, double* z, double* rr, double* pp, double* ap, double* zz, double* dg,
                        const double* ones, int max_iter, double tol) {
+    if (N <= kOneCtaMax) {
+      // small grids: the whole solve in one CTA, without launches per iteration
+      tv_cg_kernel<<<1, kCgThreads, 0, v.stream>>>(tv, r, z, rr, pp, ap, zz, dg, max_iter, tol, cg_stats);
+      qpat_status e = cuda(cudaMemcpyAsync(hstats, cg_stats, sizeof(int), cudaMemcpyDeviceToHost, v.stream), "copy");
+      if (e != QPAT_OK) return e;
+      if ((e = cuda(cudaStreamSynchronize(v.stream), "tv_solve sync")) != QPAT_OK) return e;
+      tv_iters += *hstats;
+      return QPAT_OK;
+    }
     tv_apply_kernel<<<blocks_for(N), kT, 0, v.stream>>>(tv, nullptr, dg, 1);
     qpat_status st = cuda(cudaMemsetAsync(z, 0, N * sizeof(double), v.stream), "memset");
     if (st != QPAT_OK) return st;
@@ -208,23 +373,30 @@ struct Ld {
     if ((st = precondition()) != QPAT_OK) return st;
     st = cuda(cudaMemcpyAsync(pp, zz, N * sizeof(double), cudaMemcpyDeviceToDevice, v.stream), "copy");
     if (st != QPAT_OK) return st;
-    double rz0, rz;
+    double rz0;
     if ((st = dot(rr, zz, N, &rz0)) != QPAT_OK) return st;
-    rz = rz0;
-    for (int it = 0; rz0 > 0.0 && it < max_iter; ++it) {
-      if (sqrt(rz / rz0) <= tol) break;
-      tv_apply(pp, ap);
-      double pap;
-      if ((st = dot(pp, ap, N, &pap)) != QPAT_OK) return st;
-      const double alpha = rz / pap;
-      axpby(alpha, pp, 1.0, z);
-      axpby(-alpha, ap, 1.0, rr);
-      if ((st = precondition()) != QPAT_OK) return st;
-      double rzn;
-      if ((st = dot(rr, zz, N, &rzn)) != QPAT_OK) return st;
-      axpby(1.0, zz, rzn / rz, pp);
-      rz = rzn;
-      ++tv_iters;
+    // the iterations run on the device with their scalars in sc; the host
+    // reads r^T z every kChunk iterations to test convergence
+    constexpr int kChunk = 16;
+    if ((st = cuda(cudaMemcpyAsync(sc, &rz0, sizeof(double), cudaMemcpyHostToDevice, v.stream), "copy")) != QPAT_OK)
+      return st;
+    double rz = rz0;
+    for (int it = 0; rz0 > 0.0 && it < max_iter && sqrt(fabs(rz) / rz0) > tol;) {
+      for (int k = 0; k < kChunk && it < max_iter; ++k, ++it) {
+        tv_apply(pp, ap);
+        dot_compensated<double>(1, N, pp, ap, partial, sc + 1, v.stream);
+        cg_update_kernel<<<blocks_for(N), kT, 0, v.stream>>>(N, sc, pp, ap, z, rr, zz, dg);
+        dot_compensated<double>(1, N, zz, ones, partial, sc + 3, v.stream);
+        cg_demean_kernel<<<blocks_for(N), kT, 0, v.stream>>>(N, sc, zz);
+        dot_compensated<double>(1, N, rr, zz, partial, sc + 2, v.stream);
+        cg_direction_kernel<<<blocks_for(N), kT, 0, v.stream>>>(N, sc, zz, pp);
+        cg_rotate_kernel<<<1, 32, 0, v.stream>>>(sc);
+        ++tv_iters;
+      }
+      if ((st = cuda(cudaMemcpyAsync(hsc, sc, sizeof(double), cudaMemcpyDeviceToHost, v.stream), "copy")) != QPAT_OK)
+        return st;
+      if ((st = cuda(cudaStreamSynchronize(v.stream), "tv_solve sync")) != QPAT_OK) return st;
+      rz = *hsc;
     }
     // the cap bounds the work; the result is then the last iterate
     add_const_kernel<<<blocks_for(N), kT, 0, v.stream>>>(N, m_r / tv.gamma, z, 0);
@@ -319,6 +491,8 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   char* hb = w.get<char>((size_t)nq * N * L.elt);      // H_a^* of a series per q
   L.partial = w.get<double>((size_t)kPartials * 4);
   L.dout = w.get<double>(1);
+  L.sc = w.get<double>(8);
+  L.cg_stats = w.get<int>(4);
   TVGrid tvb[2];                                       // TV operator of each unknown block
   for (int u = 0; u < U; ++u) {
     tvb[u] = TVGrid{L.v.n0, L.v.n1, L.v.n2, p.tv_edge, p.beta, p.gamma, nullptr, nullptr, nullptr};
@@ -327,8 +501,16 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
     tvb[u].wz = w.get<double>((size_t)(L.v.n2 > 1 ? L.v.n2 - 1 : 1) * L.v.n1 * L.v.n0);
   }
   if (w.err != cudaSuccess) return L.cuda(w.err, "qpat_ld_solve workspace");
-
+  struct PinnedScalars {
+    double* p = nullptr;
+    ~PinnedScalars() {
+      if (p) cudaFreeHost(p);
+    }
+  } pinned;
   qpat_status st;
+  if ((st = L.cuda(cudaMallocHost(&pinned.p, 8 * sizeof(double)), "pinned scalars")) != QPAT_OK) return st;
+  L.hsc = pinned.p;
+  L.hstats = reinterpret_cast<int*>(pinned.p + 4);
   if ((st = L.cuda(cudaMemcpyAsync(mu0, mu, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
     return st;
   if (joint &&
@@ -346,6 +528,7 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   // out = sum_q dX/dXbar o J_o,q^*(hbar_q), block by block (eq. gr / apj);
   // the acoustic halves of all illuminations have run as one batch
   auto optical_adjoint_sum = [&](double* out) -> qpat_status {
+    PhaseTimer pt(&L.sec[1], s);
     for (int q = 0; q < nq; ++q) {
       qpat_status e = (qpat_status)optics_vjp2(c, mu, phi_q(q), hb_q(q), illum[q], t2, joint ? t3 : nullptr);
       if (e != QPAT_OK) return e;
@@ -359,19 +542,26 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   auto gn_product = [&](double* dd) -> qpat_status {
     hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, mu, blk_mu(dd), t1, 0);
     if (joint) hadamard_kernel<<<blocks_for(N), kT, 0, s>>>(N, kappa, blk_k(dd), t4, 0);
-    for (int q = 0; q < nq; ++q) {
-      qpat_status e = (qpat_status)optics_jvp2(c, mu, phi_q(q), t1, joint ? t4 : nullptr, illum[q], hq_q(q));
-      if (e != QPAT_OK) return e;
+    {
+      PhaseTimer pt(&L.sec[1], s);
+      for (int q = 0; q < nq; ++q) {
+        qpat_status e = (qpat_status)optics_jvp2(c, mu, phi_q(q), t1, joint ? t4 : nullptr, illum[q], hq_q(q));
+        if (e != QPAT_OK) return e;
+      }
     }
-    qpat_status e = qpat_acoustic_forward(c, nq, hq, jv);
-    if (e != QPAT_OK) return e;
-    if ((e = qpat_acoustic_adjoint(c, nq, jv, hb)) != QPAT_OK) return e;
+    qpat_status e;
+    {
+      PhaseTimer pt(&L.sec[0], s);
+      if ((e = qpat_acoustic_forward(c, nq, hq, jv)) != QPAT_OK) return e;
+      if ((e = qpat_acoustic_adjoint(c, nq, jv, hb)) != QPAT_OK) return e;
+    }
     L.products += 2 * nq;
     return optical_adjoint_sum(hd);
   };
 
   // z = M_gamma^-1 r, block by block (D is block diagonal, eq. dd)
   auto precond = [&](double* rv, double* zv) -> qpat_status {
+    PhaseTimer pt(&L.sec[2], s);
     for (int u = 0; u < U; ++u) {
       L.tv = tvb[u];
       qpat_status e = L.tv_solve(rv + u * N, zv + u * N, c_rr, c_pp, c_ap, c_zz, c_dg, ones, p.tv_max_iter, p.tv_tol);
@@ -393,9 +583,15 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
       exp_scale_kernel<<<blocks_for(N), kT, 0, s>>>(N, kap0, blk_k(xbar), kappa);
       if ((st = qpat_set_kappa(c, kappa)) != QPAT_OK) return st;
     }
-    for (int q = 0; q < nq; ++q)
-      if ((st = (qpat_status)optics_forward(c, mu, illum[q], phi_q(q), hq_q(q))) != QPAT_OK) return st;
-    if ((st = qpat_acoustic_forward(c, nq, hq, res)) != QPAT_OK) return st;
+    {
+      PhaseTimer pt(&L.sec[1], s);
+      for (int q = 0; q < nq; ++q)
+        if ((st = (qpat_status)optics_forward(c, mu, illum[q], phi_q(q), hq_q(q))) != QPAT_OK) return st;
+    }
+    {
+      PhaseTimer pt(&L.sec[0], s);
+      if ((st = qpat_acoustic_forward(c, nq, hq, res)) != QPAT_OK) return st;
+    }
     L.products += nq;
     const long long MS = (long long)nq * L.M;
     if (L.v.prec == QPAT_FP32)
@@ -409,7 +605,10 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
     if (k >= p.k_max) break;
 
     // gradient (eq. gr)
-    if ((st = qpat_acoustic_adjoint(c, nq, res, hb)) != QPAT_OK) return st;
+    {
+      PhaseTimer pt(&L.sec[0], s);
+      if ((st = qpat_acoustic_adjoint(c, nq, res, hb)) != QPAT_OK) return st;
+    }
     L.products += nq;
     if ((st = optical_adjoint_sum(g)) != QPAT_OK) return st;
     // M_gamma^k frozen at Xbar^k (lagged diffusivity), one per block
@@ -457,6 +656,7 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
     info->products = L.products;
     info->eps_first = eps.front();
     info->eps_last = eps.back();
+    for (int j = 0; j < 3; ++j) info->seconds[j] = L.sec[j];
   }
   return QPAT_OK;
 }
