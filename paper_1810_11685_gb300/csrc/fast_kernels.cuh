@@ -47,11 +47,11 @@ struct SGeom {
   static constexpr int RP = (192 / TPT) > 0 ? (192 / TPT) : 1;   // row pairs per CTA
   // columns per CTA: 8 adjacent columns make each warp access 64 contiguous
   // bytes per row (measured on GB300: 576^2 batch 8 1.92e10 against 1.82e10
-  // cell-steps/s with 4 columns; 288^2..576^2 jvp mix 1.9e10 against 1.7e10)
-#ifndef QPAT_COL_CBW
-#define QPAT_COL_CBW 8
-#endif
-  static constexpr int CBW = QPAT_COL_CBW;
+  // cell-steps/s with 4 columns; 288^2..576^2 jvp mix 1.9e10 against 1.7e10).
+  // Fewer where 8 columns' two-slot double buffers would not fit in the 227
+  // KB of shared memory a CTA may use (extents 1024, 1080: 4 columns).
+  static constexpr int col_bytes(int cbw) { return (L + cbw * (4 * SL + 16)) * 8; }
+  static constexpr int CBW = col_bytes(8) <= 227 * 1024 ? 8 : col_bytes(4) <= 227 * 1024 ? 4 : 2;
 };
 
 template <typename T, int L, int PH>
@@ -509,6 +509,8 @@ constexpr size_t col_fast_smem() {
 
 template <typename T, int L, int PH>
 void set_row_fast_attr() {
+  static_assert(row_fast_st_smem<T, L, PH>() <= 227 * 1024 && row_fast_smem<T, L, PH>() <= 227 * 1024,
+                "row pass shared memory above the 227 KB a CTA may use");
   if constexpr (row_staged<L>())
     cudaFuncSetAttribute(row_fast_st<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)row_fast_st_smem<T, L, PH>());
@@ -518,6 +520,7 @@ void set_row_fast_attr() {
 }
 template <typename T, int L, int PH>
 void set_col_fast_attr() {
+  static_assert(col_fast_smem<T, L, PH>() <= 227 * 1024, "column pass shared memory above the 227 KB a CTA may use");
   cudaFuncSetAttribute(col_fast<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_fast_smem<T, L, PH>());
 }
 
