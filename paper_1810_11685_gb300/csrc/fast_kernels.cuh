@@ -267,8 +267,14 @@ __host__ __device__ constexpr int row_st_offset() {
   return (kRowStTwSmem(L) + rp_st<L>() * (kRowStOneBuf ? 1 : 2) * NSX * SGeom<L>::SL + 1) & ~1;
 }
 
+// At least six resident CTAs per SM (registers capped to fit; measured at
+// 576^2 batch 12, Nt 600: 2.145e10 with no bound, 2.186e10 with 6, 2.148e10
+// with 7, 2.163e10 with 8 cell-steps/s).
+#ifndef QPAT_ROWST_MINB
+#define QPAT_ROWST_MINB 6
+#endif
 template <typename T, int L, int PH>
-__global__ void __launch_bounds__(rp_st<L>() * SGeom<L>::TPT)
+__global__ void __launch_bounds__(rp_st<L>() * SGeom<L>::TPT, QPAT_ROWST_MINB)
 row_fast_st(const PropArgs<T> a) {
   constexpr int ph = PH, KIN = row_kin(PH), KOUT = row_kout(PH);
   constexpr int NSX = (KIN > KOUT ? KIN : KOUT), NF = row_nfields(PH);
