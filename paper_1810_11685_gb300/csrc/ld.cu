@@ -17,10 +17,13 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "qpat.h"
 #include "qpat_internal.h"
 
 using namespace qpat;
+namespace cgrp = cooperative_groups;
 
 namespace {
 
@@ -248,6 +251,107 @@ __global__ void __launch_bounds__(kCgThreads) tv_cg_kernel(TVGrid t, const doubl
   if (tid == 0) stats[0] = it;
 }
 
+// ---- the whole M_gamma solve in one cooperative grid --------------------------
+constexpr int kCoopThreads = 256;
+constexpr int kCoopMaxBlocks = 4096;
+
+// Deterministic sum over the grid: block sums in a fixed tree order, written
+// to one of two alternating partial arrays (a block may write the next sum's
+// partial only after every block has read this one, which the grid barrier of
+// the next sum guarantees), then every block adds all partials in index order,
+// so all threads of all blocks hold the same value.
+__device__ __forceinline__ double grid_sum(double v, double* sh, double* part, int& flip, cgrp::grid_group& g) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double* pa = part + flip * kCoopMaxBlocks;
+  flip ^= 1;
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += sh[w];
+    pa[blockIdx.x] = b;
+  }
+  g.sync();
+  if (wid == 0) {
+    double t = 0.0;
+    for (int i = lane; i < (int)gridDim.x; i += 32) t += pa[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// The iteration of tv_cg_kernel spread over a cooperative grid: four grid
+// barriers per iteration (three sums, and the new search direction before the
+// next stencil reads it).
+__global__ void __launch_bounds__(kCoopThreads) tv_cg_coop_kernel(TVGrid t, const double* r, double* z, double* rr,
+                                                                   double* pp, double* ap, double* zz, double* dg,
+                                                                   double* part, int max_iter, double tol,
+                                                                   int* stats) {
+  cgrp::grid_group g = cgrp::this_grid();
+  __shared__ double sh[33];
+  int flip = 0;
+  const long long N = (long long)t.n0 * t.n1 * t.n2;
+  const long long G = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0.0;
+  for (long long c = t0; c < N; c += G) s += r[c];
+  const double m_r = grid_sum(s, sh, part, flip, g) / (double)N;
+  s = 0.0;
+  for (long long c = t0; c < N; c += G) {
+    dg[c] = tv_row(t, nullptr, c, 1);
+    const double v = r[c] - m_r;
+    rr[c] = v;
+    zz[c] = v / dg[c];
+    z[c] = 0.0;
+    s += zz[c];
+  }
+  const double m0 = grid_sum(s, sh, part, flip, g) / (double)N;
+  s = 0.0;
+  for (long long c = t0; c < N; c += G) {
+    zz[c] -= m0;
+    pp[c] = zz[c];
+    s += rr[c] * zz[c];
+  }
+  const double rz0 = grid_sum(s, sh, part, flip, g);
+  double rz = rz0;
+  int it = 0;
+  for (; rz0 > 0.0 && it < max_iter && sqrt(fabs(rz) / rz0) > tol; ++it) {
+    s = 0.0;
+    for (long long c = t0; c < N; c += G) {
+      const double a = tv_row(t, pp, c, 0);
+      ap[c] = a;
+      s += pp[c] * a;
+    }
+    const double pap = grid_sum(s, sh, part, flip, g);
+    const double alpha = pap != 0.0 ? rz / pap : 0.0;
+    s = 0.0;
+    for (long long c = t0; c < N; c += G) {
+      z[c] += alpha * pp[c];
+      const double v = rr[c] - alpha * ap[c];
+      rr[c] = v;
+      zz[c] = v / dg[c];
+      s += zz[c];
+    }
+    const double m = grid_sum(s, sh, part, flip, g) / (double)N;
+    s = 0.0;
+    for (long long c = t0; c < N; c += G) {
+      zz[c] -= m;
+      s += rr[c] * zz[c];
+    }
+    const double rzn = grid_sum(s, sh, part, flip, g);
+    const double beta = rz != 0.0 ? rzn / rz : 0.0;
+    for (long long c = t0; c < N; c += G) pp[c] = zz[c] + beta * pp[c];
+    rz = rzn;
+    g.sync();
+  }
+  for (long long c = t0; c < N; c += G) z[c] += m_r / t.gamma;
+  if (t0 == 0) stats[0] = it;
+}
+
 // Device workspace of one reconstruction, freed on every exit path.
 struct Work {
   std::vector<void*> ptrs;
@@ -337,6 +441,24 @@ struct Ld {
   double* hsc = nullptr;
   int* cg_stats = nullptr;
   int* hstats = nullptr;
+  // cooperative grid of the M_gamma solve (0: not available)
+  int coop_blocks = 0;
+  double* coop_part = nullptr;
+
+  // Size the cooperative grid: one thread per cell, at most what can be
+  // resident at once on the device (and kCoopMaxBlocks).
+  void setup_coop() {
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tv_cg_coop_kernel, kCoopThreads, 0) != cudaSuccess)
+      return;
+    long long want = (N + kCoopThreads - 1) / kCoopThreads;
+    long long cap = (long long)sms * per_sm;
+    if (cap > kCoopMaxBlocks) cap = kCoopMaxBlocks;
+    coop_blocks = (int)(want < cap ? want : cap);
+  }
 
   // M_gamma z = r.  M annihilates constants (M 1 = 0), so M_gamma 1 = gamma 1
   // and the mean-free part is invariant: z = (mean r / gamma) 1 + y with
@@ -347,6 +469,22 @@ struct Ld {
   // rr, pp, ap, zz, dg: work vectors [N]; y accumulates in z.
   qpat_status tv_solve(const double* r, double* z, double* rr, double* pp, double* ap, double* zz, double* dg,
                        const double* ones, int max_iter, double tol) {
+    if (coop_blocks > 0) {
+      // the whole solve in one cooperative launch
+      const double* rp = r;
+      TVGrid tvv = tv;
+      void* args[] = {&tvv, &rp, &z, &rr, &pp, &ap, &zz, &dg, &coop_part, &max_iter, &tol, &cg_stats};
+      qpat_status e = cuda(cudaLaunchCooperativeKernel((const void*)tv_cg_coop_kernel, dim3(coop_blocks),
+                                                       dim3(kCoopThreads), args, 0, v.stream),
+                           "tv_cg_coop_kernel");
+      if (e != QPAT_OK) return e;
+      if ((e = cuda(cudaMemcpyAsync(hstats, cg_stats, sizeof(int), cudaMemcpyDeviceToHost, v.stream), "copy")) !=
+          QPAT_OK)
+        return e;
+      if ((e = cuda(cudaStreamSynchronize(v.stream), "tv_solve sync")) != QPAT_OK) return e;
+      tv_iters += *hstats;
+      return QPAT_OK;
+    }
     if (N <= kOneCtaMax) {
       // small grids: the whole solve in one CTA, without launches per iteration
       tv_cg_kernel<<<1, kCgThreads, 0, v.stream>>>(tv, r, z, rr, pp, ap, zz, dg, max_iter, tol, cg_stats);
@@ -493,6 +631,7 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   L.dout = w.get<double>(1);
   L.sc = w.get<double>(8);
   L.cg_stats = w.get<int>(4);
+  L.coop_part = w.get<double>(2 * (size_t)kCoopMaxBlocks);
   TVGrid tvb[2];                                       // TV operator of each unknown block
   for (int u = 0; u < U; ++u) {
     tvb[u] = TVGrid{L.v.n0, L.v.n1, L.v.n2, p.tv_edge, p.beta, p.gamma, nullptr, nullptr, nullptr};
@@ -511,6 +650,7 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   if ((st = L.cuda(cudaMallocHost(&pinned.p, 8 * sizeof(double)), "pinned scalars")) != QPAT_OK) return st;
   L.hsc = pinned.p;
   L.hstats = reinterpret_cast<int*>(pinned.p + 4);
+  L.setup_coop();
   if ((st = L.cuda(cudaMemcpyAsync(mu0, mu, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
     return st;
   if (joint &&
