@@ -21,7 +21,10 @@ Written out from Sections 4 and 5:
   stopping rule (i_max; after i_m iterations the relative reduction of r^T z
   over the last i_m iterations against Tol_in);
 * Algorithm 5 (outer loop, step alpha = 1, stop when the relative decrease of
-  eps falls to Tol_out, or after k_max linearisations).
+  eps falls to Tol_out, or after k_max linearisations);
+* Algorithm 6 (PD-IPM): per linearisation, sub-subproblems on the update d
+  with a dual variable chi per face (eqs. du, dw, pre1 with lambda = 0) and
+  the step length rule for chi (eq. sstep).
 
 Library primitives: scipy's sparse direct solve for M_gamma z = r, and the
 composite maps of ``oracle.qpat``.
@@ -257,6 +260,105 @@ def ld_newton(prob, prm: LDParams):
         d, i, _ = pcg(lambda v: prob.gn_product(xbar, v.reshape(shape)).ravel(), -g.ravel(),
                       solve_M, prm.i_max, prm.i_m, prm.tol_in)
         inner.append(i)
+        xbar = xbar + d.reshape(shape)
+        k += 1
+    return (prob.coeffs(xbar) if joint else prob.mu(xbar)), xbar, eps_hist, inner
+
+
+# ---- Algorithm 6: inexact Newton with the primal-dual interior-point TV ----------
+@dataclasses.dataclass
+class PDParams(LDParams):
+    """Algorithm 6 parameters (Section 6, 2D phantom: k'_max = 20,
+    Tol_med = 1e-3, beta = gamma = 1e-6; the PCG as in LD)."""
+    kp_max: int = 20
+    tol_med: float = 1e-3
+
+
+def pd_weights(d, chi, edge, beta):
+    """Per-face weights of M~ = D^T C (I - C chi (D d)^T) D (section
+    PD-IPM, with the outer product read face by face: the factor for face l
+    is c_l (1 - c_l chi_l (D d)_l), c_l = ((D d)_l^2 + beta)^(-1/2))."""
+    D = tv_difference(d.shape, edge)
+    g = D @ d.ravel()
+    c = 1.0 / np.sqrt(g * g + beta)
+    return D, g, c, c * (1.0 - c * chi * g)
+
+
+def pd_matrix(d, chi, edge, beta, gamma):
+    """M~_gamma = D^T diag(c (1 - c chi Dd)) D + gamma I."""
+    D, g, c, wf = pd_weights(d, chi, edge, beta)
+    M = (D.T @ sp.diags(wf) @ D).tocsr()
+    return (M + gamma * sp.identity(M.shape[0], format="csr")).tocsc()
+
+
+def pd_dual_step(d, dd, chi, edge, beta):
+    """eq. dw face by face: dchi = c (1 - c chi Dd) D dd - chi + c D d (c at
+    d), and the step length rule: s = min(1, phi*) with phi* the largest phi
+    keeping |chi + phi dchi| <= 1 on every face.  Returns chi + s dchi."""
+    D, g, c, wf = pd_weights(d, chi, edge, beta)
+    dchi = wf * (D @ dd.ravel()) - chi + c * g
+    phi = np.inf
+    pos, neg = dchi > 0, dchi < 0
+    if np.any(pos):
+        phi = min(phi, float(np.min((1.0 - chi[pos]) / dchi[pos])))
+    if np.any(neg):
+        phi = min(phi, float(np.min((-1.0 - chi[neg]) / dchi[neg])))
+    return chi + min(1.0, phi) * dchi
+
+
+def pdipm_newton(prob, prm: PDParams):
+    """Algorithm 6 for a ``Problem`` or a ``JointProblem`` (D, chi and M~
+    block by block).  Returns (coefficients, Xbar*, eps history, PCG
+    iterations of every sub-subproblem per outer iteration).
+
+    Each sub-subproblem k' solves eq. pre1 by Algorithm 4 with
+    grad eps~_k' = grad eps + H d_k' (the right-hand side of eq. du with
+    lambda = 0), updates d (alpha_k' = 1) and chi (eq. dw with the step length
+    rule).  r_k',* is the last r^T z of that PCG loop; the sub-subproblems stop
+    at k'_max or when 1 - r_k',* / r_k'-1,* <= Tol_med."""
+    joint = isinstance(prob, JointProblem)
+    shape = prob.shape if joint else prob.mu0.shape
+    blocks = 2 if joint else 1
+    bshape = shape[1:] if joint else shape
+    xbar = np.zeros(shape)
+    eps_hist: List[float] = []
+    inner: List[List[int]] = []
+    k = 0
+    while True:
+        res = prob.residuals(xbar)
+        eps_hist.append(0.5 * sum(float(np.sum(r * r)) for r in res))
+        if k > 0 and not (1.0 - eps_hist[k] / eps_hist[k - 1] > prm.tol_out):
+            break
+        if k >= prm.k_max:
+            break
+        g = prob.gradient(xbar, res).ravel()
+
+        def H(v):
+            return prob.gn_product(xbar, v.reshape(shape)).ravel()
+
+        n = int(np.prod(bshape))
+        nf = tv_difference(bshape, prm.edge).shape[0]
+        d = np.zeros(blocks * n)
+        chi = [np.zeros(nf) for _ in range(blocks)]
+        its, r_prev = [], None
+        for kp in range(prm.kp_max):
+            lus = [spla.splu(pd_matrix(d[b * n:(b + 1) * n].reshape(bshape), chi[b], prm.edge, prm.beta, prm.gamma))
+                   for b in range(blocks)]
+
+            def solve_M(r):
+                return np.concatenate([lus[b].solve(r[b * n:(b + 1) * n]) for b in range(blocks)])
+
+            dd, i, rz = pcg(H, -(g + H(d)), solve_M, prm.i_max, prm.i_m, prm.tol_in)
+            its.append(i)
+            for b in range(blocks):
+                chi[b] = pd_dual_step(d[b * n:(b + 1) * n].reshape(bshape), dd[b * n:(b + 1) * n].reshape(bshape),
+                                      chi[b], prm.edge, prm.beta)
+            d = d + dd
+            r_star = rz[-1]
+            if r_prev is not None and not (1.0 - r_star / r_prev > prm.tol_med):
+                break
+            r_prev = r_star
+        inner.append(its)
         xbar = xbar + d.reshape(shape)
         k += 1
     return (prob.coeffs(xbar) if joint else prob.mu(xbar)), xbar, eps_hist, inner

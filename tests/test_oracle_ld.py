@@ -174,3 +174,62 @@ def test_joint_ld_newton_decreases_the_misfit():
     assert len(eps) == 4 and inner == [4, 4, 4]
     assert all(eps[k + 1] < eps[k] for k in range(3))
     assert np.allclose(mu, prob.mu0 * np.exp(xbar[1])) and np.allclose(kappa, prob.kappa0 * np.exp(xbar[0]))
+
+
+# ---- Algorithm 6 (PD-IPM) ----------------------------------------------------------
+def test_pd_preconditioner_without_dual_is_the_lagged_diffusivity_one():
+    rng = np.random.default_rng(20)
+    d = rng.normal(size=(6, 7)) * 0.3
+    nf = ld.tv_difference(d.shape, 0.1).shape[0]
+    A = ld.pd_matrix(d, np.zeros(nf), 0.1, 1e-6, 1e-4).toarray()
+    B = ld.m_gamma(d, 0.1, 1e-6, 1e-4).toarray()
+    assert np.allclose(A, B, rtol=1e-14, atol=0)
+
+
+def test_pd_dual_direction_is_the_derivative_of_the_central_path():
+    """On the central path chi = C[d] D d the dual direction of eq. dw is the
+    derivative of d -> C[d] D d along the primal step (central differences),
+    and a full step from any feasible chi with a zero primal step lands on the
+    path."""
+    rng = np.random.default_rng(21)
+    edge, beta = 0.1, 1e-3
+    d = rng.normal(size=(6, 7)) * 0.3
+    dd = rng.normal(size=d.shape)
+    D = ld.tv_difference(d.shape, edge)
+
+    def chi_of(x):
+        g = D @ x.ravel()
+        return g / np.sqrt(g * g + beta)
+
+    chi = chi_of(d)
+    D_, g, c, wf = ld.pd_weights(d, chi, edge, beta)
+    t = 1e-6
+    fd = (chi_of(d + t * dd) - chi_of(d - t * dd)) / (2 * t)
+    assert np.allclose(wf * (D @ dd.ravel()), fd, rtol=1e-6, atol=1e-9)
+    chi0 = rng.uniform(-0.9, 0.9, size=chi.shape)
+    assert np.allclose(ld.pd_dual_step(d, np.zeros_like(d), chi0, edge, beta), chi, rtol=1e-12, atol=1e-14)
+
+
+def test_pd_dual_step_stays_feasible():
+    rng = np.random.default_rng(22)
+    d = rng.normal(size=(6, 7))
+    chi = rng.uniform(-1, 1, size=ld.tv_difference(d.shape, 0.1).shape[0])
+    for _ in range(5):
+        dd = 50 * rng.normal(size=d.shape)
+        chi = ld.pd_dual_step(d, dd, chi, 0.1, 1e-6)
+        assert np.max(np.abs(chi)) <= 1.0 + 1e-12
+        d = d + dd
+
+
+def test_pdipm_first_step_equals_ld_and_descends():
+    prob, mu_true, w = _problem()
+    edge = w.dx / phantoms.MM
+    one = ld.pdipm_newton(prob, ld.PDParams(k_max=1, i_max=2, i_m=2, tol_out=0.0, kp_max=1, gamma=1e-2,
+                                            beta=1e-6, edge=edge))
+    ref = ld.ld_newton(prob, ld.LDParams(k_max=1, i_max=2, i_m=2, tol_out=0.0, gamma=1e-2, beta=1e-6, edge=edge))
+    assert np.allclose(one[0], ref[0], rtol=1e-13)
+    mu, xbar, eps, inner = ld.pdipm_newton(prob, ld.PDParams(k_max=2, i_max=2, i_m=2, tol_out=0.0, kp_max=2,
+                                                             tol_med=-1.0, gamma=1e-2, beta=1e-6, edge=edge))
+    assert inner == [[2, 2], [2, 2]]
+    assert eps[2] < eps[1] < eps[0]
+    assert np.linalg.norm(mu - mu_true) < np.linalg.norm(prob.mu0 - mu_true)
