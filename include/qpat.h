@@ -234,7 +234,16 @@ qpat_status qpat_dot(qpat_ctx* ctx, int batch, long long len, const void* a, con
 
 /* Reconstruction of mu, or of kappa and mu together, by the inexact-Newton
  * lagged-diffusivity method with TV priorconditioning (Section 5.2.1,
- * Algorithms 4 and 5).
+ * Algorithms 4 and 5), or by the inexact Newton method with the primal-dual
+ * interior-point TV (Section 5.2.2, Algorithm 6: method = 1).
+ *  - Algorithm 6 replaces the single PCG of a linearisation by sub-subproblems
+ *    k' on the update d: Algorithm 4 on H dd = -(g + H d) with the
+ *    preconditioner D^T C (I - C chi (D d)^T) D + gamma I (read face by face:
+ *    face l weighs c_l (1 - c_l chi_l (D d)_l), c_l = ((D d)_l^2 + beta)^(-1/2)),
+ *    d += dd, and the dual step of eq. dw per face with the step length rule
+ *    (chi stays in [-1, 1]); they stop at kp_max or when the last r^T z of a
+ *    PCG loop falls by no more than tol_med against the previous one.  Xbar += d.
+ *    inner_hist then counts the PCG iterations of all sub-subproblems.
  *  - kappa == NULL: the unknown is mu, kappa stays the context's.  Otherwise
  *    the unknown is [kappa, mu] (eq. scaling): kappa is a device double [N],
  *    kappa0 on entry and the reconstruction on return; the derivatives in
@@ -278,11 +287,16 @@ typedef struct {
                         <= 0: dx in mm (2D), (dx in mm)^2 (3D) */
   int tv_max_iter;   /* CG iterations per M_gamma solve; <= 0: 20000 */
   double tv_tol;     /* relative residual of the M_gamma solve; <= 0: 1e-12 */
+  int method;        /* 0: lagged diffusivity (Algorithm 5); 1: primal-dual interior point
+                        (Algorithm 6) */
+  int kp_max;        /* Algorithm 6: sub-subproblems per linearisation; <= 0: 20 */
+  double tol_med;    /* Algorithm 6: Tol_med, taken as given (Section 6: 1e-3) */
 } qpat_ld_params;
 
 typedef struct {
   int outer;              /* linearisations performed */
   int inner_total;        /* PCG iterations, all outer iterations */
+  int sub_total;          /* Algorithm 6: sub-subproblems, all outer iterations */
   long long tv_iters;     /* CG iterations of all M_gamma solves */
   long long products;     /* applications of J_q or J_q^* (one propagation each) */
   double eps_first;       /* eps at mu0 */

@@ -52,11 +52,13 @@ class qpat_ld_params(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("i_max", ctypes.c_int), ("i_m", ctypes.c_int),
                 ("tol_in", ctypes.c_double), ("tol_out", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("beta", ctypes.c_double), ("tv_edge", ctypes.c_double), ("tv_max_iter", ctypes.c_int),
-                ("tv_tol", ctypes.c_double)]
+                ("tv_tol", ctypes.c_double), ("method", ctypes.c_int), ("kp_max", ctypes.c_int),
+                ("tol_med", ctypes.c_double)]
 
 
 class qpat_ld_info(ctypes.Structure):
-    _fields_ = [("outer", ctypes.c_int), ("inner_total", ctypes.c_int), ("tv_iters", ctypes.c_longlong),
+    _fields_ = [("outer", ctypes.c_int), ("inner_total", ctypes.c_int), ("sub_total", ctypes.c_int),
+                ("tv_iters", ctypes.c_longlong),
                 ("products", ctypes.c_longlong), ("eps_first", ctypes.c_double), ("eps_last", ctypes.c_double),
                 ("seconds", ctypes.c_double * 3)]
 
@@ -348,11 +350,14 @@ class Context:
         return out
 
     def ld_solve(self, data, illums, mu0, kappa0=None, k_max=10, i_max=30, i_m=5, tol_in=0.0, tol_out=1e-3,
-                 gamma=1e-6, beta=2e-5, tv_edge=0.0, tv_max_iter=0, tv_tol=0.0):
+                 gamma=1e-6, beta=2e-5, tv_edge=0.0, tv_max_iter=0, tv_tol=0.0, method="ld", kp_max=20,
+                 tol_med=1e-3):
         """qpat_ld_solve: returns (mu, eps history, inner iterations per outer
         iteration, info dict), or ((kappa, mu), ...) when kappa0 is given
         (simultaneous reconstruction).  data: [nq][nt][ns] in the context
-        precision; mu0, kappa0: FP64 interior fields (initial guesses)."""
+        precision; mu0, kappa0: FP64 interior fields (initial guesses).
+        method: "ld" (Algorithm 5) or "pdipm" (Algorithm 6, with kp_max and
+        tol_med)."""
         import torch
         nq = len(illums)
         data = data.contiguous()
@@ -360,7 +365,10 @@ class Context:
             raise TypeError("data must be a CUDA tensor [nq][nt][ns] of the context precision")
         mu = self._in(mu0, torch.float64, self.interior_shape).clone()
         kappa = None if kappa0 is None else self._in(kappa0, torch.float64, self.interior_shape).clone()
-        prm = qpat_ld_params(k_max, i_max, i_m, tol_in, tol_out, gamma, beta, tv_edge, tv_max_iter, tv_tol)
+        if method not in ("ld", "pdipm"):
+            raise ValueError("method must be 'ld' or 'pdipm'")
+        prm = qpat_ld_params(k_max, i_max, i_m, tol_in, tol_out, gamma, beta, tv_edge, tv_max_iter, tv_tol,
+                             1 if method == "pdipm" else 0, kp_max, tol_med)
         info = qpat_ld_info()
         eps = (ctypes.c_double * (max(k_max, 1) + 1))()
         inner = (ctypes.c_int * max(k_max, 1))()

@@ -149,6 +149,88 @@ __global__ void tv_apply_kernel(TVGrid t, const double* u, double* out, int diag
   }
 }
 
+// ---- faces of the primal-dual interior-point TV (Algorithm 6) --------------------
+// Faces are numbered x faces first ([n2][n1][n0 - 1]), then y ([n2][n1 - 1][n0]),
+// then z ([n2 - 1][n1][n0]), the layout of TVGrid's weights.
+__device__ __forceinline__ long long face_count(const TVGrid& t) {
+  return (long long)t.n2 * t.n1 * (t.n0 - 1) + (long long)t.n2 * (t.n1 - 1) * t.n0 +
+         (long long)(t.n2 - 1) * t.n1 * t.n0;
+}
+// cells (c1, c2) of face f, c2 the upper neighbour
+__device__ __forceinline__ void face_cells(const TVGrid& t, long long f, long long& c1, long long& c2) {
+  const long long nx = (long long)t.n2 * t.n1 * (t.n0 - 1), ny = (long long)t.n2 * (t.n1 - 1) * t.n0;
+  if (f < nx) {
+    const long long i = f % (t.n0 - 1), r = f / (t.n0 - 1);
+    c1 = r * t.n0 + i;
+    c2 = c1 + 1;
+  } else if (f < nx + ny) {
+    const long long g = f - nx, i = g % t.n0, j = (g / t.n0) % (t.n1 - 1), k = g / ((long long)t.n0 * (t.n1 - 1));
+    c1 = (k * t.n1 + j) * t.n0 + i;
+    c2 = c1 + t.n0;
+  } else {
+    const long long g = f - nx - ny;
+    c1 = g;
+    c2 = g + (long long)t.n0 * t.n1;
+  }
+}
+
+// M~ = D^T C (I - C chi (D d)^T) D read face by face: face l couples its two
+// cells with a^2 c_l (1 - c_l chi_l g_l), g_l = a (d_c1 - d_c2) = (D d)_l,
+// c_l = (g_l^2 + beta)^(-1/2) (section PD-IPM).  The weights go to t.wx.. (one
+// contiguous array in face order).
+__global__ void pd_weights_kernel(TVGrid t, const double* d, const double* chi) {
+  const long long nf = face_count(t);
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+    long long c1, c2;
+    face_cells(t, f, c1, c2);
+    const double g = t.edge * (d[c1] - d[c2]);
+    const double c = 1.0 / sqrt(g * g + t.beta);
+    t.wx[f] = t.edge * t.edge * c * (1.0 - c * chi[f] * g);
+  }
+}
+
+// eq. dw face by face: dchi = c (1 - c chi g) (D dd) - chi + c g, with c and g
+// at d; per-block minimum of the largest feasible step phi (|chi + phi dchi|
+// <= 1) into part[blockIdx.x] (+inf where no face limits it).
+__global__ void pd_dual_kernel(TVGrid t, const double* d, const double* dd, const double* chi, double* dchi,
+                               double* part) {
+  __shared__ double sh[kT];
+  const long long nf = face_count(t);
+  double phi = INFINITY;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+    long long c1, c2;
+    face_cells(t, f, c1, c2);
+    const double g = t.edge * (d[c1] - d[c2]);
+    const double c = 1.0 / sqrt(g * g + t.beta);
+    const double x = chi[f];
+    const double v = c * (1.0 - c * x * g) * t.edge * (dd[c1] - dd[c2]) - x + c * g;
+    dchi[f] = v;
+    if (v > 0.0) phi = fmin(phi, (1.0 - x) / v);
+    else if (v < 0.0) phi = fmin(phi, (-1.0 - x) / v);
+  }
+  sh[threadIdx.x] = phi;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + st]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void min_final_kernel(const double* part, int n, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double m = INFINITY;
+    for (int i = 0; i < n; ++i) m = fmin(m, part[i]);
+    out[0] = m;
+  }
+}
+
+// chi += s dchi
+__global__ void pd_chi_update_kernel(long long nf, double s, const double* dchi, double* chi) {
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x)
+    chi[f] += s * dchi[f];
+}
+
 // ---- the whole M_gamma solve in one CTA (grids up to kOneCtaMax cells) -------
 constexpr int kCgThreads = 1024;
 constexpr long long kOneCtaMax = 1LL << 18;
@@ -593,6 +675,9 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   if (p.tv_edge <= 0) p.tv_edge = L.v.dim == 3 ? (L.v.dx * 1e3) * (L.v.dx * 1e3) : L.v.dx * 1e3;
   if (p.tv_max_iter <= 0) p.tv_max_iter = 20000;
   if (p.tv_tol <= 0) p.tv_tol = 1e-12;
+  if (p.method != 0 && p.method != 1)
+    return (qpat_status)ctx_fail(c, QPAT_EINVAL, "qpat_ld_solve: method must be 0 (LD) or 1 (PD-IPM)");
+  if (p.kp_max <= 0) p.kp_max = 20;
 
   // unknowns: [kappa-bar | mu-bar] (joint) or mu-bar, each block N cells
   const bool joint = kappa != nullptr;
@@ -617,6 +702,7 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   double* t2 = w.get<double>(N);
   double* t3 = w.get<double>(N);
   double* t4 = w.get<double>(N);
+  double* t5 = w.get<double>(NU);
   double* c_rr = w.get<double>(N);
   double* c_pp = w.get<double>(N);
   double* c_ap = w.get<double>(N);
@@ -632,13 +718,24 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   L.sc = w.get<double>(8);
   L.cg_stats = w.get<int>(4);
   L.coop_part = w.get<double>(2 * (size_t)kCoopMaxBlocks);
+  const long long nfaces = (long long)L.v.n2 * L.v.n1 * (L.v.n0 - 1) + (long long)L.v.n2 * (L.v.n1 - 1) * L.v.n0 +
+                           (long long)(L.v.n2 - 1) * L.v.n1 * L.v.n0;
   TVGrid tvb[2];                                       // TV operator of each unknown block
   for (int u = 0; u < U; ++u) {
     tvb[u] = TVGrid{L.v.n0, L.v.n1, L.v.n2, p.tv_edge, p.beta, p.gamma, nullptr, nullptr, nullptr};
-    tvb[u].wx = w.get<double>((size_t)L.v.n2 * L.v.n1 * (L.v.n0 - 1));
-    tvb[u].wy = w.get<double>((size_t)L.v.n2 * (L.v.n1 - 1) * L.v.n0);
-    tvb[u].wz = w.get<double>((size_t)(L.v.n2 > 1 ? L.v.n2 - 1 : 1) * L.v.n1 * L.v.n0);
+    // the three face sets of a block back to back (face order of face_cells)
+    double* wall = w.get<double>((size_t)nfaces + 1);
+    tvb[u].wx = wall;
+    tvb[u].wy = wall + (size_t)L.v.n2 * L.v.n1 * (L.v.n0 - 1);
+    tvb[u].wz = tvb[u].wy + (size_t)L.v.n2 * (L.v.n1 - 1) * L.v.n0;
   }
+  // primal-dual state (Algorithm 6): the update d, and chi, dchi per face of each block
+  const bool pd = p.method == 1;
+  double* dvec = pd ? w.get<double>(NU) : nullptr;
+  double* chi = pd ? w.get<double>((size_t)U * nfaces + 1) : nullptr;
+  double* dchi = pd ? w.get<double>((size_t)U * nfaces + 1) : nullptr;
+  double* phipart = pd ? w.get<double>(1024) : nullptr;
+  double* phimin = pd ? w.get<double>(1) : nullptr;
   if (w.err != cudaSuccess) return L.cuda(w.err, "qpat_ld_solve workspace");
   struct PinnedScalars {
     double* p = nullptr;
@@ -713,8 +810,40 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
     axpby_kernel<<<blocks_for(NU), kT, 0, s>>>(NU, a, xv, b, yv);
   };
 
+  // Algorithm 4: PCG on H x = -gv with the preconditioner of tvb (weights set
+  // by the caller), from x = 0; iterations and the last r^T z to the caller
+  auto run_pcg = [&](const double* gv, int* iters, double* rz_last) -> qpat_status {
+    qpat_status e;
+    if ((e = L.cuda(cudaMemsetAsync(x, 0, NU * sizeof(double), s), "memset")) != QPAT_OK) return e;
+    if ((e = L.cuda(cudaMemsetAsync(r, 0, NU * sizeof(double), s), "memset")) != QPAT_OK) return e;
+    axpby_u(-1.0, gv, 1.0, r);
+    if ((e = precond(r, z)) != QPAT_OK) return e;
+    if ((e = L.cuda(cudaMemcpyAsync(d, z, NU * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
+      return e;
+    std::vector<double> rz(1);
+    if ((e = L.dot(r, z, NU, &rz[0])) != QPAT_OK) return e;
+    int i = 0;
+    while (i < p.i_max && rz[i] != 0.0 && (i < p.i_m || 1.0 - rz[i] / rz[i - p.i_m] > p.tol_in)) {
+      if ((e = gn_product(d)) != QPAT_OK) return e;
+      double dhd;
+      if ((e = L.dot(d, hd, NU, &dhd)) != QPAT_OK) return e;
+      const double alpha = rz[i] / dhd;
+      axpby_u(alpha, d, 1.0, x);
+      axpby_u(-alpha, hd, 1.0, r);
+      if ((e = precond(r, z)) != QPAT_OK) return e;
+      double rzn;
+      if ((e = L.dot(r, z, NU, &rzn)) != QPAT_OK) return e;
+      rz.push_back(rzn);
+      axpby_u(1.0, z, rz[i + 1] / rz[i], d);
+      ++i;
+    }
+    *iters = i;
+    *rz_last = rz.back();
+    return QPAT_OK;
+  };
+
   std::vector<double> eps;
-  int inner_total = 0;
+  int inner_total = 0, sub_total = 0;
   int k = 0;
   for (;;) {
     // linearisation point X^k = X0 exp(Xbar^k): coefficients, residuals, eps^k, fluences
@@ -751,39 +880,70 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
     }
     L.products += nq;
     if ((st = optical_adjoint_sum(g)) != QPAT_OK) return st;
-    // M_gamma^k frozen at Xbar^k (lagged diffusivity), one per block
-    for (int u = 0; u < U; ++u) {
-      L.tv = tvb[u];
-      if ((st = L.tv_weights(xbar + u * N)) != QPAT_OK) return st;
+    if (!pd) {
+      // M_gamma^k frozen at Xbar^k (lagged diffusivity), one per block
+      for (int u = 0; u < U; ++u) {
+        L.tv = tvb[u];
+        if ((st = L.tv_weights(xbar + u * N)) != QPAT_OK) return st;
+      }
+      int i;
+      double rz_last;
+      if ((st = run_pcg(g, &i, &rz_last)) != QPAT_OK) return st;   // H x = -g
+      if (inner_hist) inner_hist[k] = i;
+      inner_total += i;
+      axpby_u(1.0, x, 1.0, xbar);   // Xbar^{k+1} = Xbar^k + d^k (alpha^k = 1)
+    } else {
+      // Algorithm 6: sub-subproblems k' on the update d with the dual chi
+      if ((st = L.cuda(cudaMemsetAsync(dvec, 0, NU * sizeof(double), s), "memset")) != QPAT_OK) return st;
+      if ((st = L.cuda(cudaMemsetAsync(chi, 0, (size_t)U * nfaces * sizeof(double), s), "memset")) != QPAT_OK)
+        return st;
+      int its = 0;
+      double r_prev = 0.0;
+      for (int kp = 0; kp < p.kp_max; ++kp) {
+        for (int u = 0; u < U; ++u) {
+          pd_weights_kernel<<<blocks_for(nfaces), kT, 0, s>>>(tvb[u], dvec + u * N, chi + u * nfaces);
+          if ((st = L.cuda(cudaGetLastError(), "pd_weights_kernel")) != QPAT_OK) return st;
+        }
+        // grad eps~_k' = grad eps + H d_k' (eq. du with lambda = 0); H d = 0 at d = 0
+        if (kp == 0) {
+          if ((st = L.cuda(cudaMemcpyAsync(t5, g, NU * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) !=
+              QPAT_OK)
+            return st;
+        } else {
+          if ((st = gn_product(dvec)) != QPAT_OK) return st;
+          if ((st = L.cuda(cudaMemcpyAsync(t5, g, NU * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) !=
+              QPAT_OK)
+            return st;
+          axpby_u(1.0, hd, 1.0, t5);
+        }
+        int i;
+        double r_star;
+        if ((st = run_pcg(t5, &i, &r_star)) != QPAT_OK) return st;   // eq. pre1: H dd = -grad eps~
+        its += i;
+        // dual step (eq. dw) with the step length rule, then d += dd (alpha_k' = 1)
+        for (int u = 0; u < U; ++u) {
+          const int nb = 1024;
+          pd_dual_kernel<<<nb, kT, 0, s>>>(tvb[u], dvec + u * N, x + u * N, chi + u * nfaces, dchi + u * nfaces,
+                                           phipart);
+          min_final_kernel<<<1, 32, 0, s>>>(phipart, nb, phimin);
+          double phi;
+          if ((st = L.cuda(cudaMemcpyAsync(L.hsc + 2, phimin, sizeof(double), cudaMemcpyDeviceToHost, s), "copy")) !=
+              QPAT_OK)
+            return st;
+          if ((st = L.cuda(cudaStreamSynchronize(s), "dual step sync")) != QPAT_OK) return st;
+          phi = L.hsc[2];
+          pd_chi_update_kernel<<<blocks_for(nfaces), kT, 0, s>>>(nfaces, phi < 1.0 ? phi : 1.0, dchi + u * nfaces,
+                                                                 chi + u * nfaces);
+        }
+        axpby_u(1.0, x, 1.0, dvec);
+        ++sub_total;
+        if (kp > 0 && !(1.0 - r_star / r_prev > p.tol_med)) break;
+        r_prev = r_star;
+      }
+      if (inner_hist) inner_hist[k] = its;
+      inner_total += its;
+      axpby_u(1.0, dvec, 1.0, xbar);   // Xbar^{k+1} = Xbar_0^k + d (alpha^k = 1)
     }
-
-    // Algorithm 4: PCG on H d = -g, preconditioner M_gamma, from 0
-    if ((st = L.cuda(cudaMemsetAsync(x, 0, NU * sizeof(double), s), "memset")) != QPAT_OK) return st;
-    if ((st = L.cuda(cudaMemsetAsync(r, 0, NU * sizeof(double), s), "memset")) != QPAT_OK) return st;
-    axpby_u(-1.0, g, 1.0, r);   // r_0 = -grad eps
-    if ((st = precond(r, z)) != QPAT_OK) return st;
-    if ((st = L.cuda(cudaMemcpyAsync(d, z, NU * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy")) != QPAT_OK)
-      return st;
-    std::vector<double> rz(1);
-    if ((st = L.dot(r, z, NU, &rz[0])) != QPAT_OK) return st;
-    int i = 0;
-    while (i < p.i_max && rz[i] != 0.0 && (i < p.i_m || 1.0 - rz[i] / rz[i - p.i_m] > p.tol_in)) {
-      if ((st = gn_product(d)) != QPAT_OK) return st;
-      double dhd;
-      if ((st = L.dot(d, hd, NU, &dhd)) != QPAT_OK) return st;
-      const double alpha = rz[i] / dhd;
-      axpby_u(alpha, d, 1.0, x);
-      axpby_u(-alpha, hd, 1.0, r);
-      if ((st = precond(r, z)) != QPAT_OK) return st;
-      double rzn;
-      if ((st = L.dot(r, z, NU, &rzn)) != QPAT_OK) return st;
-      rz.push_back(rzn);
-      axpby_u(1.0, z, rz[i + 1] / rz[i], d);
-      ++i;
-    }
-    if (inner_hist) inner_hist[k] = i;
-    inner_total += i;
-    axpby_u(1.0, x, 1.0, xbar);   // Xbar^{k+1} = Xbar^k + d^k (alpha^k = 1)
     ++k;
   }
   if ((st = L.cuda(cudaStreamSynchronize(s), "qpat_ld_solve sync")) != QPAT_OK) return st;
@@ -792,6 +952,7 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   if (info) {
     info->outer = k;
     info->inner_total = inner_total;
+    info->sub_total = sub_total;
     info->tv_iters = L.tv_iters;
     info->products = L.products;
     info->eps_first = eps.front();

@@ -158,3 +158,54 @@ def test_joint_ld_fp32_tracks_oracle():
     assert np.allclose(eps, eps_ref, rtol=1e-3, atol=0)
     assert np.linalg.norm(mu - m_ref) <= 1e-2 * np.linalg.norm(m_ref - mu0)
     assert np.linalg.norm(kap - k_ref) <= 1e-2 * np.linalg.norm(k_ref - kappa0)
+
+
+def _run_pd(prec, joint, k_max=2, i_max=2, kp_max=2, gamma=1e-2, beta=1e-6, tol_med=-1.0):
+    from paper_1810_11685_gb300.binding import context_from_workload
+    illums = JOINT_ILLUMS if joint else ILLUMS
+    w = phantoms.small(n=8, pml=4, nt=30, n_sensors=12, seed=3)
+    S = acoustic.setup_from_workload(w)
+    rng = np.random.default_rng(3)
+    kappa0 = phantoms.optical_diffusion(w)
+    kappa_true = kappa0 * np.exp(0.3 * rng.standard_normal(w.interior_shape)) if joint else kappa0
+    mu_true = phantoms.optical_absorption(w)
+    P = np.stack([acoustic.forward(S, optics.heating(mu_true, kappa_true, S.dx, q)) for q in illums])
+    mu0 = np.full(w.interior_shape, w.mu_bg)
+    edge = w.dx / phantoms.MM
+    prm = ld.PDParams(k_max=k_max, i_max=i_max, i_m=i_max, tol_in=0.0, tol_out=0.0, gamma=gamma, beta=beta,
+                      edge=edge, kp_max=kp_max, tol_med=tol_med)
+    prob = ld.JointProblem(S, illums, P, mu0, kappa0) if joint else ld.Problem(S, kappa0, illums, P, mu0)
+    ref, _, eps_ref, inner_ref = ld.pdipm_newton(prob, prm)
+    ctx = context_from_workload(w, precision=prec, max_batch=len(illums))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    got, eps, inner, info = ctx.ld_solve(torch.as_tensor(P, dtype=dt, device="cuda"), illums,
+                                         torch.as_tensor(mu0, device="cuda"),
+                                         torch.as_tensor(kappa0, device="cuda") if joint else None,
+                                         k_max=k_max, i_max=i_max, i_m=i_max, tol_in=0.0, tol_out=0.0,
+                                         gamma=gamma, beta=beta, tv_edge=edge, method="pdipm", kp_max=kp_max,
+                                         tol_med=tol_med)
+    if joint:
+        got = tuple(t.cpu().numpy() for t in got)
+        base = (kappa0, mu0)
+    else:
+        got, ref, base = (got.cpu().numpy(),), (ref,), (mu0,)
+    return got, eps, inner, info, ref, eps_ref, inner_ref, base
+
+
+@pytest.mark.parametrize("joint", [False, True])
+def test_pdipm_fp64_matches_oracle(joint):
+    got, eps, inner, info, ref, eps_ref, inner_ref, base = _run_pd("fp64", joint)
+    assert inner == [sum(x) for x in inner_ref] == [4, 4]
+    assert info["sub_total"] == 4
+    assert eps_ref[2] < eps_ref[1] < eps_ref[0]
+    # as for the LD reconstruction: FP64 products, M~ solves to 1e-12
+    assert np.allclose(eps, eps_ref, rtol=1e-9, atol=0)
+    for a, b, b0 in zip(got, ref, base):
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b - b0)
+
+
+def test_pdipm_fp32_tracks_oracle():
+    got, eps, inner, info, ref, eps_ref, inner_ref, base = _run_pd("fp32", False)
+    assert inner == [sum(x) for x in inner_ref]
+    assert np.allclose(eps, eps_ref, rtol=1e-3, atol=0)
+    assert np.linalg.norm(got[0] - ref[0]) <= 1e-2 * np.linalg.norm(ref[0] - base[0])
