@@ -41,6 +41,13 @@ constexpr bool kLine3Pairs = QPAT_LINE3_PAIRS != 0;
 template <int L>
 constexpr int cbw3() { return 8; }
 
+// Resident CTAs per SM the 3D row pass is compiled for (registers capped to
+// fit; measured at 288^3: 6 1.171e10, 8 1.199e10, 9 1.174e10 cell-steps/s).
+#ifndef QPAT_ROW3_MINB
+#define QPAT_ROW3_MINB 8
+#endif
+constexpr int kRow3MinBlocks = QPAT_ROW3_MINB;
+
 #ifndef QPAT_ROW3_DESC
 #define QPAT_ROW3_DESC 1
 #endif
@@ -66,7 +73,7 @@ struct R3Staged {
 };
 
 template <typename T, int L, int PH>
-__global__ void __launch_bounds__(rp3<L>() * SGeom<L>::TPT, 8)
+__global__ void __launch_bounds__(rp3<L>() * SGeom<L>::TPT, kRow3MinBlocks)
 row3_fast(const Prop3<T> a) {
   constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH);
   constexpr int NSX = (KIN > KOUT ? KIN : KOUT);
