@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--nt", type=int, default=None, help="override Nt (default: workload's 2000)")
     p.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/roofline/cpu legs")
     p.add_argument("--n3", type=int, default=None, help="c5 only: interior nodes per axis (default 256)")
+    p.add_argument("--ld-method", default="ld", choices=["ld", "pdipm"],
+                   help="ld workload: lagged diffusivity (Algorithm 5) or primal-dual interior point (Algorithm 6)")
     p.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "ld"],
                    help="c2: the 576^2 forward+adjoint workload (default); c4: 48 Jacobian-vector "
                         "products over 288^2/432^2/576^2 grids in one graph; c5: the 3D 256^3 workload; "
@@ -473,6 +475,8 @@ def run_ld(args):
     mu0 = torch.full(w.interior_shape, w.mu_bg, dtype=torch.float64, device="cuda")
     kappa0 = torch.as_tensor(kappa_bg, device="cuda")
     kw = dict(k_max=3, i_max=4, i_m=4, tol_in=0.0, tol_out=0.0)
+    if args.ld_method == "pdipm":
+        kw.update(method="pdipm", i_max=2, i_m=2, kp_max=2, tol_med=-1.0, beta=1e-6)
     ctx.ld_solve(data, illums, mu0, kappa0, k_max=1, i_max=2)      # warm-up (graphs, multigrid)
     torch.cuda.synchronize()
     times, res = [], None
@@ -495,8 +499,10 @@ def run_ld(args):
             "unit": UNIT, "n_gpus": 1, "steps": len(times), "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "impl": "ours",
             "config": {"workload": f"2d {w.n}x{w.n} interior, {w.grid}x{w.grid} FFT grid, Nt={nt}, "
-                                   f"{w.n_sensors} sensors, 4 illuminations, joint (kappa, mu) LD, "
-                                   f"k_max=3, i_max=i_m=4", "nt": nt},
+                                   f"{w.n_sensors} sensors, 4 illuminations, joint (kappa, mu), "
+                                   + ("LD, k_max=3, i_max=i_m=4" if args.ld_method == "ld" else
+                                      "PD-IPM, k_max=3, k'_max=2, i_max=i_m=2"), "nt": nt,
+                       "method": args.ld_method},
             "seconds_per_solve": t, "outer": info["outer"], "inner": inner, "products": info["products"],
             "tv_cg_iterations": info["tv_iters"], "seconds_per_outer": t / max(1, info["outer"]),
             "seconds_by_phase": info["seconds"],
