@@ -1,16 +1,19 @@
-// Inexact-Newton lagged-diffusivity reconstruction of mu with TV
-// priorconditioning (Section 5.2.1, Algorithms 4 and 5).
+// Inexact-Newton reconstructions of mu, or of kappa and mu together, with TV
+// regularisation: lagged diffusivity with priorconditioning (Section 5.2.1,
+// Algorithms 4 and 5) and the primal-dual interior-point variant (Section
+// 5.2.2, Algorithm 6).
 //
 // Each application of H, J or J^* runs the optical half (the diffusion solve
-// and the heating map) per illumination and the acoustic half H_a or H_a^*
-// for all illuminations as one batch of the propagation kernels.  The kernels
-// below do the vector work on the interior grid in FP64: the log scaling
-// mu = mu0 exp(Xbar), the residuals,
-// the TV face weights C = ((D Xbar)^2 + beta)^(-1/2) and M_gamma u =
-// D^T C D u + gamma u (eqs. m, m1), and the Krylov vector updates.  Inner
-// products are the library's compensated FP64 reductions; the Krylov
-// scalars go to the host, which runs the iteration control of Algorithms 4
-// and 5.
+// and the heating map, with the kappa derivatives of Lemma 1 in the joint
+// form) per illumination and the acoustic half H_a or H_a^* for all
+// illuminations as one batch of the propagation kernels.  The kernels below do
+// the vector work on the interior grid in FP64: the log scaling
+// X = X0 exp(Xbar), the residuals, the TV face weights (C = ((D Xbar)^2 +
+// beta)^(-1/2), eqs. m, m1, or their primal-dual counterpart), the M_gamma
+// solves (one cooperative launch each), the dual step of Algorithm 6 and the
+// Krylov vector updates.  Inner products are the library's compensated FP64
+// reductions; the scalars of Algorithm 4 go to the host, which runs the
+// iteration control of Algorithms 4 to 6.
 #include <math.h>
 
 #include <chrono>
