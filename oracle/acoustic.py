@@ -21,7 +21,7 @@ sub-operation of one step is transposed and the steps are run in reverse
 order.  Arrays are C-ordered with x fastest: physical axis i (0 = x) is array
 axis ``dim - 1 - i``.
 
-Readings of points the paper leaves open (also listed in the design doc):
+Readings of points the paper leaves open:
 sinc is the unnormalised sin(x)/x of |k|; c_ref = max(c); the PML profile is
 alpha_max (c_ref/dx) (xi/P)^4 Np/s with xi the distance into the layer in
 grid units (staggered points at half-integer xi); the Y_abs symbol is 0 at
