@@ -209,7 +209,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(w, P, nt, {"reference_sample_nt": nt_s}),
+            "data": "synthetic", "config": config_dict(w, args.batch, nt, {"reference_sample_nt": nt_s,
+                                                                  "reference_problems_per_step": P}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
                              "sample": f"each step: forward+adjoint of {nt_s} of the {nt} time steps, "
                                        f"FP64 numpy, {mode}"},
