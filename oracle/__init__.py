@@ -16,6 +16,8 @@ Modules
   with its Frechet derivative and adjoint in mu (Lemma 1).
 - ``qpat``: the composite maps H = H_a H_o, J and J^* (Section 3.2.2,
   eqs. com_des and J_des).
+- ``medium``: the derivatives of H_a in the sound speed and the density, the
+  tangent loop and its exact transpose (the Discussion's next unknown).
 - ``ld``: the inexact-Newton lagged-diffusivity reconstruction of mu with the
   TV priorconditioner (Section 5.2.1, Algorithms 4 and 5; Section 5, eqs. gr,
   apj, tvm, m, m1).
