@@ -104,6 +104,23 @@ def _oracle_worker(w, nt_sample, seed, barrier, out):
     out.put((seed, t0, time.perf_counter()))
 
 
+def host_cpu():
+    """Architecture, CPU model and core count of the host running the oracle."""
+    import platform
+    model = platform.processor() or ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read().splitlines()
+        for key in ("model name", "Model", "CPU part"):
+            hit = [ln.split(":", 1)[1].strip() for ln in info if ln.split(":", 1)[0].strip() == key]
+            if hit:
+                model = hit[0] if key != "CPU part" else f"CPU part {hit[0]}"
+                break
+    except OSError:
+        pass
+    return {"machine": platform.machine(), "cpu": model, "nproc": os.cpu_count()}
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -178,7 +195,7 @@ def cpu_baseline(w, target_s=10.0):
             "sample": f"FP64 numpy oracle, {P} independent problems at once, one single-threaded process "
                       f"per core, forward+adjoint of {nt_s} steps each on the {w.grid}x{w.grid} grid "
                       f"({tp:.1f} s wall from the common start to the last finish)",
-            "single_thread": single}
+            "single_thread": single, "host": host_cpu()}
 
 
 def run_reference(args):
@@ -211,7 +228,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(w, args.batch, nt, {"reference_sample_nt": nt_s,
                                                                   "reference_problems_per_step": P}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle", "host": host_cpu(),
                              "sample": f"each step: forward+adjoint of {nt_s} of the {nt} time steps, "
                                        f"FP64 numpy, {mode}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -24,3 +24,9 @@ def test_oracle_rate_parallel_two_workers():
 def test_host_cores_positive():
     assert bench.host_cores() >= 1
 
+
+
+def test_host_cpu_record():
+    h = bench.host_cpu()
+    assert set(h) == {"machine", "cpu", "nproc"}
+    assert h["nproc"] >= 1 and h["machine"]
