@@ -51,10 +51,11 @@ def parse():
     p.add_argument("--n3", type=int, default=None, help="c5 only: interior nodes per axis (default 256)")
     p.add_argument("--ld-method", default="ld", choices=["ld", "pdipm"],
                    help="ld workload: lagged diffusivity (Algorithm 5) or primal-dual interior point (Algorithm 6)")
-    p.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "ld"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "ld", "medium"],
                    help="c2: the 576^2 forward+adjoint workload (default); c4: 48 Jacobian-vector "
                         "products over 288^2/432^2/576^2 grids in one graph; c5: the 3D 256^3 workload; "
-                        "ld: the inexact-Newton LD reconstruction (diagnostic lines)")
+                        "ld: the inexact-Newton LD reconstruction; medium: the gradient in sound speed and "
+                        "density, FP64, 168^2 grid (diagnostic lines)")
     return p.parse_args()
 
 
@@ -618,6 +619,51 @@ def run_ld(args):
     print(json.dumps(line), flush=True)
 
 
+def run_medium(args):
+    """Gradient of <w, H_a p0> in the sound speed and the density
+    (qpat_vjp_medium) and the tangent J_c dc + J_rho drho (qpat_jvp_medium),
+    FP64, on the 128^2 interior of the 2D circle-sensor workload (168^2 FFT
+    grid, 600 samples, 128 sensors).  A cell-step is one FFT-grid cell
+    advanced one time step by one sweep: the gradient runs the forward sweep
+    (keeping its history) and the reverse sweep, the tangent one paired sweep."""
+    import torch
+    from paper_1810_11685_gb300.binding import context_from_workload
+    w = phantoms.C1
+    nt = args.nt or w.nt
+    ctx = context_from_workload(w, precision="fp64", nt=nt)
+    c, rho, _ = phantoms.acoustic_medium(w)
+    rng = np.random.default_rng(w.seed + 5)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    p0 = dev(phantoms.smooth_p0(w, 2))
+    dc = dev(c * 0.05 * rng.standard_normal(c.shape))
+    drho = dev(rho * 0.05 * rng.standard_normal(rho.shape))
+    W = dev(rng.standard_normal((nt, w.n_sensors)))
+    ctx.vjp_medium(p0, W)
+    ctx.jvp_medium(p0, dc, drho)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        ts, l0 = [], ctx.stats()["launches"]
+        for _ in range(max(1, args.steps)):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)      # both calls synchronise the stream
+        return statistics.median(ts), (ctx.stats()["launches"] - l0) // max(1, args.steps)
+
+    tv, lv = timed(lambda: ctx.vjp_medium(p0, W))
+    tj, lj = timed(lambda: ctx.jvp_medium(p0, dc, drho))
+    G = w.grid * w.grid
+    line = {"metric": "medium gradient (c, rho): cell-steps/s", "value": G * nt * 2 / tv, "unit": UNIT,
+            "n_gpus": 1, "steps": max(1, args.steps), "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": f"2d {w.n}x{w.n} interior, {w.grid}x{w.grid} FFT grid, Nt={nt}, "
+                                   f"{w.n_sensors} sensors, y={w.y}, gradient in c and rho", "nt": nt},
+            "seconds_per_gradient": tv, "launches_per_gradient": lv, "us_per_launch_gradient": 1e6 * tv / lv,
+            "seconds_per_tangent": tj, "launches_per_tangent": lj, "us_per_launch_tangent": 1e6 * tj / lj,
+            "tangent_cell_steps_per_s": G * nt / tj}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "ours" and args.workload == "c4":
@@ -628,6 +674,9 @@ def main():
         return
     if args.impl == "ours" and args.workload == "ld":
         run_ld(args)
+        return
+    if args.impl == "ours" and args.workload == "medium":
+        run_medium(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -201,6 +201,26 @@ qpat_status qpat_acoustic_forward_ckpt(qpat_ctx* ctx, int batch, const void* p0,
                                        void* ckpt);
 qpat_status qpat_acoustic_resume(qpat_ctx* ctx, int batch, const void* ckpt, int K, int m, void* data);
 
+/* Derivatives of H_a in the medium: the sound speed c and the ambient
+ * density rho, both on the full FFT grid [ny][nx] (PML included), for one
+ * problem.  The paper's Discussion names the sound speed as the next
+ * unknown of a joint reconstruction; the derivative is taken of the
+ * discretised map (as H_a^* is, Section 3.2.4): c enters through C = c^2 of
+ * eq. num-p, tau and eta of eq. Twelve and the source of eq. s1; rho through
+ * rho-bar at the nodes (eqs. num-rho, num-p) and at the staggered points
+ * (eq. num-vel, the mean of two nodes).  c_ref and dt stay fixed.
+ * Needs a 2D QPAT_FP64 context (else EINVAL).  FP64 device buffers:
+ * p0 [n1][n0] interior initial pressure; dc, drho [ny][nx] (either may be
+ * NULL: zero); dP and w [nt][ns]; g_c, g_rho [ny][nx] (either may be NULL:
+ * not returned).  Workspace is allocated per call: the tangent loop needs
+ * about 27 grid fields, the adjoint 33 plus a history of 5 (lossless) or 7
+ * grid fields per time step.  Both calls synchronise the stream.
+ * qpat_jvp_medium: dP = J_c dc + J_rho drho at p0.
+ * qpat_vjp_medium: g_c = J_c^T w and g_rho = J_rho^T w at p0.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+qpat_status qpat_jvp_medium(qpat_ctx* ctx, const double* p0, const double* dc, const double* drho, double* dP);
+qpat_status qpat_vjp_medium(qpat_ctx* ctx, const double* p0, const double* w, double* g_c, double* g_rho);
+
 /* Groups: propagate several contexts (e.g. uneven grids of one Newton
  * inner loop) concurrently in one CUDA graph, each context's time loop a
  * parallel branch.  Contexts must live on one device and outlive the group.

@@ -111,6 +111,8 @@ def load():
         "qpat_set_kappa": [vp, vp],
         "qpat_jvp_kappa": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
         "qpat_vjp_kappa": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
+        "qpat_jvp_medium": [vp, vp, vp, vp, vp],
+        "qpat_vjp_medium": [vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -428,6 +430,29 @@ class Context:
                                                    _ptr(out)))
         return out
 
+    def jvp_medium(self, p0, dc=None, drho=None):
+        """qpat_jvp_medium: J_c dc + J_rho drho at the interior initial
+        pressure p0 (FP64 2D contexts); dc, drho on the full grid."""
+        import torch
+        p0 = self._in(p0, torch.float64, self.interior_shape)[0]
+        dc = None if dc is None else self._in(dc, torch.float64, self.grid_shape)[0]
+        drho = None if drho is None else self._in(drho, torch.float64, self.grid_shape)[0]
+        out = self._empty(self.nt, self.ns, dtype=torch.float64)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_jvp_medium(self._ptr, _ptr(p0), _ptr(dc), _ptr(drho), _ptr(out)))
+        return out
+
+    def vjp_medium(self, p0, w):
+        """qpat_vjp_medium: (J_c^T w, J_rho^T w) on the full grid."""
+        import torch
+        p0 = self._in(p0, torch.float64, self.interior_shape)[0]
+        w = self._in(w, torch.float64, (self.nt, self.ns))[0]
+        g_c = self._empty(*self.grid_shape, dtype=torch.float64)
+        g_rho = self._empty(*self.grid_shape, dtype=torch.float64)
+        self._stream()
+        _check(self._ptr, self._lib.qpat_vjp_medium(self._ptr, _ptr(p0), _ptr(w), _ptr(g_c), _ptr(g_rho)))
+        return g_c, g_rho
+
     def dot(self, a, b):
         a = a.contiguous()
         b = b.contiguous()
@@ -577,6 +602,14 @@ def qpat_jvp_kappa(ctx: Context, mu, dkappa, illum, phi0=None):
 
 def qpat_vjp_kappa(ctx: Context, mu, w, illum, phi0=None):
     return ctx.vjp_kappa(mu, w, illum, phi0)
+
+
+def qpat_jvp_medium(ctx: Context, p0, dc=None, drho=None):
+    return ctx.jvp_medium(p0, dc, drho)
+
+
+def qpat_vjp_medium(ctx: Context, p0, w):
+    return ctx.vjp_medium(p0, w)
 
 
 def qpat_sync(ctx: Context):

@@ -82,6 +82,16 @@ int ctx_fail(qpat_ctx* c, int st, const char* msg) {
   if (c) c->err = msg;
   return st;
 }
+const PropArgs<double>* ctx_tables64(const qpat_ctx* c, double* y, int* lossless, cudaStream_t* stream) {
+  if (!c || c->prec != QPAT_FP64 || c->dim != 2) return nullptr;
+  *y = c->cfg.y;
+  *lossless = c->cfg.lossless;
+  *stream = c->stream;
+  return &c->pd;
+}
+void ctx_add_launches(qpat_ctx* c, long long n) {
+  if (c) c->launches += n;
+}
 }  // namespace qpat
 
 namespace {

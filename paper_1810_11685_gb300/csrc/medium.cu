@@ -1,0 +1,168 @@
+// Derivatives of H_a in the sound speed and the density on the GPU: the C
+// entry points qpat_jvp_medium and qpat_vjp_medium over the loops of
+// medium_ops.cuh (tangent loop, and the forward loop with its whole history
+// kept in HBM followed by the exact transpose), run on an FP64 2D context's
+// own tables.  Every per-element functor is launched as a grid-stride
+// kernel on the context's stream.
+#include <vector>
+
+#include "medium_ops.cuh"
+#include "qpat.h"
+#include "qpat_internal.h"
+
+namespace qpat {
+// Defined in api.cu: the FP64 2D tables of a context (NULL for FP32 or 3D
+// contexts), the absorption exponent, the lossless flag and the stream.
+const PropArgs<double>* ctx_tables64(const ::qpat_ctx* c, double* y, int* lossless, cudaStream_t* stream);
+void ctx_add_launches(::qpat_ctx* c, long long n);
+}  // namespace qpat
+
+namespace {
+
+using namespace qpat;
+using namespace qpat::med;
+
+constexpr int kThreads = 256;
+constexpr long long kMaxBlocks = 152 * 16;
+
+template <class F>
+__global__ void __launch_bounds__(kThreads) for_each_kernel(const F f, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    f(i);
+}
+
+struct GpuEx {
+  cudaStream_t s;
+  long long launches = 0;
+  cudaError_t err = cudaSuccess;
+  template <class F>
+  void run(long long n, const F& f) {
+    if (n <= 0 || err != cudaSuccess) return;
+    long long blocks = (n + kThreads - 1) / kThreads;
+    if (blocks > kMaxBlocks) blocks = kMaxBlocks;
+    for_each_kernel<F><<<(unsigned)blocks, kThreads, 0, s>>>(f, n);
+    ++launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) err = e;
+  }
+};
+
+// Device workspace of one call, zero-filled, freed on every exit path.
+struct Arena {
+  std::vector<void*> ptrs;
+  cudaError_t err = cudaSuccess;
+  cudaStream_t s;
+  template <typename P>
+  P* get(long long count) {
+    void* v = nullptr;
+    if (err == cudaSuccess) err = cudaMalloc(&v, (size_t)(count > 0 ? count : 1) * sizeof(P));
+    if (err != cudaSuccess) return nullptr;
+    ptrs.push_back(v);
+    err = cudaMemsetAsync(v, 0, (size_t)(count > 0 ? count : 1) * sizeof(P), s);
+    return (P*)v;
+  }
+  ~Arena() {
+    cudaStreamSynchronize(s);
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+void copy_plan(const FFTPlan& in, Plan& out) {
+  out.L = in.L;
+  out.nstages = in.nstages;
+  for (int s = 0; s < in.nstages && s < med::kMaxStages; ++s) out.radix[s] = in.radix[s];
+}
+
+int tables_of(qpat_ctx* c, Tables& t, cudaStream_t* s) {
+  double y = 0.0;
+  int lossless = 0;
+  const PropArgs<double>* a = ctx_tables64(c, &y, &lossless, s);
+  if (!a) return ctx_fail(c, QPAT_EINVAL, "medium derivatives need a 2D FP64 context");
+  t.nx = a->nx; t.ny = a->ny; t.nxh = a->nxh; t.pml = a->pml; t.n0 = a->n0; t.n1 = a->n1; t.ns = a->ns;
+  t.nt = a->nt; t.lossless = lossless; t.dt = a->dt; t.y = y;
+  t.Cc = a->Cc; t.rho0 = a->rho0; t.dtrsx = a->dtrsx; t.dtrsy = a->dtrsy; t.tau = a->tau; t.eta = a->eta;
+  t.ax = a->ax; t.asx = a->asx; t.ay = a->ay; t.asy = a->asy;
+  t.kap = a->kap; t.kp1 = a->kp1; t.kp2 = a->kp2;
+  t.shxp = a->shxp; t.shxm = a->shxm; t.shyp = a->shyp; t.shym = a->shym; t.twx = a->twx; t.twy = a->twy;
+  t.sidx = a->sidx; t.sw = a->sw; t.rowptr = a->rowptr; t.pcol = a->pcol; t.pent = a->pent; t.esens = a->esens;
+  t.ew = a->ew;
+  copy_plan(a->px, t.px);
+  copy_plan(a->py, t.py);
+  if (a->px.nstages > med::kMaxStages || a->py.nstages > med::kMaxStages)
+    return ctx_fail(c, QPAT_EINVAL, "FFT plan has too many stages");
+  return QPAT_OK;
+}
+
+int finish(qpat_ctx* c, GpuEx& ex, Arena& w) {
+  ctx_add_launches(c, ex.launches);
+  cudaError_t e = ex.err != cudaSuccess ? ex.err : w.err;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ex.s);
+  if (e == cudaSuccess) return QPAT_OK;
+  return ctx_fail(c, e == cudaErrorMemoryAllocation ? QPAT_ENOMEM : QPAT_ECUDA, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" qpat_status qpat_jvp_medium(qpat_ctx* ctx, const double* p0, const double* dc, const double* drho,
+                                       double* dP) {
+  if (!ctx) return QPAT_EINVAL;
+  if (!p0 || !dP) return (qpat_status)ctx_fail(ctx, QPAT_EINVAL, "qpat_jvp_medium: p0 and dP are required");
+  Tables t{};
+  cudaStream_t s = nullptr;
+  int st = tables_of(ctx, t, &s);
+  if (st != QPAT_OK) return (qpat_status)st;
+  const long long G = (long long)t.nx * t.ny;
+  Arena w;
+  w.s = s;
+  GpuEx ex;
+  ex.s = s;
+  Fields f{};
+  for (double** q : {&f.P0, &f.p, &f.vx, &f.vy, &f.rx, &f.ry, &f.r, &f.u, &f.gx, &f.gy, &f.dx, &f.dy, &f.Yr, &f.Yu,
+                     &f.dp, &f.dvx, &f.dvy, &f.drx, &f.dry, &f.dr, &f.du, &f.dgx, &f.dgy, &f.ddx, &f.ddy, &f.YdR,
+                     &f.Ydu})
+    *q = w.get<double>(G);
+  double* zero = w.get<double>(G);
+  double2* Z[4];
+  for (double2*& z : Z) z = w.get<double2>(G);
+  if (w.err != cudaSuccess) return (qpat_status)finish(ctx, ex, w);
+  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1], Z[2], Z[3]};
+  ex.run(G, Embed{t, p0, f.P0});
+  jvp_loop(ex, t, S, f, dc ? dc : zero, drho ? drho : zero, dP);
+  return (qpat_status)finish(ctx, ex, w);
+}
+
+extern "C" qpat_status qpat_vjp_medium(qpat_ctx* ctx, const double* p0, const double* wts, double* g_c,
+                                       double* g_rho) {
+  if (!ctx) return QPAT_EINVAL;
+  if (!p0 || !wts) return (qpat_status)ctx_fail(ctx, QPAT_EINVAL, "qpat_vjp_medium: p0 and w are required");
+  Tables t{};
+  cudaStream_t s = nullptr;
+  int st = tables_of(ctx, t, &s);
+  if (st != QPAT_OK) return (qpat_status)st;
+  const long long G = (long long)t.nx * t.ny;
+  Arena w;
+  w.s = s;
+  GpuEx ex;
+  ex.s = s;
+  Fields f{};
+  for (double** q : {&f.P0, &f.p, &f.vx, &f.vy, &f.rx, &f.ry, &f.r, &f.u}) *q = w.get<double>(G);
+  Tape tp{};
+  for (double** q : {&tp.gx, &tp.gy, &tp.dx, &tp.dy, &tp.X}) *q = w.get<double>(G * t.nt);
+  if (!t.lossless) {
+    tp.Yr = w.get<double>(G * t.nt);
+    tp.Yu = w.get<double>(G * t.nt);
+  }
+  RevFields b{};
+  for (double** q : {&b.pb, &b.Cp, &b.e1, &b.e2, &b.t1, &b.ub, &b.rbx, &b.rby, &b.dbx, &b.dby, &b.vbx, &b.vby,
+                     &b.fx, &b.fy, &b.ex, &b.ey, &b.qb, &b.gC, &b.gtau, &b.geta, &b.grho, &b.grsx, &b.grsy})
+    *q = w.get<double>(G);
+  double* gc = g_c ? g_c : w.get<double>(G);
+  double* gr = g_rho ? g_rho : w.get<double>(G);
+  double2* Z[4];
+  for (double2*& z : Z) z = w.get<double2>(G);
+  if (w.err != cudaSuccess) return (qpat_status)finish(ctx, ex, w);
+  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1], Z[2], Z[3]};
+  ex.run(G, Embed{t, p0, f.P0});
+  vjp_loop(ex, t, S, f, tp, b, wts, gc, gr);
+  return (qpat_status)finish(ctx, ex, w);
+}

@@ -1,0 +1,553 @@
+// Derivatives of the acoustic data in the medium (sound speed c, ambient
+// density rho), FP64, 2D.
+//
+// The paper's Discussion names a joint reconstruction of the optical
+// coefficients and the sound speed as the next step.  Its Jacobian needs the
+// derivative of H_a in c and rho, taken here of the discretised map itself,
+// as for H_a^* (Section 3.2.4, Lemma 2):
+//
+//  * c enters through C = c^2 in eq. num-p, through tau = -2 alpha0 c^(y-1)
+//    and eta = 2 alpha0 c^y tan(pi y / 2) (eq. Twelve), so that
+//    d tau / dc = (y - 1) tau / c and d eta / dc = y eta / c, and through the
+//    source dt s_i = P0 / (2 d C) of eq. s1;
+//  * rho enters through rho-bar at the nodes (eq. num-rho and the absorption
+//    term of num-p) and through the staggered rho-bar_i of eq. num-vel, the
+//    mean of the two neighbouring nodes.
+//
+// c_ref (the k-space correction kappa and the PML scale) and dt are held
+// fixed: they are parameters of the discretisation.
+//
+// The tangent loop (jvp) steps the fields and their derivatives together.
+// The adjoint (vjp) runs the forward loop once, keeping the spectral
+// quantities each step's derivative needs (the whole history stays in HBM),
+// and then runs the exact transpose backwards.  Spectral operators are full
+// complex 2D FFTs: one launch per Stockham stage and axis, each thread one
+// radix-R butterfly of one grid line, then the symbol multiply (the
+// context's FP64 half-spectrum tables, mirrored), then the inverse FFT.
+//
+// Every per-element body is a functor callable on the host and the device;
+// the loops are templates over an executor that either launches a
+// grid-stride kernel or runs the functor in a host loop.
+#pragma once
+
+#include <math.h>
+#include <vector_types.h>
+
+#ifdef __CUDACC__
+#define QPAT_HD __host__ __device__ __forceinline__
+#else
+#define QPAT_HD inline
+#endif
+
+namespace qpat {
+namespace med {
+
+QPAT_HD double2 z(double a, double b) { double2 r; r.x = a; r.y = b; return r; }
+QPAT_HD double2 zadd(double2 a, double2 b) { return z(a.x + b.x, a.y + b.y); }
+QPAT_HD double2 zmul(double2 a, double2 b) { return z(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+QPAT_HD double2 zconj(double2 a) { return z(a.x, -a.y); }
+QPAT_HD double2 zscale(double2 a, double s) { return z(a.x * s, a.y * s); }
+
+constexpr int kMaxStages = 16;
+struct Plan {
+  int L = 0, nstages = 0;
+  int radix[kMaxStages] = {};
+};
+
+// Tables of one 2D FP64 context (device pointers on the GPU, host pointers
+// in a host run).  Layouts as the propagation passes use them:
+// full-grid diagonals [ny][nx]; PML per axis; k-space symbols on the half
+// spectrum [ny][nxh] divided by nx*ny; shift factors i k e^{+-i k dx/2}
+// ([nxh] along x, [ny] along y); twiddles W_L^m = e^{-2 pi i m / L};
+// sensors in gather form ([ns][4] indices and bilinear weights) and in the
+// row-wise scatter form (rowptr [ny+1], point columns, per-point entries).
+struct Tables {
+  int nx, ny, nxh, pml, n0, n1, ns, nt, lossless;
+  double dt, y;
+  const double *Cc, *rho0, *dtrsx, *dtrsy, *tau, *eta;
+  const double *ax, *asx, *ay, *asy;
+  const double *kap, *kp1, *kp2;
+  const double2 *shxp, *shxm, *shyp, *shym, *twx, *twy;
+  const int* sidx;
+  const double* sw;
+  const int *rowptr, *pcol, *pent, *esens;
+  const double* ew;
+  Plan px, py;
+};
+
+enum Symbol { kDPX = 0, kDPY = 1, kDMX = 2, kDMY = 3, kYDIS = 4, kYABS = 5 };
+
+// Symbol at spectral bin (j, i) of the full nx x ny spectrum.  Bins
+// i >= nxh mirror i' = nx - i: |k| is even in kx and i kx e^{+-i kx dx/2} is
+// Hermitian, so the value there is the conjugate of the stored one.
+QPAT_HD double2 symbol(const Tables& t, int which, int j, int i) {
+  const bool mir = i >= t.nxh;
+  const int im = mir ? t.nx - i : i;
+  const long long kt = (long long)j * t.nxh + im;
+  double2 s;
+  switch (which) {
+    case kDPX: s = t.shxp[im]; if (mir) s = zconj(s); return zscale(s, t.kap[kt]);
+    case kDMX: s = t.shxm[im]; if (mir) s = zconj(s); return zscale(s, t.kap[kt]);
+    case kDPY: return zscale(t.shyp[j], t.kap[kt]);
+    case kDMY: return zscale(t.shym[j], t.kap[kt]);
+    case kYDIS: return z(t.kp1[kt], 0.0);
+    default: return z(t.kp2[kt], 0.0);
+  }
+}
+
+// One Stockham autosort stage (decimation in time) of radix R on every grid
+// line along one axis: thread (line, j), j < L/R, takes the R points
+// j + r L/R, multiplies them by the twiddles W_{Ns R}^{r k} (k = j mod Ns),
+// applies the R-point DFT and writes the results to
+// (j / Ns) Ns R + k + s Ns, s < R.  Lines along x are grid rows (unit
+// stride), along y grid columns (stride nx).  inv conjugates every twiddle
+// (the unnormalised inverse DFT).
+struct FftStage {
+  const double2* src;
+  double2* dst;
+  const double2* tw;
+  int L, R, Ns, along_x, nx, inv;
+  QPAT_HD void operator()(long long t) const {
+    const int m = L / R;
+    const long long line = t / m;
+    const int j = (int)(t - line * m);
+    const long long base = along_x ? line * (long long)L : line;
+    const long long es = along_x ? 1 : nx;
+    const int k = j % Ns;
+    const int tstep = L / (Ns * R);
+    double2 v[8];
+    for (int r = 0; r < R; ++r) {
+      double2 w = tw[(r * k * tstep) % L];
+      if (inv) w = zconj(w);
+      v[r] = zmul(src[base + (long long)(j + r * m) * es], w);
+    }
+    const int o = (j / Ns) * Ns * R + k;
+    const int rstep = L / R;
+    for (int s = 0; s < R; ++s) {
+      double2 acc = z(0.0, 0.0);
+      for (int r = 0; r < R; ++r) {
+        double2 w = tw[((r * s) % R) * rstep];
+        if (inv) w = zconj(w);
+        acc = zadd(acc, zmul(v[r], w));
+      }
+      dst[base + (long long)(o + s * Ns) * es] = acc;
+    }
+  }
+};
+
+struct LoadReal {     // Z = f + 0 i
+  const double* f;
+  double2* Z;
+  QPAT_HD void operator()(long long g) const { Z[g] = z(f[g], 0.0); }
+};
+struct CopyZ {
+  const double2* a;
+  double2* b;
+  QPAT_HD void operator()(long long g) const { b[g] = a[g]; }
+};
+// out = alpha Re(Z), or out += alpha Re(Z) when acc
+struct StoreReal {
+  const double2* Z;
+  double* out;
+  double alpha;
+  int acc;
+  QPAT_HD void operator()(long long g) const {
+    const double v = alpha * Z[g].x;
+    out[g] = acc ? out[g] + v : v;
+  }
+};
+// Zo = sum_q sym_q (conjugated when conj) * Z_q, q < nq (nq = 1 or 2)
+struct Combine {
+  Tables t;
+  const double2* Z0;
+  const double2* Z1;
+  double2* Zo;
+  int s0, s1, nq, conj;
+  QPAT_HD void operator()(long long g) const {
+    const int i = (int)(g % t.nx), j = (int)(g / t.nx);
+    double2 a = symbol(t, s0, j, i);
+    if (conj) a = zconj(a);
+    double2 r = zmul(a, Z0[g]);
+    if (nq > 1) {
+      double2 b = symbol(t, s1, j, i);
+      if (conj) b = zconj(b);
+      r = zadd(r, zmul(b, Z1[g]));
+    }
+    Zo[g] = r;
+  }
+};
+
+// Interior p0 [n1][n0] -> full grid, zero in the PML.
+struct Embed {
+  Tables t;
+  const double* p0;
+  double* P;
+  QPAT_HD void operator()(long long g) const {
+    const int i = (int)(g % t.nx) - t.pml, j = (int)(g / t.nx) - t.pml;
+    P[g] = (i >= 0 && i < t.n0 && j >= 0 && j < t.n1) ? p0[(long long)j * t.n0 + i] : 0.0;
+  }
+};
+
+// Staggered density perturbation of axis x / y at node g: the mean of the
+// node and its + neighbour (periodic), as for rho-bar_i itself.
+QPAT_HD double stag_x(const Tables& t, const double* f, long long g) {
+  const int i = (int)(g % t.nx);
+  return 0.5 * (f[g] + f[g - i + (i + 1) % t.nx]);
+}
+QPAT_HD double stag_y(const Tables& t, const double* f, long long g) {
+  const long long G = (long long)t.nx * t.ny;
+  const long long gn = g + t.nx;
+  return 0.5 * (f[g] + f[gn >= G ? gn - G : gn]);
+}
+// Transpose of stag_x / stag_y: the mean of the node and its - neighbour.
+QPAT_HD double stag_x_T(const Tables& t, const double* f, long long g) {
+  const int i = (int)(g % t.nx);
+  return 0.5 * (f[g] + f[g - i + (i + t.nx - 1) % t.nx]);
+}
+QPAT_HD double stag_y_T(const Tables& t, const double* f, long long g) {
+  const long long G = (long long)t.nx * t.ny;
+  const long long gp = g - t.nx;
+  return 0.5 * (f[g] + f[gp < 0 ? gp + G : gp]);
+}
+
+// Sensor gather of one time sample: out[s] = sum of the 4 bilinear corners.
+struct Gather {
+  Tables t;
+  const double* f;
+  double* out;
+  QPAT_HD void operator()(long long s) const {
+    double a = 0.0;
+    for (int q = 0; q < 4; ++q) a += t.sw[4 * s + q] * f[t.sidx[4 * s + q]];
+    out[s] = a;
+  }
+};
+// Transposed sensor gather, one thread per grid row: f += M^T w.
+struct Scatter {
+  Tables t;
+  const double* w;
+  double* f;
+  QPAT_HD void operator()(long long row) const {
+    for (int p = t.rowptr[row]; p < t.rowptr[row + 1]; ++p) {
+      double a = 0.0;
+      for (int e = t.pent[p]; e < t.pent[p + 1]; ++e) a += t.ew[e] * w[t.esens[e]];
+      f[row * t.nx + t.pcol[p]] += a;
+    }
+  }
+};
+
+}  // namespace med
+}  // namespace qpat
+
+namespace qpat {
+namespace med {
+
+// ---------------------------------------------------------------------------
+// Per-cell steps of the loop (2D: axis x = array axis 1, axis y = axis 0)
+// ---------------------------------------------------------------------------
+
+// eq. num-vel, and along (dc, drho) its tangent when dvx != nullptr:
+// v_i = A_i (A_i v_i - (dt / rho_i) g_i), d(dt / rho_i) = -(dt / rho_i)^2 drho_i / dt.
+struct Vel {
+  Tables t;
+  const double *gx, *gy, *dgx, *dgy, *drho;
+  double *vx, *vy, *dvx, *dvy;
+  QPAT_HD void operator()(long long g) const {
+    const int i = (int)(g % t.nx), j = (int)(g / t.nx);
+    const double ax = t.asx[i], ay = t.asy[j], bx = t.dtrsx[g], by = t.dtrsy[g];
+    vx[g] = ax * (ax * vx[g] - bx * gx[g]);
+    vy[g] = ay * (ay * vy[g] - by * gy[g]);
+    if (dvx) {
+      dvx[g] = ax * (ax * dvx[g] - bx * dgx[g] + bx * bx / t.dt * stag_x(t, drho, g) * gx[g]);
+      dvy[g] = ay * (ay * dvy[g] - by * dgy[g] + by * by / t.dt * stag_y(t, drho, g) * gy[g]);
+    }
+  }
+};
+
+// eq. num-rho with the source of eq. s1 (src: n = -1, 0), the sums
+// r = sum rho_i and u = sum A_i rho divergence_i that eq. num-p needs, and the
+// tangents when drx != nullptr.  dt s_i = P0 / (4 C), so d(dt s_i) = -dt s_i dC / C.
+struct Rho {
+  Tables t;
+  const double *dx, *dy, *ddx, *ddy, *drho, *dc, *P0;
+  int src;
+  double *rx, *ry, *r, *u, *drx, *dry, *dr, *du;
+  QPAT_HD void operator()(long long g) const {
+    const int i = (int)(g % t.nx), j = (int)(g / t.nx);
+    const double ax = t.ax[i], ay = t.ay[j], r0 = t.rho0[g], dt = t.dt;
+    double q = 0.0, dq = 0.0;
+    if (src) {
+      const double C = t.Cc[g];
+      q = P0[g] / (4.0 * C);
+      if (drx) dq = -q * 2.0 * sqrt(C) * dc[g] / C;
+    }
+    rx[g] = ax * (ax * rx[g] - dt * r0 * dx[g]) + q;
+    ry[g] = ay * (ay * ry[g] - dt * r0 * dy[g]) + q;
+    r[g] = rx[g] + ry[g];
+    if (!t.lossless) u[g] = ax * r0 * dx[g] + ay * r0 * dy[g];
+    if (drx) {
+      const double dr0 = drho[g];
+      drx[g] = ax * (ax * drx[g] - dt * (dr0 * dx[g] + r0 * ddx[g])) + dq;
+      dry[g] = ay * (ay * dry[g] - dt * (dr0 * dy[g] + r0 * ddy[g])) + dq;
+      dr[g] = drx[g] + dry[g];
+      if (!t.lossless) du[g] = ax * (dr0 * dx[g] + r0 * ddx[g]) + ay * (dr0 * dy[g] + r0 * ddy[g]);
+    }
+  }
+};
+
+// eq. num-p: p = C X, X = r (lossless) or r - eta Y_dis r + tau Y_abs u; keeps X
+// when Xo != nullptr and forms the tangent dp = dC X + C dX when dp != nullptr.
+struct Pres {
+  Tables t;
+  const double *r, *Yr, *Yu, *dr, *YdR, *Ydu, *dc;
+  double *p, *Xo, *dp;
+  QPAT_HD void operator()(long long g) const {
+    const double C = t.Cc[g];
+    double X = r[g];
+    if (!t.lossless) X += -t.eta[g] * Yr[g] + t.tau[g] * Yu[g];
+    p[g] = C * X;
+    if (Xo) Xo[g] = X;
+    if (dp) {
+      const double c = sqrt(C), dcg = dc[g];
+      double dX = dr[g];
+      if (!t.lossless) {
+        const double dtau = (t.y - 1.0) * t.tau[g] / c * dcg, deta = t.y * t.eta[g] / c * dcg;
+        dX += -deta * Yr[g] - t.eta[g] * YdR[g] + dtau * Yu[g] + t.tau[g] * Ydu[g];
+      }
+      dp[g] = 2.0 * c * dcg * X + C * dX;
+    }
+  }
+};
+
+// Reverse of eq. num-p at one step: pb is the adjoint of p_(n+1) (sensor
+// scatter already added).  gC += pb X; Cp = C pb; lossy: g_eta -= Cp Y_dis r,
+// g_tau += Cp Y_abs u and the two fields eta Cp, tau Cp whose transposed
+// spectral products come next.
+struct RevP {
+  Tables t;
+  const double *pb, *X, *Yr, *Yu;
+  double *gC, *geta, *gtau, *Cp, *e1, *e2;
+  QPAT_HD void operator()(long long g) const {
+    const double cp = t.Cc[g] * pb[g];
+    gC[g] += pb[g] * X[g];
+    Cp[g] = cp;
+    if (!t.lossless) {
+      geta[g] -= cp * Yr[g];
+      gtau[g] += cp * Yu[g];
+      e1[g] = t.eta[g] * cp;
+      e2[g] = t.tau[g] * cp;
+    }
+  }
+};
+
+// Reverse of eq. num-rho (and of the u term of num-p): with
+// rtot_i = rb_i + (Cp - Y_dis^T eta Cp) and ub = Y_abs^T tau Cp,
+// db_i = rho A_i (ub - dt rtot_i), g_rho += A_i div_i (ub - dt rtot_i),
+// rb_i = A_i^2 rtot_i, and the source adjoint qb += sum rtot_i (src).
+struct RevRho {
+  Tables t;
+  const double *Cp, *t1, *ub, *dx, *dy;
+  int src;
+  double *rbx, *rby, *dbx, *dby, *grho, *qb;
+  QPAT_HD void operator()(long long g) const {
+    const int i = (int)(g % t.nx), j = (int)(g / t.nx);
+    const double ax = t.ax[i], ay = t.ay[j], r0 = t.rho0[g], dt = t.dt;
+    double rp = Cp[g], u = 0.0;
+    if (!t.lossless) {
+      rp -= t1[g];
+      u = ub[g];
+    }
+    const double tx = rbx[g] + rp, ty = rby[g] + rp;
+    const double hx = u - dt * tx, hy = u - dt * ty;
+    dbx[g] = r0 * ax * hx;
+    dby[g] = r0 * ay * hy;
+    grho[g] += ax * dx[g] * hx + ay * dy[g] * hy;
+    rbx[g] = ax * ax * tx;
+    rby[g] = ay * ay * ty;
+    if (src) qb[g] += tx + ty;
+  }
+};
+
+// Reverse of eq. num-vel: vtot_i = vb_i + (D-_i)^T db_i;
+// g_rho_i += vtot_i A_i (dt / rho_i)^2 / dt g_i (g_i = D+_i p of the forward
+// step); vb_i = A_i^2 vtot_i; f_i = A_i (dt / rho_i) vtot_i, whose transposed
+// D+_i products make the adjoint of p_n (with a minus sign).
+struct RevVel {
+  Tables t;
+  const double *ex, *ey, *gx, *gy;
+  double *vbx, *vby, *grsx, *grsy, *fx, *fy;
+  QPAT_HD void operator()(long long g) const {
+    const int i = (int)(g % t.nx), j = (int)(g / t.nx);
+    const double ax = t.asx[i], ay = t.asy[j], bx = t.dtrsx[g], by = t.dtrsy[g];
+    const double tx = vbx[g] + ex[g], ty = vby[g] + ey[g];
+    grsx[g] += tx * ax * bx * bx / t.dt * gx[g];
+    grsy[g] += ty * ay * by * by / t.dt * gy[g];
+    vbx[g] = ax * ax * tx;
+    vby[g] = ay * ay * ty;
+    fx[g] = ax * bx * tx;
+    fy[g] = ay * by * ty;
+  }
+};
+
+// The gradients in c and rho on the full grid: the source term of eq. s1
+// (dt s_i = P0 / (4 C)), the chain rule through C = c^2, tau and eta, and
+// the transposed staggered means.
+struct Finish {
+  Tables t;
+  const double *gC, *gtau, *geta, *qb, *P0, *grsx, *grsy, *grho;
+  double *g_c, *g_rho;
+  QPAT_HD void operator()(long long g) const {
+    const double C = t.Cc[g], c = sqrt(C);
+    const double gc = gC[g] - qb[g] * P0[g] / (4.0 * C) / C;
+    double v = 2.0 * c * gc;
+    if (!t.lossless) v += (t.y - 1.0) * t.tau[g] / c * gtau[g] + t.y * t.eta[g] / c * geta[g];
+    g_c[g] = v;
+    g_rho[g] = grho[g] + stag_x_T(t, grsx, g) + stag_y_T(t, grsy, g);
+  }
+};
+
+}  // namespace med
+}  // namespace qpat
+
+namespace qpat {
+namespace med {
+
+// Spectral products F^-1 { S F{f} } on the full complex spectrum.  Z0, Z1 hold
+// forward spectra, Zc the combined product, Zt is the Stockham scratch.
+template <class Ex>
+struct Spectral {
+  Ex& ex;
+  const Tables& t;
+  long long G;
+  double2 *Z0, *Z1, *Zc, *Zt;
+
+  void fft(double2* Z, int inv) {
+    double2* src = Z;
+    double2* dst = Zt;
+    for (int ax = 0; ax < 2; ++ax) {
+      const Plan& P = ax == 0 ? t.px : t.py;
+      const long long lines = ax == 0 ? t.ny : t.nx;
+      int Ns = 1;
+      for (int s = 0; s < P.nstages; ++s) {
+        const int R = P.radix[s];
+        ex.run(lines * (P.L / R), FftStage{src, dst, ax == 0 ? t.twx : t.twy, P.L, R, Ns, ax == 0, t.nx, inv});
+        double2* tmp = src;
+        src = dst;
+        dst = tmp;
+        Ns *= R;
+      }
+    }
+    if (src != Z) ex.run(G, CopyZ{src, Z});
+  }
+  void forward(const double* f, double2* Z) {
+    ex.run(G, LoadReal{f, Z});
+    fft(Z, 0);
+  }
+  // out = alpha Re F^-1{ sum_q S_q Z_q } (+= when acc); conj: the transposed operators
+  void apply(const double2* A, int sa, const double2* B, int sb, int nq, int conj, double* out, double alpha,
+             int acc) {
+    ex.run(G, Combine{t, A, B, Zc, sa, sb, nq, conj});
+    fft(Zc, 1);
+    ex.run(G, StoreReal{Zc, out, alpha, acc});
+  }
+  // out = F^-1{ S F{f} } (or with conj(S))
+  void op(const double* f, int sym, int conj, double* out) {
+    forward(f, Z0);
+    apply(Z0, sym, nullptr, 0, 1, conj, out, 1.0, 0);
+  }
+};
+
+// Fields of one loop, all [G] doubles (tape fields [nt][G]).
+struct Fields {
+  double *P0, *p, *vx, *vy, *rx, *ry, *r, *u;
+  double *gx, *gy, *dx, *dy, *Yr, *Yu, *X;
+  double *dp, *dvx, *dvy, *drx, *dry, *dr, *du, *dgx, *dgy, *ddx, *ddy, *YdR, *Ydu;
+};
+
+// Tangent loop: dP[n] = M dp_n for n = 0 .. nt-1 along (dc, drho), both full
+// grid.  The loop runs n = -1 .. nt-2 from zero fields (samples n + 1).
+template <class Ex>
+void jvp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const double* dc, const double* drho,
+              double* dP) {
+  const long long G = (long long)t.nx * t.ny;
+  for (int it = 0; it < t.nt; ++it) {
+    const int src = it <= 1;
+    S.forward(f.p, S.Z0);
+    S.apply(S.Z0, kDPX, nullptr, 0, 1, 0, f.gx, 1.0, 0);
+    S.apply(S.Z0, kDPY, nullptr, 0, 1, 0, f.gy, 1.0, 0);
+    S.forward(f.dp, S.Z0);
+    S.apply(S.Z0, kDPX, nullptr, 0, 1, 0, f.dgx, 1.0, 0);
+    S.apply(S.Z0, kDPY, nullptr, 0, 1, 0, f.dgy, 1.0, 0);
+    ex.run(G, Vel{t, f.gx, f.gy, f.dgx, f.dgy, drho, f.vx, f.vy, f.dvx, f.dvy});
+    S.op(f.vx, kDMX, 0, f.dx);
+    S.op(f.vy, kDMY, 0, f.dy);
+    S.op(f.dvx, kDMX, 0, f.ddx);
+    S.op(f.dvy, kDMY, 0, f.ddy);
+    ex.run(G, Rho{t, f.dx, f.dy, f.ddx, f.ddy, drho, dc, f.P0, src, f.rx, f.ry, f.r, f.u, f.drx, f.dry, f.dr, f.du});
+    if (!t.lossless) {
+      S.op(f.r, kYDIS, 0, f.Yr);
+      S.op(f.u, kYABS, 0, f.Yu);
+      S.op(f.dr, kYDIS, 0, f.YdR);
+      S.op(f.du, kYABS, 0, f.Ydu);
+    }
+    ex.run(G, Pres{t, f.r, f.Yr, f.Yu, f.dr, f.YdR, f.Ydu, dc, f.p, nullptr, f.dp});
+    ex.run(t.ns, Gather{t, f.dp, dP + (long long)it * t.ns});
+  }
+}
+
+// Forward loop keeping, per step, g_i = D+_i p_n, the divergences D-_i v_i,
+// X = p_(n+1) / C and (lossy) Y_dis r, Y_abs u: the tape of the adjoint.
+struct Tape {
+  double *gx, *gy, *dx, *dy, *X, *Yr, *Yu;   // each [nt][G]
+};
+
+// Reverse-loop fields, all [G]
+struct RevFields {
+  double *pb, *Cp, *e1, *e2, *t1, *ub, *rbx, *rby, *dbx, *dby, *vbx, *vby, *fx, *fy, *ex, *ey, *qb;
+  double *gC, *gtau, *geta, *grho, *grsx, *grsy;
+};
+
+template <class Ex>
+void vjp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const Tape& tp, const RevFields& b,
+              const double* W, double* g_c, double* g_rho) {
+  const long long G = (long long)t.nx * t.ny;
+  for (int it = 0; it < t.nt; ++it) {
+    const long long o = (long long)it * G;
+    S.forward(f.p, S.Z0);
+    S.apply(S.Z0, kDPX, nullptr, 0, 1, 0, tp.gx + o, 1.0, 0);
+    S.apply(S.Z0, kDPY, nullptr, 0, 1, 0, tp.gy + o, 1.0, 0);
+    ex.run(G, Vel{t, tp.gx + o, tp.gy + o, nullptr, nullptr, nullptr, f.vx, f.vy, nullptr, nullptr});
+    S.op(f.vx, kDMX, 0, tp.dx + o);
+    S.op(f.vy, kDMY, 0, tp.dy + o);
+    ex.run(G, Rho{t, tp.dx + o, tp.dy + o, nullptr, nullptr, nullptr, nullptr, f.P0, it <= 1, f.rx, f.ry, f.r, f.u,
+                  nullptr, nullptr, nullptr, nullptr});
+    double* Yr = t.lossless ? nullptr : tp.Yr + o;
+    double* Yu = t.lossless ? nullptr : tp.Yu + o;
+    if (!t.lossless) {
+      S.op(f.r, kYDIS, 0, Yr);
+      S.op(f.u, kYABS, 0, Yu);
+    }
+    ex.run(G, Pres{t, f.r, Yr, Yu, nullptr, nullptr, nullptr, nullptr, f.p, tp.X + o, nullptr});
+  }
+  for (int it = t.nt - 1; it >= 0; --it) {
+    const long long o = (long long)it * G;
+    const double* Yr = t.lossless ? nullptr : tp.Yr + o;
+    const double* Yu = t.lossless ? nullptr : tp.Yu + o;
+    ex.run(t.ny, Scatter{t, W + (long long)it * t.ns, b.pb});
+    ex.run(G, RevP{t, b.pb, tp.X + o, Yr, Yu, b.gC, b.geta, b.gtau, b.Cp, b.e1, b.e2});
+    if (!t.lossless) {
+      S.op(b.e1, kYDIS, 1, b.t1);
+      S.op(b.e2, kYABS, 1, b.ub);
+    }
+    ex.run(G, RevRho{t, b.Cp, b.t1, b.ub, tp.dx + o, tp.dy + o, it <= 1, b.rbx, b.rby, b.dbx, b.dby, b.grho, b.qb});
+    S.op(b.dbx, kDMX, 1, b.ex);
+    S.op(b.dby, kDMY, 1, b.ey);
+    ex.run(G, RevVel{t, b.ex, b.ey, tp.gx + o, tp.gy + o, b.vbx, b.vby, b.grsx, b.grsy, b.fx, b.fy});
+    S.forward(b.fx, S.Z0);
+    S.forward(b.fy, S.Z1);
+    S.apply(S.Z0, kDPX, S.Z1, kDPY, 2, 1, b.pb, -1.0, 0);
+  }
+  ex.run(G, Finish{t, b.gC, b.gtau, b.geta, b.qb, f.P0, b.grsx, b.grsy, b.grho, g_c, g_rho});
+}
+
+}  // namespace med
+}  // namespace qpat
