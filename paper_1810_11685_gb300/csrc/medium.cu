@@ -122,10 +122,10 @@ extern "C" qpat_status qpat_jvp_medium(qpat_ctx* ctx, const double* p0, const do
                      &f.Ydu})
     *q = w.get<double>(G);
   double* zero = w.get<double>(G);
-  double2* Z[4];
-  for (double2*& z : Z) z = w.get<double2>(G);
+  double2* Z[3];
+  for (double2*& z : Z) z = w.get<double2>(kMaxBatch * G);
   if (w.err != cudaSuccess) return (qpat_status)finish(ctx, ex, w);
-  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1], Z[2], Z[3]};
+  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1], Z[2]};
   ex.run(G, Embed{t, p0, f.P0});
   jvp_loop(ex, t, S, f, dc ? dc : zero, drho ? drho : zero, dP);
   return (qpat_status)finish(ctx, ex, w);
@@ -158,10 +158,10 @@ extern "C" qpat_status qpat_vjp_medium(qpat_ctx* ctx, const double* p0, const do
     *q = w.get<double>(G);
   double* gc = g_c ? g_c : w.get<double>(G);
   double* gr = g_rho ? g_rho : w.get<double>(G);
-  double2* Z[4];
-  for (double2*& z : Z) z = w.get<double2>(G);
+  double2* Z[3];
+  for (double2*& z : Z) z = w.get<double2>(kMaxBatch * G);
   if (w.err != cudaSuccess) return (qpat_status)finish(ctx, ex, w);
-  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1], Z[2], Z[3]};
+  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1], Z[2]};
   ex.run(G, Embed{t, p0, f.P0});
   vjp_loop(ex, t, S, f, tp, b, wts, gc, gr);
   return (qpat_status)finish(ctx, ex, w);

@@ -33,6 +33,8 @@
 #include <math.h>
 #include <vector_types.h>
 
+#include <initializer_list>
+
 #ifdef __CUDACC__
 #define QPAT_HD __host__ __device__ __forceinline__
 #else
@@ -96,22 +98,26 @@ QPAT_HD double2 symbol(const Tables& t, int which, int j, int i) {
 }
 
 // One Stockham autosort stage (decimation in time) of radix R on every grid
-// line along one axis: thread (line, j), j < L/R, takes the R points
-// j + r L/R, multiplies them by the twiddles W_{Ns R}^{r k} (k = j mod Ns),
-// applies the R-point DFT and writes the results to
-// (j / Ns) Ns R + k + s Ns, s < R.  Lines along x are grid rows (unit
-// stride), along y grid columns (stride nx).  inv conjugates every twiddle
-// (the unnormalised inverse DFT).
+// line along one axis of nb fields stored one after another (G points
+// each): thread (field, line, j), j < L/R, takes the R points j + r L/R,
+// multiplies them by the twiddles W_{Ns R}^{r k} (k = j mod Ns), applies the
+// R-point DFT and writes the results to (j / Ns) Ns R + k + s Ns, s < R.
+// Lines along x are grid rows (unit stride), along y grid columns (stride
+// nx).  inv conjugates every twiddle (the unnormalised inverse DFT).
 struct FftStage {
   const double2* src;
   double2* dst;
   const double2* tw;
   int L, R, Ns, along_x, nx, inv;
+  long long lines, G;
   QPAT_HD void operator()(long long t) const {
     const int m = L / R;
-    const long long line = t / m;
-    const int j = (int)(t - line * m);
-    const long long base = along_x ? line * (long long)L : line;
+    const long long per = lines * m;
+    const long long b = t / per;
+    const long long tt = t - b * per;
+    const long long line = tt / m;
+    const int j = (int)(tt - line * m);
+    const long long base = b * G + (along_x ? line * (long long)L : line);
     const long long es = along_x ? 1 : nx;
     const int k = j % Ns;
     const int tstep = L / (Ns * R);
@@ -135,45 +141,55 @@ struct FftStage {
   }
 };
 
-struct LoadReal {     // Z = f + 0 i
-  const double* f;
+constexpr int kMaxBatch = 4;
+
+// Z[b G + g] = f_b[g] + 0 i for nb fields
+struct LoadReal {
+  const double* f[kMaxBatch];
   double2* Z;
-  QPAT_HD void operator()(long long g) const { Z[g] = z(f[g], 0.0); }
+  long long G;
+  QPAT_HD void operator()(long long t) const {
+    const long long b = t / G;
+    Z[t] = z(f[b][t - b * G], 0.0);
+  }
 };
 struct CopyZ {
   const double2* a;
   double2* b;
   QPAT_HD void operator()(long long g) const { b[g] = a[g]; }
 };
-// out = alpha Re(Z), or out += alpha Re(Z) when acc
+// out_b = alpha Re(Z[b G + .]), or out_b += alpha Re(...) when acc
 struct StoreReal {
   const double2* Z;
-  double* out;
+  double* out[kMaxBatch];
   double alpha;
   int acc;
-  QPAT_HD void operator()(long long g) const {
-    const double v = alpha * Z[g].x;
-    out[g] = acc ? out[g] + v : v;
+  long long G;
+  QPAT_HD void operator()(long long t) const {
+    const long long b = t / G, g = t - b * G;
+    const double v = alpha * Z[t].x;
+    out[b][g] = acc ? out[b][g] + v : v;
   }
 };
-// Zo = sum_q sym_q (conjugated when conj) * Z_q, q < nq (nq = 1 or 2)
+// Output o: Zo[o G + g] = sum over its nterm[o] terms q of sym[o][q]
+// (conjugated when conj) * Zi[in[o][q] G + g].
 struct Combine {
   Tables t;
-  const double2* Z0;
-  const double2* Z1;
+  const double2* Zi;
   double2* Zo;
-  int s0, s1, nq, conj;
-  QPAT_HD void operator()(long long g) const {
+  int nterm[kMaxBatch], in[kMaxBatch][2], sym[kMaxBatch][2];
+  int conj;
+  long long G;
+  QPAT_HD void operator()(long long u) const {
+    const long long o = u / G, g = u - o * G;
     const int i = (int)(g % t.nx), j = (int)(g / t.nx);
-    double2 a = symbol(t, s0, j, i);
-    if (conj) a = zconj(a);
-    double2 r = zmul(a, Z0[g]);
-    if (nq > 1) {
-      double2 b = symbol(t, s1, j, i);
-      if (conj) b = zconj(b);
-      r = zadd(r, zmul(b, Z1[g]));
+    double2 r = z(0.0, 0.0);
+    for (int q = 0; q < nterm[o]; ++q) {
+      double2 a = symbol(t, sym[o][q], j, i);
+      if (conj) a = zconj(a);
+      r = zadd(r, zmul(a, Zi[in[o][q] * G + g]));
     }
-    Zo[g] = r;
+    Zo[u] = r;
   }
 };
 
@@ -411,16 +427,17 @@ struct Finish {
 namespace qpat {
 namespace med {
 
-// Spectral products F^-1 { S F{f} } on the full complex spectrum.  Z0, Z1 hold
-// forward spectra, Zc the combined product, Zt is the Stockham scratch.
+// Spectral products F^-1 { S F{f} } on the full complex spectrum, several
+// fields per launch.  Zi holds up to kMaxBatch forward spectra, Zc the
+// combined products, Zt is the Stockham scratch (each kMaxBatch * G).
 template <class Ex>
 struct Spectral {
   Ex& ex;
   const Tables& t;
   long long G;
-  double2 *Z0, *Z1, *Zc, *Zt;
+  double2 *Zi, *Zc, *Zt;
 
-  void fft(double2* Z, int inv) {
+  void fft(double2* Z, int nb, int inv) {
     double2* src = Z;
     double2* dst = Zt;
     for (int ax = 0; ax < 2; ++ax) {
@@ -429,30 +446,56 @@ struct Spectral {
       int Ns = 1;
       for (int s = 0; s < P.nstages; ++s) {
         const int R = P.radix[s];
-        ex.run(lines * (P.L / R), FftStage{src, dst, ax == 0 ? t.twx : t.twy, P.L, R, Ns, ax == 0, t.nx, inv});
+        ex.run(nb * lines * (P.L / R),
+               FftStage{src, dst, ax == 0 ? t.twx : t.twy, P.L, R, Ns, ax == 0, t.nx, inv, lines, G});
         double2* tmp = src;
         src = dst;
         dst = tmp;
         Ns *= R;
       }
     }
-    if (src != Z) ex.run(G, CopyZ{src, Z});
+    if (src != Z) ex.run(nb * G, CopyZ{src, Z});
   }
-  void forward(const double* f, double2* Z) {
-    ex.run(G, LoadReal{f, Z});
-    fft(Z, 0);
+  // spectra of the fields f[0..nb) into Zi
+  void forward(std::initializer_list<const double*> f) {
+    LoadReal op{};
+    int nb = 0;
+    for (const double* p : f) op.f[nb++] = p;
+    op.Z = Zi;
+    op.G = G;
+    ex.run(nb * G, op);
+    fft(Zi, nb, 0);
   }
-  // out = alpha Re F^-1{ sum_q S_q Z_q } (+= when acc); conj: the transposed operators
-  void apply(const double2* A, int sa, const double2* B, int sb, int nq, int conj, double* out, double alpha,
-             int acc) {
-    ex.run(G, Combine{t, A, B, Zc, sa, sb, nq, conj});
-    fft(Zc, 1);
-    ex.run(G, StoreReal{Zc, out, alpha, acc});
-  }
-  // out = F^-1{ S F{f} } (or with conj(S))
-  void op(const double* f, int sym, int conj, double* out) {
-    forward(f, Z0);
-    apply(Z0, sym, nullptr, 0, 1, conj, out, 1.0, 0);
+  // outputs o: out[o] = alpha Re F^-1{ sum_q S_(o,q) Zi[in_(o,q)] }; terms
+  // list (in, symbol) pairs per output; conj: the transposed operators.
+  void apply(std::initializer_list<std::initializer_list<int>> terms, int conj,
+             std::initializer_list<double*> out, double alpha) {
+    Combine cb{};
+    cb.t = t;
+    cb.Zi = Zi;
+    cb.Zo = Zc;
+    cb.conj = conj;
+    cb.G = G;
+    int no = 0;
+    for (const auto& tl : terms) {
+      int q = 0, k = 0;
+      for (int v : tl) {
+        if (k % 2 == 0) cb.in[no][q] = v;
+        else cb.sym[no][q++] = v;
+        ++k;
+      }
+      cb.nterm[no++] = q;
+    }
+    ex.run(no * G, cb);
+    fft(Zc, no, 1);
+    StoreReal st{};
+    st.Z = Zc;
+    int nb = 0;
+    for (double* p : out) st.out[nb++] = p;
+    st.alpha = alpha;
+    st.acc = 0;
+    st.G = G;
+    ex.run(nb * G, st);
   }
 };
 
@@ -471,23 +514,15 @@ void jvp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const d
   const long long G = (long long)t.nx * t.ny;
   for (int it = 0; it < t.nt; ++it) {
     const int src = it <= 1;
-    S.forward(f.p, S.Z0);
-    S.apply(S.Z0, kDPX, nullptr, 0, 1, 0, f.gx, 1.0, 0);
-    S.apply(S.Z0, kDPY, nullptr, 0, 1, 0, f.gy, 1.0, 0);
-    S.forward(f.dp, S.Z0);
-    S.apply(S.Z0, kDPX, nullptr, 0, 1, 0, f.dgx, 1.0, 0);
-    S.apply(S.Z0, kDPY, nullptr, 0, 1, 0, f.dgy, 1.0, 0);
+    S.forward({f.p, f.dp});
+    S.apply({{0, kDPX}, {0, kDPY}, {1, kDPX}, {1, kDPY}}, 0, {f.gx, f.gy, f.dgx, f.dgy}, 1.0);
     ex.run(G, Vel{t, f.gx, f.gy, f.dgx, f.dgy, drho, f.vx, f.vy, f.dvx, f.dvy});
-    S.op(f.vx, kDMX, 0, f.dx);
-    S.op(f.vy, kDMY, 0, f.dy);
-    S.op(f.dvx, kDMX, 0, f.ddx);
-    S.op(f.dvy, kDMY, 0, f.ddy);
+    S.forward({f.vx, f.vy, f.dvx, f.dvy});
+    S.apply({{0, kDMX}, {1, kDMY}, {2, kDMX}, {3, kDMY}}, 0, {f.dx, f.dy, f.ddx, f.ddy}, 1.0);
     ex.run(G, Rho{t, f.dx, f.dy, f.ddx, f.ddy, drho, dc, f.P0, src, f.rx, f.ry, f.r, f.u, f.drx, f.dry, f.dr, f.du});
     if (!t.lossless) {
-      S.op(f.r, kYDIS, 0, f.Yr);
-      S.op(f.u, kYABS, 0, f.Yu);
-      S.op(f.dr, kYDIS, 0, f.YdR);
-      S.op(f.du, kYABS, 0, f.Ydu);
+      S.forward({f.r, f.u, f.dr, f.du});
+      S.apply({{0, kYDIS}, {1, kYABS}, {2, kYDIS}, {3, kYABS}}, 0, {f.Yr, f.Yu, f.YdR, f.Ydu}, 1.0);
     }
     ex.run(G, Pres{t, f.r, f.Yr, f.Yu, f.dr, f.YdR, f.Ydu, dc, f.p, nullptr, f.dp});
     ex.run(t.ns, Gather{t, f.dp, dP + (long long)it * t.ns});
@@ -512,19 +547,18 @@ void vjp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const T
   const long long G = (long long)t.nx * t.ny;
   for (int it = 0; it < t.nt; ++it) {
     const long long o = (long long)it * G;
-    S.forward(f.p, S.Z0);
-    S.apply(S.Z0, kDPX, nullptr, 0, 1, 0, tp.gx + o, 1.0, 0);
-    S.apply(S.Z0, kDPY, nullptr, 0, 1, 0, tp.gy + o, 1.0, 0);
+    S.forward({f.p});
+    S.apply({{0, kDPX}, {0, kDPY}}, 0, {tp.gx + o, tp.gy + o}, 1.0);
     ex.run(G, Vel{t, tp.gx + o, tp.gy + o, nullptr, nullptr, nullptr, f.vx, f.vy, nullptr, nullptr});
-    S.op(f.vx, kDMX, 0, tp.dx + o);
-    S.op(f.vy, kDMY, 0, tp.dy + o);
+    S.forward({f.vx, f.vy});
+    S.apply({{0, kDMX}, {1, kDMY}}, 0, {tp.dx + o, tp.dy + o}, 1.0);
     ex.run(G, Rho{t, tp.dx + o, tp.dy + o, nullptr, nullptr, nullptr, nullptr, f.P0, it <= 1, f.rx, f.ry, f.r, f.u,
                   nullptr, nullptr, nullptr, nullptr});
     double* Yr = t.lossless ? nullptr : tp.Yr + o;
     double* Yu = t.lossless ? nullptr : tp.Yu + o;
     if (!t.lossless) {
-      S.op(f.r, kYDIS, 0, Yr);
-      S.op(f.u, kYABS, 0, Yu);
+      S.forward({f.r, f.u});
+      S.apply({{0, kYDIS}, {1, kYABS}}, 0, {Yr, Yu}, 1.0);
     }
     ex.run(G, Pres{t, f.r, Yr, Yu, nullptr, nullptr, nullptr, nullptr, f.p, tp.X + o, nullptr});
   }
@@ -535,16 +569,15 @@ void vjp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const T
     ex.run(t.ny, Scatter{t, W + (long long)it * t.ns, b.pb});
     ex.run(G, RevP{t, b.pb, tp.X + o, Yr, Yu, b.gC, b.geta, b.gtau, b.Cp, b.e1, b.e2});
     if (!t.lossless) {
-      S.op(b.e1, kYDIS, 1, b.t1);
-      S.op(b.e2, kYABS, 1, b.ub);
+      S.forward({b.e1, b.e2});
+      S.apply({{0, kYDIS}, {1, kYABS}}, 1, {b.t1, b.ub}, 1.0);
     }
     ex.run(G, RevRho{t, b.Cp, b.t1, b.ub, tp.dx + o, tp.dy + o, it <= 1, b.rbx, b.rby, b.dbx, b.dby, b.grho, b.qb});
-    S.op(b.dbx, kDMX, 1, b.ex);
-    S.op(b.dby, kDMY, 1, b.ey);
+    S.forward({b.dbx, b.dby});
+    S.apply({{0, kDMX}, {1, kDMY}}, 1, {b.ex, b.ey}, 1.0);
     ex.run(G, RevVel{t, b.ex, b.ey, tp.gx + o, tp.gy + o, b.vbx, b.vby, b.grsx, b.grsy, b.fx, b.fy});
-    S.forward(b.fx, S.Z0);
-    S.forward(b.fy, S.Z1);
-    S.apply(S.Z0, kDPX, S.Z1, kDPY, 2, 1, b.pb, -1.0, 0);
+    S.forward({b.fx, b.fy});
+    S.apply({{0, kDPX, 1, kDPY}}, 1, {b.pb}, -1.0);
   }
   ex.run(G, Finish{t, b.gC, b.gtau, b.geta, b.qb, f.P0, b.grsx, b.grsy, b.grho, g_c, g_rho});
 }
