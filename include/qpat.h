@@ -212,9 +212,10 @@ qpat_status qpat_acoustic_resume(qpat_ctx* ctx, int batch, const void* ckpt, int
  * Needs a 2D QPAT_FP64 context (else EINVAL).  FP64 device buffers:
  * p0 [n1][n0] interior initial pressure; dc, drho [ny][nx] (either may be
  * NULL: zero); dP and w [nt][ns]; g_c, g_rho [ny][nx] (either may be NULL:
- * not returned).  Workspace is allocated per call: the tangent loop needs
- * about 27 grid fields, the adjoint 33 plus a history of 5 (lossless) or 7
- * grid fields per time step.  Both calls synchronise the stream.
+ * not returned).  Workspace is allocated per call: the tangent needs 28
+ * real and 12 complex grid fields, the gradient up to 33 real and 12 complex
+ * plus a history of 5 (lossless) or 7 real grid fields per time step.  Both
+ * calls synchronise the stream.
  * qpat_jvp_medium: dP = J_c dc + J_rho drho at p0.
  * qpat_vjp_medium: g_c = J_c^T w and g_rho = J_rho^T w at p0.
  * Errors: EINVAL, ENOMEM, ECUDA. */
