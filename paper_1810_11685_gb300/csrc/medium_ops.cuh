@@ -23,7 +23,9 @@
 // and then runs the exact transpose backwards.  Spectral operators are full
 // complex 2D FFTs: one launch per Stockham stage and axis, each thread one
 // radix-R butterfly of one grid line, then the symbol multiply (the
-// context's FP64 half-spectrum tables, mirrored), then the inverse FFT.
+// context's FP64 half-spectrum tables, mirrored), then the inverse FFT; up
+// to four fields (a field and its tangent, the velocity components, the
+// absorption inputs) share each launch.
 //
 // Every per-element body is a functor callable on the host and the device;
 // the loops are templates over an executor that either launches a
