@@ -27,3 +27,22 @@ def to_gpu(a, dtype):
 
 def to_np(t):
     return t.detach().double().cpu().numpy()
+
+
+def _oracle_job(job):
+    """One oracle evaluation in a worker process: ("forward" | "adjoint",
+    workload, nt, input array)."""
+    kind, w, nt, x = job
+    S = acoustic.setup_from_workload(w, nt=nt)
+    return acoustic.forward(S, x) if kind == "forward" else acoustic.adjoint(S, x)
+
+
+def oracle_many(jobs, procs=None):
+    """Run independent oracle evaluations in spawned processes (safe after
+    CUDA is up); results in job order."""
+    import concurrent.futures
+    import multiprocessing as mp
+    import os
+    n = procs or min(len(jobs), max(1, (os.cpu_count() or 1)))
+    with concurrent.futures.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_oracle_job, jobs))

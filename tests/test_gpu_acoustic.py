@@ -129,15 +129,17 @@ def test_nonfinite_detection():
     ctx.sync()   # flag cleared, healthy call passes
 
 
+@pytest.mark.parametrize("wname", ["C2", "C2_Y11"])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
-def test_c2_grid_first_steps(prec, tol):
+def test_c2_grid_first_steps(prec, tol, wname):
     """The bench workload's grid (512^2 interior, 576^2 FFT grid, 256 perimeter
-    sensors, y = 1.5), first 120 of its 2000 steps, forward and adjoint against
-    the oracle on the same seeded inputs, batch of 2 in the launch.  The
-    initial pressures are white noise so that the perimeter sensors see
-    signal from the first step (smooth central sources would not reach them
-    within 120 steps, leaving only rounding-level data)."""
-    w = phantoms.C2
+    sensors) at both of its power-law exponents (y = 1.5 and y = 1.1), first
+    120 of its 2000 steps, forward and adjoint against the oracle on the same
+    seeded inputs, batch of 2 in the launch.  The initial pressures are white
+    noise so that the perimeter sensors see signal from the first step (smooth
+    central sources would not reach them within 120 steps, leaving only
+    rounding-level data)."""
+    w = getattr(phantoms, wname)
     ctx, S = make_pair(w, prec, max_batch=2, nt=120)
     dt = torch.float64 if prec == "fp64" else torch.float32
     p0 = np.stack([phantoms.random_field(w.interior_shape, 40), phantoms.random_field(w.interior_shape, 41)])
@@ -159,11 +161,22 @@ def test_specialised_and_generic_passes_agree_fp32():
     assert rel_l2(to_np(a.acoustic_forward(p0)), to_np(g.acoustic_forward(p0))) <= 1e-5
 
 
-def test_c2_fp32_full_length_against_fp64_gpu():
-    """Full 2000-step series on the bench grid: the FP32 path against the FP64
-    GPU path (itself pinned to the oracle above), relative L2 <= 2e-4, and the
-    FP32 dot-product test at full size."""
-    w = phantoms.C2
+@pytest.mark.parametrize("wname", ["C2", "C2_Y11"])
+def test_c2_fp32_full_length_against_fp64_gpu(wname):
+    """Full 2000-step series on the bench grid at both exponents: the FP32 path
+    against the FP64 GPU path (itself pinned to the oracle above), relative L2
+    <= 2e-4, and the FP32 adjoint dot test <H p0, w> = <p0, H^* w> at full
+    length, <= 1e-5.
+
+    The dot test's discrepancy relative to |<H p0, w>| depends on how much
+    that inner product cancels.  With a non-cancelling w = H p0 + noise it is
+    measured at ~8e-8 at every length from 500 to 2000 steps; with a white-
+    noise w it fluctuates with |<H p0, w>| (5e-6 at 2000 steps for y = 1.5,
+    1.2e-5 for y = 1.1, 6.7e-4 at 120 steps, where the smooth central source
+    has not reached the sensors yet), without growth in Nt.  The white-noise
+    form is therefore bounded relative to ||H p0|| ||w||, which carries no
+    cancellation."""
+    w = getattr(phantoms, wname)
     c32, _ = make_pair(w, "fp32", nt=w.nt)
     c64, _ = make_pair(w, "fp64", nt=w.nt)
     p0 = phantoms.smooth_p0(w)
@@ -174,9 +187,14 @@ def test_c2_fp32_full_length_against_fp64_gpu():
     a32 = to_np(c32.acoustic_adjoint(to_gpu(W, torch.float32)))
     a64 = to_np(c64.acoustic_adjoint(to_gpu(W, torch.float64)))
     assert rel_l2(a32, a64) <= 2e-4
-    # FP32 rounding of forward and adjoint accumulates over the 2000 steps:
-    # the discrepancy measured on GB300 is ~1.5e-5 here (the <= 1e-5 dot test
-    # holds at the shorter lengths of test_dot_product_on_gpu)
+    # white-noise w, bounded against the norms
     lhs = float(np.sum(d32[0].astype(np.float64) * W))
     rhs = float(np.sum(p0 * a32[0]))
-    assert abs(lhs - rhs) <= 3e-5 * abs(lhs)
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(d32[0]) * np.linalg.norm(W)
+    # non-cancelling w, bounded against |<H p0, w>| itself
+    Wc = d32[0] + 0.1 * np.abs(d32[0]).max() * phantoms.random_field((w.nt, w.n_sensors), 21)
+    ac = to_np(c32.acoustic_adjoint(to_gpu(Wc, torch.float32)))[0]
+    Wc32 = to_np(to_gpu(Wc, torch.float32))
+    lhs = float(np.sum(d32[0] * Wc32))
+    rhs = float(np.sum(p0.astype(np.float32).astype(np.float64) * ac))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)

@@ -32,11 +32,18 @@ def test_backward_matches_oracle_vjp():
     assert rel_l2(to_np(mu_g.grad), qpat.vjp(S, mu, kappa, 0b0001, W)) <= 1e-9
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-4), ("fp32", 1e-3)])
-def test_gradient_against_central_differences(prec, tol):
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gradient_against_central_differences(prec):
     """Gradient of 1/2 ||P-hat(mu) - d||^2 (eq. obj_couple) along 32 random
     directions vs central differences of the GPU objective (FP64 objective
-    accumulation)."""
+    accumulation), every direction checked.
+
+    FP64: relative error <= 1e-4 in each direction (measured max 7.4e-7 at
+    the relative step 1e-3).  FP32: the objective carries FP32 rounding of the
+    series (~1e-6 of it), which a central difference divides by the step, so
+    no step reaches 1e-4 in every direction (measured max over the 32: 1.0e-3
+    at the step 1e-2, 4.3e-3 at 1e-3); there each direction is bounded at
+    2e-3 and the median at 1e-4 (measured 2.1e-5)."""
     from paper_1810_11685_gb300.autograd import qpat_data
     w = problem(seed=7)
     ctx, _ = make_pair(w, prec)
@@ -51,14 +58,18 @@ def test_gradient_against_central_differences(prec, tol):
     objective(m).backward()
     g = m.grad.clone()
     rng = np.random.default_rng(5)
+    step = 1e-3 if prec == "fp64" else 1e-2
     errs = []
     for _ in range(32):
         v = to_gpu(rng.standard_normal(w.interior_shape), torch.float64)
-        eps = 1e-3 * float(torch.linalg.norm(mu) / torch.linalg.norm(v))
+        eps = step * float(torch.linalg.norm(mu) / torch.linalg.norm(v))
         fd = (objective(mu + eps * v) - objective(mu - eps * v)) / (2 * eps)
         an = float((g * v).sum())
         errs.append(abs(float(fd) - an) / max(abs(an), 1e-300))
-    assert np.median(errs) <= tol, errs
+    if prec == "fp64":
+        assert max(errs) <= 1e-4, errs
+    else:
+        assert max(errs) <= 2e-3 and np.median(errs) <= 1e-4, errs
 
 
 def test_forward_mode_matches_jvp_and_oracle():
