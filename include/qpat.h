@@ -51,7 +51,7 @@ typedef enum {
   QPAT_EUNSTABLE = 2,   /* time step violates the stability check */
   QPAT_ENONFINITE = 3,  /* a NaN/Inf appeared in the fields */
   QPAT_ENOCONV = 4,     /* diffusion solve hit its iteration cap */
-  QPAT_ETIMEOUT = 5,    /* reserved: a bounded device wait gave up */
+  QPAT_ETIMEOUT = 5,    /* a bounded device wait (grid barrier) gave up */
   QPAT_ENOMEM = 6,      /* device allocation failed */
   QPAT_ECUDA = 7        /* any other CUDA runtime error */
 } qpat_status;
@@ -213,14 +213,24 @@ qpat_status qpat_acoustic_resume(qpat_ctx* ctx, int batch, const void* ckpt, int
  * p0 [n1][n0] interior initial pressure; dc, drho [ny][nx] (either may be
  * NULL: zero); dP and w [nt][ns]; g_c, g_rho [ny][nx] (either may be NULL:
  * not returned).  Workspace is allocated per call: the tangent needs 28
- * real and 12 complex grid fields, the gradient up to 33 real and 12 complex
- * plus a history of 5 (lossless) or 7 real grid fields per time step.  Both
- * calls synchronise the stream.
+ * real and 8 complex grid fields, the gradient up to 33 real and 8 complex
+ * plus a tape of 5 (lossless) or 7 real grid fields per stored time step.
+ * The gradient keeps the tape of every step while that history fits in
+ * 2 GiB; beyond, it stores the loop state (5 real grid fields) every K steps
+ * during the forward sweep and recomputes each segment's tape from its
+ * checkpoint before the segment's transposed steps (K tape slots; K near
+ * sqrt(5 nt / fields), or as set by qpat_set_medium_checkpoints).  The
+ * result is the same bit for bit for every K.  Both calls synchronise the
+ * stream.
  * qpat_jvp_medium: dP = J_c dc + J_rho drho at p0.
  * qpat_vjp_medium: g_c = J_c^T w and g_rho = J_rho^T w at p0.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 qpat_status qpat_jvp_medium(qpat_ctx* ctx, const double* p0, const double* dc, const double* drho, double* dP);
 qpat_status qpat_vjp_medium(qpat_ctx* ctx, const double* p0, const double* w, double* g_c, double* g_rho);
+/* Checkpoint interval of qpat_vjp_medium on this context: K > 0 forces
+ * checkpoints every K steps (K >= nt: the whole history), 0 restores the
+ * automatic choice.  EINVAL for K < 0. */
+qpat_status qpat_set_medium_checkpoints(qpat_ctx* ctx, int K);
 
 /* Groups: propagate several contexts (e.g. uneven grids of one Newton
  * inner loop) concurrently in one CUDA graph, each context's time loop a
@@ -239,6 +249,53 @@ qpat_status qpat_group_propagate(qpat_group* group, int dir, const int* batches,
 qpat_status qpat_group_jvp(qpat_group* group, const int* batches, const double* const* mu,
                            const double* const* phi0, const double* const* dmu, unsigned illum,
                            void* const* dP, void* stream);
+
+/* Launch shape of group calls.
+ * multi = 1: every pass kind of a time step runs as ONE launch for all
+ *   members: its work list spans (member, problem, tile) items over the
+ *   members' uneven grids, one item per CTA, running the same
+ *   length-specialised pass bodies as the members' own launches (results are
+ *   bit for bit the same).  The members' loops are aligned on the time index;
+ *   a member drops out of the launches when its Nt ends.  Applies when every
+ *   member with work is a 2D QPAT_FP32 context on a square grid of FFT extent
+ *   288, 432 or 576 (each extent at most once), with the specialised passes
+ *   selected (generic_fft = 0), all lossy or all lossless; otherwise the call
+ *   falls back to multi = 0.
+ * multi = 0: each member's own launch sequence is a parallel branch of one
+ *   CUDA graph.
+ * row_block: threads per row-pass CTA, 144 or 288 (row pairs per CTA:
+ *   row_block / 48 at extent 288, row_block / 72 at 432 and 576).
+ * col_block: threads per column-pass CTA, 288 or 576 (adjacent columns per
+ *   CTA: col_block / 48 or col_block / 72).
+ * largest_first: 1 hands the work items of the largest extent to the first
+ *   CTAs.  Default {1, 144, 576, 1}. */
+typedef struct {
+  int multi;
+  int row_block;
+  int col_block;
+  int largest_first;
+} qpat_group_shape;
+
+/* Set the shape of later group calls (EINVAL for values outside the lists). */
+qpat_status qpat_group_set_shape(qpat_group* group, const qpat_group_shape* shape);
+
+/* The present shape; *multi_ready (optional) = 1 when the members with work
+ * in `batches` (per member, may be NULL) qualify for multi-problem launches. */
+qpat_status qpat_group_get_shape(const qpat_group* group, qpat_group_shape* shape, int* multi_ready,
+                                 const int* batches);
+
+/* Autotuner of the group's launch shape: times a `steps`-step forward +
+ * adjoint of batches[i] problems per member (a CUDA graph per direction,
+ * second of two runs, CUDA events on `stream`) for multi = 0 and for every
+ * multi-problem shape (row_block x col_block x largest_first) when the
+ * members qualify, keeps the fastest as the group's shape and returns it in
+ * *best.  ms (optional, up to 16 entries) receives each candidate's time in
+ * candidate order (multi = 0 first, then row_block 144/288 x col_block
+ * 288/576 x largest_first 1/0); *ncand (optional) their count.  The members'
+ * loops are shortened to `steps` during the call.  Allocates and frees
+ * temporary input and output buffers; synchronises. */
+qpat_status qpat_group_tune(qpat_group* group, const int* batches, int steps, void* stream,
+                            qpat_group_shape* best, double* ms, int* ncand);
 
 /* Autotuner: time a `steps`-step forward + adjoint of `batch` problems with
  * every supported choice of pass kernels (specialised or generic row passes,
@@ -295,7 +352,8 @@ qpat_status qpat_dot(qpat_ctx* ctx, int batch, long long len, const void* a, con
  * and 2 nq N prec values, and the face weights); synchronises (the Krylov
  * scalars are read on the host every iteration).  mu0 must be positive (log scaling); this is
  * not checked.  Errors: EINVAL (nq < 1 or > max_batch, bad masks), ENOCONV
- * (a diffusion solve), ENOMEM, ECUDA. */
+ * (a diffusion solve), ETIMEOUT (a grid-barrier wait of the cooperative
+ * M_gamma solve gave up, see qpat_barrier_check), ENOMEM, ECUDA. */
 typedef struct {
   int k_max;         /* outer linearisations; <= 0: 10 */
   int i_max;         /* PCG iterations per linearisation; <= 0: 30 */
@@ -349,6 +407,19 @@ qpat_status qpat_get_stats(const qpat_ctx* ctx, long long out[3]);
 qpat_status qpat_profile(qpat_ctx* ctx, int phase);
 qpat_status qpat_profile_read(qpat_ctx* ctx, double* total_ms, long long* count);
 
+/* Check of the bounded grid barrier that cooperative launches of this library
+ * use (the M_gamma solve of qpat_ld_solve): a cooperative grid of `blocks`
+ * CTAs runs `rounds` rounds of barriers; the first `absent` CTAs return
+ * before the first barrier, so with absent > 0 every wait of the others
+ * gives up after limit_s seconds of device time (at most 10) and the call
+ * returns QPAT_ETIMEOUT, the status a solver reports when a barrier wait
+ * gives up; with absent = 0 it returns QPAT_OK once every round has let
+ * exactly the whole grid through.  *status receives the same code.  blocks
+ * must fit on the device at once (else EINVAL).  Allocates 32 bytes of
+ * device memory; synchronises `stream`.  The paper has no counterpart: this
+ * is instrumentation for the failure path. */
+qpat_status qpat_barrier_check(int blocks, int rounds, int absent, double limit_s, void* stream, int* status);
+
 /* Inner products <a_b, c_b> exactly as qpat_dot computes them, for callers
  * that may not allocate device memory where they call it (a frozen memory
  * pool, a host framework that owns all device allocations, an inner solver
@@ -356,6 +427,8 @@ qpat_status qpat_profile_read(qpat_ctx* ctx, double* total_ms, long long* count)
  * The paper has no counterpart: this is an interface convenience.
  * prec: QPAT_FP32 or QPAT_FP64 element type of a and b (device, [batch][len]);
  * out: device double [batch]; stream: cudaStream_t (NULL = legacy default).
+ * a, b, out and stream must all belong to the current device: the scratch
+ * address and the launch are those of the current device.
  * Allocates nothing: the scratch is a fixed 512 KiB device array inside the
  * library, so batch is limited to 1..64 (EINVAL beyond, message in
  * qpat_noalloc_last_error).  The first call on each device looks up that

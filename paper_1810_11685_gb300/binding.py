@@ -48,6 +48,11 @@ class qpat_medium(ctypes.Structure):
                 ("kappa", ctypes.c_void_p)]
 
 
+class qpat_group_shape(ctypes.Structure):
+    _fields_ = [("multi", ctypes.c_int), ("row_block", ctypes.c_int), ("col_block", ctypes.c_int),
+                ("largest_first", ctypes.c_int)]
+
+
 class qpat_ld_params(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("i_max", ctypes.c_int), ("i_m", ctypes.c_int),
                 ("tol_in", ctypes.c_double), ("tol_out", ctypes.c_double), ("gamma", ctypes.c_double),
@@ -101,6 +106,10 @@ def load():
         "qpat_group_propagate": [vp, i, vp, vp, vp, vp],
         "qpat_group_jvp": [vp, vp, vp, vp, vp, ctypes.c_uint, vp, vp],
         "qpat_autotune": [vp, i, i, ctypes.POINTER(i)],
+        "qpat_group_set_shape": [vp, ctypes.POINTER(qpat_group_shape)],
+        "qpat_group_get_shape": [vp, ctypes.POINTER(qpat_group_shape), ctypes.POINTER(i), vp],
+        "qpat_group_tune": [vp, vp, i, vp, ctypes.POINTER(qpat_group_shape), ctypes.POINTER(d),
+                            ctypes.POINTER(i)],
         "qpat_acoustic_forward_ckpt": [vp, i, vp, vp, i, vp],
         "qpat_acoustic_resume": [vp, i, vp, i, i, vp],
         "qpat_profile": [vp, i],
@@ -113,6 +122,7 @@ def load():
         "qpat_vjp_kappa": [vp, i, vp, vp, vp, ctypes.c_uint, vp],
         "qpat_jvp_medium": [vp, vp, vp, vp, vp],
         "qpat_vjp_medium": [vp, vp, vp, vp, vp],
+        "qpat_set_medium_checkpoints": [vp, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -120,6 +130,8 @@ def load():
         f.restype = ctypes.c_int
     lib.qpat_last_error.argtypes = [vp]
     lib.qpat_last_error.restype = ctypes.c_char_p
+    lib.qpat_barrier_check.argtypes = [i, i, i, d, vp, ctypes.POINTER(i)]
+    lib.qpat_barrier_check.restype = ctypes.c_int
     lib.qpat_dot_noalloc.argtypes = [i, i, ll, vp, vp, vp, vp]
     lib.qpat_dot_noalloc.restype = ctypes.c_int
     lib.qpat_noalloc_last_error.argtypes = []
@@ -223,6 +235,13 @@ class Context:
         if tuple(t.shape[1:]) != tuple(shape_tail):
             raise ValueError(f"expected trailing shape {shape_tail}, got {tuple(t.shape)}")
         return t
+
+    @staticmethod
+    def _one(t, name):
+        """The single problem of a [1][...] tensor (entry points without a batch)."""
+        if t.shape[0] != 1:
+            raise ValueError(f"{name}: this entry point takes one problem, got a batch of {t.shape[0]}")
+        return t[0]
 
     def close(self):
         if getattr(self, "_ptr", None):
@@ -434,19 +453,23 @@ class Context:
         """qpat_jvp_medium: J_c dc + J_rho drho at the interior initial
         pressure p0 (FP64 2D contexts); dc, drho on the full grid."""
         import torch
-        p0 = self._in(p0, torch.float64, self.interior_shape)[0]
-        dc = None if dc is None else self._in(dc, torch.float64, self.grid_shape)[0]
-        drho = None if drho is None else self._in(drho, torch.float64, self.grid_shape)[0]
+        p0 = self._one(self._in(p0, torch.float64, self.interior_shape), "p0")
+        dc = None if dc is None else self._one(self._in(dc, torch.float64, self.grid_shape), "dc")
+        drho = None if drho is None else self._one(self._in(drho, torch.float64, self.grid_shape), "drho")
         out = self._empty(self.nt, self.ns, dtype=torch.float64)
         self._stream()
         _check(self._ptr, self._lib.qpat_jvp_medium(self._ptr, _ptr(p0), _ptr(dc), _ptr(drho), _ptr(out)))
         return out
 
+    def set_medium_checkpoints(self, K=0):
+        """qpat_set_medium_checkpoints: checkpoint interval of vjp_medium (0: automatic)."""
+        _check(self._ptr, self._lib.qpat_set_medium_checkpoints(self._ptr, int(K)))
+
     def vjp_medium(self, p0, w):
         """qpat_vjp_medium: (J_c^T w, J_rho^T w) on the full grid."""
         import torch
-        p0 = self._in(p0, torch.float64, self.interior_shape)[0]
-        w = self._in(w, torch.float64, (self.nt, self.ns))[0]
+        p0 = self._one(self._in(p0, torch.float64, self.interior_shape), "p0")
+        w = self._one(self._in(w, torch.float64, (self.nt, self.ns)), "w")
         g_c = self._empty(*self.grid_shape, dtype=torch.float64)
         g_rho = self._empty(*self.grid_shape, dtype=torch.float64)
         self._stream()
@@ -501,10 +524,44 @@ class Group:
             raise QpatError(st, self._lib.qpat_last_error(self.ctxs[0]._ptr).decode())
         return outs
 
-    def acoustic_forward(self, p0s):
-        """H_a of every member: p0s[i] is [B_i][n1][n0] (or None to skip)."""
+    SHAPE_KEYS = ("multi", "row_block", "col_block", "largest_first")
+
+    def set_shape(self, multi=1, row_block=144, col_block=576, largest_first=1):
+        """qpat_group_set_shape (see include/qpat.h)."""
+        sh = qpat_group_shape(int(multi), int(row_block), int(col_block), int(largest_first))
+        _check(None, self._lib.qpat_group_set_shape(self._ptr, ctypes.byref(sh)))
+
+    def shape(self, batches=None):
+        """(shape dict, multi_ready) for members with work in ``batches``."""
+        sh = qpat_group_shape()
+        ready = ctypes.c_int()
+        arr = None if batches is None else (ctypes.c_int * len(self.ctxs))(*[int(b) for b in batches])
+        _check(None, self._lib.qpat_group_get_shape(self._ptr, ctypes.byref(sh), ctypes.byref(ready), arr))
+        return {k: getattr(sh, k) for k in self.SHAPE_KEYS}, bool(ready.value)
+
+    def tune(self, batches, steps=10):
+        """qpat_group_tune: returns (best shape dict, [(shape dict, ms), ...])."""
+        import torch
+        n = len(self.ctxs)
+        arr = (ctypes.c_int * n)(*[int(b) for b in batches])
+        best = qpat_group_shape()
+        ms = (ctypes.c_double * 16)()
+        nc = ctypes.c_int()
+        st = self._lib.qpat_group_tune(self._ptr, arr, int(steps),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                       ctypes.byref(best), ms, ctypes.byref(nc))
+        if st != 0:
+            raise QpatError(st, self._lib.qpat_last_error(self.ctxs[0]._ptr).decode())
+        shapes = [(0, 144, 576, 1)] + [(1, rb, cb, lf) for rb in (144, 288) for cb in (288, 576) for lf in (1, 0)]
+        cands = [(dict(zip(self.SHAPE_KEYS, sh)), ms[k]) for k, sh in enumerate(shapes[:nc.value])]
+        return {k: getattr(best, k) for k in self.SHAPE_KEYS}, cands
+
+    def acoustic_forward(self, p0s, outs=None):
+        """H_a of every member: p0s[i] is [B_i][n1][n0] (or None to skip);
+        outs[i] (optional) the [B_i][nt][ns] output."""
         ins = [None if p is None else c._in(p, c.dtype, c.interior_shape) for c, p in zip(self.ctxs, p0s)]
-        outs = [None if p is None else c._empty(p.shape[0], c.nt, c.ns) for c, p in zip(self.ctxs, ins)]
+        if outs is None:
+            outs = [None if p is None else c._empty(p.shape[0], c.nt, c.ns) for c, p in zip(self.ctxs, ins)]
         return self._run(0, ins, outs)
 
     def acoustic_adjoint(self, datas):
@@ -572,16 +629,41 @@ def qpat_dot_noalloc(a, b, out=None):
     caller owns every buffer).  a, b: CUDA float32/float64 [batch][len]."""
     import torch
     lib = load()
+    for name, t in (("a", a), ("b", b)):
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise TypeError(f"qpat_dot_noalloc: {name} must be a CUDA tensor")
+        if t.dtype not in (torch.float32, torch.float64):
+            raise TypeError(f"qpat_dot_noalloc: {name} must be float32 or float64, not {t.dtype}")
     if a.dtype != b.dtype or a.shape != b.shape or a.dim() != 2:
-        raise TypeError("qpat_dot_noalloc wants two [batch][len] tensors of one dtype")
+        raise ValueError("qpat_dot_noalloc wants two [batch][len] tensors of one dtype and shape")
+    if a.device != b.device:
+        raise ValueError("qpat_dot_noalloc: a and b must be on one device")
+    a = a.contiguous()
+    b = b.contiguous()
     if out is None:
         out = torch.empty(a.shape[0], dtype=torch.float64, device=a.device)
+    elif (not isinstance(out, torch.Tensor) or out.dtype != torch.float64 or out.device != a.device
+          or out.numel() != a.shape[0] or not out.is_contiguous()):
+        raise ValueError("qpat_dot_noalloc: out must be a contiguous float64 tensor of `batch` elements "
+                         "on the device of a and b")
     prec = FP32 if a.dtype == torch.float32 else FP64
-    st = lib.qpat_dot_noalloc(prec, a.shape[0], a.shape[1], _ptr(a), _ptr(b), _ptr(out),
-                              ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream))
+    # the library looks up its scratch and launches on the current device
+    with torch.cuda.device(a.device):
+        st = lib.qpat_dot_noalloc(prec, a.shape[0], a.shape[1], _ptr(a), _ptr(b), _ptr(out),
+                                  ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream))
     if st != 0:
         raise QpatError(st, lib.qpat_noalloc_last_error().decode())
     return out
+
+
+def qpat_barrier_check(blocks, rounds=4, absent=0, limit_s=1.0):
+    """Run the bounded grid barrier's check kernel on the current device and
+    stream; returns the status code (0 = QPAT_OK, 5 = QPAT_ETIMEOUT)."""
+    import torch
+    st = ctypes.c_int()
+    load().qpat_barrier_check(int(blocks), int(rounds), int(absent), float(limit_s),
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(st))
+    return st.value
 
 
 def qpat_ld_solve(ctx: Context, data, illums, mu0, kappa0=None, **params):

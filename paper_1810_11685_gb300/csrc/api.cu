@@ -20,6 +20,7 @@
 #include "qpat.h"
 #include "qpat_internal.h"
 #include "prop3d.h"
+#include "multi.h"
 
 using namespace qpat;
 
@@ -60,6 +61,7 @@ struct qpat_ctx {
   std::map<int, std::pair<cudaGraphExec_t, long long>> graphs;   // (dir, batch) -> graph, kernels
   std::vector<cudaEvent_t> prof_events;
   size_t prof_used = 0;
+  int medium_k = 0;            // checkpoint interval of the medium gradient (0: automatic)
 };
 
 namespace qpat {
@@ -92,6 +94,7 @@ const PropArgs<double>* ctx_tables64(const qpat_ctx* c, double* y, int* lossless
 void ctx_add_launches(qpat_ctx* c, long long n) {
   if (c) c->launches += n;
 }
+int ctx_medium_k(const qpat_ctx* c) { return c ? c->medium_k : 0; }
 }  // namespace qpat
 
 namespace {
@@ -110,6 +113,12 @@ qpat_status cuda_fail(qpat_ctx* c, cudaError_t e, const char* where) {
   do {                                                             \
     cudaError_t e_ = (expr);                                       \
     if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr);         \
+  } while (0)
+
+#define QCK2(ctx, expr)                                            \
+  do {                                                             \
+    cudaError_t e_ = (expr);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr);       \
   } while (0)
 
 template <typename P>
@@ -1130,6 +1139,7 @@ struct qpat_group {
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
   std::map<std::vector<int>, std::pair<cudaGraphExec_t, long long>> graphs;
+  qpat_group_shape shape{1, 144, 576, 1};
 };
 
 namespace {
@@ -1141,6 +1151,194 @@ void set_io_for(qpat_ctx* c, int dir, const void* in, void* out, cudaStream_t s)
   else launch_set_io<T>(io, nullptr, nullptr, (const T*)in, (T*)out, nullptr, s);
 }
 
+// ---- multi-problem launches (multi.h) --------------------------------------
+struct MMember {
+  qpat_ctx* c;
+  int slot, batch, nt;
+};
+
+// The members a multi-problem sequence can serve: every member with work is a
+// 2D FP32 context on a square grid whose extent has a slot, with the
+// length-specialised passes selected, slots distinct, absorption on all or
+// off on all.  Empty when any member does not qualify.
+std::vector<MMember> multi_members(const qpat_group* g, const int* batches) {
+  std::vector<MMember> mm;
+  int used = 0, lossless = -1;
+  for (size_t i = 0; i < g->ctxs.size(); ++i) {
+    qpat_ctx* c = g->ctxs[i];
+    if (batches[i] == 0) continue;
+    const int slot = multi_slot_of(c->nx);
+    if (c->prec != QPAT_FP32 || c->dim != 2 || c->nx != c->ny || slot < 0 || !c->pf.fast_rows ||
+        !c->pf.fast_cols || (used >> slot) & 1 || (lossless >= 0 && lossless != (c->cfg.lossless != 0)))
+      return {};
+    used |= 1 << slot;
+    lossless = c->cfg.lossless != 0;
+    mm.push_back({c, slot, batches[i], c->nt});
+  }
+  if (mm.empty() || multi_prepare() != (int)cudaSuccess) return {};
+  return mm;
+}
+
+// One multi-problem launch of `phase`: act(member, n, flags) says whether the
+// member takes part and sets its time index and flags.  Returns the launches.
+template <class Act>
+long long multi_pass(const std::vector<MMember>& mm, const qpat_group_shape& sh, int phase, bool row, Act act,
+                     cudaStream_t s) {
+  MultiArgs m{};
+  int tot = 0;
+  for (int slot = 0; slot < kMultiSlots; ++slot) {
+    m.first[slot] = tot;
+    m.per[slot] = 1;
+    for (const MMember& e : mm) {
+      if (e.slot != slot) continue;
+      int n = 0, flags = 0;
+      if (!act(e, n, flags)) break;
+      m.a[slot] = e.c->pf;
+      m.a[slot].n = n;
+      m.a[slot].flags = flags;
+      const int per = row ? multi_row_tiles(slot, sh.row_block, e.c->ny) : multi_col_tiles(slot, sh.col_block, e.c->nxh);
+      m.per[slot] = per;
+      tot += per * e.batch;
+    }
+  }
+  m.first[kMultiSlots] = tot;
+  m.reverse = sh.largest_first != 0;
+  if (tot == 0) return 0;
+  if (row) launch_multi_row(m, phase, sh.row_block, tot, s);
+  else launch_multi_col(m, phase, sh.col_block, tot, s);
+  return 1;
+}
+
+// H_a of every member in one launch sequence: the members' loops are aligned
+// on the time index n (Section 3.2.3 loop from n = -1); a member drops out of
+// the launches once its own Nt is reached, and its last sample is gathered
+// at the end (its state is no longer touched by then).
+long long seq_multi_forward(const std::vector<MMember>& mm, const qpat_group_shape& sh, cudaStream_t s) {
+  long long cnt = 0;
+  int maxnt = 0;
+  const bool lossless = mm[0].c->cfg.lossless != 0;
+  for (const MMember& e : mm) {
+    zero_state<float>(e.c, e.batch, s);
+    maxnt = std::max(maxnt, e.nt);
+  }
+  auto all = [](int flags) {
+    return [flags](const MMember&, int& n, int& f) { n = 0; f = flags; return true; };
+  };
+  if (!lossless) {
+    cnt += multi_pass(mm, sh, F_R3, true, all(kSkipInput | kSource), s);    // step n = -1
+    cnt += multi_pass(mm, sh, F_C3, false, all(0), s);
+    for (int n = 0; n <= maxnt - 1; ++n) {
+      cnt += multi_pass(mm, sh, F_R1, true, [n](const MMember& e, int& nn, int& f) {
+        if (n > e.nt - 1) return false;
+        nn = n;
+        f = (n == e.nt - 1) ? kSkipOutput : 0;                             // p_(Nt-1), last pass
+        return true;
+      }, s);
+      auto step = [n](int flags) {
+        return [n, flags](const MMember& e, int& nn, int& f) {
+          if (n > e.nt - 2) return false;
+          nn = n;
+          f = flags;
+          return true;
+        };
+      };
+      cnt += multi_pass(mm, sh, F_C1, false, step(0), s);
+      cnt += multi_pass(mm, sh, F_R2, true, step(0), s);
+      cnt += multi_pass(mm, sh, F_C2, false, step(0), s);
+      cnt += multi_pass(mm, sh, F_R3, true, step(n == 0 ? kSource : 0), s);
+      cnt += multi_pass(mm, sh, F_C3, false, step(0), s);
+    }
+  } else {
+    cnt += multi_pass(mm, sh, F_R3L, true, all(kSkipInput | kSource), s);   // p_0
+    for (int n = 0; n <= maxnt - 2; ++n) {
+      auto step = [n](int flags) {
+        return [n, flags](const MMember& e, int& nn, int& f) {
+          if (n > e.nt - 2) return false;
+          nn = n;
+          f = flags;
+          return true;
+        };
+      };
+      cnt += multi_pass(mm, sh, F_C1, false, step(0), s);
+      cnt += multi_pass(mm, sh, F_R2, true, step(0), s);
+      cnt += multi_pass(mm, sh, F_C2, false, step(0), s);
+      cnt += multi_pass(mm, sh, F_R3L, true, step(n == 0 ? kSource : 0), s);
+    }
+  }
+  for (const MMember& e : mm) {
+    PropArgs<float> a = e.c->pf;
+    a.n = e.nt - 1;
+    launch_gather<float>(a, e.batch, s);
+    ++cnt;
+  }
+  return cnt;
+}
+
+// H_a^* of every member: the transposed steps in reverse, aligned so that
+// every member reaches n = -1 in the same launch (Section 3.2.4).
+long long seq_multi_adjoint(const std::vector<MMember>& mm, const qpat_group_shape& sh, cudaStream_t s) {
+  long long cnt = 0;
+  int maxnt = 0;
+  const bool lossless = mm[0].c->cfg.lossless != 0;
+  for (const MMember& e : mm) {
+    zero_state<float>(e.c, e.batch, s);
+    maxnt = std::max(maxnt, e.nt);
+  }
+  for (int n = maxnt - 2; n >= -1; --n) {
+    // kind 0: first pass of the step, 1: the source-adjoint pass, 2: both
+    // (lossless), 3: the others
+    auto act = [n](int kind) {
+      return [n, kind](const MMember& e, int& nn, int& f) {
+        if (n > e.nt - 2) return false;
+        nn = n + 1;                                                         // the sample p_(n+1)
+        const int first = (n == e.nt - 2) ? kSkipInput : 0;
+        const int acc = (n == 0) ? kAccWrite : (n == -1 ? kAccAdd : 0);
+        const int last = (n == -1) ? kSkipOutput : 0;
+        f = kind == 0 ? first : kind == 1 ? (acc | last) : kind == 2 ? (first | acc | last) : 0;
+        return true;
+      };
+    };
+    if (!lossless) {
+      cnt += multi_pass(mm, sh, A_R1, true, act(0), s);
+      cnt += multi_pass(mm, sh, A_C2, false, act(3), s);
+      cnt += multi_pass(mm, sh, A_R3, true, act(1), s);
+    } else {
+      cnt += multi_pass(mm, sh, A_R1L, true, act(2), s);
+    }
+    if (n > -1) {
+      cnt += multi_pass(mm, sh, A_C4, false, act(3), s);
+      cnt += multi_pass(mm, sh, A_R5, true, act(3), s);
+      cnt += multi_pass(mm, sh, A_C6, false, act(3), s);
+    }
+  }
+  return cnt;
+}
+
+// The launch sequence of a group call on the capture stream: one multi-problem
+// sequence when the shape asks for it and the members qualify, else each
+// member's own sequence as a parallel branch.
+long long seq_group(qpat_group* g, int dir, const int* batches, bool multi) {
+  if (multi) {
+    std::vector<MMember> mm = multi_members(g, batches);
+    return dir == 0 ? seq_multi_forward(mm, g->shape, g->cap) : seq_multi_adjoint(mm, g->shape, g->cap);
+  }
+  long long kernels = 0;
+  cudaEventRecord(g->fork, g->cap);
+  for (size_t i = 0; i < g->ctxs.size(); ++i) {
+    if (batches[i] == 0) continue;
+    qpat_ctx* c = g->ctxs[i];
+    cudaStreamWaitEvent(c->cap_stream, g->fork, 0);
+    kernels += seq_any(c, dir, batches[i], c->cap_stream);
+    cudaEventRecord(g->join[i], c->cap_stream);
+    cudaStreamWaitEvent(g->cap, g->join[i], 0);
+  }
+  return kernels;
+}
+
+bool shape_valid(const qpat_group_shape& sh) {
+  return (sh.multi == 0 || sh.multi == 1) && (sh.row_block == 144 || sh.row_block == 288) &&
+         (sh.col_block == 288 || sh.col_block == 576) && (sh.largest_first == 0 || sh.largest_first == 1);
+}
 
 }  // namespace
 
@@ -1200,21 +1398,19 @@ qpat_status qpat_group_propagate(qpat_group* g, int dir, const int* batches, con
     if (c->prec == QPAT_FP32) set_io_for<float>(c, dir, in[i], out[i], s);
     else set_io_for<double>(c, dir, in[i], out[i], s);
   }
+  const bool multi = g->shape.multi && !multi_members(g, batches).empty();
+  key.push_back(multi ? 1 : 0);
+  if (multi) {
+    key.push_back(g->shape.row_block);
+    key.push_back(g->shape.col_block);
+    key.push_back(g->shape.largest_first);
+  }
   auto it = g->graphs.find(key);
   if (it == g->graphs.end()) {
     qpat_ctx* c0 = g->ctxs[0];
     cudaError_t e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(c0, e, "group capture");
-    long long kernels = 0;
-    cudaEventRecord(g->fork, g->cap);
-    for (int i = 0; i < n; ++i) {
-      if (batches[i] == 0) continue;
-      qpat_ctx* c = g->ctxs[i];
-      cudaStreamWaitEvent(c->cap_stream, g->fork, 0);
-      kernels += seq_any(c, dir, batches[i], c->cap_stream);
-      cudaEventRecord(g->join[i], c->cap_stream);
-      cudaStreamWaitEvent(g->cap, g->join[i], 0);
-    }
+    const long long kernels = seq_group(g, dir, batches, multi);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(g->cap, &graph);
     if (e != cudaSuccess) return cuda_fail(c0, e, "group capture end");
@@ -1246,6 +1442,121 @@ qpat_status qpat_group_jvp(qpat_group* g, const int* batches, const double* cons
     in[i] = c->tw_p0;
   }
   return qpat_group_propagate(g, 0, batches, in.data(), dP, stream);
+}
+
+qpat_status qpat_group_set_shape(qpat_group* g, const qpat_group_shape* shape) {
+  if (!g || !shape || !shape_valid(*shape)) return QPAT_EINVAL;
+  g->shape = *shape;
+  return QPAT_OK;
+}
+
+qpat_status qpat_group_get_shape(const qpat_group* g, qpat_group_shape* shape, int* multi_ready,
+                                 const int* batches) {
+  if (!g || !shape) return QPAT_EINVAL;
+  *shape = g->shape;
+  if (multi_ready) *multi_ready = batches ? (int)!multi_members(g, batches).empty() : 0;
+  return QPAT_OK;
+}
+
+qpat_status qpat_group_tune(qpat_group* g, const int* batches, int steps, void* stream, qpat_group_shape* best,
+                            double* ms, int* ncand) {
+  if (!g || !batches || steps < 2) return QPAT_EINVAL;
+  const int n = (int)g->ctxs.size();
+  qpat_ctx* c0 = g->ctxs[0];
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < n; ++i) {
+    qpat_ctx* c = g->ctxs[i];
+    if (batches[i] < 0 || batches[i] > c->maxb) return fail(c, QPAT_EINVAL, "group batch out of range");
+    if (c->prof_phase >= 0) return fail(c, QPAT_EINVAL, "profiling is not available in group calls");
+  }
+  std::vector<qpat_group_shape> cand{{0, 144, 576, 1}};
+  if (!multi_members(g, batches).empty())
+    for (int rb : {144, 288})
+      for (int cb : {288, 576})
+        for (int lf : {1, 0}) cand.push_back({1, rb, cb, lf});
+  // Tuning buffers: the kernels address the sensor series with each
+  // context's full nt as the batch stride, so the series keep the full
+  // [batch][nt][ns] shape while only the first `steps` samples are produced.
+  struct Buf {
+    std::vector<void*> p;
+    ~Buf() {
+      for (void* q : p) cudaFree(q);
+    }
+  } buf;
+  std::vector<void*> in(n, nullptr), out(n, nullptr);
+  std::vector<int> saved(n);
+  for (int i = 0; i < n; ++i) {
+    qpat_ctx* c = g->ctxs[i];
+    saved[i] = c->nt;
+    if (batches[i] == 0) continue;
+    const size_t esz = c->prec == QPAT_FP32 ? 4 : 8;
+    const size_t b_in = (size_t)batches[i] * c->N * esz, b_out = (size_t)batches[i] * c->nt * c->ns * esz;
+    void *a = nullptr, *b = nullptr;
+    if (cudaMalloc(&a, b_in) != cudaSuccess) return fail(c, QPAT_ENOMEM, "group tuning buffers");
+    buf.p.push_back(a);
+    if (cudaMalloc(&b, b_out) != cudaSuccess) return fail(c, QPAT_ENOMEM, "group tuning buffers");
+    buf.p.push_back(b);
+    QCK2(c, cudaMemsetAsync(a, 0, b_in, s));
+    QCK2(c, cudaMemsetAsync(b, 0, b_out, s));
+    in[i] = a;
+    out[i] = b;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  QCK2(c0, cudaEventCreate(&e0));
+  QCK2(c0, cudaEventCreate(&e1));
+  const qpat_group_shape keep = g->shape;
+  double best_ms = 1e300;
+  int best_k = 0;
+  qpat_status st = QPAT_OK;
+  for (int i = 0; i < n; ++i) g->ctxs[i]->nt = std::max(2, std::min(steps, saved[i]));
+  for (size_t k = 0; k < cand.size() && st == QPAT_OK; ++k) {
+    g->shape = cand[k];
+    const bool multi = cand[k].multi != 0;
+    cudaGraphExec_t ex[2] = {nullptr, nullptr};
+    for (int dir = 0; dir < 2 && st == QPAT_OK; ++dir) {
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        seq_group(g, dir, batches, multi);
+        e = cudaStreamEndCapture(g->cap, &graph);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ex[dir], graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) st = cuda_fail(c0, e, "group tuning graph");
+    }
+    float t = 0.f;
+    for (int rep = 0; rep < 2 && st == QPAT_OK; ++rep) {   // the first repetition warms up
+      cudaEventRecord(e0, s);
+      for (int dir = 0; dir < 2; ++dir) {
+        for (int i = 0; i < n; ++i) {
+          qpat_ctx* c = g->ctxs[i];
+          c->stream = s;
+          if (batches[i] == 0) continue;
+          if (c->prec == QPAT_FP32) set_io_for<float>(c, dir, dir == 0 ? in[i] : out[i], dir == 0 ? out[i] : in[i], s);
+          else set_io_for<double>(c, dir, dir == 0 ? in[i] : out[i], dir == 0 ? out[i] : in[i], s);
+        }
+        cudaGraphLaunch(ex[dir], s);
+      }
+      cudaEventRecord(e1, s);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) st = cuda_fail(c0, e, "group tuning run");
+      else cudaEventElapsedTime(&t, e0, e1);
+    }
+    for (cudaGraphExec_t x : ex)
+      if (x) cudaGraphExecDestroy(x);
+    if (ms && k < 16) ms[k] = t;
+    if (st == QPAT_OK && t < best_ms) {
+      best_ms = t;
+      best_k = (int)k;
+    }
+  }
+  for (int i = 0; i < n; ++i) g->ctxs[i]->nt = saved[i];
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->shape = st == QPAT_OK ? cand[best_k] : keep;
+  if (best) *best = g->shape;
+  if (ncand) *ncand = (int)cand.size();
+  return st;
 }
 
 qpat_status qpat_autotune(qpat_ctx* c, int batch, int steps, int* choice) {
@@ -1305,6 +1616,12 @@ qpat_status qpat_autotune(qpat_ctx* c, int batch, int steps, int* choice) {
   cudaFree(data);
   QCK(cudaGetLastError());
   if (choice) *choice = best_choice;
+  return QPAT_OK;
+}
+
+qpat_status qpat_set_medium_checkpoints(qpat_ctx* c, int K) {
+  if (!c || K < 0) return QPAT_EINVAL;
+  c->medium_k = K;
   return QPAT_OK;
 }
 

@@ -262,9 +262,9 @@ constexpr bool kRowStOneBuf = QPAT_ROWST_ONEBUF != 0;
 constexpr bool kRowStTwGlobal = QPAT_ROWST_TWG != 0;
 constexpr int kRowStTwSmem(int L) { return kRowStTwGlobal ? 0 : L; }
 
-template <int L, int NSX>
+template <int L, int NSX, int RP = rp_st<L>()>
 __host__ __device__ constexpr int row_st_offset() {
-  return (kRowStTwSmem(L) + rp_st<L>() * (kRowStOneBuf ? 1 : 2) * NSX * SGeom<L>::SL + 1) & ~1;
+  return (kRowStTwSmem(L) + RP * (kRowStOneBuf ? 1 : 2) * NSX * SGeom<L>::SL + 1) & ~1;
 }
 
 // At least six resident CTAs per SM (registers capped to fit; measured at
@@ -273,18 +273,22 @@ __host__ __device__ constexpr int row_st_offset() {
 #ifndef QPAT_ROWST_MINB
 #define QPAT_ROWST_MINB 6
 #endif
-template <typename T, int L, int PH>
-__global__ void __launch_bounds__(rp_st<L>() * SGeom<L>::TPT, QPAT_ROWST_MINB)
-row_fast_st(const PropArgs<T> a) {
+// Body of the staged row pass for row-pair block `blk` of problem b, run by
+// RP * TPT threads (threadIdx.x), shared memory at smem_raw
+// (row_fast_st_smem bytes).  Every thread of the CTA must call it.
+template <typename T, int L, int PH, int RP>
+__device__ __forceinline__ void row_st_body(const PropArgs<T>& a, const int b, const int blk,
+                                            unsigned char* smem_raw) {
   constexpr int ph = PH, KIN = row_kin(PH), KOUT = row_kout(PH);
   constexpr int NSX = (KIN > KOUT ? KIN : KOUT), NF = row_nfields(PH);
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
-  constexpr int TPT = G::TPT, SL = G::SL, RP = rp_st<L>();
+  constexpr int TPT = G::TPT, SL = G::SL;
   constexpr int Q1 = G::Q1, QL = G::QL, P1 = G::P1;
   constexpr int NB = kRowStOneBuf ? 1 : 2;
   static_assert((L * sizeof(T)) % 16 == 0, "staged rows are copied in 16-byte pieces");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  static_assert(SL % 2 == 0 && row_st_offset<L, NSX, RP>() % 2 == 0,
+                "row-group buffers and the staging area must start on 16-byte boundaries");
   const int m = threadIdx.x / TPT;
   const int j = threadIdx.x - m * TPT;
   C* const sbase = reinterpret_cast<C*>(smem_raw);
@@ -292,11 +296,10 @@ row_fast_st(const PropArgs<T> a) {
   const C* tw = kRowStTwGlobal ? a.twx : tws;
   C* bufA = sbase + kRowStTwSmem(L) + m * NB * NSX * SL;
   C* bufB = kRowStOneBuf ? bufA : bufA + NSX * SL;
-  constexpr int OFF = row_st_offset<L, NSX>();
+  constexpr int OFF = row_st_offset<L, NSX, RP>();
   T* stage = reinterpret_cast<T*>(sbase + OFF) + m * NF * 2 * L;
   T* sc = reinterpret_cast<T*>(sbase + OFF) + RP * NF * 2 * L + m * 2 * L;
-  const int b = blockIdx.y;
-  const int jp = blockIdx.x * RP + m;
+  const int jp = blk * RP + m;
   const bool valid = jp < (a.ny >> 1);
   const int j0 = valid ? 2 * jp : 0;
   C* spec = a.spec + (long long)b * a.sstride;
@@ -322,7 +325,7 @@ row_fast_st(const PropArgs<T> a) {
     }
   }
   if constexpr (!kRowStTwGlobal)
-    for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
+    for (int t = threadIdx.x; t < L; t += RP * TPT) tws[t] = a.twx[t];
 
   // 1. inverse x-transform of the incoming half spectra (reversed plan)
   C y[KIN][Q1];
@@ -420,18 +423,31 @@ row_fast_st(const PropArgs<T> a) {
 }
 
 template <typename T, int L, int PH>
+__global__ void __launch_bounds__(rp_st<L>() * SGeom<L>::TPT, QPAT_ROWST_MINB)
+row_fast_st(const PropArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  row_st_body<T, L, PH, rp_st<L>()>(a, blockIdx.y, blockIdx.x, smem_raw);
+}
+
+template <typename T, int L, int PH, int RP = rp_st<L>()>
 constexpr size_t row_fast_st_smem() {
   typedef typename V2<T>::t C;
   constexpr int KIN = row_kin(PH), KOUT = row_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT);
-  return row_st_offset<L, NSX>() * sizeof(C) + (size_t)rp_st<L>() * (row_nfields(PH) * 2 * L) * sizeof(T) +
-         (KIN == 1 ? (size_t)rp_st<L>() * 2 * L * sizeof(T) : 0);
+  return row_st_offset<L, NSX, RP>() * sizeof(C) + (size_t)RP * (row_nfields(PH) * 2 * L) * sizeof(T) +
+         (KIN == 1 ? (size_t)RP * 2 * L * sizeof(T) : 0);
 }
 
 // Per-column shared-memory stride: congruent to 16/CBW complex values mod 16
-// so that the CBW columns of a half warp fall on distinct banks.
+// so that the CBW columns of a half warp fall on distinct banks, and always
+// an even number of complex values: the paired Stockham stages move 16-byte
+// entries, so every column's buffers must start on a 16-byte boundary (for
+// CBW that does not divide 16 the residue is rounded up to an even count).
+__host__ __device__ constexpr int col_pad_target(int cbw) {
+  return (16 / cbw) < 2 ? 2 : ((16 / cbw) & ~1);
+}
 template <int L, int NSX, int CBW>
 __host__ __device__ constexpr int col_stride() {
-  return 2 * NSX * SGeom<L>::SL + ((16 / CBW - (2 * NSX * SGeom<L>::SL) % 16) + 16) % 16;
+  return 2 * NSX * SGeom<L>::SL + ((col_pad_target(CBW) - (2 * NSX * SGeom<L>::SL) % 16) + 16) % 16;
 }
 
 #ifndef QPAT_COL_PAIRS
@@ -439,29 +455,32 @@ __host__ __device__ constexpr int col_stride() {
 #endif
 constexpr bool kColPairs = QPAT_COL_PAIRS != 0;
 
-template <typename T, int L, int PH>
-__global__ void __launch_bounds__(SGeom<L>::CBW * SGeom<L>::TPT)
-col_fast(const PropArgs<T> a) {
+// Body of the column pass for column block `blk` (CBW adjacent columns) of
+// problem b, run by CBW * TPT threads; nblk = column blocks per problem (the
+// sensor gather of F_C1 is strided over all of them).  Shared memory at
+// smem_raw (col_fast_smem bytes).  Every thread of the CTA must call it.
+template <typename T, int L, int PH, int CBW>
+__device__ __forceinline__ void col_body(const PropArgs<T>& a, const int b, const int blk, const int nblk,
+                                         unsigned char* smem_raw) {
   constexpr int ph = PH, KIN = col_kin(PH), KOUT = col_kout(PH);
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
-  constexpr int SL = G::SL, CBW = G::CBW, NSX = (KIN > KOUT ? KIN : KOUT);
+  constexpr int SL = G::SL, NSX = (KIN > KOUT ? KIN : KOUT);
   constexpr int Q1 = G::Q1, QL = G::QL;
   constexpr int CS = col_stride<L, NSX, CBW>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  static_assert(CS % 2 == 0 && L % 2 == 0 && SL % 2 == 0, "column buffers must start on 16-byte boundaries");
   const int c = threadIdx.x % CBW;
   const int j = threadIdx.x / CBW;
   C* tws = reinterpret_cast<C*>(smem_raw);                       // W_L^m table
   C* bufA = tws + L + c * CS;
   C* bufB = bufA + NSX * SL;
-  const int b = blockIdx.y;
-  const int kx = blockIdx.x * CBW + c;
+  const int kx = blk * CBW + c;
   const bool valid = kx < a.nxh;
   const int kxs = valid ? kx : 0;
   C* spec = a.spec + (long long)b * a.sstride;
   const long long slot = (long long)a.ny * a.pitch;
 
-  if (ph == F_C1) sensor_gather<T>(a, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  if (ph == F_C1) sensor_gather<T>(a, b, blk * CBW * G::TPT + threadIdx.x, nblk * CBW * G::TPT);
 
   C v[KIN][Q1];
   if (j < L / Q1) {
@@ -472,7 +491,7 @@ col_fast(const PropArgs<T> a) {
   }
   // twiddles to shared memory and the symbol operands of this thread's
   // points into registers before the transforms
-  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twy[t];
+  for (int t = threadIdx.x; t < L; t += CBW * G::TPT) tws[t] = a.twy[t];
   ColIn<T, C> cst[QL];
 #pragma unroll
   for (int r = 0; r < QL; ++r)
@@ -501,16 +520,23 @@ col_fast(const PropArgs<T> a) {
 }
 
 template <typename T, int L, int PH>
+__global__ void __launch_bounds__(SGeom<L>::CBW * SGeom<L>::TPT)
+col_fast(const PropArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  col_body<T, L, PH, SGeom<L>::CBW>(a, blockIdx.y, blockIdx.x, gridDim.x, smem_raw);
+}
+
+template <typename T, int L, int PH>
 constexpr size_t row_fast_smem() {
   typedef typename V2<T>::t C;
   constexpr int KIN = row_kin(PH), KOUT = row_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT);
   return (L + SGeom<L>::RP * 2 * NSX * SGeom<L>::SL) * sizeof(C) + (KIN == 1 ? SGeom<L>::RP * 2 * L * sizeof(T) : 0);
 }
-template <typename T, int L, int PH>
+template <typename T, int L, int PH, int CBW = SGeom<L>::CBW>
 constexpr size_t col_fast_smem() {
   typedef typename V2<T>::t C;
   constexpr int KIN = col_kin(PH), KOUT = col_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT);
-  return ((size_t)L + (size_t)SGeom<L>::CBW * col_stride<L, NSX, SGeom<L>::CBW>()) * sizeof(C);
+  return ((size_t)L + (size_t)CBW * col_stride<L, NSX, CBW>()) * sizeof(C);
 }
 
 template <typename T, int L, int PH>

@@ -20,13 +20,12 @@
 #include <string>
 #include <vector>
 
-#include <cooperative_groups.h>
+#include "grid_sync.cuh"
 
 #include "qpat.h"
 #include "qpat_internal.h"
 
 using namespace qpat;
-namespace cgrp = cooperative_groups;
 
 namespace {
 
@@ -338,14 +337,18 @@ __global__ void __launch_bounds__(kCgThreads) tv_cg_kernel(TVGrid t, const doubl
 
 // ---- the whole M_gamma solve in one cooperative grid --------------------------
 constexpr int kCoopThreads = 256;
+// a grid-barrier wait gives up after this much device time
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;
 constexpr int kCoopMaxBlocks = 4096;
 
 // Deterministic sum over the grid: block sums in a fixed tree order, written
 // to one of two alternating partial arrays (a block may write the next sum's
 // partial only after every block has read this one, which the grid barrier of
 // the next sum guarantees), then every block adds all partials in index order,
-// so all threads of all blocks hold the same value.
-__device__ __forceinline__ double grid_sum(double v, double* sh, double* part, int& flip, cgrp::grid_group& g) {
+// so all threads of all blocks hold the same value.  ok turns false (in the
+// whole CTA) when the grid barrier gave up; the kernel must then return.
+__device__ __forceinline__ double grid_sum(double v, double* sh, double* part, int& flip, const GridBar& gb,
+                                           bool& ok) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
@@ -358,7 +361,8 @@ __device__ __forceinline__ double grid_sum(double v, double* sh, double* part, i
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += sh[w];
     pa[blockIdx.x] = b;
   }
-  g.sync();
+  ok = grid_barrier(gb);
+  if (!ok) return 0.0;
   if (wid == 0) {
     double t = 0.0;
     for (int i = lane; i < (int)gridDim.x; i += 32) t += pa[i];
@@ -371,20 +375,22 @@ __device__ __forceinline__ double grid_sum(double v, double* sh, double* part, i
 
 // The iteration of tv_cg_kernel spread over a cooperative grid: four grid
 // barriers per iteration (three sums, and the new search direction before the
-// next stencil reads it).
+// next stencil reads it).  Every barrier wait is bounded (grid_sync.cuh); a
+// wait that gives up leaves QPAT_ETIMEOUT in stats[1] and the kernel returns.
 __global__ void __launch_bounds__(kCoopThreads) tv_cg_coop_kernel(TVGrid t, const double* r, double* z, double* rr,
                                                                    double* pp, double* ap, double* zz, double* dg,
                                                                    double* part, int max_iter, double tol,
-                                                                   int* stats) {
-  cgrp::grid_group g = cgrp::this_grid();
+                                                                   int* stats, GridBar gb) {
   __shared__ double sh[33];
+  bool ok = true;
   int flip = 0;
   const long long N = (long long)t.n0 * t.n1 * t.n2;
   const long long G = (long long)gridDim.x * blockDim.x;
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double s = 0.0;
   for (long long c = t0; c < N; c += G) s += r[c];
-  const double m_r = grid_sum(s, sh, part, flip, g) / (double)N;
+  const double m_r = grid_sum(s, sh, part, flip, gb, ok) / (double)N;
+  if (!ok) return;
   s = 0.0;
   for (long long c = t0; c < N; c += G) {
     dg[c] = tv_row(t, nullptr, c, 1);
@@ -394,14 +400,16 @@ __global__ void __launch_bounds__(kCoopThreads) tv_cg_coop_kernel(TVGrid t, cons
     z[c] = 0.0;
     s += zz[c];
   }
-  const double m0 = grid_sum(s, sh, part, flip, g) / (double)N;
+  const double m0 = grid_sum(s, sh, part, flip, gb, ok) / (double)N;
+  if (!ok) return;
   s = 0.0;
   for (long long c = t0; c < N; c += G) {
     zz[c] -= m0;
     pp[c] = zz[c];
     s += rr[c] * zz[c];
   }
-  const double rz0 = grid_sum(s, sh, part, flip, g);
+  const double rz0 = grid_sum(s, sh, part, flip, gb, ok);
+  if (!ok) return;
   double rz = rz0;
   int it = 0;
   for (; rz0 > 0.0 && it < max_iter && sqrt(fabs(rz) / rz0) > tol; ++it) {
@@ -411,7 +419,8 @@ __global__ void __launch_bounds__(kCoopThreads) tv_cg_coop_kernel(TVGrid t, cons
       ap[c] = a;
       s += pp[c] * a;
     }
-    const double pap = grid_sum(s, sh, part, flip, g);
+    const double pap = grid_sum(s, sh, part, flip, gb, ok);
+    if (!ok) return;
     const double alpha = pap != 0.0 ? rz / pap : 0.0;
     s = 0.0;
     for (long long c = t0; c < N; c += G) {
@@ -421,17 +430,19 @@ __global__ void __launch_bounds__(kCoopThreads) tv_cg_coop_kernel(TVGrid t, cons
       zz[c] = v / dg[c];
       s += zz[c];
     }
-    const double m = grid_sum(s, sh, part, flip, g) / (double)N;
+    const double m = grid_sum(s, sh, part, flip, gb, ok) / (double)N;
+    if (!ok) return;
     s = 0.0;
     for (long long c = t0; c < N; c += G) {
       zz[c] -= m;
       s += rr[c] * zz[c];
     }
-    const double rzn = grid_sum(s, sh, part, flip, g);
+    const double rzn = grid_sum(s, sh, part, flip, gb, ok);
+    if (!ok) return;
     const double beta = rz != 0.0 ? rzn / rz : 0.0;
     for (long long c = t0; c < N; c += G) pp[c] = zz[c] + beta * pp[c];
     rz = rzn;
-    g.sync();
+    if (!grid_barrier(gb)) return;
   }
   for (long long c = t0; c < N; c += G) z[c] += m_r / t.gamma;
   if (t0 == 0) stats[0] = it;
@@ -556,17 +567,24 @@ struct Ld {
                        const double* ones, int max_iter, double tol) {
     if (coop_blocks > 0) {
       // the whole solve in one cooperative launch
+      // cg_stats: [0] iterations, [1] barrier status, [2] arrivals, [3] generation
       const double* rp = r;
       TVGrid tvv = tv;
-      void* args[] = {&tvv, &rp, &z, &rr, &pp, &ap, &zz, &dg, &coop_part, &max_iter, &tol, &cg_stats};
-      qpat_status e = cuda(cudaLaunchCooperativeKernel((const void*)tv_cg_coop_kernel, dim3(coop_blocks),
-                                                       dim3(kCoopThreads), args, 0, v.stream),
-                           "tv_cg_coop_kernel");
+      GridBar gb{reinterpret_cast<unsigned*>(cg_stats + 2), reinterpret_cast<unsigned*>(cg_stats + 3),
+                 cg_stats + 1, kBarrierLimitNs};
+      qpat_status e = cuda(cudaMemsetAsync(cg_stats, 0, 4 * sizeof(int), v.stream), "memset");
       if (e != QPAT_OK) return e;
-      if ((e = cuda(cudaMemcpyAsync(hstats, cg_stats, sizeof(int), cudaMemcpyDeviceToHost, v.stream), "copy")) !=
-          QPAT_OK)
+      void* args[] = {&tvv, &rp, &z, &rr, &pp, &ap, &zz, &dg, &coop_part, &max_iter, &tol, &cg_stats, &gb};
+      e = cuda(cudaLaunchCooperativeKernel((const void*)tv_cg_coop_kernel, dim3(coop_blocks), dim3(kCoopThreads),
+                                           args, 0, v.stream),
+               "tv_cg_coop_kernel");
+      if (e != QPAT_OK) return e;
+      if ((e = cuda(cudaMemcpyAsync(hstats, cg_stats, 2 * sizeof(int), cudaMemcpyDeviceToHost, v.stream),
+                    "copy")) != QPAT_OK)
         return e;
       if ((e = cuda(cudaStreamSynchronize(v.stream), "tv_solve sync")) != QPAT_OK) return e;
+      if (hstats[1] != 0)
+        return (qpat_status)ctx_fail(c, QPAT_ETIMEOUT, "M_gamma solve: a grid-barrier wait gave up");
       tv_iters += *hstats;
       return QPAT_OK;
     }

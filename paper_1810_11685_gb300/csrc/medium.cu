@@ -1,9 +1,13 @@
 // Derivatives of H_a in the sound speed and the density on the GPU: the C
 // entry points qpat_jvp_medium and qpat_vjp_medium over the loops of
-// medium_ops.cuh (tangent loop, and the forward loop with its whole history
-// kept in HBM followed by the exact transpose), run on an FP64 2D context's
-// own tables.  Every per-element functor is launched as a grid-stride
-// kernel on the context's stream.
+// medium_ops.cuh (tangent loop; forward loop followed by its exact transpose,
+// with the forward fields kept for every step or recomputed segment by
+// segment from forward-state checkpoints), run on an FP64 2D context's own
+// tables.  Every per-element functor is launched as a grid-stride kernel on
+// the context's stream; 2D FFTs run as one shared-memory line-FFT launch per
+// axis.
+#include <math.h>
+
 #include <vector>
 
 #include "medium_ops.cuh"
@@ -15,6 +19,8 @@ namespace qpat {
 // contexts), the absorption exponent, the lossless flag and the stream.
 const PropArgs<double>* ctx_tables64(const ::qpat_ctx* c, double* y, int* lossless, cudaStream_t* stream);
 void ctx_add_launches(::qpat_ctx* c, long long n);
+// Checkpoint interval of the medium gradient set on the context (0: automatic).
+int ctx_medium_k(const ::qpat_ctx* c);
 }  // namespace qpat
 
 namespace {
@@ -23,6 +29,8 @@ using namespace qpat;
 using namespace qpat::med;
 
 constexpr int kThreads = 256;
+// Largest whole-history tape of the medium gradient (beyond it: checkpoints).
+constexpr double kFullTapeBytes = 2.0 * 1024 * 1024 * 1024;
 constexpr long long kMaxBlocks = 152 * 16;
 
 template <class F>
@@ -31,10 +39,93 @@ __global__ void __launch_bounds__(kThreads) for_each_kernel(const F f, long long
     f(i);
 }
 
+// Complex FFT of every grid line along one axis (rows when ALONG_X, else
+// columns) of field blockIdx.y (G points each), in place.  A CTA loads M
+// lines (M consecutive rows, or M adjacent columns so that a warp's loads of
+// one row are contiguous) into shared memory with the row stride S = L + 1,
+// runs the mixed-radix Stockham stages of fft_batch there and stores back.
+// inv: the unnormalised inverse DFT, as conj(FFT(conj x)).
+constexpr int kLineThreads = 256;
+template <bool ALONG_X>
+__global__ void __launch_bounds__(kLineThreads) line_fft_kernel(double2* Z, long long G, int nx, int ny,
+                                                                 const FFTPlan plan, const double2* tw, int inv,
+                                                                 int M) {
+  extern __shared__ double2 sm_line[];
+  const int L = plan.L, S = L + 1;
+  double2* buf0 = sm_line;
+  double2* buf1 = sm_line + M * S;
+  const int nlines = ALONG_X ? ny : nx;
+  const int line0 = blockIdx.x * M;
+  const int mloc = min(M, nlines - line0);
+  double2* Zb = Z + (long long)blockIdx.y * G;
+  for (int t = threadIdx.x; t < M * L; t += blockDim.x) {
+    const int m = ALONG_X ? t / L : t % M;
+    const int i = ALONG_X ? t - m * L : t / M;
+    double2 v = make_double2(0.0, 0.0);
+    if (m < mloc) {
+      v = Zb[ALONG_X ? (long long)(line0 + m) * nx + i : (long long)i * nx + line0 + m];
+      if (inv) v.y = -v.y;
+    }
+    buf0[m * S + i] = v;
+  }
+  __syncthreads();
+  const double2* res = fft_batch(plan, buf0, buf1, M, S, tw);
+  for (int t = threadIdx.x; t < M * L; t += blockDim.x) {
+    const int m = ALONG_X ? t / L : t % M;
+    const int i = ALONG_X ? t - m * L : t / M;
+    if (m < mloc) {
+      double2 v = res[m * S + i];
+      if (inv) v.y = -v.y;
+      Zb[ALONG_X ? (long long)(line0 + m) * nx + i : (long long)i * nx + line0 + m] = v;
+    }
+  }
+}
+
+// Lines per CTA: about 48 KB of shared memory per buffer, 1 to 16 lines.
+int lines_per_cta(int L) {
+  const int m = 49152 / ((L + 1) * (int)sizeof(double2));
+  return m < 1 ? 1 : m > 16 ? 16 : m;
+}
+
+FFTPlan to_fft_plan(const Plan& p) {
+  FFTPlan f{};
+  f.L = p.L;
+  f.nstages = p.nstages;
+  for (int s = 0; s < p.nstages && s < qpat::kMaxStages; ++s) f.radix[s] = p.radix[s];
+  return f;
+}
+
 struct GpuEx {
   cudaStream_t s;
   long long launches = 0;
   cudaError_t err = cudaSuccess;
+  // 2D FFT of nb fields of G points in place: the rows, then the columns
+  void fft2(double2* Z, int nb, int inv, const Tables& t, long long G) {
+    if (nb <= 0 || err != cudaSuccess) return;
+    for (int ax = 0; ax < 2; ++ax) {
+      const FFTPlan plan = to_fft_plan(ax == 0 ? t.px : t.py);
+      const int M = lines_per_cta(plan.L);
+      const int nlines = ax == 0 ? t.ny : t.nx;
+      const size_t smem = 2 * (size_t)M * (plan.L + 1) * sizeof(double2);
+      const dim3 grid((nlines + M - 1) / M, nb);
+      cudaError_t e = ax == 0 ? cudaFuncSetAttribute(line_fft_kernel<true>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                              : cudaFuncSetAttribute(line_fft_kernel<false>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) {
+        err = e;
+        return;
+      }
+      if (ax == 0) line_fft_kernel<true><<<grid, kLineThreads, smem, s>>>(Z, G, t.nx, t.ny, plan, t.twx, inv, M);
+      else line_fft_kernel<false><<<grid, kLineThreads, smem, s>>>(Z, G, t.nx, t.ny, plan, t.twy, inv, M);
+      ++launches;
+      e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        err = e;
+        return;
+      }
+    }
+  }
   template <class F>
   void run(long long n, const F& f) {
     if (n <= 0 || err != cudaSuccess) return;
@@ -44,6 +135,10 @@ struct GpuEx {
     ++launches;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) err = e;
+  }
+  // record a host-side failure; later run() calls launch nothing
+  void fail(cudaError_t e) {
+    if (err == cudaSuccess) err = e;
   }
 };
 
@@ -122,10 +217,10 @@ extern "C" qpat_status qpat_jvp_medium(qpat_ctx* ctx, const double* p0, const do
                      &f.Ydu})
     *q = w.get<double>(G);
   double* zero = w.get<double>(G);
-  double2* Z[3];
+  double2* Z[2];
   for (double2*& z : Z) z = w.get<double2>(kMaxBatch * G);
   if (w.err != cudaSuccess) return (qpat_status)finish(ctx, ex, w);
-  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1], Z[2]};
+  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1]};
   ex.run(G, Embed{t, p0, f.P0});
   jvp_loop(ex, t, S, f, dc ? dc : zero, drho ? drho : zero, dP);
   return (qpat_status)finish(ctx, ex, w);
@@ -146,23 +241,36 @@ extern "C" qpat_status qpat_vjp_medium(qpat_ctx* ctx, const double* p0, const do
   ex.s = s;
   Fields f{};
   for (double** q : {&f.P0, &f.p, &f.vx, &f.vy, &f.rx, &f.ry, &f.r, &f.u}) *q = w.get<double>(G);
-  Tape tp{};
-  for (double** q : {&tp.gx, &tp.gy, &tp.dx, &tp.dy, &tp.X}) *q = w.get<double>(G * t.nt);
-  if (!t.lossless) {
-    tp.Yr = w.get<double>(G * t.nt);
-    tp.Yu = w.get<double>(G * t.nt);
+  // Tape length: every step while the whole history stays within
+  // kFullTapeBytes, else checkpoints every K steps with K near
+  // sqrt(5 nt / fields), which minimises checkpoints (5 fields each) plus
+  // tape (fields per step); a K set with qpat_set_medium_checkpoints wins.
+  const int nf = t.lossless ? 5 : 7;
+  int K = ctx_medium_k(ctx);
+  if (K <= 0) {
+    K = (double)t.nt * nf * G * sizeof(double) <= kFullTapeBytes
+            ? t.nt
+            : (int)ceil(sqrt(5.0 * t.nt / nf));
   }
+  if (K > t.nt) K = t.nt;
+  Tape tp{};
+  for (double** q : {&tp.gx, &tp.gy, &tp.dx, &tp.dy, &tp.X}) *q = w.get<double>(G * K);
+  if (!t.lossless) {
+    tp.Yr = w.get<double>(G * K);
+    tp.Yu = w.get<double>(G * K);
+  }
+  double* ck = K < t.nt ? w.get<double>(5 * G * ((t.nt + K - 1) / K)) : nullptr;
   RevFields b{};
   for (double** q : {&b.pb, &b.Cp, &b.e1, &b.e2, &b.t1, &b.ub, &b.rbx, &b.rby, &b.dbx, &b.dby, &b.vbx, &b.vby,
                      &b.fx, &b.fy, &b.ex, &b.ey, &b.qb, &b.gC, &b.gtau, &b.geta, &b.grho, &b.grsx, &b.grsy})
     *q = w.get<double>(G);
   double* gc = g_c ? g_c : w.get<double>(G);
   double* gr = g_rho ? g_rho : w.get<double>(G);
-  double2* Z[3];
+  double2* Z[2];
   for (double2*& z : Z) z = w.get<double2>(kMaxBatch * G);
   if (w.err != cudaSuccess) return (qpat_status)finish(ctx, ex, w);
-  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1], Z[2]};
+  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1]};
   ex.run(G, Embed{t, p0, f.P0});
-  vjp_loop(ex, t, S, f, tp, b, wts, gc, gr);
+  vjp_loop(ex, t, S, f, tp, b, K, ck, wts, gc, gr);
   return (qpat_status)finish(ctx, ex, w);
 }

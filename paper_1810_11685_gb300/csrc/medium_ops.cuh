@@ -21,15 +21,15 @@
 // The adjoint (vjp) runs the forward loop once, keeping the spectral
 // quantities each step's derivative needs (the whole history stays in HBM),
 // and then runs the exact transpose backwards.  Spectral operators are full
-// complex 2D FFTs: one launch per Stockham stage and axis, each thread one
-// radix-R butterfly of one grid line, then the symbol multiply (the
-// context's FP64 half-spectrum tables, mirrored), then the inverse FFT; up
-// to four fields (a field and its tangent, the velocity components, the
+// complex 2D FFTs: one launch per axis, each CTA transforming several grid
+// lines in shared memory (mixed-radix Stockham), then the symbol multiply
+// (the context's FP64 half-spectrum tables, mirrored), then the inverse FFT;
+// up to four fields (a field and its tangent, the velocity components, the
 // absorption inputs) share each launch.
 //
-// Every per-element body is a functor callable on the host and the device;
-// the loops are templates over an executor that either launches a
-// grid-stride kernel or runs the functor in a host loop.
+// Every per-element body is a functor; the loops are templates over the
+// executor type, whose one implementation (GpuEx in medium.cu) launches each
+// functor as a grid-stride kernel on the context's stream.
 #pragma once
 
 #include <math.h>
@@ -99,50 +99,6 @@ QPAT_HD double2 symbol(const Tables& t, int which, int j, int i) {
   }
 }
 
-// One Stockham autosort stage (decimation in time) of radix R on every grid
-// line along one axis of nb fields stored one after another (G points
-// each): thread (field, line, j), j < L/R, takes the R points j + r L/R,
-// multiplies them by the twiddles W_{Ns R}^{r k} (k = j mod Ns), applies the
-// R-point DFT and writes the results to (j / Ns) Ns R + k + s Ns, s < R.
-// Lines along x are grid rows (unit stride), along y grid columns (stride
-// nx).  inv conjugates every twiddle (the unnormalised inverse DFT).
-struct FftStage {
-  const double2* src;
-  double2* dst;
-  const double2* tw;
-  int L, R, Ns, along_x, nx, inv;
-  long long lines, G;
-  QPAT_HD void operator()(long long t) const {
-    const int m = L / R;
-    const long long per = lines * m;
-    const long long b = t / per;
-    const long long tt = t - b * per;
-    const long long line = tt / m;
-    const int j = (int)(tt - line * m);
-    const long long base = b * G + (along_x ? line * (long long)L : line);
-    const long long es = along_x ? 1 : nx;
-    const int k = j % Ns;
-    const int tstep = L / (Ns * R);
-    double2 v[8];
-    for (int r = 0; r < R; ++r) {
-      double2 w = tw[(r * k * tstep) % L];
-      if (inv) w = zconj(w);
-      v[r] = zmul(src[base + (long long)(j + r * m) * es], w);
-    }
-    const int o = (j / Ns) * Ns * R + k;
-    const int rstep = L / R;
-    for (int s = 0; s < R; ++s) {
-      double2 acc = z(0.0, 0.0);
-      for (int r = 0; r < R; ++r) {
-        double2 w = tw[((r * s) % R) * rstep];
-        if (inv) w = zconj(w);
-        acc = zadd(acc, zmul(v[r], w));
-      }
-      dst[base + (long long)(o + s * Ns) * es] = acc;
-    }
-  }
-};
-
 constexpr int kMaxBatch = 4;
 
 // Z[b G + g] = f_b[g] + 0 i for nb fields
@@ -154,11 +110,6 @@ struct LoadReal {
     const long long b = t / G;
     Z[t] = z(f[b][t - b * G], 0.0);
   }
-};
-struct CopyZ {
-  const double2* a;
-  double2* b;
-  QPAT_HD void operator()(long long g) const { b[g] = a[g]; }
 };
 // out_b = alpha Re(Z[b G + .]), or out_b += alpha Re(...) when acc
 struct StoreReal {
@@ -431,35 +382,23 @@ namespace med {
 
 // Spectral products F^-1 { S F{f} } on the full complex spectrum, several
 // fields per launch.  Zi holds up to kMaxBatch forward spectra, Zc the
-// combined products, Zt is the Stockham scratch (each kMaxBatch * G).
+// combined products (each kMaxBatch * G).
 template <class Ex>
 struct Spectral {
   Ex& ex;
   const Tables& t;
   long long G;
-  double2 *Zi, *Zc, *Zt;
+  double2 *Zi, *Zc;
 
-  void fft(double2* Z, int nb, int inv) {
-    double2* src = Z;
-    double2* dst = Zt;
-    for (int ax = 0; ax < 2; ++ax) {
-      const Plan& P = ax == 0 ? t.px : t.py;
-      const long long lines = ax == 0 ? t.ny : t.nx;
-      int Ns = 1;
-      for (int s = 0; s < P.nstages; ++s) {
-        const int R = P.radix[s];
-        ex.run(nb * lines * (P.L / R),
-               FftStage{src, dst, ax == 0 ? t.twx : t.twy, P.L, R, Ns, ax == 0, t.nx, inv, lines, G});
-        double2* tmp = src;
-        src = dst;
-        dst = tmp;
-        Ns *= R;
-      }
-    }
-    if (src != Z) ex.run(nb * G, CopyZ{src, Z});
-  }
+  // 2D FFT of nb fields in place (inv: the unnormalised inverse), one launch
+  // per axis: every grid line is transformed in shared memory
+  void fft(double2* Z, int nb, int inv) { ex.fft2(Z, nb, inv, t, G); }
   // spectra of the fields f[0..nb) into Zi
   void forward(std::initializer_list<const double*> f) {
+    if (f.size() < 1 || f.size() > (size_t)kMaxBatch) {
+      ex.fail(cudaErrorInvalidValue);
+      return;
+    }
     LoadReal op{};
     int nb = 0;
     for (const double* p : f) op.f[nb++] = p;
@@ -472,6 +411,13 @@ struct Spectral {
   // list (in, symbol) pairs per output; conj: the transposed operators.
   void apply(std::initializer_list<std::initializer_list<int>> terms, int conj,
              std::initializer_list<double*> out, double alpha) {
+    // at most kMaxBatch outputs, each of one or two (input, symbol) terms
+    bool ok = terms.size() >= 1 && terms.size() <= (size_t)kMaxBatch && out.size() == terms.size();
+    for (const auto& tl : terms) ok = ok && tl.size() >= 2 && tl.size() <= 4 && tl.size() % 2 == 0;
+    if (!ok) {
+      ex.fail(cudaErrorInvalidValue);
+      return;
+    }
     Combine cb{};
     cb.t = t;
     cb.Zi = Zi;
@@ -531,10 +477,11 @@ void jvp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const d
   }
 }
 
-// Forward loop keeping, per step, g_i = D+_i p_n, the divergences D-_i v_i,
-// X = p_(n+1) / C and (lossy) Y_dis r, Y_abs u: the tape of the adjoint.
+// Fields of one forward step that the reverse step needs: g_i = D+_i p_n,
+// the divergences D-_i v_i, X = p_(n+1) / C and (lossy) Y_dis r, Y_abs u.
+// Tape holds them for a run of consecutive steps ([steps][G] each).
 struct Tape {
-  double *gx, *gy, *dx, *dy, *X, *Yr, *Yu;   // each [nt][G]
+  double *gx, *gy, *dx, *dy, *X, *Yr, *Yu;
 };
 
 // Reverse-loop fields, all [G]
@@ -543,43 +490,98 @@ struct RevFields {
   double *gC, *gtau, *geta, *grho, *grsx, *grsy;
 };
 
-template <class Ex>
-void vjp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const Tape& tp, const RevFields& b,
-              const double* W, double* g_c, double* g_rho) {
-  const long long G = (long long)t.nx * t.ny;
-  for (int it = 0; it < t.nt; ++it) {
-    const long long o = (long long)it * G;
-    S.forward({f.p});
-    S.apply({{0, kDPX}, {0, kDPY}}, 0, {tp.gx + o, tp.gy + o}, 1.0);
-    ex.run(G, Vel{t, tp.gx + o, tp.gy + o, nullptr, nullptr, nullptr, f.vx, f.vy, nullptr, nullptr});
-    S.forward({f.vx, f.vy});
-    S.apply({{0, kDMX}, {1, kDMY}}, 0, {tp.dx + o, tp.dy + o}, 1.0);
-    ex.run(G, Rho{t, tp.dx + o, tp.dy + o, nullptr, nullptr, nullptr, nullptr, f.P0, it <= 1, f.rx, f.ry, f.r, f.u,
-                  nullptr, nullptr, nullptr, nullptr});
-    double* Yr = t.lossless ? nullptr : tp.Yr + o;
-    double* Yu = t.lossless ? nullptr : tp.Yu + o;
-    if (!t.lossless) {
-      S.forward({f.r, f.u});
-      S.apply({{0, kYDIS}, {1, kYABS}}, 0, {Yr, Yu}, 1.0);
-    }
-    ex.run(G, Pres{t, f.r, Yr, Yu, nullptr, nullptr, nullptr, nullptr, f.p, tp.X + o, nullptr});
+// Copy the loop state (p, v_x, v_y, rho_x, rho_y) to or from a checkpoint
+// [5][G].
+struct StateCopy {
+  const double* src[5];
+  double* dst[5];
+  long long G;
+  QPAT_HD void operator()(long long u) const {
+    const long long k = u / G, g = u - k * G;
+    dst[k][g] = src[k][g];
   }
-  for (int it = t.nt - 1; it >= 0; --it) {
-    const long long o = (long long)it * G;
-    const double* Yr = t.lossless ? nullptr : tp.Yr + o;
-    const double* Yu = t.lossless ? nullptr : tp.Yu + o;
-    ex.run(t.ny, Scatter{t, W + (long long)it * t.ns, b.pb});
-    ex.run(G, RevP{t, b.pb, tp.X + o, Yr, Yu, b.gC, b.geta, b.gtau, b.Cp, b.e1, b.e2});
-    if (!t.lossless) {
-      S.forward({b.e1, b.e2});
-      S.apply({{0, kYDIS}, {1, kYABS}}, 1, {b.t1, b.ub}, 1.0);
+};
+
+// Forward step it (loop index n = it - 1) of the gradient's forward sweep,
+// writing its tape fields to slot k of tp.
+template <class Ex>
+void tape_step(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const Tape& tp, int it, int k) {
+  const long long G = (long long)t.nx * t.ny, o = (long long)k * G;
+  S.forward({f.p});
+  S.apply({{0, kDPX}, {0, kDPY}}, 0, {tp.gx + o, tp.gy + o}, 1.0);
+  ex.run(G, Vel{t, tp.gx + o, tp.gy + o, nullptr, nullptr, nullptr, f.vx, f.vy, nullptr, nullptr});
+  S.forward({f.vx, f.vy});
+  S.apply({{0, kDMX}, {1, kDMY}}, 0, {tp.dx + o, tp.dy + o}, 1.0);
+  ex.run(G, Rho{t, tp.dx + o, tp.dy + o, nullptr, nullptr, nullptr, nullptr, f.P0, it <= 1, f.rx, f.ry, f.r, f.u,
+                nullptr, nullptr, nullptr, nullptr});
+  double* Yr = t.lossless ? nullptr : tp.Yr + o;
+  double* Yu = t.lossless ? nullptr : tp.Yu + o;
+  if (!t.lossless) {
+    S.forward({f.r, f.u});
+    S.apply({{0, kYDIS}, {1, kYABS}}, 0, {Yr, Yu}, 1.0);
+  }
+  ex.run(G, Pres{t, f.r, Yr, Yu, nullptr, nullptr, nullptr, nullptr, f.p, tp.X + o, nullptr});
+}
+
+// Transposed step it, reading the tape fields of step it from slot k.
+template <class Ex>
+void reverse_step(Ex& ex, const Tables& t, Spectral<Ex>& S, const Tape& tp, const RevFields& b, const double* W,
+                  int it, int k) {
+  const long long G = (long long)t.nx * t.ny, o = (long long)k * G;
+  const double* Yr = t.lossless ? nullptr : tp.Yr + o;
+  const double* Yu = t.lossless ? nullptr : tp.Yu + o;
+  ex.run(t.ny, Scatter{t, W + (long long)it * t.ns, b.pb});
+  ex.run(G, RevP{t, b.pb, tp.X + o, Yr, Yu, b.gC, b.geta, b.gtau, b.Cp, b.e1, b.e2});
+  if (!t.lossless) {
+    S.forward({b.e1, b.e2});
+    S.apply({{0, kYDIS}, {1, kYABS}}, 1, {b.t1, b.ub}, 1.0);
+  }
+  ex.run(G, RevRho{t, b.Cp, b.t1, b.ub, tp.dx + o, tp.dy + o, it <= 1, b.rbx, b.rby, b.dbx, b.dby, b.grho, b.qb});
+  S.forward({b.dbx, b.dby});
+  S.apply({{0, kDMX}, {1, kDMY}}, 1, {b.ex, b.ey}, 1.0);
+  ex.run(G, RevVel{t, b.ex, b.ey, tp.gx + o, tp.gy + o, b.vbx, b.vby, b.grsx, b.grsy, b.fx, b.fy});
+  S.forward({b.fx, b.fy});
+  S.apply({{0, kDPX, 1, kDPY}}, 1, {b.pb}, -1.0);
+}
+
+// The gradient: the forward loop, then its exact transpose backwards.
+// K >= nt: the tape holds every step (nt slots), written by the one forward
+// sweep.  K < nt: the tape holds K steps; the forward sweep stores the loop
+// state at the start of every segment of K steps in ck ([ceil(nt/K)][5][G]),
+// and the reverse sweep, segment by segment from the last, restores that
+// state, recomputes the segment's tape and runs its transposed steps.  The
+// recomputation repeats the same kernels on the same inputs, so the tape
+// and the gradient are the same bit for bit for every K.
+template <class Ex>
+void vjp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const Tape& tp, const RevFields& b, int K,
+              double* ck, const double* W, double* g_c, double* g_rho) {
+  const long long G = (long long)t.nx * t.ny;
+  if (K >= t.nt) {
+    for (int it = 0; it < t.nt; ++it) tape_step(ex, t, S, f, tp, it, it);
+    for (int it = t.nt - 1; it >= 0; --it) reverse_step(ex, t, S, tp, b, W, it, it);
+  } else {
+    auto state = [&](int seg, bool save) {
+      double* c = ck + (long long)seg * 5 * G;
+      double* live[5] = {f.p, f.vx, f.vy, f.rx, f.ry};
+      StateCopy op{};
+      for (int q = 0; q < 5; ++q) {
+        op.src[q] = save ? live[q] : c + q * G;
+        op.dst[q] = save ? c + q * G : live[q];
+      }
+      op.G = G;
+      ex.run(5 * G, op);
+    };
+    const int nseg = (t.nt + K - 1) / K;
+    for (int it = 0; it < t.nt; ++it) {
+      if (it % K == 0) state(it / K, true);
+      tape_step(ex, t, S, f, tp, it, 0);                   // slot 0 as scratch
     }
-    ex.run(G, RevRho{t, b.Cp, b.t1, b.ub, tp.dx + o, tp.dy + o, it <= 1, b.rbx, b.rby, b.dbx, b.dby, b.grho, b.qb});
-    S.forward({b.dbx, b.dby});
-    S.apply({{0, kDMX}, {1, kDMY}}, 1, {b.ex, b.ey}, 1.0);
-    ex.run(G, RevVel{t, b.ex, b.ey, tp.gx + o, tp.gy + o, b.vbx, b.vby, b.grsx, b.grsy, b.fx, b.fy});
-    S.forward({b.fx, b.fy});
-    S.apply({{0, kDPX, 1, kDPY}}, 1, {b.pb}, -1.0);
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+      const int first = seg * K, end = first + K < t.nt ? first + K : t.nt;
+      state(seg, false);
+      for (int it = first; it < end; ++it) tape_step(ex, t, S, f, tp, it, it - first);
+      for (int it = end - 1; it >= first; --it) reverse_step(ex, t, S, tp, b, W, it, it - first);
+    }
   }
   ex.run(G, Finish{t, b.gC, b.gtau, b.geta, b.qb, f.P0, b.grsx, b.grsy, b.grho, g_c, g_rho});
 }

@@ -72,3 +72,20 @@ def test_smallest_problem_matches_oracle(prec, tol):
     W = phantoms.random_field((w.nt, w.n_sensors), 3)
     got = to_np(ctx.acoustic_adjoint(to_gpu(W, dt)))[0]
     assert rel_l2(got, acoustic.adjoint(S, W)) <= tol
+
+
+def test_grid_barrier_wait_gives_up_and_device_stays_usable():
+    """The bounded grid barrier of the cooperative kernels: with one CTA that
+    never arrives, the others' waits give up after the limit and the call
+    reports QPAT_ETIMEOUT; the device then runs the full check and a
+    propagation normally."""
+    from paper_1810_11685_gb300.binding import qpat_barrier_check
+    assert qpat_barrier_check(blocks=152, rounds=8, absent=0, limit_s=1.0) == 0
+    assert qpat_barrier_check(blocks=152, rounds=8, absent=1, limit_s=0.05) == 5
+    assert qpat_barrier_check(blocks=152, rounds=8, absent=0, limit_s=1.0) == 0
+    w = phantoms.small(n=24, pml=4, nt=20, n_sensors=8, seed=3)
+    ctx, S = make_pair(w, "fp64")
+    p0 = phantoms.random_field(w.interior_shape, 2)
+    got = to_np(ctx.acoustic_forward(to_gpu(p0, torch.float64)))[0]
+    assert rel_l2(got, acoustic.forward(S, p0)) <= 1e-10
+    ctx.sync()

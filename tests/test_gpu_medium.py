@@ -77,3 +77,25 @@ def test_medium_errors():
     assert ctx64._lib.qpat_vjp_medium(ctx64._ptr, p0.data_ptr(), None, None, None) == 1
     zero = to_np(ctx64.jvp_medium(p0))                   # no direction: zero derivative
     assert np.all(zero == 0.0)
+
+
+@pytest.mark.parametrize("lossless", [False, True])
+def test_medium_gradient_checkpoints_give_the_same_gradient(lossless):
+    """The gradient from forward-state checkpoints (the tape recomputed segment
+    by segment) equals the whole-history gradient bit for bit, for segment
+    lengths that divide Nt and that leave a short last segment, and matches
+    the oracle."""
+    w = phantoms.small(n=20, pml=4, nt=30, lossless=lossless, seed=5, n_sensors=10)
+    ctx, S = make_pair(w, "fp64")
+    p0, _, _, W = _inputs(w, S, 13)
+    g = lambda a: to_gpu(a, torch.float64)
+    ctx.set_medium_checkpoints(w.nt)
+    full = [t.clone() for t in ctx.vjp_medium(g(p0), g(W))]
+    for K in (1, 5, 7, 29):
+        ctx.set_medium_checkpoints(K)
+        got = ctx.vjp_medium(g(p0), g(W))
+        assert torch.equal(got[0], full[0]) and torch.equal(got[1], full[1]), K
+    ctx.set_medium_checkpoints(0)
+    rc, rr = medium.vjp_medium(S, w.y, acoustic.embed(S, p0), W)
+    assert rel_l2(to_np(full[0]), rc) <= 1e-10
+    assert rel_l2(to_np(full[1]), rr) <= 1e-10

@@ -36,3 +36,27 @@ def test_noalloc_dot_matches_context_dot_twice(prec):
     with pytest.raises(QpatError):
         big = torch.zeros(65, 4, dtype=dt, device="cuda")
         qpat_dot_noalloc(big, big, torch.empty(65, dtype=torch.float64, device="cuda"))
+
+
+def test_noalloc_dot_rejects_bad_buffers_before_the_call():
+    """Inputs the kernels would misread (wrong dtype, host memory, a short or
+    mistyped output) are refused in the binding, before any device access."""
+    from paper_1810_11685_gb300.binding import qpat_dot_noalloc
+    a = torch.ones(3, 8, dtype=torch.float32, device="cuda")
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        qpat_dot_noalloc(a.half(), a.half(), out)
+    with pytest.raises(TypeError):
+        qpat_dot_noalloc(a.to(torch.int32), a.to(torch.int32), out)
+    with pytest.raises(TypeError):
+        qpat_dot_noalloc(a.cpu(), a.cpu(), out)
+    with pytest.raises(ValueError):
+        qpat_dot_noalloc(a, a, torch.empty(2, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        qpat_dot_noalloc(a, a, torch.empty(3, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        qpat_dot_noalloc(a, a.double(), out)
+    # a transposed (non-contiguous) view is made contiguous, not misread
+    t = torch.arange(24, dtype=torch.float64, device="cuda").reshape(8, 3).t()
+    got = qpat_dot_noalloc(t, t, out).cpu().numpy()
+    np.testing.assert_allclose(got, (t * t).sum(dim=1).cpu().numpy(), rtol=1e-14)
