@@ -20,7 +20,10 @@ Modules
   tangent loop and its exact transpose (the Discussion's next unknown).
 - ``ld``: the inexact-Newton lagged-diffusivity reconstruction of mu with the
   TV priorconditioner (Section 5.2.1, Algorithms 4 and 5; Section 5, eqs. gr,
-  apj, tvm, m, m1).
+  apj, tvm, m, m1), and the primal-dual interior-point variant (Algorithm 6).
+- ``admm``: the gradient-based benchmark, TV by ADMM with L-BFGS search
+  directions and a Wolfe backtracking line search (Section 5.1, Algorithms
+  1-3, eqs. FAm, thre, LBFGSsearch, wo, linscale).
 
 Every function is pinned by tests in ``tests/test_oracle_*.py`` against
 closed forms, invariants, brute force or the paper's printed values; none is
