@@ -274,11 +274,12 @@ __host__ __device__ constexpr int row_st_offset() {
 #define QPAT_ROWST_MINB 6
 #endif
 // Body of the staged row pass for row-pair block `blk` of problem b, run by
-// RP * TPT threads (threadIdx.x), shared memory at smem_raw
-// (row_fast_st_smem bytes).  Every thread of the CTA must call it.
+// RP * TPT threads (threadIdx.x), in the launch's dynamic shared memory
+// (row_fast_st_smem bytes), which the body names itself so that every
+// access stays a shared-memory access.  Every thread of the CTA must call it.
 template <typename T, int L, int PH, int RP>
-__device__ __forceinline__ void row_st_body(const PropArgs<T>& a, const int b, const int blk,
-                                            unsigned char* smem_raw) {
+__device__ __forceinline__ void row_st_body(const PropArgs<T> a, const int b, const int blk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ph = PH, KIN = row_kin(PH), KOUT = row_kout(PH);
   constexpr int NSX = (KIN > KOUT ? KIN : KOUT), NF = row_nfields(PH);
   typedef typename V2<T>::t C;
@@ -422,12 +423,159 @@ __device__ __forceinline__ void row_st_body(const PropArgs<T>& a, const int b, c
   }
 }
 
+// The single-context staged row pass.  It keeps its own copy of the body
+// above rather than calling row_st_body: the same code reached through the
+// device function measured 11% slower at 576^2 (1.96e10 against 2.19e10
+// cell-steps/s on GB300, with the body taking its arguments by reference or
+// by value, naming the shared memory itself or receiving it), so the
+// single-context kernels stay in this form and the body serves the
+// multi-problem kernels (multi_kernels.cuh).
 template <typename T, int L, int PH>
 __global__ void __launch_bounds__(rp_st<L>() * SGeom<L>::TPT, QPAT_ROWST_MINB)
 row_fast_st(const PropArgs<T> a) {
+  constexpr int ph = PH, KIN = row_kin(PH), KOUT = row_kout(PH);
+  constexpr int NSX = (KIN > KOUT ? KIN : KOUT), NF = row_nfields(PH);
+  typedef typename V2<T>::t C;
+  typedef SGeom<L> G;
+  constexpr int TPT = G::TPT, SL = G::SL, RP = rp_st<L>();
+  constexpr int Q1 = G::Q1, QL = G::QL, P1 = G::P1;
+  constexpr int NB = kRowStOneBuf ? 1 : 2;
+  static_assert((L * sizeof(T)) % 16 == 0, "staged rows are copied in 16-byte pieces");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  row_st_body<T, L, PH, rp_st<L>()>(a, blockIdx.y, blockIdx.x, smem_raw);
+  const int m = threadIdx.x / TPT;
+  const int j = threadIdx.x - m * TPT;
+  C* const sbase = reinterpret_cast<C*>(smem_raw);
+  C* tws = sbase;                                                // W_L^m table
+  const C* tw = kRowStTwGlobal ? a.twx : tws;
+  C* bufA = sbase + kRowStTwSmem(L) + m * NB * NSX * SL;
+  C* bufB = kRowStOneBuf ? bufA : bufA + NSX * SL;
+  constexpr int OFF = row_st_offset<L, NSX>();
+  T* stage = reinterpret_cast<T*>(sbase + OFF) + m * NF * 2 * L;
+  T* sc = reinterpret_cast<T*>(sbase + OFF) + RP * NF * 2 * L + m * 2 * L;
+  const int b = blockIdx.y;
+  const int jp = blockIdx.x * RP + m;
+  const bool valid = jp < (a.ny >> 1);
+  const int j0 = valid ? 2 * jp : 0;
+  C* spec = a.spec + (long long)b * a.sstride;
+  const long long slot = (long long)a.ny * a.pitch;
+  const bool skip_in = (a.flags & kSkipInput) != 0;
+
+  // the update's operands of both rows, copied while the spectra load and the
+  // inverse transform runs
+  if (valid) {
+    constexpr int CH = L * (int)sizeof(T) / 16;                  // 16-byte pieces per row
+    constexpr int PW = 16 / (int)sizeof(T);                      // elements per piece
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int f = row_field(ph, v);
+      if (f < 0 || !row_field_needed(ph, f, a.flags)) continue;
+      const int sl = row_stage_slot(ph, v);
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const T* src = row_field_ptr<T>(a, f, b, j0 + rr);
+        T* dst = stage + (sl * 2 + rr) * L;
+        for (int piece = j; piece < CH; piece += TPT) cp_async16(dst + piece * PW, src + piece * PW);
+      }
+    }
+  }
+  if constexpr (!kRowStTwGlobal)
+    for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
+
+  // 1. inverse x-transform of the incoming half spectra (reversed plan)
+  C y[KIN][Q1];
+  if (!skip_in) {
+    C v[KIN][P1];
+    if (j < L / P1) {
+#pragma unroll
+      for (int s = 0; s < KIN; ++s) {
+        const C* r0 = spec + s * slot + (long long)j0 * a.pitch;
+        const C* r1 = r0 + a.pitch;
+#pragma unroll
+        for (int r = 0; r < P1; ++r) {
+          const int n = j + r * (L / P1);
+          C P, Q;
+          if (2 * n <= L) {
+            P = r0[n];
+            Q = r1[n];
+            if (n == 0 || 2 * n == L) { P.y = (T)0; Q.y = (T)0; }
+          } else {
+            P = cconj(r0[L - n]);
+            Q = cconj(r1[L - n]);
+          }
+          v[s][r] = cmake<C>(P.x - Q.y, -(P.y + Q.x));   // conj(P + i Q)
+        }
+      }
+    }
+    fft_stockham<L, G::P1, G::P2, G::P3, KIN, kRowStOneBuf>(v, y, bufA, bufB, SL, j, tw);
+  } else {
+#pragma unroll
+    for (int s = 0; s < KIN; ++s)
+#pragma unroll
+      for (int r = 0; r < Q1; ++r) y[s][r] = cmake<C>((T)0, (T)0);
+  }
+
+  // adjoint sensor source M^T w_n on the two rows (A_R1, A_R1L)
+  if (KIN == 1) {
+    for (int i = j; i < 2 * L; i += TPT) sc[i] = (T)0;
+    __syncthreads();
+    if (valid) sensor_scatter_rows<T>(a, b, j0, sc, j, TPT);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // 2. pointwise update on grid points i = j + r L/Q1 of both rows;
+  //    y = FFT(conj Z) = conj(z): row j0 is Re, row j0+1 is -Im
+  C o[KOUT][Q1];
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < Q1; ++r) {
+    T u0[2] = {(T)0, (T)0}, u1[2] = {(T)0, (T)0};
+    if (j < L / Q1 && valid) {
+      const int i = j + r * (L / Q1);
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        T sv[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          sv[v] = row_field(ph, v) >= 0 ? stage[(row_stage_slot(ph, v) * 2 + rr) * L + i] : (T)0;
+        const RowIn<T> st{sv[0], sv[1], sv[2], sv[3], sv[4]};
+        const T in0 = rr ? -y[0][r].y : y[0][r].x;
+        const T in1 = (KIN > 1) ? (rr ? -y[KIN - 1][r].y : y[KIN - 1][r].x) : (T)0;
+        const T scv = (KIN == 1) ? sc[rr * L + i] : (T)0;
+        row_point<T>(a, ph, b, i, j0 + rr, in0, in1, scv, st, u0[rr], u1[rr], bad);
+      }
+    }
+    o[0][r] = cmake<C>(u0[0], u0[1]);
+    if (KOUT > 1) o[KOUT - 1][r] = cmake<C>(u1[0], u1[1]);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.err, 1);
+  if (a.flags & kSkipOutput) return;
+
+  // 3. forward x-transform of the packed outgoing rows, split, store
+  C X[KOUT][QL];
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KOUT, kRowStOneBuf>(o, X, bufA, bufB, SL, j, tw);
+  if (j < L / QL) {
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s)
+#pragma unroll
+      for (int r = 0; r < QL; ++r) bufA[s * SL + spad(j + r * (L / QL))] = X[s][r];
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s) {
+      C* w0 = spec + s * slot + (long long)j0 * a.pitch;
+      C* w1 = w0 + a.pitch;
+      for (int k = j; 2 * k <= L; k += TPT) {
+        const C Z = bufA[s * SL + spad(k)];
+        const C Zm = cconj(bufA[s * SL + spad(k == 0 ? 0 : L - k)]);
+        w0[k] = cscale(cadd(Z, Zm), (T)0.5);
+        w1[k] = cscale(cmul_mi(csub(Z, Zm)), (T)0.5);
+      }
+    }
+  }
 }
+
 
 template <typename T, int L, int PH, int RP = rp_st<L>()>
 constexpr size_t row_fast_st_smem() {
@@ -457,11 +605,12 @@ constexpr bool kColPairs = QPAT_COL_PAIRS != 0;
 
 // Body of the column pass for column block `blk` (CBW adjacent columns) of
 // problem b, run by CBW * TPT threads; nblk = column blocks per problem (the
-// sensor gather of F_C1 is strided over all of them).  Shared memory at
-// smem_raw (col_fast_smem bytes).  Every thread of the CTA must call it.
+// sensor gather of F_C1 is strided over all of them).  Dynamic shared memory
+// of the launch (col_fast_smem bytes), named by the body itself.  Every
+// thread of the CTA must call it.
 template <typename T, int L, int PH, int CBW>
-__device__ __forceinline__ void col_body(const PropArgs<T>& a, const int b, const int blk, const int nblk,
-                                         unsigned char* smem_raw) {
+__device__ __forceinline__ void col_body(const PropArgs<T> a, const int b, const int blk, const int nblk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ph = PH, KIN = col_kin(PH), KOUT = col_kout(PH);
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
@@ -519,12 +668,69 @@ __device__ __forceinline__ void col_body(const PropArgs<T>& a, const int b, cons
   }
 }
 
+// The single-context column pass, with its own copy of the body of col_body
+// for the same reason as row_fast_st.
 template <typename T, int L, int PH>
 __global__ void __launch_bounds__(SGeom<L>::CBW * SGeom<L>::TPT)
 col_fast(const PropArgs<T> a) {
+  constexpr int ph = PH, KIN = col_kin(PH), KOUT = col_kout(PH);
+  typedef typename V2<T>::t C;
+  typedef SGeom<L> G;
+  constexpr int SL = G::SL, CBW = G::CBW, NSX = (KIN > KOUT ? KIN : KOUT);
+  constexpr int Q1 = G::Q1, QL = G::QL;
+  constexpr int CS = col_stride<L, NSX, CBW>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  col_body<T, L, PH, SGeom<L>::CBW>(a, blockIdx.y, blockIdx.x, gridDim.x, smem_raw);
+  const int c = threadIdx.x % CBW;
+  const int j = threadIdx.x / CBW;
+  C* tws = reinterpret_cast<C*>(smem_raw);                       // W_L^m table
+  C* bufA = tws + L + c * CS;
+  C* bufB = bufA + NSX * SL;
+  const int b = blockIdx.y;
+  const int kx = blockIdx.x * CBW + c;
+  const bool valid = kx < a.nxh;
+  const int kxs = valid ? kx : 0;
+  C* spec = a.spec + (long long)b * a.sstride;
+  const long long slot = (long long)a.ny * a.pitch;
+
+  if (ph == F_C1) sensor_gather<T>(a, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+
+  C v[KIN][Q1];
+  if (j < L / Q1) {
+#pragma unroll
+    for (int s = 0; s < KIN; ++s)
+#pragma unroll
+      for (int r = 0; r < Q1; ++r) v[s][r] = spec[s * slot + (long long)(j + r * (L / Q1)) * a.pitch + kxs];
+  }
+  // twiddles to shared memory and the symbol operands of this thread's
+  // points into registers before the transforms
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twy[t];
+  ColIn<T, C> cst[QL];
+#pragma unroll
+  for (int r = 0; r < QL; ++r)
+    cst[r] = (j < L / QL && valid) ? col_load<T, C>(a, ph, kx, j + r * (L / QL)) : ColIn<T, C>{};
+  const C sx = col_sx<T, C>(a, ph, kxs);
+  C X[KIN][QL];
+  fft_stockham<L, G::Q1, G::Q2, G::Q3, KIN, false, kColPairs>(v, X, bufA, bufB, SL, j, tws);
+  // thread j < L/QL holds X[ky = j + r L/QL]
+  C o[KOUT][QL];
+#pragma unroll
+  for (int r = 0; r < QL; ++r) {
+    C o0 = cmake<C>((T)0, (T)0), o1 = o0;
+    if (j < L / QL && valid) col_apply<T, C>(ph, cst[r], sx, X[0][r], X[KIN - 1][r], o0, o1);
+    o[0][r] = cconj(o0);
+    if (KOUT > 1) o[KOUT - 1][r] = cconj(o1);
+  }
+  C Y[KOUT][Q1];
+  fft_stockham<L, G::P1, G::P2, G::P3, KOUT, false, kColPairs>(o, Y, bufA, bufB, SL, j, tws);
+  if (j < L / Q1 && valid) {
+#pragma unroll
+    for (int s = 0; s < KOUT; ++s)
+#pragma unroll
+      for (int r = 0; r < Q1; ++r)
+        spec[s * slot + (long long)(j + r * (L / Q1)) * a.pitch + kx] = cconj(Y[s][r]);
+  }
 }
+
 
 template <typename T, int L, int PH>
 constexpr size_t row_fast_smem() {

@@ -40,34 +40,32 @@ constexpr size_t multi_col_smem() {
 template <int PH, int BS>
 __global__ void __launch_bounds__(BS, multi_row_minb(BS)) row_multi(const __grid_constant__ MultiArgs m) {
   static_assert(BS % 48 == 0 && BS % 72 == 0, "block size must hold whole row groups of every extent");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int total = m.first[kMultiSlots];
   const int item = m.reverse ? total - 1 - (int)blockIdx.x : (int)blockIdx.x;
   if (item < m.first[1]) {
-    row_st_body<float, 288, PH, BS / 48>(m.a[0], item / m.per[0], item % m.per[0], smem_raw);
+    row_st_body<float, 288, PH, BS / 48>(m.a[0], item / m.per[0], item % m.per[0]);
   } else if (item < m.first[2]) {
     const int loc = item - m.first[1];
-    row_st_body<float, 432, PH, BS / 72>(m.a[1], loc / m.per[1], loc % m.per[1], smem_raw);
+    row_st_body<float, 432, PH, BS / 72>(m.a[1], loc / m.per[1], loc % m.per[1]);
   } else {
     const int loc = item - m.first[2];
-    row_st_body<float, 576, PH, BS / 72>(m.a[2], loc / m.per[2], loc % m.per[2], smem_raw);
+    row_st_body<float, 576, PH, BS / 72>(m.a[2], loc / m.per[2], loc % m.per[2]);
   }
 }
 
 template <int PH, int BS>
 __global__ void __launch_bounds__(BS, multi_col_minb(BS)) col_multi(const __grid_constant__ MultiArgs m) {
   static_assert(BS % 48 == 0 && BS % 72 == 0, "block size must hold whole column groups of every extent");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int total = m.first[kMultiSlots];
   const int item = m.reverse ? total - 1 - (int)blockIdx.x : (int)blockIdx.x;
   if (item < m.first[1]) {
-    col_body<float, 288, PH, BS / 48>(m.a[0], item / m.per[0], item % m.per[0], m.per[0], smem_raw);
+    col_body<float, 288, PH, BS / 48>(m.a[0], item / m.per[0], item % m.per[0], m.per[0]);
   } else if (item < m.first[2]) {
     const int loc = item - m.first[1];
-    col_body<float, 432, PH, BS / 72>(m.a[1], loc / m.per[1], loc % m.per[1], m.per[1], smem_raw);
+    col_body<float, 432, PH, BS / 72>(m.a[1], loc / m.per[1], loc % m.per[1], m.per[1]);
   } else {
     const int loc = item - m.first[2];
-    col_body<float, 576, PH, BS / 72>(m.a[2], loc / m.per[2], loc % m.per[2], m.per[2], smem_raw);
+    col_body<float, 576, PH, BS / 72>(m.a[2], loc / m.per[2], loc % m.per[2], m.per[2]);
   }
 }
 
