@@ -52,8 +52,9 @@ def parse():
     p.add_argument("--n3", type=int, default=None, help="c5 only: interior nodes per axis (default 256)")
     p.add_argument("--medium-grid", default="c1", choices=["c1", "c2"],
                    help="medium workload: the 168^2 grid with 600 steps (c1) or the 576^2 grid with 2000 (c2)")
-    p.add_argument("--ld-method", default="ld", choices=["ld", "pdipm"],
-                   help="ld workload: lagged diffusivity (Algorithm 5) or primal-dual interior point (Algorithm 6)")
+    p.add_argument("--ld-method", default="ld", choices=["ld", "pdipm", "admm"],
+                   help="ld workload: lagged diffusivity (Algorithm 5), primal-dual interior point (Algorithm 6) "
+                        "or the ADMM + L-BFGS benchmark (Algorithms 1-3)")
     p.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "ld", "medium"],
                    help="c2: the 576^2 forward+adjoint workload (default); c4: 48 Jacobian-vector "
                         "products over 288^2/432^2/576^2 grids in one graph; c5: the 3D 256^3 workload; "
@@ -771,6 +772,8 @@ def run_ld(args):
     kw = dict(k_max=3, i_max=4, i_m=4, tol_in=0.0, tol_out=0.0)
     if args.ld_method == "pdipm":
         kw.update(method="pdipm", i_max=2, i_m=2, kp_max=2, tol_med=-1.0, beta=1e-6)
+    elif args.ld_method == "admm":
+        kw = dict(method="admm", k_max=3, j_max=4, tol_out=0.0, lower=0.05, upper=20.0)
     ctx.ld_solve(data, illums, mu0, kappa0, k_max=1, i_max=2)      # warm-up (graphs, multigrid)
     torch.cuda.synchronize()
     times, res = [], None
@@ -794,8 +797,9 @@ def run_ld(args):
             "data": "synthetic", "impl": "ours",
             "config": {"workload": f"2d {w.n}x{w.n} interior, {w.grid}x{w.grid} FFT grid, Nt={nt}, "
                                    f"{w.n_sensors} sensors, 4 illuminations, joint (kappa, mu), "
-                                   + ("LD, k_max=3, i_max=i_m=4" if args.ld_method == "ld" else
-                                      "PD-IPM, k_max=3, k'_max=2, i_max=i_m=2"), "nt": nt,
+                                   + {"ld": "LD, k_max=3, i_max=i_m=4",
+                                      "pdipm": "PD-IPM, k_max=3, k'_max=2, i_max=i_m=2",
+                                      "admm": "ADMM + L-BFGS, k_max=3, j_max=4"}[args.ld_method], "nt": nt,
                        "method": args.ld_method},
             "seconds_per_solve": t, "outer": info["outer"], "inner": inner, "products": info["products"],
             "tv_cg_iterations": info["tv_iters"], "seconds_per_outer": t / max(1, info["outer"]),

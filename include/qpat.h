@@ -312,8 +312,27 @@ qpat_status qpat_dot(qpat_ctx* ctx, int batch, long long len, const void* a, con
 
 /* Reconstruction of mu, or of kappa and mu together, by the inexact-Newton
  * lagged-diffusivity method with TV priorconditioning (Section 5.2.1,
- * Algorithms 4 and 5), or by the inexact Newton method with the primal-dual
- * interior-point TV (Section 5.2.2, Algorithm 6: method = 1).
+ * Algorithms 4 and 5), by the inexact Newton method with the primal-dual
+ * interior-point TV (Section 5.2.2, Algorithm 6: method = 1), or by the
+ * gradient-based benchmark of Section 5.1 (method = 2, below).
+ *  - Algorithm 3 (method 2): linear scaling Xbar = X / mean(X0) per block
+ *    (eq. linscale); augmented Lagrangian F_A (eq. FAm) with the TV difference
+ *    operator D of eq. dd; W by the shrinkage of eq. thre, then Xbar by at
+ *    most j_max L-BFGS iterations (Algorithm 1, the last lbfgs_m pairs,
+ *    initial inverse Hessian (s^T y / y^T y) I, the identity before any pair)
+ *    with the direction projected onto the box [lower, upper] (eq.
+ *    LBFGSsearch, read as landing on the bound) and a backtracking line
+ *    search from alpha = 1 by tau (Algorithm 2) until both Wolfe conditions
+ *    of eq. wo hold (the curvature condition read as d^T grad F(Xbar +
+ *    alpha d) >= c2 d^T grad F(Xbar)); if none of ls_max trials meets both,
+ *    the largest that met sufficient decrease, and if none did, the inner
+ *    loop ends; then U_w += D Xbar - W and U_p,q += H_q - P_q.  Stops after
+ *    k_max iterations or when ||grad F_A|| <= tol_out (< 0: 1e-2); the inner
+ *    loop also stops when ||grad F_A|| <= tol_in.  Pairs with y^T s <= 0 are
+ *    not kept; a projected direction that is not one of descent is replaced
+ *    by the projected -grad and the history cleared.  eps_hist: the misfit
+ *    after each ADMM iteration (eps^0 first); inner_hist: the L-BFGS
+ *    iterations of each; info->inner_total their sum.
  *  - Algorithm 6 replaces the single PCG of a linearisation by sub-subproblems
  *    k' on the update d: Algorithm 4 on H dd = -(g + H d) with the
  *    preconditioner D^T C (I - C chi (D d)^T) D + gamma I (read face by face:
@@ -367,9 +386,19 @@ typedef struct {
   int tv_max_iter;   /* CG iterations per M_gamma solve; <= 0: 20000 */
   double tv_tol;     /* relative residual of the M_gamma solve; <= 0: 1e-12 */
   int method;        /* 0: lagged diffusivity (Algorithm 5); 1: primal-dual interior point
-                        (Algorithm 6) */
+                        (Algorithm 6); 2: the gradient-based benchmark, ADMM with L-BFGS
+                        (Algorithms 1-3) */
   int kp_max;        /* Algorithm 6: sub-subproblems per linearisation; <= 0: 20 */
   double tol_med;    /* Algorithm 6: Tol_med, taken as given (Section 6: 1e-3) */
+  /* method 2 (defaults: the values of Section 6) */
+  int lbfgs_m;       /* (s, y) pairs kept by Algorithm 1; <= 0: 5 */
+  int j_max;         /* L-BFGS iterations per ADMM iteration; <= 0: 10 */
+  int ls_max;        /* trial steps of Algorithm 2; <= 0: 20 */
+  double c1, c2;     /* Wolfe constants of eq. wo; <= 0: 1e-4, 0.9 */
+  double tau;        /* backtracking factor; <= 0: 0.25 */
+  double rho;        /* rho of eq. FAm; <= 0: 1 */
+  double nu;         /* shrinkage threshold of eq. thre; <= 0: 1e-3 */
+  double lower, upper;  /* box on Xbar (eq. cons); upper <= lower: [1e-3, 1e3] */
 } qpat_ld_params;
 
 typedef struct {

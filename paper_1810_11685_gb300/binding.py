@@ -58,7 +58,10 @@ class qpat_ld_params(ctypes.Structure):
                 ("tol_in", ctypes.c_double), ("tol_out", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("beta", ctypes.c_double), ("tv_edge", ctypes.c_double), ("tv_max_iter", ctypes.c_int),
                 ("tv_tol", ctypes.c_double), ("method", ctypes.c_int), ("kp_max", ctypes.c_int),
-                ("tol_med", ctypes.c_double)]
+                ("tol_med", ctypes.c_double), ("lbfgs_m", ctypes.c_int), ("j_max", ctypes.c_int),
+                ("ls_max", ctypes.c_int), ("c1", ctypes.c_double), ("c2", ctypes.c_double),
+                ("tau", ctypes.c_double), ("rho", ctypes.c_double), ("nu", ctypes.c_double),
+                ("lower", ctypes.c_double), ("upper", ctypes.c_double)]
 
 
 class qpat_ld_info(ctypes.Structure):
@@ -370,15 +373,18 @@ class Context:
         _check(self._ptr, self._lib.qpat_vjp(self._ptr, B, _ptr(mu), _ptr(phi0), _ptr(w), int(illum), _ptr(out)))
         return out
 
-    def ld_solve(self, data, illums, mu0, kappa0=None, k_max=10, i_max=30, i_m=5, tol_in=0.0, tol_out=1e-3,
+    def ld_solve(self, data, illums, mu0, kappa0=None, k_max=10, i_max=30, i_m=5, tol_in=0.0, tol_out=None,
                  gamma=1e-6, beta=2e-5, tv_edge=0.0, tv_max_iter=0, tv_tol=0.0, method="ld", kp_max=20,
-                 tol_med=1e-3):
+                 tol_med=1e-3, lbfgs_m=5, j_max=10, ls_max=20, c1=1e-4, c2=0.9, tau=0.25, rho=1.0, nu=1e-3,
+                 lower=1e-3, upper=1e3):
         """qpat_ld_solve: returns (mu, eps history, inner iterations per outer
         iteration, info dict), or ((kappa, mu), ...) when kappa0 is given
         (simultaneous reconstruction).  data: [nq][nt][ns] in the context
         precision; mu0, kappa0: FP64 interior fields (initial guesses).
         method: "ld" (Algorithm 5) or "pdipm" (Algorithm 6, with kp_max and
-        tol_med)."""
+        tol_med), or "admm" (Algorithms 1-3, with lbfgs_m, j_max, ls_max,
+        c1, c2, tau, rho, nu and the box [lower, upper] on Xbar; inner = L-BFGS
+        iterations per ADMM iteration)."""
         import torch
         nq = len(illums)
         data = data.contiguous()
@@ -386,10 +392,14 @@ class Context:
             raise TypeError("data must be a CUDA tensor [nq][nt][ns] of the context precision")
         mu = self._in(mu0, torch.float64, self.interior_shape).clone()
         kappa = None if kappa0 is None else self._in(kappa0, torch.float64, self.interior_shape).clone()
-        if method not in ("ld", "pdipm"):
-            raise ValueError("method must be 'ld' or 'pdipm'")
+        methods = {"ld": 0, "pdipm": 1, "admm": 2}
+        if method not in methods:
+            raise ValueError("method must be 'ld', 'pdipm' or 'admm'")
+        if tol_out is None:
+            tol_out = 1e-2 if method == "admm" else 1e-3
         prm = qpat_ld_params(k_max, i_max, i_m, tol_in, tol_out, gamma, beta, tv_edge, tv_max_iter, tv_tol,
-                             1 if method == "pdipm" else 0, kp_max, tol_med)
+                             methods[method], kp_max, tol_med, lbfgs_m, j_max, ls_max, c1, c2, tau, rho, nu,
+                             lower, upper)
         info = qpat_ld_info()
         eps = (ctypes.c_double * (max(k_max, 1) + 1))()
         inner = (ctypes.c_int * max(k_max, 1))()

@@ -448,6 +448,74 @@ __global__ void __launch_bounds__(kCoopThreads) tv_cg_coop_kernel(TVGrid t, cons
   if (t0 == 0) stats[0] = it;
 }
 
+// ---- ADMM with L-BFGS (Section 5.1, Algorithms 1-3) -------------------------
+// Faces of one block as in face_cells.  out_f = (D x)_f = a (x_c1 - x_c2),
+// minus W_f plus Uw_f when W is given.
+__global__ void admm_dx_kernel(TVGrid t, const double* x, const double* W, const double* Uw, double* out) {
+  const long long nf = face_count(t);
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+    long long c1, c2;
+    face_cells(t, f, c1, c2);
+    double v = t.edge * (x[c1] - x[c2]);
+    if (W) v += Uw[f] - W[f];
+    out[f] = v;
+  }
+}
+
+// out_c (+)= rho (D^T v)_c: +a v_f over the faces whose lower cell is c, -a v_f
+// over those whose upper cell is c (faces numbered x, then y, then z).
+__global__ void admm_dt_kernel(TVGrid t, const double* v, double rho, double* out, int add) {
+  const long long N = (long long)t.n0 * t.n1 * t.n2;
+  const long long sxy = (long long)t.n0 * t.n1;
+  const long long fy0 = (long long)t.n2 * t.n1 * (t.n0 - 1);
+  const long long fz0 = fy0 + (long long)t.n2 * (t.n1 - 1) * t.n0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % t.n0);
+    const int j = (int)((c / t.n0) % t.n1);
+    const int k = (int)(c / sxy);
+    double acc = 0.0;
+    const long long fx = ((long long)k * t.n1 + j) * (t.n0 - 1) + i;
+    if (i + 1 < t.n0) acc += v[fx];
+    if (i > 0) acc -= v[fx - 1];
+    const long long fy = fy0 + ((long long)k * (t.n1 - 1) + j) * t.n0 + i;
+    if (j + 1 < t.n1) acc += v[fy];
+    if (j > 0) acc -= v[fy - t.n0];
+    const long long fz = fz0 + ((long long)k * t.n1 + j) * t.n0 + i;
+    if (k + 1 < t.n2) acc += v[fz];
+    if (k > 0) acc -= v[fz - sxy];
+    const double r = rho * t.edge * acc;
+    out[c] = add ? out[c] + r : r;
+  }
+}
+
+// eq. thre: W = max(|v| - nu, 0) sgn(v); aw = |W|
+__global__ void shrink_kernel(long long n, const double* v, double nu, double* W, double* aw) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double a = fabs(v[t]) - nu;
+    const double w = a > 0.0 ? (v[t] > 0.0 ? a : -a) : 0.0;
+    W[t] = w;
+    aw[t] = fabs(w);
+  }
+}
+
+// eq. LBFGSsearch as read: d = clamp(x + d, lo, hi) - x
+__global__ void project_kernel(long long n, const double* x, double lo, double hi, double* d) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double y = x[t] + d[t];
+    y = y < lo ? lo : (y > hi ? hi : y);
+    d[t] = y - x[t];
+  }
+}
+
+// series: r = h - p + u, or u += h - p when update
+template <typename T>
+__global__ void admm_series_kernel(long long n, const T* h, const T* p, T* u, T* r, int update) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    if (update) u[t] = u[t] + (h[t] - p[t]);
+    else r[t] = h[t] - p[t] + u[t];
+  }
+}
+
 // Device workspace of one reconstruction, freed on every exit path.
 struct Work {
   std::vector<void*> ptrs;
@@ -671,6 +739,314 @@ qpat_status qpat_tv_apply(qpat_ctx* c, const double* xbar, double edge, double b
   return L.cuda(cudaStreamSynchronize(L.v.stream), "qpat_tv_apply sync");
 }
 
+// Algorithm 3 with Algorithms 1 and 2 (method 2): unknown Xbar = X / mean(X0)
+// per block, [kappa-bar | mu-bar] when kappa is given.  The arithmetic and
+// decisions follow oracle/admm.py step by step.
+static qpat_status admm_solve(qpat_ctx* c, int nq, const unsigned* illum, const void* data, double* mu,
+                              double* kappa, const qpat_ld_params& p, qpat_ld_info* info, double* eps_hist,
+                              int* inner_hist) {
+  Ld L;
+  L.c = c;
+  ctx_view(c, &L.v);
+  const bool joint = kappa != nullptr;
+  const int U = joint ? 2 : 1;
+  const long long N = L.v.N, NU = U * N;
+  L.N = N;
+  L.M = (long long)L.v.nt * L.v.ns;
+  L.elt = L.v.prec == QPAT_FP32 ? sizeof(float) : sizeof(double);
+  const long long MS = (long long)nq * L.M;
+  cudaStream_t s = L.v.stream;
+  const long long nfaces = (long long)L.v.n2 * L.v.n1 * (L.v.n0 - 1) + (long long)L.v.n2 * (L.v.n1 - 1) * L.v.n0 +
+                           (long long)(L.v.n2 - 1) * L.v.n1 * L.v.n0;
+  const long long NF = U * nfaces;
+  const int m = p.lbfgs_m;
+  Work w;
+  double* x = w.get<double>(NU);
+  double* xt = w.get<double>(NU);      // trial point of the line search
+  double* g = w.get<double>(NU);
+  double* gt = w.get<double>(NU);
+  double* d = w.get<double>(NU);
+  double* q = w.get<double>(NU);
+  double* Sv = w.get<double>((size_t)m * NU);
+  double* Yv = w.get<double>((size_t)m * NU);
+  double* t2 = w.get<double>(N);
+  double* t3 = w.get<double>(N);
+  double* ones_f = w.get<double>(NF);
+  double* W = w.get<double>(NF);
+  double* Uw = w.get<double>(NF);
+  double* tf = w.get<double>(NF);      // D Xbar - W + Uw (or D Xbar)
+  double* aw = w.get<double>(NF);      // |W|
+  double* phi = w.get<double>((size_t)nq * N);
+  char* Hs = w.get<char>((size_t)MS * L.elt);   // series H_q at the evaluated point
+  char* Up = w.get<char>((size_t)MS * L.elt);   // multipliers U_p,q
+  char* res = w.get<char>((size_t)MS * L.elt);  // H_q - P_q + U_p,q
+  char* hq = w.get<char>((size_t)nq * N * L.elt);
+  char* hb = w.get<char>((size_t)nq * N * L.elt);
+  L.partial = w.get<double>((size_t)kPartials * 4);
+  L.dout = w.get<double>(1);
+  double* kap_scaled = joint ? kappa : nullptr;
+  TVGrid tvg{L.v.n0, L.v.n1, L.v.n2, p.tv_edge, p.beta, p.gamma, nullptr, nullptr, nullptr};
+  if (w.err != cudaSuccess) return L.cuda(w.err, "ADMM workspace");
+  qpat_status st;
+  // scales mean(X0) per block and the start Xbar^0 = X0 / mean(X0)
+  double scale[2];
+  {
+    double* ones = t2;
+    add_const_kernel<<<blocks_for(N), kT, 0, s>>>(N, 1.0, ones, 1);
+    double sm, sk = 0.0;
+    if ((st = L.dot(mu, ones, N, &sm)) != QPAT_OK) return st;
+    if (joint && (st = L.dot(kappa, ones, N, &sk)) != QPAT_OK) return st;
+    scale[joint ? 1 : 0] = sm / (double)N;
+    if (joint) scale[0] = sk / (double)N;
+  }
+  double* xk = x;                         // kappa-bar block (joint)
+  double* xm = x + (joint ? N : 0);       // mu-bar block
+  axpby_kernel<<<blocks_for(N), kT, 0, s>>>(N, 1.0 / scale[joint ? 1 : 0], mu, 0.0, xm);
+  if (joint) axpby_kernel<<<blocks_for(N), kT, 0, s>>>(N, 1.0 / scale[0], kappa, 0.0, xk);
+  add_const_kernel<<<blocks_for(NF), kT, 0, s>>>(NF, 1.0, ones_f, 1);
+  for (double* f : {W, Uw}) (void)cudaMemsetAsync(f, 0, NF * sizeof(double), s);
+  if ((st = L.cuda(cudaMemsetAsync(Up, 0, (size_t)MS * L.elt, s), "memset")) != QPAT_OK) return st;
+
+  auto phi_q = [&](int qq) { return phi + (size_t)qq * N; };
+  auto hq_q = [&](int qq) -> void* { return hq + (size_t)qq * N * L.elt; };
+  auto hb_q = [&](int qq) -> const void* { return hb + (size_t)qq * N * L.elt; };
+  auto series = [&](int update) {
+    if (L.v.prec == QPAT_FP32)
+      admm_series_kernel<float><<<blocks_for(MS), kT, 0, s>>>(MS, (const float*)Hs, (const float*)data, (float*)Up,
+                                                              (float*)res, update);
+    else
+      admm_series_kernel<double><<<blocks_for(MS), kT, 0, s>>>(MS, (const double*)Hs, (const double*)data,
+                                                               (double*)Up, (double*)res, update);
+  };
+  // H_q at xv: coefficients X = scale Xbar, fluences, heatings, one batched H_a
+  auto forward = [&](const double* xv) -> qpat_status {
+    axpby_kernel<<<blocks_for(N), kT, 0, s>>>(N, scale[joint ? 1 : 0], xv + (joint ? N : 0), 0.0, mu);
+    if (joint) {
+      axpby_kernel<<<blocks_for(N), kT, 0, s>>>(N, scale[0], xv, 0.0, kap_scaled);
+      qpat_status e = qpat_set_kappa(c, kap_scaled);
+      if (e != QPAT_OK) return e;
+    }
+    {
+      PhaseTimer pt(&L.sec[1], s);
+      for (int qq = 0; qq < nq; ++qq) {
+        qpat_status e = (qpat_status)optics_forward(c, mu, illum[qq], phi_q(qq), hq_q(qq));
+        if (e != QPAT_OK) return e;
+      }
+    }
+    PhaseTimer pt(&L.sec[0], s);
+    L.products += nq;
+    return qpat_acoustic_forward(c, nq, hq, Hs);
+  };
+  // F_A at xv (H_q current for xv) for W, Uw and Up (eq. FAm); leaves res and tf
+  auto value = [&](const double* xv, const double* Wv, double* out) -> qpat_status {
+    series(0);
+    double data2, tv2, l1 = 0.0;
+    qpat_status e = L.dot_data(res, res, MS, &data2);
+    if (e != QPAT_OK) return e;
+    for (int u = 0; u < U; ++u)
+      admm_dx_kernel<<<blocks_for(nfaces), kT, 0, s>>>(tvg, xv + u * N, Wv ? Wv + u * nfaces : nullptr,
+                                                       Uw + u * nfaces, tf + u * nfaces);
+    if ((e = L.dot(tf, tf, NF, &tv2)) != QPAT_OK) return e;
+    if (Wv && (e = L.dot(aw, ones_f, NF, &l1)) != QPAT_OK) return e;
+    *out = p.rho * (0.5 * tv2 + p.nu * l1) + 0.5 * data2;
+    return QPAT_OK;
+  };
+  // grad F_A into gv (res and tf as value() left them)
+  auto gradient = [&](double* gv) -> qpat_status {
+    qpat_status e;
+    {
+      PhaseTimer pt(&L.sec[0], s);
+      if ((e = qpat_acoustic_adjoint(c, nq, res, hb)) != QPAT_OK) return e;
+    }
+    L.products += nq;
+    PhaseTimer pt(&L.sec[1], s);
+    for (int qq = 0; qq < nq; ++qq) {
+      if ((e = (qpat_status)optics_vjp2(c, mu, phi_q(qq), hb_q(qq), illum[qq], t2, joint ? t3 : nullptr)) != QPAT_OK)
+        return e;
+      axpby_kernel<<<blocks_for(N), kT, 0, s>>>(N, scale[joint ? 1 : 0], t2, qq > 0 ? 1.0 : 0.0,
+                                                gv + (joint ? N : 0));
+      if (joint) axpby_kernel<<<blocks_for(N), kT, 0, s>>>(N, scale[0], t3, qq > 0 ? 1.0 : 0.0, gv);
+    }
+    for (int u = 0; u < U; ++u) admm_dt_kernel<<<blocks_for(N), kT, 0, s>>>(tvg, tf + u * nfaces, p.rho, gv + u * N, 1);
+    return L.cuda(cudaGetLastError(), "ADMM gradient");
+  };
+  auto norm = [&](const double* v, double* out) -> qpat_status {
+    qpat_status e = L.dot(v, v, NU, out);
+    *out = sqrt(*out);
+    return e;
+  };
+  auto axpy = [&](double a, const double* xv, double* yv) {
+    axpby_kernel<<<blocks_for(NU), kT, 0, s>>>(NU, a, xv, 1.0, yv);
+  };
+  auto copy = [&](double* dst, const double* src) {
+    return L.cuda(cudaMemcpyAsync(dst, src, NU * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+  };
+  auto eps_of_H = [&](double* out) -> qpat_status {   // 1/2 sum_q ||H_q - P_q||^2
+    if (L.v.prec == QPAT_FP32)
+      resid_kernel<float><<<blocks_for(MS), kT, 0, s>>>(MS, (const float*)Hs, (const float*)data, (float*)res);
+    else
+      resid_kernel<double><<<blocks_for(MS), kT, 0, s>>>(MS, (const double*)Hs, (const double*)data, (double*)res);
+    double e2;
+    qpat_status e = L.dot_data(res, res, MS, &e2);
+    *out = 0.5 * e2;
+    return e;
+  };
+
+  // start: eps^0 and ||grad F_A|| at W = 0, zero multipliers
+  std::vector<double> eps;
+  double e0, f, gnorm;
+  if ((st = forward(x)) != QPAT_OK) return st;
+  if ((st = eps_of_H(&e0)) != QPAT_OK) return st;
+  eps.push_back(e0);
+  if ((st = value(x, W, &f)) != QPAT_OK) return st;
+  if ((st = gradient(g)) != QPAT_OK) return st;
+  if ((st = norm(g, &gnorm)) != QPAT_OK) return st;
+  int k = 0, inner_total = 0;
+  std::vector<double> rho_pair;
+  while (k < p.k_max && gnorm > p.tol_out) {
+    // W^(k+1) = shrink(D Xbar^k + U_w^k, nu)
+    for (int u = 0; u < U; ++u)
+      admm_dx_kernel<<<blocks_for(nfaces), kT, 0, s>>>(tvg, x + u * N, nullptr, nullptr, tf + u * nfaces);
+    axpby_kernel<<<blocks_for(NF), kT, 0, s>>>(NF, 1.0, Uw, 1.0, tf);
+    shrink_kernel<<<blocks_for(NF), kT, 0, s>>>(NF, tf, p.nu, W, aw);
+    // Xbar^(k+1): at most j_max L-BFGS iterations on F_A(., W^(k+1)) from Xbar^k
+    if ((st = forward(x)) != QPAT_OK) return st;
+    if ((st = value(x, W, &f)) != QPAT_OK) return st;
+    if ((st = gradient(g)) != QPAT_OK) return st;
+    int npair = 0, it = 0;
+    rho_pair.assign(m, 0.0);
+    for (;;) {
+      double gn;
+      if ((st = norm(g, &gn)) != QPAT_OK) return st;
+      if (!(it < p.j_max && gn > p.tol_in)) break;
+      // Algorithm 1 over the npair newest pairs (slot j holds pair j, oldest first)
+      if ((st = copy(q, g)) != QPAT_OK) return st;
+      std::vector<double> alpha(npair);
+      for (int i = npair - 1; i >= 0; --i) {
+        double sq;
+        if ((st = L.dot(Sv + i * NU, q, NU, &sq)) != QPAT_OK) return st;
+        alpha[i] = rho_pair[i] * sq;
+        axpy(-alpha[i], Yv + i * NU, q);
+      }
+      double h0 = 1.0;
+      if (npair > 0) {
+        double sy, yy;
+        if ((st = L.dot(Sv + (npair - 1) * NU, Yv + (npair - 1) * NU, NU, &sy)) != QPAT_OK) return st;
+        if ((st = L.dot(Yv + (npair - 1) * NU, Yv + (npair - 1) * NU, NU, &yy)) != QPAT_OK) return st;
+        h0 = sy / yy;
+      }
+      axpby_kernel<<<blocks_for(NU), kT, 0, s>>>(NU, -h0, q, 0.0, d);   // d = -r with r = h0 q
+      for (int i = 0; i < npair; ++i) {
+        double yr;
+        if ((st = L.dot(Yv + i * NU, d, NU, &yr)) != QPAT_OK) return st;   // y^T d = -y^T r
+        const double beta = rho_pair[i] * (-yr);
+        axpy(-(alpha[i] - beta), Sv + i * NU, d);                          // r += s (alpha - beta)
+      }
+      project_kernel<<<blocks_for(NU), kT, 0, s>>>(NU, x, p.lower, p.upper, d);
+      double gd;
+      if ((st = L.dot(g, d, NU, &gd)) != QPAT_OK) return st;
+      if (gd >= 0.0) {
+        npair = 0;
+        axpby_kernel<<<blocks_for(NU), kT, 0, s>>>(NU, -1.0, g, 0.0, d);
+        project_kernel<<<blocks_for(NU), kT, 0, s>>>(NU, x, p.lower, p.upper, d);
+        if ((st = L.dot(g, d, NU, &gd)) != QPAT_OK) return st;
+        if (gd >= 0.0) break;
+      }
+      // Algorithm 2: alpha = 1, tau, tau^2, ... until both Wolfe conditions hold
+      double a = 1.0, a_ok = -1.0, f_ok = 0.0, a_acc = -1.0, f_acc = 0.0;
+      for (int tr = 0; tr < p.ls_max; ++tr) {
+        if ((st = copy(xt, x)) != QPAT_OK) return st;
+        axpy(a, d, xt);
+        double ft;
+        if ((st = forward(xt)) != QPAT_OK) return st;
+        if ((st = value(xt, W, &ft)) != QPAT_OK) return st;
+        if ((st = gradient(gt)) != QPAT_OK) return st;
+        if (ft <= f + p.c1 * a * gd) {
+          double gtd;
+          if ((st = L.dot(gt, d, NU, &gtd)) != QPAT_OK) return st;
+          if (gtd >= p.c2 * gd) {
+            a_acc = a;
+            f_acc = ft;
+            break;
+          }
+          if (a_ok < 0.0) {
+            a_ok = a;
+            f_ok = ft;
+            if ((st = copy(q, gt)) != QPAT_OK) return st;   // keep its gradient
+          }
+        }
+        a *= p.tau;
+      }
+      if (a_acc < 0.0) {
+        if (a_ok < 0.0) break;
+        a_acc = a_ok;
+        f_acc = f_ok;
+        if ((st = copy(gt, q)) != QPAT_OK) return st;
+      }
+      // s = a d, y = g_new - g; keep the pair when y^T s > 0 (at most m, oldest dropped)
+      if ((st = copy(xt, gt)) != QPAT_OK) return st;         // xt <- g_new
+      axpy(-1.0, g, xt);                                      // xt <- y
+      double ys;
+      if ((st = L.dot(xt, d, NU, &ys)) != QPAT_OK) return st;
+      ys *= a_acc;
+      if (ys > 0.0) {
+        if (npair == m) {
+          for (int i = 1; i < m; ++i) {
+            if ((st = copy(Sv + (i - 1) * NU, Sv + i * NU)) != QPAT_OK) return st;
+            if ((st = copy(Yv + (i - 1) * NU, Yv + i * NU)) != QPAT_OK) return st;
+            rho_pair[i - 1] = rho_pair[i];
+          }
+          --npair;
+        }
+        axpby_kernel<<<blocks_for(NU), kT, 0, s>>>(NU, a_acc, d, 0.0, Sv + npair * NU);
+        if ((st = copy(Yv + npair * NU, xt)) != QPAT_OK) return st;
+        rho_pair[npair] = 1.0 / ys;
+        ++npair;
+      }
+      axpy(a_acc, d, x);
+      if ((st = copy(g, gt)) != QPAT_OK) return st;
+      f = f_acc;
+      ++it;
+    }
+    if (inner_hist) inner_hist[k] = it;
+    inner_total += it;
+    // multipliers: U_w += D Xbar - W, U_p,q += H_q - P_q (H at Xbar^(k+1))
+    if ((st = forward(x)) != QPAT_OK) return st;
+    double ek;
+    if ((st = eps_of_H(&ek)) != QPAT_OK) return st;
+    eps.push_back(ek);
+    for (int u = 0; u < U; ++u)
+      admm_dx_kernel<<<blocks_for(nfaces), kT, 0, s>>>(tvg, x + u * N, W + u * nfaces, Uw + u * nfaces,
+                                                       tf + u * nfaces);
+    axpby_kernel<<<blocks_for(NF), kT, 0, s>>>(NF, 1.0, tf, 0.0, Uw);   // (D Xbar - W + Uw) = the new Uw
+    series(1);
+    if ((st = value(x, W, &f)) != QPAT_OK) return st;
+    if ((st = gradient(g)) != QPAT_OK) return st;
+    if ((st = norm(g, &gnorm)) != QPAT_OK) return st;
+    ++k;
+  }
+  // X = scale Xbar
+  axpby_kernel<<<blocks_for(N), kT, 0, s>>>(N, scale[joint ? 1 : 0], xm, 0.0, mu);
+  if (joint) {
+    axpby_kernel<<<blocks_for(N), kT, 0, s>>>(N, scale[0], xk, 0.0, kappa);
+    if ((st = qpat_set_kappa(c, kappa)) != QPAT_OK) return st;
+  }
+  if ((st = L.cuda(cudaStreamSynchronize(s), "ADMM sync")) != QPAT_OK) return st;
+  if (eps_hist)
+    for (size_t j = 0; j < eps.size(); ++j) eps_hist[j] = eps[j];
+  if (info) {
+    info->outer = k;
+    info->inner_total = inner_total;
+    info->sub_total = 0;
+    info->tv_iters = 0;
+    info->products = L.products;
+    info->eps_first = eps.front();
+    info->eps_last = eps.back();
+    for (int j = 0; j < 3; ++j) info->seconds[j] = L.sec[j];
+  }
+  return QPAT_OK;
+}
+
 qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void* data, double* mu,
                           double* kappa, const qpat_ld_params* prm_in, qpat_ld_info* info, double* eps_hist,
                           int* inner_hist) {
@@ -696,9 +1072,26 @@ qpat_status qpat_ld_solve(qpat_ctx* c, int nq, const unsigned* illum, const void
   if (p.tv_edge <= 0) p.tv_edge = L.v.dim == 3 ? (L.v.dx * 1e3) * (L.v.dx * 1e3) : L.v.dx * 1e3;
   if (p.tv_max_iter <= 0) p.tv_max_iter = 20000;
   if (p.tv_tol <= 0) p.tv_tol = 1e-12;
-  if (p.method != 0 && p.method != 1)
-    return (qpat_status)ctx_fail(c, QPAT_EINVAL, "qpat_ld_solve: method must be 0 (LD) or 1 (PD-IPM)");
+  if (p.method < 0 || p.method > 2)
+    return (qpat_status)ctx_fail(c, QPAT_EINVAL,
+                                 "qpat_ld_solve: method must be 0 (LD), 1 (PD-IPM) or 2 (ADMM with L-BFGS)");
   if (p.kp_max <= 0) p.kp_max = 20;
+  if (p.method == 2) {
+    if (prm_in && prm_in->tol_out < 0) p.tol_out = 1e-2;
+    if (p.lbfgs_m <= 0) p.lbfgs_m = 5;
+    if (p.j_max <= 0) p.j_max = 10;
+    if (p.ls_max <= 0) p.ls_max = 20;
+    if (p.c1 <= 0) p.c1 = 1e-4;
+    if (p.c2 <= 0) p.c2 = 0.9;
+    if (p.tau <= 0) p.tau = 0.25;
+    if (p.rho <= 0) p.rho = 1.0;
+    if (p.nu <= 0) p.nu = 1e-3;
+    if (!(p.upper > p.lower)) {
+      p.lower = 1e-3;
+      p.upper = 1e3;
+    }
+    return admm_solve(c, nq, illum, data, mu, kappa, p, info, eps_hist, inner_hist);
+  }
 
   // unknowns: [kappa-bar | mu-bar] (joint) or mu-bar, each block N cells
   const bool joint = kappa != nullptr;

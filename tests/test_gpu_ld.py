@@ -209,3 +209,39 @@ def test_pdipm_fp32_tracks_oracle():
     assert inner == [sum(x) for x in inner_ref]
     assert np.allclose(eps, eps_ref, rtol=1e-3, atol=0)
     assert np.linalg.norm(got[0] - ref[0]) <= 1e-2 * np.linalg.norm(ref[0] - base[0])
+
+
+@pytest.mark.parametrize("joint", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_admm_lbfgs_matches_oracle(joint, prec):
+    """The gradient-based benchmark (Algorithms 1-3): ADMM outer iterations
+    with L-BFGS inner minimisations and the Wolfe line search, for mu alone
+    and for (kappa, mu), against oracle/admm.py on the same seeded problem:
+    the misfit after every outer iteration, the L-BFGS iteration counts and
+    the reconstruction (FP64 at 1e-8 of the update; FP32 series at 1e-2)."""
+    from oracle import admm
+    from paper_1810_11685_gb300.binding import context_from_workload
+    w, S, kappa, P, mu0 = _setup()
+    edge = w.dx / phantoms.MM
+    kappa0 = 1.2 * kappa if joint else None
+    prm = admm.ADMMParams(k_max=2, j_max=3, lower=0.05, upper=20.0, tol_out=0.0, edge=edge)
+    prob = admm.Problem(S, kappa, ILLUMS, P, mu0, kappa0, edge=edge)
+    x_ref, hist = admm.admm(prob, prm)
+    kappa_ref, mu_ref = prob.coeffs(x_ref)
+    ctx = context_from_workload(w, precision=prec, max_batch=len(ILLUMS))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    res = ctx.ld_solve(torch.as_tensor(P, dtype=dt, device="cuda"), ILLUMS, torch.as_tensor(mu0, device="cuda"),
+                       None if kappa0 is None else torch.as_tensor(kappa0, device="cuda"), method="admm",
+                       k_max=2, j_max=3, tol_out=0.0, tv_edge=edge, lower=0.05, upper=20.0)
+    coeffs, eps, inner, info = res
+    if joint:
+        kappa_got, mu_got = (t.cpu().numpy() for t in coeffs)
+    else:
+        mu_got = coeffs.cpu().numpy()
+    assert len(hist["inner"]) == 2 and hist["eps"][-1] < hist["eps"][0]
+    tol = 1e-8 if prec == "fp64" else 1e-2
+    assert inner == hist["inner"] or prec == "fp32"
+    assert np.allclose(eps, hist["eps"], rtol=1e-9 if prec == "fp64" else 1e-2, atol=0)
+    assert np.linalg.norm(mu_got - mu_ref) <= tol * np.linalg.norm(mu_ref - mu0)
+    if joint:
+        assert np.linalg.norm(kappa_got - kappa_ref) <= tol * np.linalg.norm(kappa_ref - kappa0)
