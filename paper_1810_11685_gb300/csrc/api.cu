@@ -864,6 +864,7 @@ qpat_status qpat_sync(qpat_ctx* c) {
     QCK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     QCK(cudaStreamSynchronize(c->stream));
     if (*c->h_err & 1) return fail(c, QPAT_ENONFINITE, "non-finite value in the acoustic fields");
+    if (*c->h_err & 2) return fail(c, QPAT_ETIMEOUT, "a bounded wait for a bulk copy gave up");
   }
   return QPAT_OK;
 }

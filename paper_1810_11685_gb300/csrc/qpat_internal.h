@@ -98,7 +98,7 @@ struct PropArgs {
   const IoPtrs<T>* io;
   int n;                  // sample index this launch reads or writes
   int flags;
-  int* err;               // device flags word (bit 0: non-finite)
+  int* err;               // device flags word (bit 0: non-finite; bit 1: a bounded wait gave up)
 };
 
 template <typename T>
