@@ -2,9 +2,10 @@
 // of fft_reg.cuh (the 3D counterpart of fast_kernels.cuh).
 //
 // x row pass (one thread group per pair of y-rows (k, j0), (k, j0 + 1)):
-//   start asynchronous copies (cp.async) of the two rows of every state and
-//   medium field the update reads into shared memory; load up to three
-//   incoming half spectra into registers, Hermitian-extend and pack the two
+//   start bulk copies of the two rows of up to three incoming half spectra
+//   and of every state and medium field the update reads into shared memory
+//   (cp.async pieces and direct spectrum loads at the small extents); take
+//   the spectra into registers, Hermitian-extend and pack the two
 //   rows into one complex sequence -> inverse x-FFT via conj(FFT(conj .))
 //   with the reversed plan -> wait for the copies -> pointwise update of one
 //   equation (row3_point) on the registers -> forward x-FFT -> split into the
@@ -53,6 +54,18 @@ constexpr int kRow3MinBlocks = QPAT_ROW3_MINB;
 #endif
 constexpr bool kRow3Descending = QPAT_ROW3_DESC != 0;
 
+// Row pass fed by bulk copies (cp.async.bulk issued by one thread onto two
+// mbarriers: the incoming half-spectrum rows before the inverse transform,
+// the operand rows before the update) instead of per-thread spectrum loads
+// and cp.async pieces (measured on GB300 at 288^3, N_t 300: 1.279e10 against
+// 1.192e10 forward+adjoint cell-steps/s).
+#ifndef QPAT_ROW3_BULK
+#define QPAT_ROW3_BULK 1
+#endif
+// (extents with one row pair per CTA; the small extents keep cp.async)
+template <int L>
+constexpr bool row3_bulk() { return QPAT_ROW3_BULK && rp3<L>() == 1; }
+
 // The row pass runs its Stockham stages in one shared buffer per row pair
 // (288^3: 1.11e10 against 1.09e10 cell-steps/s with two buffers).
 constexpr bool kRow3OneBuf = true;
@@ -62,6 +75,24 @@ constexpr bool kRow3OneBuf = true;
 template <int L, int NSX>
 constexpr int row3_stage_offset() {
   return (L + rp3<L>() * (kRow3OneBuf ? 1 : 2) * NSX * SGeom<L>::SL + 1) & ~1;
+}
+
+template <typename T, int L, int PH>
+constexpr size_t row3_fast_smem_base() {
+  typedef typename V2<T>::t C;
+  constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT), RP = rp3<L>();
+  constexpr bool SCATTER = (PH == A_R1 || PH == A_R1L);
+  return (size_t)row3_stage_offset<L, NSX>() * sizeof(C) + (size_t)RP * r3_nfields(PH) * 2 * L * sizeof(T) +
+         (SCATTER ? RP * 2 * L * sizeof(T) : 0);
+}
+// Byte offset of the bulk-copy mbarriers (after everything else, 16-aligned).
+template <typename T, int L, int PH>
+constexpr size_t row3_bulk_bar_offset() {
+  return (row3_fast_smem_base<T, L, PH>() + 15) & ~(size_t)15;
+}
+template <typename T, int L, int PH>
+constexpr size_t row3_fast_smem() {
+  return row3_bulk<L>() ? row3_bulk_bar_offset<T, L, PH>() + 16 : row3_fast_smem_base<T, L, PH>();
 }
 
 // Operand loader reading the staged rows: field f of row rr at point i.
@@ -105,19 +136,51 @@ row3_fast(const Prop3<T> a) {
   C* spec = a.spec + (long long)b * a.sstride + ((long long)k * a.ny + j0) * a.pitch;
   const bool skip_in = (a.flags & kSkipInput) != 0;
 
-  // the update's operands of both rows, copied while the spectra load and the
-  // inverse transform runs
-  if (valid) {
-    constexpr int CH = L * (int)sizeof(T) / 16;                  // 16-byte pieces per row
-    constexpr int PW = 16 / (int)sizeof(T);                      // elements per piece
+  constexpr bool BULK = row3_bulk<L>();
+  constexpr int kSpecRow = ((L / 2 + 1) + 1) & ~1;               // complex values per staged row (16-byte pieces)
+  static_assert(!BULK || kSpecRow * 2 * KIN <= NSX * SL, "staged spectra must fit the Stockham buffer");
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + row3_bulk_bar_offset<T, L, PH>());
+  C* const sp = bufA;
+  if constexpr (BULK) {
+    // one thread issues bulk copies of the incoming half-spectrum rows (into
+    // the Stockham buffer, which the first stage reads before anything writes
+    // it; counted on bar[0]) and of the update's operand rows (bar[1], waited
+    // for only before the update)
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      mbar_init(bar + 1, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const bool load_in = valid && !skip_in;
+      mbar_arrive_expect_tx(bar, load_in ? 2u * KIN * kSpecRow * (unsigned)sizeof(C) : 0u);
+      if (load_in)
+        for (int s = 0; s < KIN; ++s)
+          for (int rr = 0; rr < 2; ++rr)
+            bulk_g2s(sp + (s * 2 + rr) * kSpecRow, spec + s * a.slot + rr * a.pitch, kSpecRow * (unsigned)sizeof(C),
+                     bar);
+      mbar_arrive_expect_tx(bar + 1, valid ? 2u * NF * L * (unsigned)sizeof(T) : 0u);
+      if (valid)
+        for (int f = 0; f < NF; ++f)
+          for (int rr = 0; rr < 2; ++rr)
+            bulk_g2s(stage + (f * 2 + rr) * L, r3_row<T>(a, r3_field(PH, f), b, (long long)k * a.ny + j0 + rr),
+                     L * (unsigned)sizeof(T), bar + 1);
+    }
+  } else {
+    // the update's operands of both rows, copied while the spectra load and the
+    // inverse transform runs
+    if (valid) {
+      constexpr int CH = L * (int)sizeof(T) / 16;                  // 16-byte pieces per row
+      constexpr int PW = 16 / (int)sizeof(T);                      // elements per piece
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
+      for (int f = 0; f < NF; ++f)
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const T* src = r3_row<T>(a, r3_field(PH, f), b, (long long)k * a.ny + j0 + rr);
-        T* dst = stage + (f * 2 + rr) * L;
-        for (int piece = j; piece < CH; piece += TPT) cp_async16(dst + piece * PW, src + piece * PW);
-      }
+        for (int rr = 0; rr < 2; ++rr) {
+          const T* src = r3_row<T>(a, r3_field(PH, f), b, (long long)k * a.ny + j0 + rr);
+          T* dst = stage + (f * 2 + rr) * L;
+          for (int piece = j; piece < CH; piece += TPT) cp_async16(dst + piece * PW, src + piece * PW);
+        }
+    }
   }
   for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
 
@@ -125,11 +188,12 @@ row3_fast(const Prop3<T> a) {
   C y[KIN][Q1];
   if (!skip_in) {
     C v[KIN][P1];
+    if constexpr (BULK) row_bulk_wait(bar, a.err);
     if (j < L / P1) {
 #pragma unroll
       for (int s = 0; s < KIN; ++s) {
-        const C* r0 = spec + s * a.slot;
-        const C* r1 = r0 + a.pitch;
+        const C* r0 = BULK ? sp + (s * 2) * kSpecRow : spec + s * a.slot;
+        const C* r1 = BULK ? r0 + kSpecRow : r0 + a.pitch;
 #pragma unroll
         for (int r = 0; r < P1; ++r) {
           const int n = j + r * (L / P1);
@@ -146,6 +210,7 @@ row3_fast(const Prop3<T> a) {
         }
       }
     }
+    if constexpr (BULK) __syncthreads();                          // staged spectra read before the first stage writes
     fft_stockham<L, G::P1, G::P2, G::P3, KIN, kRow3OneBuf>(v, y, bufA, bufB, SL, j, tws);
   } else {
 #pragma unroll
@@ -160,7 +225,10 @@ row3_fast(const Prop3<T> a) {
     __syncthreads();
     if (valid) sensor_scatter_rows3<T>(a, b, k * a.ny + j0, sc, j, TPT);
   }
-  cp_async_wait_all();
+  if constexpr (BULK)
+    row_bulk_wait(bar + 1, a.err);
+  else
+    cp_async_wait_all();
   __syncthreads();
 
   // 2. pointwise update on grid points i = j + r L/Q1 of both rows;
@@ -324,14 +392,6 @@ zpass3_fast(const Prop3<T> a) {
   }
 }
 
-template <typename T, int L, int PH>
-constexpr size_t row3_fast_smem() {
-  typedef typename V2<T>::t C;
-  constexpr int KIN = r3_kin(PH), KOUT = r3_kout(PH), NSX = (KIN > KOUT ? KIN : KOUT), RP = rp3<L>();
-  constexpr bool SCATTER = (PH == A_R1 || PH == A_R1L);
-  return (size_t)row3_stage_offset<L, NSX>() * sizeof(C) + (size_t)RP * r3_nfields(PH) * 2 * L * sizeof(T) +
-         (SCATTER ? RP * 2 * L * sizeof(T) : 0);
-}
 template <typename T, int L, int NSX>
 constexpr size_t line3_fast_smem() {
   typedef typename V2<T>::t C;
