@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--n3", type=int, default=None, help="c5 only: interior nodes per axis (default 256)")
     p.add_argument("--medium-grid", default="c1", choices=["c1", "c2"],
                    help="medium workload: the 168^2 grid with 600 steps (c1) or the 576^2 grid with 2000 (c2)")
+    p.add_argument("--medium-precision", default="fp64", choices=["fp64", "fp32"],
+                   help="sweep precision of --workload medium (gradient sums FP64 in both)")
     p.add_argument("--ld-method", default="ld", choices=["ld", "pdipm", "admm"],
                    help="ld workload: lagged diffusivity (Algorithm 5), primal-dual interior point (Algorithm 6) "
                         "or the ADMM + L-BFGS benchmark (Algorithms 1-3)")
@@ -813,7 +815,8 @@ def run_ld(args):
 def run_medium(args):
     """Gradient of <w, H_a p0> in the sound speed and the density
     (qpat_vjp_medium) and the tangent J_c dc + J_rho drho (qpat_jvp_medium),
-    FP64, on the 128^2 interior of the 2D circle-sensor workload (168^2 FFT
+    with FP64 sweeps (or FP32 sweeps and FP64 gradient sums with
+    --medium-precision fp32), on the 128^2 interior of the 2D circle-sensor workload (168^2 FFT
     grid, 600 samples, 128 sensors), or with --medium-grid c2 on the 512^2
     bench workload (576^2 grid, 2000 samples, 256 sensors).  A cell-step is one FFT-grid cell
     advanced one time step by one sweep: the gradient runs the forward sweep
@@ -822,7 +825,8 @@ def run_medium(args):
     from paper_1810_11685_gb300.binding import context_from_workload
     w = phantoms.C1 if args.medium_grid == "c1" else phantoms.C2
     nt = args.nt or w.nt
-    ctx = context_from_workload(w, precision="fp64", nt=nt)
+    prec = args.medium_precision
+    ctx = context_from_workload(w, precision=prec, nt=nt)
     c, rho, _ = phantoms.acoustic_medium(w)
     rng = np.random.default_rng(w.seed + 5)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
@@ -845,8 +849,9 @@ def run_medium(args):
     tv, lv = timed(lambda: ctx.vjp_medium(p0, W))
     tj, lj = timed(lambda: ctx.jvp_medium(p0, dc, drho))
     G = w.grid * w.grid
-    # the plain FP64 forward + adjoint of the same problem, for scale
-    p0b, Wb = p0.unsqueeze(0), W.unsqueeze(0)
+    # the plain forward + adjoint of the same problem and precision, for scale
+    dt_ctx = torch.float64 if prec == "fp64" else torch.float32
+    p0b, Wb = p0.unsqueeze(0).to(dt_ctx), W.unsqueeze(0).to(dt_ctx)
     ctx.acoustic_forward(p0b)
     ctx.acoustic_adjoint(Wb)
     torch.cuda.synchronize()
@@ -856,14 +861,15 @@ def run_medium(args):
     torch.cuda.synchronize()
     tfa = time.perf_counter() - t0
     line = {"metric": "medium gradient (c, rho): cell-steps/s", "value": G * nt * 2 / tv, "unit": UNIT,
-            "n_gpus": 1, "steps": max(1, args.steps), "higher_is_better": True, "dtype": "f64",
+            "n_gpus": 1, "steps": max(1, args.steps), "higher_is_better": True,
+            "dtype": "f64" if prec == "fp64" else "f32 sweeps, f64 gradient sums",
             "data": "synthetic", "impl": "ours",
             "config": {"workload": f"2d {w.n}x{w.n} interior, {w.grid}x{w.grid} FFT grid, Nt={nt}, "
                                    f"{w.n_sensors} sensors, y={w.y}, gradient in c and rho", "nt": nt},
             "seconds_per_gradient": tv, "launches_per_gradient": lv, "us_per_launch_gradient": 1e6 * tv / lv,
             "seconds_per_tangent": tj, "launches_per_tangent": lj, "us_per_launch_tangent": 1e6 * tj / lj,
             "tangent_cell_steps_per_s": G * nt / tj,
-            "seconds_fp64_forward_plus_adjoint": tfa, "gradient_over_forward_plus_adjoint": tv / tfa}
+            f"seconds_{prec}_forward_plus_adjoint": tfa, "gradient_over_forward_plus_adjoint": tv / tfa}
     print(json.dumps(line), flush=True)
 
 

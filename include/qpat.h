@@ -209,14 +209,17 @@ qpat_status qpat_acoustic_resume(qpat_ctx* ctx, int batch, const void* ckpt, int
  * eq. num-p, tau and eta of eq. Twelve and the source of eq. s1; rho through
  * rho-bar at the nodes (eqs. num-rho, num-p) and at the staggered points
  * (eq. num-vel, the mean of two nodes).  c_ref and dt stay fixed.
- * Needs a 2D QPAT_FP64 context (else EINVAL).  FP64 device buffers:
- * p0 [n1][n0] interior initial pressure; dc, drho [ny][nx] (either may be
- * NULL: zero); dP and w [nt][ns]; g_c, g_rho [ny][nx] (either may be NULL:
- * not returned).  Workspace is allocated per call: the tangent needs 28
- * real and 8 complex grid fields, the gradient up to 33 real and 8 complex
- * plus a tape of 5 (lossless) or 7 real grid fields per stored time step.
- * The gradient keeps the tape of every step while that history fits in
- * 2 GiB; beyond, it stores the loop state (5 real grid fields) every K steps
+ * Needs a 2D context (else EINVAL).  The sweeps run in the context's
+ * precision; the directions, the weights, the outputs and the gradient sums
+ * over the time steps are FP64 in both.  FP64 device buffers whatever the
+ * context precision: p0 [n1][n0] interior initial pressure; dc, drho
+ * [ny][nx] (either may be NULL: zero); dP and w [nt][ns]; g_c, g_rho
+ * [ny][nx] (either may be NULL: not returned).  Workspace is allocated per
+ * call: the tangent needs 27 real grid fields of the context precision, one
+ * FP64 and 8 complex; the gradient up to 24 real of the context precision,
+ * 7 to 9 FP64 and 8 complex, plus a tape of 5 (lossless) or 7 real grid
+ * fields per stored time step.  The gradient keeps the tape of every step
+ * while that history fits in 2 GiB; beyond, it stores the loop state (5 real grid fields) every K steps
  * during the forward sweep and recomputes each segment's tape from its
  * checkpoint before the segment's transposed steps (K tape slots; K near
  * sqrt(5 nt / fields), or as set by qpat_set_medium_checkpoints).  The

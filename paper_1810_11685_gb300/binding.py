@@ -461,7 +461,8 @@ class Context:
 
     def jvp_medium(self, p0, dc=None, drho=None):
         """qpat_jvp_medium: J_c dc + J_rho drho at the interior initial
-        pressure p0 (FP64 2D contexts); dc, drho on the full grid."""
+        pressure p0 (2D contexts; the sweep in the context precision, the
+        buffers FP64); dc, drho on the full grid."""
         import torch
         p0 = self._one(self._in(p0, torch.float64, self.interior_shape), "p0")
         dc = None if dc is None else self._one(self._in(dc, torch.float64, self.grid_shape), "dc")

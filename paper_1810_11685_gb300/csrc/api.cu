@@ -91,6 +91,13 @@ const PropArgs<double>* ctx_tables64(const qpat_ctx* c, double* y, int* lossless
   *stream = c->stream;
   return &c->pd;
 }
+const PropArgs<float>* ctx_tables32(const qpat_ctx* c, double* y, int* lossless, cudaStream_t* stream) {
+  if (!c || c->prec != QPAT_FP32 || c->dim != 2) return nullptr;
+  *y = c->cfg.y;
+  *lossless = c->cfg.lossless;
+  *stream = c->stream;
+  return &c->pf;
+}
 void ctx_add_launches(qpat_ctx* c, long long n) {
   if (c) c->launches += n;
 }

@@ -2,8 +2,9 @@
 // entry points qpat_jvp_medium and qpat_vjp_medium over the loops of
 // medium_ops.cuh (tangent loop; forward loop followed by its exact transpose,
 // with the forward fields kept for every step or recomputed segment by
-// segment from forward-state checkpoints), run on an FP64 2D context's own
-// tables.  Every per-element functor is launched as a grid-stride kernel on
+// segment from forward-state checkpoints), run on a 2D context's own tables
+// in its precision (FP64 or FP32; directions, weights, outputs and gradient
+// sums FP64).  Every per-element functor is launched as a grid-stride kernel on
 // the context's stream; 2D FFTs run as one shared-memory line-FFT launch per
 // axis.
 #include <math.h>
@@ -15,9 +16,11 @@
 #include "qpat_internal.h"
 
 namespace qpat {
-// Defined in api.cu: the FP64 2D tables of a context (NULL for FP32 or 3D
-// contexts), the absorption exponent, the lossless flag and the stream.
+// Defined in api.cu: the FP64 (FP32) 2D tables of a context (NULL for a
+// context of the other precision or a 3D context), the absorption exponent,
+// the lossless flag and the stream.
 const PropArgs<double>* ctx_tables64(const ::qpat_ctx* c, double* y, int* lossless, cudaStream_t* stream);
+const PropArgs<float>* ctx_tables32(const ::qpat_ctx* c, double* y, int* lossless, cudaStream_t* stream);
 void ctx_add_launches(::qpat_ctx* c, long long n);
 // Checkpoint interval of the medium gradient set on the context (0: automatic).
 int ctx_medium_k(const ::qpat_ctx* c);
@@ -46,22 +49,24 @@ __global__ void __launch_bounds__(kThreads) for_each_kernel(const F f, long long
 // runs the mixed-radix Stockham stages of fft_batch there and stores back.
 // inv: the unnormalised inverse DFT, as conj(FFT(conj x)).
 constexpr int kLineThreads = 256;
-template <bool ALONG_X>
-__global__ void __launch_bounds__(kLineThreads) line_fft_kernel(double2* Z, long long G, int nx, int ny,
-                                                                 const FFTPlan plan, const double2* tw, int inv,
-                                                                 int M) {
-  extern __shared__ double2 sm_line[];
+template <bool ALONG_X, typename C>
+__global__ void __launch_bounds__(kLineThreads) line_fft_kernel(C* Z, long long G, int nx, int ny,
+                                                                 const FFTPlan plan, const C* tw, int inv, int M) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* sm_line = reinterpret_cast<C*>(sm_raw);
   const int L = plan.L, S = L + 1;
-  double2* buf0 = sm_line;
-  double2* buf1 = sm_line + M * S;
+  C* buf0 = sm_line;
+  C* buf1 = sm_line + M * S;
   const int nlines = ALONG_X ? ny : nx;
   const int line0 = blockIdx.x * M;
   const int mloc = min(M, nlines - line0);
-  double2* Zb = Z + (long long)blockIdx.y * G;
+  C* Zb = Z + (long long)blockIdx.y * G;
   for (int t = threadIdx.x; t < M * L; t += blockDim.x) {
     const int m = ALONG_X ? t / L : t % M;
     const int i = ALONG_X ? t - m * L : t / M;
-    double2 v = make_double2(0.0, 0.0);
+    C v;
+    v.x = 0;
+    v.y = 0;
     if (m < mloc) {
       v = Zb[ALONG_X ? (long long)(line0 + m) * nx + i : (long long)i * nx + line0 + m];
       if (inv) v.y = -v.y;
@@ -69,12 +74,12 @@ __global__ void __launch_bounds__(kLineThreads) line_fft_kernel(double2* Z, long
     buf0[m * S + i] = v;
   }
   __syncthreads();
-  const double2* res = fft_batch(plan, buf0, buf1, M, S, tw);
+  const C* res = fft_batch(plan, buf0, buf1, M, S, tw);
   for (int t = threadIdx.x; t < M * L; t += blockDim.x) {
     const int m = ALONG_X ? t / L : t % M;
     const int i = ALONG_X ? t - m * L : t / M;
     if (m < mloc) {
-      double2 v = res[m * S + i];
+      C v = res[m * S + i];
       if (inv) v.y = -v.y;
       Zb[ALONG_X ? (long long)(line0 + m) * nx + i : (long long)i * nx + line0 + m] = v;
     }
@@ -82,8 +87,8 @@ __global__ void __launch_bounds__(kLineThreads) line_fft_kernel(double2* Z, long
 }
 
 // Lines per CTA: about 48 KB of shared memory per buffer, 1 to 16 lines.
-int lines_per_cta(int L) {
-  const int m = 49152 / ((L + 1) * (int)sizeof(double2));
+int lines_per_cta(int L, int csize) {
+  const int m = 49152 / ((L + 1) * csize);
   return m < 1 ? 1 : m > 16 ? 16 : m;
 }
 
@@ -100,24 +105,28 @@ struct GpuEx {
   long long launches = 0;
   cudaError_t err = cudaSuccess;
   // 2D FFT of nb fields of G points in place: the rows, then the columns
-  void fft2(double2* Z, int nb, int inv, const Tables& t, long long G) {
+  template <typename R>
+  void fft2(Cplx<R>* Z, int nb, int inv, const Tables<R>& t, long long G) {
+    typedef Cplx<R> C;
     if (nb <= 0 || err != cudaSuccess) return;
     for (int ax = 0; ax < 2; ++ax) {
       const FFTPlan plan = to_fft_plan(ax == 0 ? t.px : t.py);
-      const int M = lines_per_cta(plan.L);
+      const int M = lines_per_cta(plan.L, (int)sizeof(C));
       const int nlines = ax == 0 ? t.ny : t.nx;
-      const size_t smem = 2 * (size_t)M * (plan.L + 1) * sizeof(double2);
+      const size_t smem = 2 * (size_t)M * (plan.L + 1) * sizeof(C);
       const dim3 grid((nlines + M - 1) / M, nb);
-      cudaError_t e = ax == 0 ? cudaFuncSetAttribute(line_fft_kernel<true>,
+      cudaError_t e = ax == 0 ? cudaFuncSetAttribute(line_fft_kernel<true, C>,
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                              : cudaFuncSetAttribute(line_fft_kernel<false>,
+                              : cudaFuncSetAttribute(line_fft_kernel<false, C>,
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) {
         err = e;
         return;
       }
-      if (ax == 0) line_fft_kernel<true><<<grid, kLineThreads, smem, s>>>(Z, G, t.nx, t.ny, plan, t.twx, inv, M);
-      else line_fft_kernel<false><<<grid, kLineThreads, smem, s>>>(Z, G, t.nx, t.ny, plan, t.twy, inv, M);
+      if (ax == 0)
+        line_fft_kernel<true, C><<<grid, kLineThreads, smem, s>>>(Z, G, t.nx, t.ny, plan, t.twx, inv, M);
+      else
+        line_fft_kernel<false, C><<<grid, kLineThreads, smem, s>>>(Z, G, t.nx, t.ny, plan, t.twy, inv, M);
       ++launches;
       e = cudaGetLastError();
       if (e != cudaSuccess) {
@@ -168,11 +177,16 @@ void copy_plan(const FFTPlan& in, Plan& out) {
   for (int s = 0; s < in.nstages && s < med::kMaxStages; ++s) out.radix[s] = in.radix[s];
 }
 
-int tables_of(qpat_ctx* c, Tables& t, cudaStream_t* s) {
+// Tables of a 2D context of precision R; QPAT_EINVAL when the context is of
+// the other precision or 3D.
+template <typename R>
+int tables_of(qpat_ctx* c, Tables<R>& t, cudaStream_t* s) {
   double y = 0.0;
   int lossless = 0;
-  const PropArgs<double>* a = ctx_tables64(c, &y, &lossless, s);
-  if (!a) return ctx_fail(c, QPAT_EINVAL, "medium derivatives need a 2D FP64 context");
+  const PropArgs<R>* a;
+  if constexpr (sizeof(R) == sizeof(double)) a = ctx_tables64(c, &y, &lossless, s);
+  else a = ctx_tables32(c, &y, &lossless, s);
+  if (!a) return ctx_fail(c, QPAT_EINVAL, "medium derivatives need a 2D context");
   t.nx = a->nx; t.ny = a->ny; t.nxh = a->nxh; t.pml = a->pml; t.n0 = a->n0; t.n1 = a->n1; t.ns = a->ns;
   t.nt = a->nt; t.lossless = lossless; t.dt = a->dt; t.y = y;
   t.Cc = a->Cc; t.rho0 = a->rho0; t.dtrsx = a->dtrsx; t.dtrsy = a->dtrsy; t.tau = a->tau; t.eta = a->eta;
@@ -196,13 +210,9 @@ int finish(qpat_ctx* c, GpuEx& ex, Arena& w) {
   return ctx_fail(c, e == cudaErrorMemoryAllocation ? QPAT_ENOMEM : QPAT_ECUDA, cudaGetErrorString(e));
 }
 
-}  // namespace
-
-extern "C" qpat_status qpat_jvp_medium(qpat_ctx* ctx, const double* p0, const double* dc, const double* drho,
-                                       double* dP) {
-  if (!ctx) return QPAT_EINVAL;
-  if (!p0 || !dP) return (qpat_status)ctx_fail(ctx, QPAT_EINVAL, "qpat_jvp_medium: p0 and dP are required");
-  Tables t{};
+template <typename R>
+qpat_status jvp_medium(qpat_ctx* ctx, const double* p0, const double* dc, const double* drho, double* dP) {
+  Tables<R> t{};
   cudaStream_t s = nullptr;
   int st = tables_of(ctx, t, &s);
   if (st != QPAT_OK) return (qpat_status)st;
@@ -211,26 +221,23 @@ extern "C" qpat_status qpat_jvp_medium(qpat_ctx* ctx, const double* p0, const do
   w.s = s;
   GpuEx ex;
   ex.s = s;
-  Fields f{};
-  for (double** q : {&f.P0, &f.p, &f.vx, &f.vy, &f.rx, &f.ry, &f.r, &f.u, &f.gx, &f.gy, &f.dx, &f.dy, &f.Yr, &f.Yu,
-                     &f.dp, &f.dvx, &f.dvy, &f.drx, &f.dry, &f.dr, &f.du, &f.dgx, &f.dgy, &f.ddx, &f.ddy, &f.YdR,
-                     &f.Ydu})
-    *q = w.get<double>(G);
+  Fields<R> f{};
+  for (R** q : {&f.P0, &f.p, &f.vx, &f.vy, &f.rx, &f.ry, &f.r, &f.u, &f.gx, &f.gy, &f.dx, &f.dy, &f.Yr, &f.Yu,
+                &f.dp, &f.dvx, &f.dvy, &f.drx, &f.dry, &f.dr, &f.du, &f.dgx, &f.dgy, &f.ddx, &f.ddy, &f.YdR, &f.Ydu})
+    *q = w.get<R>(G);
   double* zero = w.get<double>(G);
-  double2* Z[2];
-  for (double2*& z : Z) z = w.get<double2>(kMaxBatch * G);
+  Cplx<R>* Z[2];
+  for (Cplx<R>*& z : Z) z = w.get<Cplx<R>>(kMaxBatch * G);
   if (w.err != cudaSuccess) return (qpat_status)finish(ctx, ex, w);
-  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1]};
-  ex.run(G, Embed{t, p0, f.P0});
+  Spectral<GpuEx, R> S{ex, t, G, Z[0], Z[1]};
+  ex.run(G, Embed<R>{t, p0, f.P0});
   jvp_loop(ex, t, S, f, dc ? dc : zero, drho ? drho : zero, dP);
   return (qpat_status)finish(ctx, ex, w);
 }
 
-extern "C" qpat_status qpat_vjp_medium(qpat_ctx* ctx, const double* p0, const double* wts, double* g_c,
-                                       double* g_rho) {
-  if (!ctx) return QPAT_EINVAL;
-  if (!p0 || !wts) return (qpat_status)ctx_fail(ctx, QPAT_EINVAL, "qpat_vjp_medium: p0 and w are required");
-  Tables t{};
+template <typename R>
+qpat_status vjp_medium(qpat_ctx* ctx, const double* p0, const double* wts, double* g_c, double* g_rho) {
+  Tables<R> t{};
   cudaStream_t s = nullptr;
   int st = tables_of(ctx, t, &s);
   if (st != QPAT_OK) return (qpat_status)st;
@@ -239,8 +246,8 @@ extern "C" qpat_status qpat_vjp_medium(qpat_ctx* ctx, const double* p0, const do
   w.s = s;
   GpuEx ex;
   ex.s = s;
-  Fields f{};
-  for (double** q : {&f.P0, &f.p, &f.vx, &f.vy, &f.rx, &f.ry, &f.r, &f.u}) *q = w.get<double>(G);
+  Fields<R> f{};
+  for (R** q : {&f.P0, &f.p, &f.vx, &f.vy, &f.rx, &f.ry, &f.r, &f.u}) *q = w.get<R>(G);
   // Tape length: every step while the whole history stays within
   // kFullTapeBytes, else checkpoints every K steps with K near
   // sqrt(5 nt / fields), which minimises checkpoints (5 fields each) plus
@@ -248,29 +255,56 @@ extern "C" qpat_status qpat_vjp_medium(qpat_ctx* ctx, const double* p0, const do
   const int nf = t.lossless ? 5 : 7;
   int K = ctx_medium_k(ctx);
   if (K <= 0) {
-    K = (double)t.nt * nf * G * sizeof(double) <= kFullTapeBytes
-            ? t.nt
-            : (int)ceil(sqrt(5.0 * t.nt / nf));
+    K = (double)t.nt * nf * G * sizeof(R) <= kFullTapeBytes ? t.nt : (int)ceil(sqrt(5.0 * t.nt / nf));
   }
   if (K > t.nt) K = t.nt;
-  Tape tp{};
-  for (double** q : {&tp.gx, &tp.gy, &tp.dx, &tp.dy, &tp.X}) *q = w.get<double>(G * K);
+  Tape<R> tp{};
+  for (R** q : {&tp.gx, &tp.gy, &tp.dx, &tp.dy, &tp.X}) *q = w.get<R>(G * K);
   if (!t.lossless) {
-    tp.Yr = w.get<double>(G * K);
-    tp.Yu = w.get<double>(G * K);
+    tp.Yr = w.get<R>(G * K);
+    tp.Yu = w.get<R>(G * K);
   }
-  double* ck = K < t.nt ? w.get<double>(5 * G * ((t.nt + K - 1) / K)) : nullptr;
-  RevFields b{};
-  for (double** q : {&b.pb, &b.Cp, &b.e1, &b.e2, &b.t1, &b.ub, &b.rbx, &b.rby, &b.dbx, &b.dby, &b.vbx, &b.vby,
-                     &b.fx, &b.fy, &b.ex, &b.ey, &b.qb, &b.gC, &b.gtau, &b.geta, &b.grho, &b.grsx, &b.grsy})
-    *q = w.get<double>(G);
+  R* ck = K < t.nt ? w.get<R>(5 * G * ((t.nt + K - 1) / K)) : nullptr;
+  RevFields<R> b{};
+  for (R** q : {&b.pb, &b.Cp, &b.e1, &b.e2, &b.t1, &b.ub, &b.rbx, &b.rby, &b.dbx, &b.dby, &b.vbx, &b.vby, &b.fx,
+                &b.fy, &b.ex, &b.ey})
+    *q = w.get<R>(G);
+  for (double** q : {&b.qb, &b.gC, &b.gtau, &b.geta, &b.grho, &b.grsx, &b.grsy}) *q = w.get<double>(G);
   double* gc = g_c ? g_c : w.get<double>(G);
   double* gr = g_rho ? g_rho : w.get<double>(G);
-  double2* Z[2];
-  for (double2*& z : Z) z = w.get<double2>(kMaxBatch * G);
+  Cplx<R>* Z[2];
+  for (Cplx<R>*& z : Z) z = w.get<Cplx<R>>(kMaxBatch * G);
   if (w.err != cudaSuccess) return (qpat_status)finish(ctx, ex, w);
-  Spectral<GpuEx> S{ex, t, G, Z[0], Z[1]};
-  ex.run(G, Embed{t, p0, f.P0});
+  Spectral<GpuEx, R> S{ex, t, G, Z[0], Z[1]};
+  ex.run(G, Embed<R>{t, p0, f.P0});
   vjp_loop(ex, t, S, f, tp, b, K, ck, wts, gc, gr);
   return (qpat_status)finish(ctx, ex, w);
+}
+
+// Sweep precision of a context: its own (FP64 or FP32), -1 for 3D.
+int sweep_precision(qpat_ctx* c) {
+  double y;
+  int lossless;
+  cudaStream_t s;
+  if (ctx_tables64(c, &y, &lossless, &s)) return QPAT_FP64;
+  if (ctx_tables32(c, &y, &lossless, &s)) return QPAT_FP32;
+  return -1;
+}
+
+}  // namespace
+
+extern "C" qpat_status qpat_jvp_medium(qpat_ctx* ctx, const double* p0, const double* dc, const double* drho,
+                                       double* dP) {
+  if (!ctx) return QPAT_EINVAL;
+  if (!p0 || !dP) return (qpat_status)ctx_fail(ctx, QPAT_EINVAL, "qpat_jvp_medium: p0 and dP are required");
+  return sweep_precision(ctx) == QPAT_FP32 ? jvp_medium<float>(ctx, p0, dc, drho, dP)
+                                           : jvp_medium<double>(ctx, p0, dc, drho, dP);
+}
+
+extern "C" qpat_status qpat_vjp_medium(qpat_ctx* ctx, const double* p0, const double* wts, double* g_c,
+                                       double* g_rho) {
+  if (!ctx) return QPAT_EINVAL;
+  if (!p0 || !wts) return (qpat_status)ctx_fail(ctx, QPAT_EINVAL, "qpat_vjp_medium: p0 and w are required");
+  return sweep_precision(ctx) == QPAT_FP32 ? vjp_medium<float>(ctx, p0, wts, g_c, g_rho)
+                                           : vjp_medium<double>(ctx, p0, wts, g_c, g_rho);
 }

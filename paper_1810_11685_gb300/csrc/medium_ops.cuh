@@ -1,5 +1,6 @@
 // Derivatives of the acoustic data in the medium (sound speed c, ambient
-// density rho), FP64, 2D.
+// density rho), 2D, with the sweeps in the context's precision (FP64 or FP32)
+// and the gradient sums in FP64.
 //
 // The paper's Discussion names a joint reconstruction of the optical
 // coefficients and the sound speed as the next step.  Its Jacobian needs the
@@ -27,9 +28,13 @@
 // up to four fields (a field and its tangent, the velocity components, the
 // absorption inputs) share each launch.
 //
-// Every per-element body is a functor; the loops are templates over the
-// executor type, whose one implementation (GpuEx in medium.cu) launches each
-// functor as a grid-stride kernel on the context's stream.
+// Every per-element body is a functor templated on the sweep's real type R;
+// the loops are templates over R and the executor type, whose one
+// implementation (GpuEx in medium.cu) launches each functor as a grid-stride
+// kernel on the context's stream.  The directions (dc, drho), the sensor
+// weights w and every output are FP64 whatever R is; the products that feed
+// the gradient are formed and summed in FP64 over the N_t steps, so that an
+// FP32 sweep rounds each step's contribution once instead of the running sum.
 #pragma once
 
 #include <math.h>
@@ -46,11 +51,26 @@
 namespace qpat {
 namespace med {
 
-QPAT_HD double2 z(double a, double b) { double2 r; r.x = a; r.y = b; return r; }
-QPAT_HD double2 zadd(double2 a, double2 b) { return z(a.x + b.x, a.y + b.y); }
-QPAT_HD double2 zmul(double2 a, double2 b) { return z(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-QPAT_HD double2 zconj(double2 a) { return z(a.x, -a.y); }
-QPAT_HD double2 zscale(double2 a, double s) { return z(a.x * s, a.y * s); }
+// Complex type of a real type.
+template <typename R>
+struct CplxOf;
+template <>
+struct CplxOf<double> { typedef double2 t; };
+template <>
+struct CplxOf<float> { typedef float2 t; };
+template <typename R>
+using Cplx = typename CplxOf<R>::t;
+
+template <typename R>
+QPAT_HD Cplx<R> z(R a, R b) { Cplx<R> r; r.x = a; r.y = b; return r; }
+template <typename C>
+QPAT_HD C zadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C>
+QPAT_HD C zmul(C a, C b) { C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r; }
+template <typename C>
+QPAT_HD C zconj(C a) { a.y = -a.y; return a; }
+template <typename C, typename R>
+QPAT_HD C zscale(C a, R s) { a.x *= s; a.y *= s; return a; }
 
 constexpr int kMaxStages = 16;
 struct Plan {
@@ -65,17 +85,20 @@ struct Plan {
 // ([nxh] along x, [ny] along y); twiddles W_L^m = e^{-2 pi i m / L};
 // sensors in gather form ([ns][4] indices and bilinear weights) and in the
 // row-wise scatter form (rowptr [ny+1], point columns, per-point entries).
+template <typename R>
 struct Tables {
+  typedef Cplx<R> C;
   int nx, ny, nxh, pml, n0, n1, ns, nt, lossless;
-  double dt, y;
-  const double *Cc, *rho0, *dtrsx, *dtrsy, *tau, *eta;
-  const double *ax, *asx, *ay, *asy;
-  const double *kap, *kp1, *kp2;
-  const double2 *shxp, *shxm, *shyp, *shym, *twx, *twy;
+  R dt;
+  double y;
+  const R *Cc, *rho0, *dtrsx, *dtrsy, *tau, *eta;
+  const R *ax, *asx, *ay, *asy;
+  const R *kap, *kp1, *kp2;
+  const C *shxp, *shxm, *shyp, *shym, *twx, *twy;
   const int* sidx;
-  const double* sw;
+  const R* sw;
   const int *rowptr, *pcol, *pent, *esens;
-  const double* ew;
+  const R* ew;
   Plan px, py;
 };
 
@@ -84,61 +107,65 @@ enum Symbol { kDPX = 0, kDPY = 1, kDMX = 2, kDMY = 3, kYDIS = 4, kYABS = 5 };
 // Symbol at spectral bin (j, i) of the full nx x ny spectrum.  Bins
 // i >= nxh mirror i' = nx - i: |k| is even in kx and i kx e^{+-i kx dx/2} is
 // Hermitian, so the value there is the conjugate of the stored one.
-QPAT_HD double2 symbol(const Tables& t, int which, int j, int i) {
+template <typename R>
+QPAT_HD Cplx<R> symbol(const Tables<R>& t, int which, int j, int i) {
   const bool mir = i >= t.nxh;
   const int im = mir ? t.nx - i : i;
   const long long kt = (long long)j * t.nxh + im;
-  double2 s;
+  Cplx<R> s;
   switch (which) {
     case kDPX: s = t.shxp[im]; if (mir) s = zconj(s); return zscale(s, t.kap[kt]);
     case kDMX: s = t.shxm[im]; if (mir) s = zconj(s); return zscale(s, t.kap[kt]);
     case kDPY: return zscale(t.shyp[j], t.kap[kt]);
     case kDMY: return zscale(t.shym[j], t.kap[kt]);
-    case kYDIS: return z(t.kp1[kt], 0.0);
-    default: return z(t.kp2[kt], 0.0);
+    case kYDIS: return z<R>(t.kp1[kt], (R)0);
+    default: return z<R>(t.kp2[kt], (R)0);
   }
 }
 
 constexpr int kMaxBatch = 4;
 
 // Z[b G + g] = f_b[g] + 0 i for nb fields
+template <typename R>
 struct LoadReal {
-  const double* f[kMaxBatch];
-  double2* Z;
+  const R* f[kMaxBatch];
+  Cplx<R>* Z;
   long long G;
   QPAT_HD void operator()(long long t) const {
     const long long b = t / G;
-    Z[t] = z(f[b][t - b * G], 0.0);
+    Z[t] = z<R>(f[b][t - b * G], (R)0);
   }
 };
 // out_b = alpha Re(Z[b G + .]), or out_b += alpha Re(...) when acc
+template <typename R>
 struct StoreReal {
-  const double2* Z;
-  double* out[kMaxBatch];
-  double alpha;
+  const Cplx<R>* Z;
+  R* out[kMaxBatch];
+  R alpha;
   int acc;
   long long G;
   QPAT_HD void operator()(long long t) const {
     const long long b = t / G, g = t - b * G;
-    const double v = alpha * Z[t].x;
+    const R v = alpha * Z[t].x;
     out[b][g] = acc ? out[b][g] + v : v;
   }
 };
 // Output o: Zo[o G + g] = sum over its nterm[o] terms q of sym[o][q]
 // (conjugated when conj) * Zi[in[o][q] G + g].
+template <typename R>
 struct Combine {
-  Tables t;
-  const double2* Zi;
-  double2* Zo;
+  Tables<R> t;
+  const Cplx<R>* Zi;
+  Cplx<R>* Zo;
   int nterm[kMaxBatch], in[kMaxBatch][2], sym[kMaxBatch][2];
   int conj;
   long long G;
   QPAT_HD void operator()(long long u) const {
     const long long o = u / G, g = u - o * G;
     const int i = (int)(g % t.nx), j = (int)(g / t.nx);
-    double2 r = z(0.0, 0.0);
+    Cplx<R> r = z<R>((R)0, (R)0);
     for (int q = 0; q < nterm[o]; ++q) {
-      double2 a = symbol(t, sym[o][q], j, i);
+      Cplx<R> a = symbol(t, sym[o][q], j, i);
       if (conj) a = zconj(a);
       r = zadd(r, zmul(a, Zi[in[o][q] * G + g]));
     }
@@ -146,60 +173,70 @@ struct Combine {
   }
 };
 
-// Interior p0 [n1][n0] -> full grid, zero in the PML.
+// Interior p0 [n1][n0] (FP64) -> full grid in the sweep's precision, zero
+// in the PML.
+template <typename R>
 struct Embed {
-  Tables t;
+  Tables<R> t;
   const double* p0;
-  double* P;
+  R* P;
   QPAT_HD void operator()(long long g) const {
     const int i = (int)(g % t.nx) - t.pml, j = (int)(g / t.nx) - t.pml;
-    P[g] = (i >= 0 && i < t.n0 && j >= 0 && j < t.n1) ? p0[(long long)j * t.n0 + i] : 0.0;
+    P[g] = (i >= 0 && i < t.n0 && j >= 0 && j < t.n1) ? (R)p0[(long long)j * t.n0 + i] : (R)0;
   }
 };
 
 // Staggered density perturbation of axis x / y at node g: the mean of the
 // node and its + neighbour (periodic), as for rho-bar_i itself.
-QPAT_HD double stag_x(const Tables& t, const double* f, long long g) {
+// (F: the field's type.)
+template <class Tb, typename F>
+QPAT_HD F stag_x(const Tb& t, const F* f, long long g) {
   const int i = (int)(g % t.nx);
-  return 0.5 * (f[g] + f[g - i + (i + 1) % t.nx]);
+  return (F)0.5 * (f[g] + f[g - i + (i + 1) % t.nx]);
 }
-QPAT_HD double stag_y(const Tables& t, const double* f, long long g) {
+template <class Tb, typename F>
+QPAT_HD F stag_y(const Tb& t, const F* f, long long g) {
   const long long G = (long long)t.nx * t.ny;
   const long long gn = g + t.nx;
-  return 0.5 * (f[g] + f[gn >= G ? gn - G : gn]);
+  return (F)0.5 * (f[g] + f[gn >= G ? gn - G : gn]);
 }
 // Transpose of stag_x / stag_y: the mean of the node and its - neighbour.
-QPAT_HD double stag_x_T(const Tables& t, const double* f, long long g) {
+template <class Tb, typename F>
+QPAT_HD F stag_x_T(const Tb& t, const F* f, long long g) {
   const int i = (int)(g % t.nx);
-  return 0.5 * (f[g] + f[g - i + (i + t.nx - 1) % t.nx]);
+  return (F)0.5 * (f[g] + f[g - i + (i + t.nx - 1) % t.nx]);
 }
-QPAT_HD double stag_y_T(const Tables& t, const double* f, long long g) {
+template <class Tb, typename F>
+QPAT_HD F stag_y_T(const Tb& t, const F* f, long long g) {
   const long long G = (long long)t.nx * t.ny;
   const long long gp = g - t.nx;
-  return 0.5 * (f[g] + f[gp < 0 ? gp + G : gp]);
+  return (F)0.5 * (f[g] + f[gp < 0 ? gp + G : gp]);
 }
 
-// Sensor gather of one time sample: out[s] = sum of the 4 bilinear corners.
+// Sensor gather of one time sample: out[s] = sum of the 4 bilinear corners
+// (summed and stored in FP64).
+template <typename R>
 struct Gather {
-  Tables t;
-  const double* f;
+  Tables<R> t;
+  const R* f;
   double* out;
   QPAT_HD void operator()(long long s) const {
     double a = 0.0;
-    for (int q = 0; q < 4; ++q) a += t.sw[4 * s + q] * f[t.sidx[4 * s + q]];
+    for (int q = 0; q < 4; ++q) a += (double)t.sw[4 * s + q] * f[t.sidx[4 * s + q]];
     out[s] = a;
   }
 };
-// Transposed sensor gather, one thread per grid row: f += M^T w.
+// Transposed sensor gather, one thread per grid row: f += M^T w (w FP64).
+template <typename R>
 struct Scatter {
-  Tables t;
+  Tables<R> t;
   const double* w;
-  double* f;
+  R* f;
   QPAT_HD void operator()(long long row) const {
     for (int p = t.rowptr[row]; p < t.rowptr[row + 1]; ++p) {
       double a = 0.0;
-      for (int e = t.pent[p]; e < t.pent[p + 1]; ++e) a += t.ew[e] * w[t.esens[e]];
-      f[row * t.nx + t.pcol[p]] += a;
+      for (int e = t.pent[p]; e < t.pent[p + 1]; ++e) a += (double)t.ew[e] * w[t.esens[e]];
+      f[row * t.nx + t.pcol[p]] += (R)a;
     }
   }
 };
@@ -216,18 +253,20 @@ namespace med {
 
 // eq. num-vel, and along (dc, drho) its tangent when dvx != nullptr:
 // v_i = A_i (A_i v_i - (dt / rho_i) g_i), d(dt / rho_i) = -(dt / rho_i)^2 drho_i / dt.
+template <typename R>
 struct Vel {
-  Tables t;
-  const double *gx, *gy, *dgx, *dgy, *drho;
-  double *vx, *vy, *dvx, *dvy;
+  Tables<R> t;
+  const R *gx, *gy, *dgx, *dgy;
+  const double* drho;
+  R *vx, *vy, *dvx, *dvy;
   QPAT_HD void operator()(long long g) const {
     const int i = (int)(g % t.nx), j = (int)(g / t.nx);
-    const double ax = t.asx[i], ay = t.asy[j], bx = t.dtrsx[g], by = t.dtrsy[g];
+    const R ax = t.asx[i], ay = t.asy[j], bx = t.dtrsx[g], by = t.dtrsy[g];
     vx[g] = ax * (ax * vx[g] - bx * gx[g]);
     vy[g] = ay * (ay * vy[g] - by * gy[g]);
     if (dvx) {
-      dvx[g] = ax * (ax * dvx[g] - bx * dgx[g] + bx * bx / t.dt * stag_x(t, drho, g) * gx[g]);
-      dvy[g] = ay * (ay * dvy[g] - by * dgy[g] + by * by / t.dt * stag_y(t, drho, g) * gy[g]);
+      dvx[g] = ax * (ax * dvx[g] - bx * dgx[g] + bx * bx / t.dt * (R)stag_x(t, drho, g) * gx[g]);
+      dvy[g] = ay * (ay * dvy[g] - by * dgy[g] + by * by / t.dt * (R)stag_y(t, drho, g) * gy[g]);
     }
   }
 };
@@ -235,26 +274,29 @@ struct Vel {
 // eq. num-rho with the source of eq. s1 (src: n = -1, 0), the sums
 // r = sum rho_i and u = sum A_i rho divergence_i that eq. num-p needs, and the
 // tangents when drx != nullptr.  dt s_i = P0 / (4 C), so d(dt s_i) = -dt s_i dC / C.
+template <typename R>
 struct Rho {
-  Tables t;
-  const double *dx, *dy, *ddx, *ddy, *drho, *dc, *P0;
+  Tables<R> t;
+  const R *dx, *dy, *ddx, *ddy;
+  const double *drho, *dc;
+  const R* P0;
   int src;
-  double *rx, *ry, *r, *u, *drx, *dry, *dr, *du;
+  R *rx, *ry, *r, *u, *drx, *dry, *dr, *du;
   QPAT_HD void operator()(long long g) const {
     const int i = (int)(g % t.nx), j = (int)(g / t.nx);
-    const double ax = t.ax[i], ay = t.ay[j], r0 = t.rho0[g], dt = t.dt;
-    double q = 0.0, dq = 0.0;
+    const R ax = t.ax[i], ay = t.ay[j], r0 = t.rho0[g], dt = t.dt;
+    R q = (R)0, dq = (R)0;
     if (src) {
-      const double C = t.Cc[g];
-      q = P0[g] / (4.0 * C);
-      if (drx) dq = -q * 2.0 * sqrt(C) * dc[g] / C;
+      const R C = t.Cc[g];
+      q = P0[g] / ((R)4 * C);
+      if (drx) dq = -q * (R)2 * sqrt(C) * (R)dc[g] / C;
     }
     rx[g] = ax * (ax * rx[g] - dt * r0 * dx[g]) + q;
     ry[g] = ay * (ay * ry[g] - dt * r0 * dy[g]) + q;
     r[g] = rx[g] + ry[g];
     if (!t.lossless) u[g] = ax * r0 * dx[g] + ay * r0 * dy[g];
     if (drx) {
-      const double dr0 = drho[g];
+      const R dr0 = (R)drho[g];
       drx[g] = ax * (ax * drx[g] - dt * (dr0 * dx[g] + r0 * ddx[g])) + dq;
       dry[g] = ay * (ay * dry[g] - dt * (dr0 * dy[g] + r0 * ddy[g])) + dq;
       dr[g] = drx[g] + dry[g];
@@ -265,24 +307,26 @@ struct Rho {
 
 // eq. num-p: p = C X, X = r (lossless) or r - eta Y_dis r + tau Y_abs u; keeps X
 // when Xo != nullptr and forms the tangent dp = dC X + C dX when dp != nullptr.
+template <typename R>
 struct Pres {
-  Tables t;
-  const double *r, *Yr, *Yu, *dr, *YdR, *Ydu, *dc;
-  double *p, *Xo, *dp;
+  Tables<R> t;
+  const R *r, *Yr, *Yu, *dr, *YdR, *Ydu;
+  const double* dc;
+  R *p, *Xo, *dp;
   QPAT_HD void operator()(long long g) const {
-    const double C = t.Cc[g];
-    double X = r[g];
+    const R C = t.Cc[g];
+    R X = r[g];
     if (!t.lossless) X += -t.eta[g] * Yr[g] + t.tau[g] * Yu[g];
     p[g] = C * X;
     if (Xo) Xo[g] = X;
     if (dp) {
-      const double c = sqrt(C), dcg = dc[g];
-      double dX = dr[g];
+      const R c = sqrt(C), dcg = (R)dc[g];
+      R dX = dr[g];
       if (!t.lossless) {
-        const double dtau = (t.y - 1.0) * t.tau[g] / c * dcg, deta = t.y * t.eta[g] / c * dcg;
+        const R dtau = (R)(t.y - 1.0) * t.tau[g] / c * dcg, deta = (R)t.y * t.eta[g] / c * dcg;
         dX += -deta * Yr[g] - t.eta[g] * YdR[g] + dtau * Yu[g] + t.tau[g] * Ydu[g];
       }
-      dp[g] = 2.0 * c * dcg * X + C * dX;
+      dp[g] = (R)2 * c * dcg * X + C * dX;
     }
   }
 };
@@ -291,17 +335,19 @@ struct Pres {
 // scatter already added).  gC += pb X; Cp = C pb; lossy: g_eta -= Cp Y_dis r,
 // g_tau += Cp Y_abs u and the two fields eta Cp, tau Cp whose transposed
 // spectral products come next.
+template <typename R>
 struct RevP {
-  Tables t;
-  const double *pb, *X, *Yr, *Yu;
-  double *gC, *geta, *gtau, *Cp, *e1, *e2;
+  Tables<R> t;
+  const R *pb, *X, *Yr, *Yu;
+  double *gC, *geta, *gtau;
+  R *Cp, *e1, *e2;
   QPAT_HD void operator()(long long g) const {
-    const double cp = t.Cc[g] * pb[g];
-    gC[g] += pb[g] * X[g];
+    const R cp = t.Cc[g] * pb[g];
+    gC[g] += (double)pb[g] * X[g];
     Cp[g] = cp;
     if (!t.lossless) {
-      geta[g] -= cp * Yr[g];
-      gtau[g] += cp * Yu[g];
+      geta[g] -= (double)cp * Yr[g];
+      gtau[g] += (double)cp * Yu[g];
       e1[g] = t.eta[g] * cp;
       e2[g] = t.tau[g] * cp;
     }
@@ -312,27 +358,29 @@ struct RevP {
 // rtot_i = rb_i + (Cp - Y_dis^T eta Cp) and ub = Y_abs^T tau Cp,
 // db_i = rho A_i (ub - dt rtot_i), g_rho += A_i div_i (ub - dt rtot_i),
 // rb_i = A_i^2 rtot_i, and the source adjoint qb += sum rtot_i (src).
+template <typename R>
 struct RevRho {
-  Tables t;
-  const double *Cp, *t1, *ub, *dx, *dy;
+  Tables<R> t;
+  const R *Cp, *t1, *ub, *dx, *dy;
   int src;
-  double *rbx, *rby, *dbx, *dby, *grho, *qb;
+  R *rbx, *rby, *dbx, *dby;
+  double *grho, *qb;
   QPAT_HD void operator()(long long g) const {
     const int i = (int)(g % t.nx), j = (int)(g / t.nx);
-    const double ax = t.ax[i], ay = t.ay[j], r0 = t.rho0[g], dt = t.dt;
-    double rp = Cp[g], u = 0.0;
+    const R ax = t.ax[i], ay = t.ay[j], r0 = t.rho0[g], dt = t.dt;
+    R rp = Cp[g], u = (R)0;
     if (!t.lossless) {
       rp -= t1[g];
       u = ub[g];
     }
-    const double tx = rbx[g] + rp, ty = rby[g] + rp;
-    const double hx = u - dt * tx, hy = u - dt * ty;
+    const R tx = rbx[g] + rp, ty = rby[g] + rp;
+    const R hx = u - dt * tx, hy = u - dt * ty;
     dbx[g] = r0 * ax * hx;
     dby[g] = r0 * ay * hy;
-    grho[g] += ax * dx[g] * hx + ay * dy[g] * hy;
+    grho[g] += (double)ax * dx[g] * hx + (double)ay * dy[g] * hy;
     rbx[g] = ax * ax * tx;
     rby[g] = ay * ay * ty;
-    if (src) qb[g] += tx + ty;
+    if (src) qb[g] += (double)tx + ty;
   }
 };
 
@@ -340,16 +388,19 @@ struct RevRho {
 // g_rho_i += vtot_i A_i (dt / rho_i)^2 / dt g_i (g_i = D+_i p of the forward
 // step); vb_i = A_i^2 vtot_i; f_i = A_i (dt / rho_i) vtot_i, whose transposed
 // D+_i products make the adjoint of p_n (with a minus sign).
+template <typename R>
 struct RevVel {
-  Tables t;
-  const double *ex, *ey, *gx, *gy;
-  double *vbx, *vby, *grsx, *grsy, *fx, *fy;
+  Tables<R> t;
+  const R *ex, *ey, *gx, *gy;
+  R *vbx, *vby;
+  double *grsx, *grsy;
+  R *fx, *fy;
   QPAT_HD void operator()(long long g) const {
     const int i = (int)(g % t.nx), j = (int)(g / t.nx);
-    const double ax = t.asx[i], ay = t.asy[j], bx = t.dtrsx[g], by = t.dtrsy[g];
-    const double tx = vbx[g] + ex[g], ty = vby[g] + ey[g];
-    grsx[g] += tx * ax * bx * bx / t.dt * gx[g];
-    grsy[g] += ty * ay * by * by / t.dt * gy[g];
+    const R ax = t.asx[i], ay = t.asy[j], bx = t.dtrsx[g], by = t.dtrsy[g];
+    const R tx = vbx[g] + ex[g], ty = vby[g] + ey[g];
+    grsx[g] += (double)tx * ax * bx * bx / t.dt * gx[g];
+    grsy[g] += (double)ty * ay * by * by / t.dt * gy[g];
     vbx[g] = ax * ax * tx;
     vby[g] = ay * ay * ty;
     fx[g] = ax * bx * tx;
@@ -360,15 +411,18 @@ struct RevVel {
 // The gradients in c and rho on the full grid: the source term of eq. s1
 // (dt s_i = P0 / (4 C)), the chain rule through C = c^2, tau and eta, and
 // the transposed staggered means.
+template <typename R>
 struct Finish {
-  Tables t;
-  const double *gC, *gtau, *geta, *qb, *P0, *grsx, *grsy, *grho;
+  Tables<R> t;
+  const double *gC, *gtau, *geta, *qb;
+  const R* P0;
+  const double *grsx, *grsy, *grho;
   double *g_c, *g_rho;
   QPAT_HD void operator()(long long g) const {
     const double C = t.Cc[g], c = sqrt(C);
-    const double gc = gC[g] - qb[g] * P0[g] / (4.0 * C) / C;
+    const double gc = gC[g] - qb[g] * (double)P0[g] / (4.0 * C) / C;
     double v = 2.0 * c * gc;
-    if (!t.lossless) v += (t.y - 1.0) * t.tau[g] / c * gtau[g] + t.y * t.eta[g] / c * geta[g];
+    if (!t.lossless) v += (t.y - 1.0) * (double)t.tau[g] / c * gtau[g] + t.y * (double)t.eta[g] / c * geta[g];
     g_c[g] = v;
     g_rho[g] = grho[g] + stag_x_T(t, grsx, g) + stag_y_T(t, grsy, g);
   }
@@ -383,25 +437,25 @@ namespace med {
 // Spectral products F^-1 { S F{f} } on the full complex spectrum, several
 // fields per launch.  Zi holds up to kMaxBatch forward spectra, Zc the
 // combined products (each kMaxBatch * G).
-template <class Ex>
+template <class Ex, typename R>
 struct Spectral {
   Ex& ex;
-  const Tables& t;
+  const Tables<R>& t;
   long long G;
-  double2 *Zi, *Zc;
+  Cplx<R> *Zi, *Zc;
 
   // 2D FFT of nb fields in place (inv: the unnormalised inverse), one launch
   // per axis: every grid line is transformed in shared memory
-  void fft(double2* Z, int nb, int inv) { ex.fft2(Z, nb, inv, t, G); }
+  void fft(Cplx<R>* Z, int nb, int inv) { ex.fft2(Z, nb, inv, t, G); }
   // spectra of the fields f[0..nb) into Zi
-  void forward(std::initializer_list<const double*> f) {
+  void forward(std::initializer_list<const R*> f) {
     if (f.size() < 1 || f.size() > (size_t)kMaxBatch) {
       ex.fail(cudaErrorInvalidValue);
       return;
     }
-    LoadReal op{};
+    LoadReal<R> op{};
     int nb = 0;
-    for (const double* p : f) op.f[nb++] = p;
+    for (const R* p : f) op.f[nb++] = p;
     op.Z = Zi;
     op.G = G;
     ex.run(nb * G, op);
@@ -410,7 +464,7 @@ struct Spectral {
   // outputs o: out[o] = alpha Re F^-1{ sum_q S_(o,q) Zi[in_(o,q)] }; terms
   // list (in, symbol) pairs per output; conj: the transposed operators.
   void apply(std::initializer_list<std::initializer_list<int>> terms, int conj,
-             std::initializer_list<double*> out, double alpha) {
+             std::initializer_list<R*> out, R alpha) {
     // at most kMaxBatch outputs, each of one or two (input, symbol) terms
     bool ok = terms.size() >= 1 && terms.size() <= (size_t)kMaxBatch && out.size() == terms.size();
     for (const auto& tl : terms) ok = ok && tl.size() >= 2 && tl.size() <= 4 && tl.size() % 2 == 0;
@@ -418,7 +472,7 @@ struct Spectral {
       ex.fail(cudaErrorInvalidValue);
       return;
     }
-    Combine cb{};
+    Combine<R> cb{};
     cb.t = t;
     cb.Zi = Zi;
     cb.Zo = Zc;
@@ -436,10 +490,10 @@ struct Spectral {
     }
     ex.run(no * G, cb);
     fft(Zc, no, 1);
-    StoreReal st{};
+    StoreReal<R> st{};
     st.Z = Zc;
     int nb = 0;
-    for (double* p : out) st.out[nb++] = p;
+    for (R* p : out) st.out[nb++] = p;
     st.alpha = alpha;
     st.acc = 0;
     st.G = G;
@@ -447,54 +501,60 @@ struct Spectral {
   }
 };
 
-// Fields of one loop, all [G] doubles (tape fields [nt][G]).
+// Fields of one loop, all [G] in the sweep's precision.
+template <typename R>
 struct Fields {
-  double *P0, *p, *vx, *vy, *rx, *ry, *r, *u;
-  double *gx, *gy, *dx, *dy, *Yr, *Yu, *X;
-  double *dp, *dvx, *dvy, *drx, *dry, *dr, *du, *dgx, *dgy, *ddx, *ddy, *YdR, *Ydu;
+  R *P0, *p, *vx, *vy, *rx, *ry, *r, *u;
+  R *gx, *gy, *dx, *dy, *Yr, *Yu, *X;
+  R *dp, *dvx, *dvy, *drx, *dry, *dr, *du, *dgx, *dgy, *ddx, *ddy, *YdR, *Ydu;
 };
 
 // Tangent loop: dP[n] = M dp_n for n = 0 .. nt-1 along (dc, drho), both full
 // grid.  The loop runs n = -1 .. nt-2 from zero fields (samples n + 1).
-template <class Ex>
-void jvp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const double* dc, const double* drho,
-              double* dP) {
+template <class Ex, typename R>
+void jvp_loop(Ex& ex, const Tables<R>& t, Spectral<Ex, R>& S, const Fields<R>& f, const double* dc,
+              const double* drho, double* dP) {
   const long long G = (long long)t.nx * t.ny;
   for (int it = 0; it < t.nt; ++it) {
     const int src = it <= 1;
     S.forward({f.p, f.dp});
     S.apply({{0, kDPX}, {0, kDPY}, {1, kDPX}, {1, kDPY}}, 0, {f.gx, f.gy, f.dgx, f.dgy}, 1.0);
-    ex.run(G, Vel{t, f.gx, f.gy, f.dgx, f.dgy, drho, f.vx, f.vy, f.dvx, f.dvy});
+    ex.run(G, Vel<R>{t, f.gx, f.gy, f.dgx, f.dgy, drho, f.vx, f.vy, f.dvx, f.dvy});
     S.forward({f.vx, f.vy, f.dvx, f.dvy});
     S.apply({{0, kDMX}, {1, kDMY}, {2, kDMX}, {3, kDMY}}, 0, {f.dx, f.dy, f.ddx, f.ddy}, 1.0);
-    ex.run(G, Rho{t, f.dx, f.dy, f.ddx, f.ddy, drho, dc, f.P0, src, f.rx, f.ry, f.r, f.u, f.drx, f.dry, f.dr, f.du});
+    ex.run(G, Rho<R>{t, f.dx, f.dy, f.ddx, f.ddy, drho, dc, f.P0, src, f.rx, f.ry, f.r, f.u, f.drx, f.dry, f.dr,
+                     f.du});
     if (!t.lossless) {
       S.forward({f.r, f.u, f.dr, f.du});
       S.apply({{0, kYDIS}, {1, kYABS}, {2, kYDIS}, {3, kYABS}}, 0, {f.Yr, f.Yu, f.YdR, f.Ydu}, 1.0);
     }
-    ex.run(G, Pres{t, f.r, f.Yr, f.Yu, f.dr, f.YdR, f.Ydu, dc, f.p, nullptr, f.dp});
-    ex.run(t.ns, Gather{t, f.dp, dP + (long long)it * t.ns});
+    ex.run(G, Pres<R>{t, f.r, f.Yr, f.Yu, f.dr, f.YdR, f.Ydu, dc, f.p, nullptr, f.dp});
+    ex.run(t.ns, Gather<R>{t, f.dp, dP + (long long)it * t.ns});
   }
 }
 
 // Fields of one forward step that the reverse step needs: g_i = D+_i p_n,
 // the divergences D-_i v_i, X = p_(n+1) / C and (lossy) Y_dis r, Y_abs u.
 // Tape holds them for a run of consecutive steps ([steps][G] each).
+template <typename R>
 struct Tape {
-  double *gx, *gy, *dx, *dy, *X, *Yr, *Yu;
+  R *gx, *gy, *dx, *dy, *X, *Yr, *Yu;
 };
 
-// Reverse-loop fields, all [G]
+// Reverse-loop fields, all [G]: the adjoint fields in the sweep's precision,
+// the gradient sums in FP64.
+template <typename R>
 struct RevFields {
-  double *pb, *Cp, *e1, *e2, *t1, *ub, *rbx, *rby, *dbx, *dby, *vbx, *vby, *fx, *fy, *ex, *ey, *qb;
-  double *gC, *gtau, *geta, *grho, *grsx, *grsy;
+  R *pb, *Cp, *e1, *e2, *t1, *ub, *rbx, *rby, *dbx, *dby, *vbx, *vby, *fx, *fy, *ex, *ey;
+  double *qb, *gC, *gtau, *geta, *grho, *grsx, *grsy;
 };
 
 // Copy the loop state (p, v_x, v_y, rho_x, rho_y) to or from a checkpoint
 // [5][G].
+template <typename R>
 struct StateCopy {
-  const double* src[5];
-  double* dst[5];
+  const R* src[5];
+  R* dst[5];
   long long G;
   QPAT_HD void operator()(long long u) const {
     const long long k = u / G, g = u - k * G;
@@ -504,42 +564,44 @@ struct StateCopy {
 
 // Forward step it (loop index n = it - 1) of the gradient's forward sweep,
 // writing its tape fields to slot k of tp.
-template <class Ex>
-void tape_step(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const Tape& tp, int it, int k) {
+template <class Ex, typename R>
+void tape_step(Ex& ex, const Tables<R>& t, Spectral<Ex, R>& S, const Fields<R>& f, const Tape<R>& tp, int it,
+               int k) {
   const long long G = (long long)t.nx * t.ny, o = (long long)k * G;
   S.forward({f.p});
   S.apply({{0, kDPX}, {0, kDPY}}, 0, {tp.gx + o, tp.gy + o}, 1.0);
-  ex.run(G, Vel{t, tp.gx + o, tp.gy + o, nullptr, nullptr, nullptr, f.vx, f.vy, nullptr, nullptr});
+  ex.run(G, Vel<R>{t, tp.gx + o, tp.gy + o, nullptr, nullptr, nullptr, f.vx, f.vy, nullptr, nullptr});
   S.forward({f.vx, f.vy});
   S.apply({{0, kDMX}, {1, kDMY}}, 0, {tp.dx + o, tp.dy + o}, 1.0);
-  ex.run(G, Rho{t, tp.dx + o, tp.dy + o, nullptr, nullptr, nullptr, nullptr, f.P0, it <= 1, f.rx, f.ry, f.r, f.u,
-                nullptr, nullptr, nullptr, nullptr});
-  double* Yr = t.lossless ? nullptr : tp.Yr + o;
-  double* Yu = t.lossless ? nullptr : tp.Yu + o;
+  ex.run(G, Rho<R>{t, tp.dx + o, tp.dy + o, nullptr, nullptr, nullptr, nullptr, f.P0, it <= 1, f.rx, f.ry, f.r,
+                   f.u, nullptr, nullptr, nullptr, nullptr});
+  R* Yr = t.lossless ? nullptr : tp.Yr + o;
+  R* Yu = t.lossless ? nullptr : tp.Yu + o;
   if (!t.lossless) {
     S.forward({f.r, f.u});
     S.apply({{0, kYDIS}, {1, kYABS}}, 0, {Yr, Yu}, 1.0);
   }
-  ex.run(G, Pres{t, f.r, Yr, Yu, nullptr, nullptr, nullptr, nullptr, f.p, tp.X + o, nullptr});
+  ex.run(G, Pres<R>{t, f.r, Yr, Yu, nullptr, nullptr, nullptr, nullptr, f.p, tp.X + o, nullptr});
 }
 
 // Transposed step it, reading the tape fields of step it from slot k.
-template <class Ex>
-void reverse_step(Ex& ex, const Tables& t, Spectral<Ex>& S, const Tape& tp, const RevFields& b, const double* W,
-                  int it, int k) {
+template <class Ex, typename R>
+void reverse_step(Ex& ex, const Tables<R>& t, Spectral<Ex, R>& S, const Tape<R>& tp, const RevFields<R>& b,
+                  const double* W, int it, int k) {
   const long long G = (long long)t.nx * t.ny, o = (long long)k * G;
-  const double* Yr = t.lossless ? nullptr : tp.Yr + o;
-  const double* Yu = t.lossless ? nullptr : tp.Yu + o;
-  ex.run(t.ny, Scatter{t, W + (long long)it * t.ns, b.pb});
-  ex.run(G, RevP{t, b.pb, tp.X + o, Yr, Yu, b.gC, b.geta, b.gtau, b.Cp, b.e1, b.e2});
+  const R* Yr = t.lossless ? nullptr : tp.Yr + o;
+  const R* Yu = t.lossless ? nullptr : tp.Yu + o;
+  ex.run(t.ny, Scatter<R>{t, W + (long long)it * t.ns, b.pb});
+  ex.run(G, RevP<R>{t, b.pb, tp.X + o, Yr, Yu, b.gC, b.geta, b.gtau, b.Cp, b.e1, b.e2});
   if (!t.lossless) {
     S.forward({b.e1, b.e2});
     S.apply({{0, kYDIS}, {1, kYABS}}, 1, {b.t1, b.ub}, 1.0);
   }
-  ex.run(G, RevRho{t, b.Cp, b.t1, b.ub, tp.dx + o, tp.dy + o, it <= 1, b.rbx, b.rby, b.dbx, b.dby, b.grho, b.qb});
+  ex.run(G, RevRho<R>{t, b.Cp, b.t1, b.ub, tp.dx + o, tp.dy + o, it <= 1, b.rbx, b.rby, b.dbx, b.dby, b.grho,
+                      b.qb});
   S.forward({b.dbx, b.dby});
   S.apply({{0, kDMX}, {1, kDMY}}, 1, {b.ex, b.ey}, 1.0);
-  ex.run(G, RevVel{t, b.ex, b.ey, tp.gx + o, tp.gy + o, b.vbx, b.vby, b.grsx, b.grsy, b.fx, b.fy});
+  ex.run(G, RevVel<R>{t, b.ex, b.ey, tp.gx + o, tp.gy + o, b.vbx, b.vby, b.grsx, b.grsy, b.fx, b.fy});
   S.forward({b.fx, b.fy});
   S.apply({{0, kDPX, 1, kDPY}}, 1, {b.pb}, -1.0);
 }
@@ -552,18 +614,18 @@ void reverse_step(Ex& ex, const Tables& t, Spectral<Ex>& S, const Tape& tp, cons
 // state, recomputes the segment's tape and runs its transposed steps.  The
 // recomputation repeats the same kernels on the same inputs, so the tape
 // and the gradient are the same bit for bit for every K.
-template <class Ex>
-void vjp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const Tape& tp, const RevFields& b, int K,
-              double* ck, const double* W, double* g_c, double* g_rho) {
+template <class Ex, typename R>
+void vjp_loop(Ex& ex, const Tables<R>& t, Spectral<Ex, R>& S, const Fields<R>& f, const Tape<R>& tp,
+              const RevFields<R>& b, int K, R* ck, const double* W, double* g_c, double* g_rho) {
   const long long G = (long long)t.nx * t.ny;
   if (K >= t.nt) {
     for (int it = 0; it < t.nt; ++it) tape_step(ex, t, S, f, tp, it, it);
     for (int it = t.nt - 1; it >= 0; --it) reverse_step(ex, t, S, tp, b, W, it, it);
   } else {
     auto state = [&](int seg, bool save) {
-      double* c = ck + (long long)seg * 5 * G;
-      double* live[5] = {f.p, f.vx, f.vy, f.rx, f.ry};
-      StateCopy op{};
+      R* c = ck + (long long)seg * 5 * G;
+      R* live[5] = {f.p, f.vx, f.vy, f.rx, f.ry};
+      StateCopy<R> op{};
       for (int q = 0; q < 5; ++q) {
         op.src[q] = save ? live[q] : c + q * G;
         op.dst[q] = save ? c + q * G : live[q];
@@ -583,7 +645,7 @@ void vjp_loop(Ex& ex, const Tables& t, Spectral<Ex>& S, const Fields& f, const T
       for (int it = end - 1; it >= first; --it) reverse_step(ex, t, S, tp, b, W, it, it - first);
     }
   }
-  ex.run(G, Finish{t, b.gC, b.gtau, b.geta, b.qb, f.P0, b.grsx, b.grsy, b.grho, g_c, g_rho});
+  ex.run(G, Finish<R>{t, b.gC, b.gtau, b.geta, b.qb, f.P0, b.grsx, b.grsy, b.grho, g_c, g_rho});
 }
 
 }  // namespace med
