@@ -42,54 +42,138 @@ __global__ void __launch_bounds__(kThreads) for_each_kernel(const F f, long long
     f(i);
 }
 
-// Complex FFT of every grid line along one axis (rows when ALONG_X, else
-// columns) of field blockIdx.y (G points each), in place.  A CTA loads M
-// lines (M consecutive rows, or M adjacent columns so that a warp's loads of
-// one row are contiguous) into shared memory with the row stride S = L + 1,
-// runs the mixed-radix Stockham stages of fft_batch there and stores back.
-// inv: the unnormalised inverse DFT, as conj(FFT(conj x)).
+// x transforms of nb real fields of G points: Z[b] = F_x (f_b + 0 i), field
+// b = blockIdx.y.  A CTA loads M consecutive rows into shared memory (row
+// stride S = L + 1), runs the mixed-radix Stockham stages of fft_batch there
+// and stores the complex rows.
 constexpr int kLineThreads = 256;
-template <bool ALONG_X, typename C>
-__global__ void __launch_bounds__(kLineThreads) line_fft_kernel(C* Z, long long G, int nx, int ny,
-                                                                 const FFTPlan plan, const C* tw, int inv, int M) {
+template <typename R>
+__global__ void __launch_bounds__(kLineThreads) rows_fwd_kernel(const FieldPtrs<const R*> f, Cplx<R>* Z, long long G,
+                                                                 int nx, int ny, const FFTPlan plan,
+                                                                 const Cplx<R>* tw, int M) {
+  typedef Cplx<R> C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C* sm_line = reinterpret_cast<C*>(sm_raw);
   const int L = plan.L, S = L + 1;
-  C* buf0 = sm_line;
-  C* buf1 = sm_line + M * S;
-  const int nlines = ALONG_X ? ny : nx;
+  C* buf0 = reinterpret_cast<C*>(sm_raw);
+  C* buf1 = buf0 + M * S;
   const int line0 = blockIdx.x * M;
-  const int mloc = min(M, nlines - line0);
-  C* Zb = Z + (long long)blockIdx.y * G;
+  const int mloc = min(M, ny - line0);
+  const R* fb = f.p[blockIdx.y];
   for (int t = threadIdx.x; t < M * L; t += blockDim.x) {
-    const int m = ALONG_X ? t / L : t % M;
-    const int i = ALONG_X ? t - m * L : t / M;
+    const int m = t / L, i = t - m * L;
     C v;
-    v.x = 0;
+    v.x = m < mloc ? fb[(long long)(line0 + m) * nx + i] : (R)0;
     v.y = 0;
-    if (m < mloc) {
-      v = Zb[ALONG_X ? (long long)(line0 + m) * nx + i : (long long)i * nx + line0 + m];
-      if (inv) v.y = -v.y;
-    }
     buf0[m * S + i] = v;
   }
   __syncthreads();
   const C* res = fft_batch(plan, buf0, buf1, M, S, tw);
+  C* Zb = Z + (long long)blockIdx.y * G;
   for (int t = threadIdx.x; t < M * L; t += blockDim.x) {
-    const int m = ALONG_X ? t / L : t % M;
-    const int i = ALONG_X ? t - m * L : t / M;
-    if (m < mloc) {
-      C v = res[m * S + i];
-      if (inv) v.y = -v.y;
-      Zb[ALONG_X ? (long long)(line0 + m) * nx + i : (long long)i * nx + line0 + m] = v;
-    }
+    const int m = t / L, i = t - m * L;
+    if (m < mloc) Zb[(long long)(line0 + m) * nx + i] = res[m * S + i];
   }
 }
 
-// Lines per CTA: about 48 KB of shared memory per buffer, 1 to 16 lines.
+// Per group of M adjacent columns (x index col0 + m): the y transforms of the
+// nin x-transformed inputs, the combined products of the tm.no outputs and
+// their inverse y transforms (as conj(FFT(conj .))), Zc[o] on the same
+// layout.  Shared memory: two buffers of W = max(nin, no) lines per column,
+// line (b M + m) of each holding column m of field b; the loads and stores
+// run with m fastest, so a warp moves M adjacent values of each row.
+constexpr int kColThreads = 512;
+template <typename R>
+__global__ void __launch_bounds__(kColThreads) cols_kernel(const Cplx<R>* Zi, int nin, Cplx<R>* Zc, const Terms tm,
+                                                            const Tables<R> t, long long G, const FFTPlan plan, int M,
+                                                            int W) {
+  typedef Cplx<R> C;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int L = plan.L, S = L + 1, nx = t.nx;
+  C* A = reinterpret_cast<C*>(sm_raw);
+  C* B = A + (long long)W * M * S;
+  const int col0 = blockIdx.x * M;
+  const int mloc = min(M, nx - col0);
+  for (int u = threadIdx.x; u < nin * M * L; u += blockDim.x) {
+    const int b = u / (M * L), r = u - b * M * L, i = r / M, m = r - i * M;
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (m < mloc) v = Zi[b * G + (long long)i * nx + col0 + m];
+    A[(b * M + m) * S + i] = v;
+  }
+  __syncthreads();
+  C* res = fft_batch(plan, A, B, nin * M, S, t.twy);
+  C* oth = res == A ? B : A;
+  for (int u = threadIdx.x; u < tm.no * M * L; u += blockDim.x) {
+    const int o = u / (M * L), r = u - o * M * L, j = r / M, m = r - j * M;
+    C acc = z<R>((R)0, (R)0);
+    if (m < mloc) {
+      for (int q = 0; q < tm.nterm[o]; ++q) {
+        C s = symbol(t, tm.sym[o][q], j, col0 + m);
+        if (tm.conj) s = zconj(s);
+        acc = zadd(acc, zmul(s, res[(tm.in[o][q] * M + m) * S + j]));
+      }
+    }
+    oth[(o * M + m) * S + j] = zconj(acc);
+  }
+  __syncthreads();
+  const C* res2 = fft_batch(plan, oth, res, tm.no * M, S, t.twy);
+  for (int u = threadIdx.x; u < tm.no * M * L; u += blockDim.x) {
+    const int o = u / (M * L), r = u - o * M * L, j = r / M, m = r - j * M;
+    if (m < mloc) Zc[o * G + (long long)j * nx + col0 + m] = zconj(res2[(o * M + m) * S + j]);
+  }
+}
+
+// Inverse x transforms of no spectra (as conj(FFT(conj .))), keeping
+// out[o] = alpha Re(.), output o = blockIdx.y; M rows per CTA.
+template <typename R>
+__global__ void __launch_bounds__(kLineThreads) rows_inv_kernel(const Cplx<R>* Z, const FieldPtrs<R*> out, R alpha,
+                                                                 long long G, int nx, int ny, const FFTPlan plan,
+                                                                 const Cplx<R>* tw, int M) {
+  typedef Cplx<R> C;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int L = plan.L, S = L + 1;
+  C* buf0 = reinterpret_cast<C*>(sm_raw);
+  C* buf1 = buf0 + M * S;
+  const int line0 = blockIdx.x * M;
+  const int mloc = min(M, ny - line0);
+  const C* Zb = Z + (long long)blockIdx.y * G;
+  for (int t = threadIdx.x; t < M * L; t += blockDim.x) {
+    const int m = t / L, i = t - m * L;
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (m < mloc) v = zconj(Zb[(long long)(line0 + m) * nx + i]);
+    buf0[m * S + i] = v;
+  }
+  __syncthreads();
+  const C* res = fft_batch(plan, buf0, buf1, M, S, tw);
+  R* ob = out.p[blockIdx.y];
+  for (int t = threadIdx.x; t < M * L; t += blockDim.x) {
+    const int m = t / L, i = t - m * L;
+    if (m < mloc) ob[(long long)(line0 + m) * nx + i] = alpha * res[m * S + i].x;
+  }
+}
+
+// Lines per CTA of the row launches: about 48 KB of shared memory per
+// buffer, 1 to 16 lines.
 int lines_per_cta(int L, int csize) {
   const int m = 49152 / ((L + 1) * csize);
   return m < 1 ? 1 : m > 16 ? 16 : m;
+}
+// Columns per CTA of the column launch: two buffers of W lines per column
+// within the shared-memory budget, a power of two from 1 to 8 (so that a
+// warp's accesses to a row cover whole 32-byte sectors where possible).
+// Budget 110 KB in FP32 (two CTAs per SM) and 220 KB in FP64 (measured at
+// 576^2, 2000 steps, gradient / tangent: FP32 1.95 / 0.79 s against 2.51 /
+// 0.85 s with 220 KB and 1.89 / 0.89 s with 56 KB; FP64 4.73 / 2.90 s with
+// 220 KB against 4.93 / 3.06 s with 110 KB).
+int cols_per_cta(int L, int W, int csize) {
+  const int budget = csize >= 16 ? 225280 : 112640;
+  const int m = budget / (2 * W * (L + 1) * csize);
+  int p = 1;
+  while (2 * p <= m && 2 * p <= 8) p *= 2;
+  return p;
 }
 
 FFTPlan to_fft_plan(const Plan& p) {
@@ -104,36 +188,50 @@ struct GpuEx {
   cudaStream_t s;
   long long launches = 0;
   cudaError_t err = cudaSuccess;
-  // 2D FFT of nb fields of G points in place: the rows, then the columns
+  // shared-memory limit of a launch, then the launch bookkeeping
+  template <class K>
+  bool smem_limit(K* kernel, size_t smem) {
+    if (err != cudaSuccess) return false;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) err = e;
+    return e == cudaSuccess;
+  }
+  void launched() {
+    ++launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  }
+  // Z[b] = F_x f_b for b < nb
   template <typename R>
-  void fft2(Cplx<R>* Z, int nb, int inv, const Tables<R>& t, long long G) {
-    typedef Cplx<R> C;
-    if (nb <= 0 || err != cudaSuccess) return;
-    for (int ax = 0; ax < 2; ++ax) {
-      const FFTPlan plan = to_fft_plan(ax == 0 ? t.px : t.py);
-      const int M = lines_per_cta(plan.L, (int)sizeof(C));
-      const int nlines = ax == 0 ? t.ny : t.nx;
-      const size_t smem = 2 * (size_t)M * (plan.L + 1) * sizeof(C);
-      const dim3 grid((nlines + M - 1) / M, nb);
-      cudaError_t e = ax == 0 ? cudaFuncSetAttribute(line_fft_kernel<true, C>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                              : cudaFuncSetAttribute(line_fft_kernel<false, C>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) {
-        err = e;
-        return;
-      }
-      if (ax == 0)
-        line_fft_kernel<true, C><<<grid, kLineThreads, smem, s>>>(Z, G, t.nx, t.ny, plan, t.twx, inv, M);
-      else
-        line_fft_kernel<false, C><<<grid, kLineThreads, smem, s>>>(Z, G, t.nx, t.ny, plan, t.twy, inv, M);
-      ++launches;
-      e = cudaGetLastError();
-      if (e != cudaSuccess) {
-        err = e;
-        return;
-      }
-    }
+  void rows_forward(const FieldPtrs<const R*>& f, int nb, Cplx<R>* Z, const Tables<R>& t, long long G) {
+    const FFTPlan plan = to_fft_plan(t.px);
+    const int M = lines_per_cta(plan.L, (int)sizeof(Cplx<R>));
+    const size_t smem = 2 * (size_t)M * (plan.L + 1) * sizeof(Cplx<R>);
+    if (nb <= 0 || !smem_limit(rows_fwd_kernel<R>, smem)) return;
+    rows_fwd_kernel<R><<<dim3((t.ny + M - 1) / M, nb), kLineThreads, smem, s>>>(f, Z, G, t.nx, t.ny, plan, t.twx, M);
+    launched();
+  }
+  // per column: y transforms of Zi[0..nin), the products tm, inverse y transforms into Zc
+  template <typename R>
+  void cols_combine(const Cplx<R>* Zi, int nin, Cplx<R>* Zc, const Terms& tm, const Tables<R>& t, long long G) {
+    const FFTPlan plan = to_fft_plan(t.py);
+    const int W = nin > tm.no ? nin : tm.no;
+    const int M = cols_per_cta(plan.L, W, (int)sizeof(Cplx<R>));
+    const size_t smem = 2 * (size_t)W * M * (plan.L + 1) * sizeof(Cplx<R>);
+    if (nin <= 0 || !smem_limit(cols_kernel<R>, smem)) return;
+    cols_kernel<R><<<(t.nx + M - 1) / M, kColThreads, smem, s>>>(Zi, nin, Zc, tm, t, G, plan, M, W);
+    launched();
+  }
+  // out[o] = alpha Re F_x^-1 Z[o] for o < no
+  template <typename R>
+  void rows_inverse(const Cplx<R>* Z, const FieldPtrs<R*>& out, int no, R alpha, const Tables<R>& t, long long G) {
+    const FFTPlan plan = to_fft_plan(t.px);
+    const int M = lines_per_cta(plan.L, (int)sizeof(Cplx<R>));
+    const size_t smem = 2 * (size_t)M * (plan.L + 1) * sizeof(Cplx<R>);
+    if (no <= 0 || !smem_limit(rows_inv_kernel<R>, smem)) return;
+    rows_inv_kernel<R><<<dim3((t.ny + M - 1) / M, no), kLineThreads, smem, s>>>(Z, out, alpha, G, t.nx, t.ny, plan,
+                                                                                t.twx, M);
+    launched();
   }
   template <class F>
   void run(long long n, const F& f) {

@@ -19,14 +19,16 @@
 // fixed: they are parameters of the discretisation.
 //
 // The tangent loop (jvp) steps the fields and their derivatives together.
-// The adjoint (vjp) runs the forward loop once, keeping the spectral
-// quantities each step's derivative needs (the whole history stays in HBM),
-// and then runs the exact transpose backwards.  Spectral operators are full
-// complex 2D FFTs: one launch per axis, each CTA transforming several grid
-// lines in shared memory (mixed-radix Stockham), then the symbol multiply
-// (the context's FP64 half-spectrum tables, mirrored), then the inverse FFT;
-// up to four fields (a field and its tangent, the velocity components, the
-// absorption inputs) share each launch.
+// The adjoint (vjp) runs the forward loop, keeping the spectral quantities
+// each step's derivative needs (for every step, or recomputed segment by
+// segment from checkpoints), and then runs the exact transpose backwards.
+// Spectral operators are full complex 2D FFTs in three launches: the x
+// transforms of the real inputs; per group of adjacent columns the y
+// transforms, the symbol products (the context's half-spectrum tables,
+// mirrored) and the inverse y transforms; the inverse x transforms keeping
+// the real part.  Each CTA transforms several grid lines in shared memory
+// (mixed-radix Stockham), and up to four fields (a field and its tangent,
+// the velocity components, the absorption inputs) share each launch.
 //
 // Every per-element body is a functor templated on the sweep's real type R;
 // the loops are templates over R and the executor type, whose one
@@ -125,52 +127,18 @@ QPAT_HD Cplx<R> symbol(const Tables<R>& t, int which, int j, int i) {
 
 constexpr int kMaxBatch = 4;
 
-// Z[b G + g] = f_b[g] + 0 i for nb fields
-template <typename R>
-struct LoadReal {
-  const R* f[kMaxBatch];
-  Cplx<R>* Z;
-  long long G;
-  QPAT_HD void operator()(long long t) const {
-    const long long b = t / G;
-    Z[t] = z<R>(f[b][t - b * G], (R)0);
-  }
-};
-// out_b = alpha Re(Z[b G + .]), or out_b += alpha Re(...) when acc
-template <typename R>
-struct StoreReal {
-  const Cplx<R>* Z;
-  R* out[kMaxBatch];
-  R alpha;
-  int acc;
-  long long G;
-  QPAT_HD void operator()(long long t) const {
-    const long long b = t / G, g = t - b * G;
-    const R v = alpha * Z[t].x;
-    out[b][g] = acc ? out[b][g] + v : v;
-  }
-};
-// Output o: Zo[o G + g] = sum over its nterm[o] terms q of sym[o][q]
-// (conjugated when conj) * Zi[in[o][q] G + g].
-template <typename R>
-struct Combine {
-  Tables<R> t;
-  const Cplx<R>* Zi;
-  Cplx<R>* Zo;
+// The terms of the outputs of one spectral product: output o is the sum
+// over its nterm[o] terms q of sym[o][q] (conjugated when conj) times input
+// spectrum in[o][q].
+struct Terms {
+  int no;
   int nterm[kMaxBatch], in[kMaxBatch][2], sym[kMaxBatch][2];
   int conj;
-  long long G;
-  QPAT_HD void operator()(long long u) const {
-    const long long o = u / G, g = u - o * G;
-    const int i = (int)(g % t.nx), j = (int)(g / t.nx);
-    Cplx<R> r = z<R>((R)0, (R)0);
-    for (int q = 0; q < nterm[o]; ++q) {
-      Cplx<R> a = symbol(t, sym[o][q], j, i);
-      if (conj) a = zconj(a);
-      r = zadd(r, zmul(a, Zi[in[o][q] * G + g]));
-    }
-    Zo[u] = r;
-  }
+};
+// Up to kMaxBatch field pointers, passed by value to a kernel.
+template <typename P>
+struct FieldPtrs {
+  P p[kMaxBatch];
 };
 
 // Interior p0 [n1][n0] (FP64) -> full grid in the sweep's precision, zero
@@ -435,69 +403,68 @@ namespace qpat {
 namespace med {
 
 // Spectral products F^-1 { S F{f} } on the full complex spectrum, several
-// fields per launch.  Zi holds up to kMaxBatch forward spectra, Zc the
-// combined products (each kMaxBatch * G).
+// fields per launch, in three launches: the x transforms of the real inputs
+// (forward), then per group of adjacent columns the y transforms, the
+// symbol products and the inverse y transforms, then the inverse x
+// transforms keeping alpha times the real part (apply).  Zi holds up to
+// kMaxBatch x-transformed inputs, Zc the combined products (each
+// kMaxBatch * G).
 template <class Ex, typename R>
 struct Spectral {
   Ex& ex;
   const Tables<R>& t;
   long long G;
   Cplx<R> *Zi, *Zc;
+  int nin = 0;                                    // inputs of the last forward()
 
-  // 2D FFT of nb fields in place (inv: the unnormalised inverse), one launch
-  // per axis: every grid line is transformed in shared memory
-  void fft(Cplx<R>* Z, int nb, int inv) { ex.fft2(Z, nb, inv, t, G); }
-  // spectra of the fields f[0..nb) into Zi
+  // x transforms of the fields f[0..nb) into Zi
   void forward(std::initializer_list<const R*> f) {
     if (f.size() < 1 || f.size() > (size_t)kMaxBatch) {
       ex.fail(cudaErrorInvalidValue);
       return;
     }
-    LoadReal<R> op{};
+    FieldPtrs<const R*> in{};
     int nb = 0;
-    for (const R* p : f) op.f[nb++] = p;
-    op.Z = Zi;
-    op.G = G;
-    ex.run(nb * G, op);
-    fft(Zi, nb, 0);
+    for (const R* p : f) in.p[nb++] = p;
+    nin = nb;
+    ex.rows_forward(in, nb, Zi, t, G);
   }
-  // outputs o: out[o] = alpha Re F^-1{ sum_q S_(o,q) Zi[in_(o,q)] }; terms
+  // outputs o: out[o] = alpha Re F^-1{ sum_q S_(o,q) F{f_(in_(o,q))} }; terms
   // list (in, symbol) pairs per output; conj: the transposed operators.
   void apply(std::initializer_list<std::initializer_list<int>> terms, int conj,
              std::initializer_list<R*> out, R alpha) {
     // at most kMaxBatch outputs, each of one or two (input, symbol) terms
+    // over the inputs of the last forward()
     bool ok = terms.size() >= 1 && terms.size() <= (size_t)kMaxBatch && out.size() == terms.size();
     for (const auto& tl : terms) ok = ok && tl.size() >= 2 && tl.size() <= 4 && tl.size() % 2 == 0;
+    Terms tm{};
+    tm.conj = conj;
+    int no = 0;
+    if (ok) {
+      for (const auto& tl : terms) {
+        int q = 0, k = 0;
+        for (int v : tl) {
+          if (k % 2 == 0) {
+            ok = ok && v >= 0 && v < nin;
+            tm.in[no][q] = v;
+          } else {
+            tm.sym[no][q++] = v;
+          }
+          ++k;
+        }
+        tm.nterm[no++] = q;
+      }
+    }
     if (!ok) {
       ex.fail(cudaErrorInvalidValue);
       return;
     }
-    Combine<R> cb{};
-    cb.t = t;
-    cb.Zi = Zi;
-    cb.Zo = Zc;
-    cb.conj = conj;
-    cb.G = G;
-    int no = 0;
-    for (const auto& tl : terms) {
-      int q = 0, k = 0;
-      for (int v : tl) {
-        if (k % 2 == 0) cb.in[no][q] = v;
-        else cb.sym[no][q++] = v;
-        ++k;
-      }
-      cb.nterm[no++] = q;
-    }
-    ex.run(no * G, cb);
-    fft(Zc, no, 1);
-    StoreReal<R> st{};
-    st.Z = Zc;
+    tm.no = no;
+    ex.cols_combine(Zi, nin, Zc, tm, t, G);
+    FieldPtrs<R*> o{};
     int nb = 0;
-    for (R* p : out) st.out[nb++] = p;
-    st.alpha = alpha;
-    st.acc = 0;
-    st.G = G;
-    ex.run(nb * G, st);
+    for (R* p : out) o.p[nb++] = p;
+    ex.rows_inverse(Zc, o, no, alpha, t, G);
   }
 };
 
