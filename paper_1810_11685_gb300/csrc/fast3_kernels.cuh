@@ -4,7 +4,7 @@
 // x row pass (one thread group per pair of y-rows (k, j0), (k, j0 + 1)):
 //   start bulk copies of the two rows of up to three incoming half spectra
 //   and of every state and medium field the update reads into shared memory
-//   (cp.async pieces and direct spectrum loads at the small extents); take
+//   (one thread for all row pairs of the CTA); take
 //   the spectra into registers, Hermitian-extend and pack the two
 //   rows into one complex sequence -> inverse x-FFT via conj(FFT(conj .))
 //   with the reversed plan -> wait for the copies -> pointwise update of one
@@ -21,11 +21,19 @@
 
 namespace qpat {
 
-// Row pairs per CTA of the 3D row pass: about 48 threads, i.e. one row pair
-// at extent 288 (measured on GB300 at 288^3: 48 threads 8.7e9, 96 threads
-// 8.3e9, 144 threads 8.0e9 forward+adjoint cell-steps/s).
+// Row pairs per CTA of the 3D row pass: about QPAT_ROW3_THREADS threads, i.e.
+// one row pair at extent 288 with 48 (measured on GB300 at 288^3 with
+// per-thread operand loads: 48 threads 8.7e9, 96 threads 8.3e9, 144 threads
+// 8.0e9 forward+adjoint cell-steps/s; with bulk copies, N_t 300: 48 threads
+// 1.285e10, 96 threads (no idle lanes) 1.281e10 with 4 and 1.274e10 with 5
+// resident CTAs per SM).
+#ifndef QPAT_ROW3_THREADS
+#define QPAT_ROW3_THREADS 48
+#endif
 template <int L>
-constexpr int rp3() { return (48 / SGeom<L>::TPT) > 0 ? (48 / SGeom<L>::TPT) : 1; }
+constexpr int rp3() {
+  return (QPAT_ROW3_THREADS / SGeom<L>::TPT) > 0 ? (QPAT_ROW3_THREADS / SGeom<L>::TPT) : 1;
+}
 
 // The y and z passes run their Stockham stages in one shared buffer per line
 // (measured on GB300 at 288^3, 8 lines per CTA: 1.08e10 against 1.00e10
@@ -62,9 +70,8 @@ constexpr bool kRow3Descending = QPAT_ROW3_DESC != 0;
 #ifndef QPAT_ROW3_BULK
 #define QPAT_ROW3_BULK 1
 #endif
-// (extents with one row pair per CTA; the small extents keep cp.async)
 template <int L>
-constexpr bool row3_bulk() { return QPAT_ROW3_BULK && rp3<L>() == 1; }
+constexpr bool row3_bulk() { return QPAT_ROW3_BULK != 0; }
 
 // The row pass runs its Stockham stages in one shared buffer per row pair
 // (288^3: 1.11e10 against 1.09e10 cell-steps/s with two buffers).
@@ -139,6 +146,7 @@ row3_fast(const Prop3<T> a) {
   constexpr bool BULK = row3_bulk<L>();
   constexpr int kSpecRow = ((L / 2 + 1) + 1) & ~1;               // complex values per staged row (16-byte pieces)
   static_assert(!BULK || kSpecRow * 2 * KIN <= NSX * SL, "staged spectra must fit the Stockham buffer");
+  static_assert(!BULK || (L % 2 == 0 && SL % 2 == 0), "every row pair's buffers start on 16-byte boundaries");
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + row3_bulk_bar_offset<T, L, PH>());
   C* const sp = bufA;
   if constexpr (BULK) {
@@ -152,19 +160,34 @@ row3_fast(const Prop3<T> a) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const bool load_in = valid && !skip_in;
-      mbar_arrive_expect_tx(bar, load_in ? 2u * KIN * kSpecRow * (unsigned)sizeof(C) : 0u);
-      if (load_in)
-        for (int s = 0; s < KIN; ++s)
-          for (int rr = 0; rr < 2; ++rr)
-            bulk_g2s(sp + (s * 2 + rr) * kSpecRow, spec + s * a.slot + rr * a.pitch, kSpecRow * (unsigned)sizeof(C),
-                     bar);
-      mbar_arrive_expect_tx(bar + 1, valid ? 2u * NF * L * (unsigned)sizeof(T) : 0u);
-      if (valid)
+      // every row pair mm of the CTA: its spectra into its Stockham buffer,
+      // its operand rows into its staging area
+      unsigned in_bytes = 0, op_bytes = 0;
+      for (int mm = 0; mm < RP; ++mm) {
+        if (blockIdx.x * RP + mm >= (a.ny >> 1)) continue;
+        if (!skip_in) in_bytes += 2u * KIN * kSpecRow * (unsigned)sizeof(C);
+        op_bytes += 2u * NF * L * (unsigned)sizeof(T);
+      }
+      mbar_arrive_expect_tx(bar, in_bytes);
+      mbar_arrive_expect_tx(bar + 1, op_bytes);
+      for (int mm = 0; mm < RP; ++mm) {
+        const int jm = blockIdx.x * RP + mm;
+        if (jm >= (a.ny >> 1)) continue;
+        const int j0m = 2 * jm;
+        if (!skip_in) {
+          C* spm = tws + L + mm * NB * NSX * SL;
+          const C* specm = a.spec + (long long)b * a.sstride + ((long long)k * a.ny + j0m) * a.pitch;
+          for (int s = 0; s < KIN; ++s)
+            for (int rr = 0; rr < 2; ++rr)
+              bulk_g2s(spm + (s * 2 + rr) * kSpecRow, specm + s * a.slot + rr * a.pitch,
+                       kSpecRow * (unsigned)sizeof(C), bar);
+        }
+        T* stm = reinterpret_cast<T*>(tws + STAGE_OFF) + mm * NF * 2 * L;
         for (int f = 0; f < NF; ++f)
           for (int rr = 0; rr < 2; ++rr)
-            bulk_g2s(stage + (f * 2 + rr) * L, r3_row<T>(a, r3_field(PH, f), b, (long long)k * a.ny + j0 + rr),
+            bulk_g2s(stm + (f * 2 + rr) * L, r3_row<T>(a, r3_field(PH, f), b, (long long)k * a.ny + j0m + rr),
                      L * (unsigned)sizeof(T), bar + 1);
+      }
     }
   } else {
     // the update's operands of both rows, copied while the spectra load and the
