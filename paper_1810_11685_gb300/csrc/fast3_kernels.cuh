@@ -72,6 +72,13 @@ constexpr bool kRow3Descending = QPAT_ROW3_DESC != 0;
 #endif
 template <int L>
 constexpr bool row3_bulk() { return QPAT_ROW3_BULK != 0; }
+// With bulk copies the stage twiddles W_L^m come into shared memory by one
+// more bulk copy (on the spectra's mbarrier) instead of per-thread copies
+// (measured on GB300 at 288^3, N_t 300: 1.335e10 against 1.285e10
+// forward+adjoint cell-steps/s).
+#ifndef QPAT_ROW3_TWBULK
+#define QPAT_ROW3_TWBULK 1
+#endif
 
 // The row pass runs its Stockham stages in one shared buffer per row pair
 // (288^3: 1.11e10 against 1.09e10 cell-steps/s with two buffers).
@@ -162,7 +169,7 @@ row3_fast(const Prop3<T> a) {
     if (threadIdx.x == 0) {
       // every row pair mm of the CTA: its spectra into its Stockham buffer,
       // its operand rows into its staging area
-      unsigned in_bytes = 0, op_bytes = 0;
+      unsigned in_bytes = QPAT_ROW3_TWBULK ? L * (unsigned)sizeof(C) : 0u, op_bytes = 0;
       for (int mm = 0; mm < RP; ++mm) {
         if (blockIdx.x * RP + mm >= (a.ny >> 1)) continue;
         if (!skip_in) in_bytes += 2u * KIN * kSpecRow * (unsigned)sizeof(C);
@@ -170,6 +177,7 @@ row3_fast(const Prop3<T> a) {
       }
       mbar_arrive_expect_tx(bar, in_bytes);
       mbar_arrive_expect_tx(bar + 1, op_bytes);
+      if (QPAT_ROW3_TWBULK) bulk_g2s(tws, a.twx, L * (unsigned)sizeof(C), bar);
       for (int mm = 0; mm < RP; ++mm) {
         const int jm = blockIdx.x * RP + mm;
         if (jm >= (a.ny >> 1)) continue;
@@ -205,13 +213,14 @@ row3_fast(const Prop3<T> a) {
         }
     }
   }
-  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
+  if (!BULK || !QPAT_ROW3_TWBULK)
+    for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = a.twx[t];
+  if constexpr (BULK) row_bulk_wait(bar, a.err);                 // spectra (and twiddles) in shared memory
 
   // 1. inverse x-transform of the incoming half spectra (reversed plan)
   C y[KIN][Q1];
   if (!skip_in) {
     C v[KIN][P1];
-    if constexpr (BULK) row_bulk_wait(bar, a.err);
     if (j < L / P1) {
 #pragma unroll
       for (int s = 0; s < KIN; ++s) {
