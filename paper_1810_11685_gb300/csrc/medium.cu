@@ -9,6 +9,7 @@
 // axis.
 #include <math.h>
 
+#include <map>
 #include <vector>
 
 #include "medium_ops.cuh"
@@ -186,14 +187,18 @@ FFTPlan to_fft_plan(const Plan& p) {
 
 struct GpuEx {
   cudaStream_t s;
+  std::map<const void*, size_t> smem_set;
   long long launches = 0;
   cudaError_t err = cudaSuccess;
   // shared-memory limit of a launch, then the launch bookkeeping
   template <class K>
   bool smem_limit(K* kernel, size_t smem) {
     if (err != cudaSuccess) return false;
+    size_t& set = smem_set[reinterpret_cast<const void*>(kernel)];   // limit already set during this call
+    if (smem <= set) return true;
     const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) err = e;
+    else set = smem;
     return e == cudaSuccess;
   }
   void launched() {
