@@ -12,6 +12,7 @@
 #include <map>
 #include <vector>
 
+#include "fast_kernels.cuh"
 #include "medium_ops.cuh"
 #include "qpat.h"
 #include "qpat_internal.h"
@@ -156,6 +157,52 @@ __global__ void __launch_bounds__(kLineThreads) rows_inv_kernel(const Cplx<R>* Z
   }
 }
 
+// FP32 x transforms (forward: real fields in, spectra out; inverse: spectra
+// in as conj(FFT(conj .)), alpha times the real part out) on the
+// compile-time Stockham FFT of the propagation passes, for the extents that
+// have one: TPT threads per row, several rows per CTA, the twiddles read
+// through L1.  Field blockIdx.y.
+template <int L>
+constexpr int med_rows_per_cta() { return (256 / SGeom<L>::TPT) > 0 ? 256 / SGeom<L>::TPT : 1; }
+template <int L, bool INV>
+__global__ void __launch_bounds__(med_rows_per_cta<L>() * SGeom<L>::TPT)
+rows_fast_kernel(const FieldPtrs<const float*> fin, const float2* Zin, float2* Zout, const FieldPtrs<float*> fout,
+                 float alpha, long long G, int nx, int ny, const float2* tw) {
+  typedef SGeom<L> Gm;
+  constexpr int TPT = Gm::TPT, SL = Gm::SL, Q1 = Gm::Q1, QL = Gm::QL, RPC = med_rows_per_cta<L>();
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int m = threadIdx.x / TPT, j = threadIdx.x - m * TPT;
+  float2* bufA = reinterpret_cast<float2*>(sm_raw) + m * 2 * SL;
+  float2* bufB = bufA + SL;
+  const int row = blockIdx.x * RPC + m;
+  const bool valid = row < ny;
+  const long long o = (long long)(valid ? row : 0) * nx;
+  const long long of = (long long)blockIdx.y * G + o;
+  float2 v[1][Q1];
+  if (j < L / Q1) {
+#pragma unroll
+    for (int r = 0; r < Q1; ++r) {
+      const int i = j + r * (L / Q1);
+      float2 x = make_float2(0.f, 0.f);
+      if (valid) {
+        if (INV) x = zconj(Zin[of + i]);
+        else x.x = fin.p[blockIdx.y][o + i];
+      }
+      v[0][r] = x;
+    }
+  }
+  float2 X[1][QL];
+  fft_stockham<L, Gm::Q1, Gm::Q2, Gm::Q3, 1, false, false>(v, X, bufA, bufB, SL, j, tw);
+  if (valid && j < L / QL) {
+#pragma unroll
+    for (int r = 0; r < QL; ++r) {
+      const int k = j + r * (L / QL);
+      if (INV) fout.p[blockIdx.y][o + k] = alpha * X[0][r].x;
+      else Zout[of + k] = X[0][r];
+    }
+  }
+}
+
 // Lines per CTA of the row launches: about 48 KB of shared memory per
 // buffer, 1 to 16 lines.
 int lines_per_cta(int L, int csize) {
@@ -206,9 +253,36 @@ struct GpuEx {
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess && err == cudaSuccess) err = e;
   }
+  // the compile-time x transforms (FP32, extents 24, 168, 576); false when
+  // the extent has none
+  template <int L, bool INV>
+  bool rows_fast_len(const FieldPtrs<const float*>& fin, const float2* Zin, float2* Zout,
+                     const FieldPtrs<float*>& fout, float alpha, int nf, const Tables<float>& t, long long G) {
+    constexpr int RPC = med_rows_per_cta<L>();
+    const size_t smem = (size_t)RPC * 2 * SGeom<L>::SL * sizeof(float2);
+    if (!smem_limit(rows_fast_kernel<L, INV>, smem)) return true;
+    rows_fast_kernel<L, INV><<<dim3((t.ny + RPC - 1) / RPC, nf), RPC * SGeom<L>::TPT, smem, s>>>(
+        fin, Zin, Zout, fout, alpha, G, t.nx, t.ny, t.twx);
+    launched();
+    return true;
+  }
+  template <bool INV>
+  bool rows_fast(const FieldPtrs<const float*>& fin, const float2* Zin, float2* Zout, const FieldPtrs<float*>& fout,
+                 float alpha, int nf, const Tables<float>& t, long long G) {
+    if (t.px.L != t.nx) return false;
+    switch (t.nx) {
+      case 24: return rows_fast_len<24, INV>(fin, Zin, Zout, fout, alpha, nf, t, G);
+      case 168: return rows_fast_len<168, INV>(fin, Zin, Zout, fout, alpha, nf, t, G);
+      case 576: return rows_fast_len<576, INV>(fin, Zin, Zout, fout, alpha, nf, t, G);
+      default: return false;
+    }
+  }
   // Z[b] = F_x f_b for b < nb
   template <typename R>
   void rows_forward(const FieldPtrs<const R*>& f, int nb, Cplx<R>* Z, const Tables<R>& t, long long G) {
+    if constexpr (std::is_same<R, float>::value) {
+      if (nb > 0 && err == cudaSuccess && rows_fast<false>(f, nullptr, Z, FieldPtrs<float*>{}, 1.f, nb, t, G)) return;
+    }
     const FFTPlan plan = to_fft_plan(t.px);
     const int M = lines_per_cta(plan.L, (int)sizeof(Cplx<R>));
     const size_t smem = 2 * (size_t)M * (plan.L + 1) * sizeof(Cplx<R>);
@@ -230,6 +304,10 @@ struct GpuEx {
   // out[o] = alpha Re F_x^-1 Z[o] for o < no
   template <typename R>
   void rows_inverse(const Cplx<R>* Z, const FieldPtrs<R*>& out, int no, R alpha, const Tables<R>& t, long long G) {
+    if constexpr (std::is_same<R, float>::value) {
+      if (no > 0 && err == cudaSuccess && rows_fast<true>(FieldPtrs<const float*>{}, Z, nullptr, out, alpha, no, t, G))
+        return;
+    }
     const FFTPlan plan = to_fft_plan(t.px);
     const int M = lines_per_cta(plan.L, (int)sizeof(Cplx<R>));
     const size_t smem = 2 * (size_t)M * (plan.L + 1) * sizeof(Cplx<R>);

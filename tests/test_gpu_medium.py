@@ -10,8 +10,8 @@ FP32 bounds: each FP32 sweep rounds every field once per operation (unit
 roundoff 6e-8) through about ten FFT stages and pointwise updates per step.
 Measured on GB300: relative l2 errors of 3e-7 to 1e-6 for the tangent and the
 gradients on the small grids over 24-30 steps; at 168^2 over 600 steps
-0.8e-5 to 1.9e-5 against the FP64 sweeps and 5.4e-6 for the transpose
-identity, whose two sides come from independent FP32 sweeps.  The bound is
+0.8e-5 to 1.9e-5 against the FP64 sweeps and 5e-6 to 1.3e-5 for the
+transpose identity, whose two sides come from independent FP32 sweeps.  The bound is
 1e-4 (the FP32 sensor-series bound of the propagation tests, halved) for
 all of them."""
 import numpy as np
