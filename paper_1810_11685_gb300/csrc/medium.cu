@@ -203,6 +203,76 @@ rows_fast_kernel(const FieldPtrs<const float*> fin, const float2* Zin, float2* Z
   }
 }
 
+// FP32 y transforms, products and inverse y transforms of M adjacent columns
+// on the compile-time Stockham FFT (extents with one): the columns are
+// staged as in cols_kernel, then NG thread groups of TPT threads transform
+// one staged line each per wave, reading it into registers and writing the
+// transform back in natural order (in place); the products and the stores
+// follow as in cols_kernel.  Every thread runs every wave (the transforms
+// synchronise the CTA).
+template <int L>
+constexpr int med_col_groups() { return L >= 512 ? 8 : 16; }
+template <int L>
+__global__ void __launch_bounds__(med_col_groups<L>() * SGeom<L>::TPT)
+cols_fast_kernel(const float2* Zi, int nin, float2* Zc, const Terms tm, const Tables<float> t, long long G, int M) {
+  typedef SGeom<L> Gm;
+  typedef float2 C;
+  constexpr int TPT = Gm::TPT, SL = Gm::SL, Q1 = Gm::Q1, QL = Gm::QL, NG = med_col_groups<L>(), S = L + 1;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* A = reinterpret_cast<C*>(sm_raw);                           // [nin M][S] inputs, then their transforms
+  C* B = A + (long long)nin * M * S;                             // [no M][S] products, then their transforms
+  C* scr = B + (long long)tm.no * M * S;                         // [NG][SL] Stockham buffer per group
+  const int g = threadIdx.x / TPT, j = threadIdx.x - g * TPT;
+  C* buf = scr + g * SL;
+  const int nx = t.nx, col0 = blockIdx.x * M, mloc = min(M, nx - col0);
+  for (int u = threadIdx.x; u < nin * M * L; u += blockDim.x) {
+    const int b = u / (M * L), r = u - b * M * L, i = r / M, m = r - i * M;
+    C v = make_float2(0.f, 0.f);
+    if (m < mloc) v = Zi[b * G + (long long)i * nx + col0 + m];
+    A[(b * M + m) * S + i] = v;
+  }
+  __syncthreads();
+  // lines [0, n) of X in place: forward transforms (the inverse ones are
+  // fed conjugated and stored conjugated by the caller's loops)
+  auto transform = [&](C* X, int n) {
+    for (int w0 = 0; w0 < n; w0 += NG) {
+      const int line = w0 + g;
+      const bool lv = line < n;
+      C v[1][Q1];
+      if (j < L / Q1) {
+#pragma unroll
+        for (int r = 0; r < Q1; ++r) v[0][r] = lv ? X[line * S + j + r * (L / Q1)] : make_float2(0.f, 0.f);
+      }
+      C Y[1][QL];
+      fft_stockham<L, Gm::Q1, Gm::Q2, Gm::Q3, 1, true, false>(v, Y, buf, buf, SL, j, t.twy);
+      if (lv && j < L / QL) {
+#pragma unroll
+        for (int r = 0; r < QL; ++r) X[line * S + j + r * (L / QL)] = Y[0][r];
+      }
+      __syncthreads();
+    }
+  };
+  transform(A, nin * M);
+  for (int u = threadIdx.x; u < tm.no * M * L; u += blockDim.x) {
+    const int o = u / (M * L), r = u - o * M * L, jj = r / M, m = r - jj * M;
+    C acc = make_float2(0.f, 0.f);
+    if (m < mloc) {
+      for (int q = 0; q < tm.nterm[o]; ++q) {
+        C sy = symbol(t, tm.sym[o][q], jj, col0 + m);
+        if (tm.conj) sy = zconj(sy);
+        acc = zadd(acc, zmul(sy, A[(tm.in[o][q] * M + m) * S + jj]));
+      }
+    }
+    B[(o * M + m) * S + jj] = zconj(acc);
+  }
+  __syncthreads();
+  transform(B, tm.no * M);
+  for (int u = threadIdx.x; u < tm.no * M * L; u += blockDim.x) {
+    const int o = u / (M * L), r = u - o * M * L, jj = r / M, m = r - jj * M;
+    if (m < mloc) Zc[o * G + (long long)jj * nx + col0 + m] = zconj(B[(o * M + m) * S + jj]);
+  }
+}
+
 // Lines per CTA of the row launches: about 48 KB of shared memory per
 // buffer, 1 to 16 lines.
 int lines_per_cta(int L, int csize) {
@@ -290,9 +360,32 @@ struct GpuEx {
     rows_fwd_kernel<R><<<dim3((t.ny + M - 1) / M, nb), kLineThreads, smem, s>>>(f, Z, G, t.nx, t.ny, plan, t.twx, M);
     launched();
   }
+  // the compile-time column launch (FP32, extents 24, 168, 576)
+  template <int L>
+  bool cols_fast_len(const float2* Zi, int nin, float2* Zc, const Terms& tm, const Tables<float>& t, long long G) {
+    constexpr int NG = med_col_groups<L>();
+    const int W = nin > tm.no ? nin : tm.no;
+    int M = 1;
+    while (2 * M * W <= NG && 2 * M <= 8) M *= 2;                // a wave transforms M W lines
+    const size_t smem = ((size_t)(nin + tm.no) * M * (L + 1) + (size_t)NG * SGeom<L>::SL) * sizeof(float2);
+    if (!smem_limit(cols_fast_kernel<L>, smem)) return true;
+    cols_fast_kernel<L><<<(t.nx + M - 1) / M, NG * SGeom<L>::TPT, smem, s>>>(Zi, nin, Zc, tm, t, G, M);
+    launched();
+    return true;
+  }
   // per column: y transforms of Zi[0..nin), the products tm, inverse y transforms into Zc
   template <typename R>
   void cols_combine(const Cplx<R>* Zi, int nin, Cplx<R>* Zc, const Terms& tm, const Tables<R>& t, long long G) {
+    if constexpr (std::is_same<R, float>::value) {
+      if (nin > 0 && err == cudaSuccess && t.py.L == t.ny) {
+        switch (t.ny) {
+          case 24: cols_fast_len<24>(Zi, nin, Zc, tm, t, G); return;
+          case 168: cols_fast_len<168>(Zi, nin, Zc, tm, t, G); return;
+          case 576: cols_fast_len<576>(Zi, nin, Zc, tm, t, G); return;
+          default: break;
+        }
+      }
+    }
     const FFTPlan plan = to_fft_plan(t.py);
     const int W = nin > tm.no ? nin : tm.no;
     const int M = cols_per_cta(plan.L, W, (int)sizeof(Cplx<R>));
