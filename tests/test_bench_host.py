@@ -30,3 +30,27 @@ def test_host_cpu_record():
     h = bench.host_cpu()
     assert set(h) == {"machine", "cpu", "nproc"}
     assert h["nproc"] >= 1 and h["machine"]
+
+
+def test_algorithmic_bytes_per_cell_step():
+    """State z_n read and written ((2 d + 1) fields), one read of c, rho-bar,
+    the d staggered rho-bar_i and alpha0 where it varies: 60 B in 2D FP32
+    with alpha0(r), 76 B in 3D FP32 with a uniform alpha0."""
+    assert bench.b_alg(2) == 60
+    assert bench.b_alg(3, alpha_varies=False) == 76
+    assert bench.b_alg(2, "f64") == 120
+
+
+def test_step_roofline_fraction_is_recomputable():
+    r = bench.roofline_step(2.0e10, 2, 12 * 576 * 576, traffic=123.0, what="step")
+    assert r["achieved"] == 2.0e10 * 60 / 1e9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
+    assert r["alg_bytes_per_launch"] == 60 * 12 * 576 * 576 and r["traffic"] == 123.0
+
+
+def test_parse_medium_precision(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "medium", "--medium-precision", "fp32"])
+    a = bench.parse()
+    assert a.workload == "medium" and a.medium_precision == "fp32"
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    assert bench.parse().medium_precision == "fp64"
