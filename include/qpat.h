@@ -51,7 +51,8 @@ typedef enum {
   QPAT_EUNSTABLE = 2,   /* time step violates the stability check */
   QPAT_ENONFINITE = 3,  /* a NaN/Inf appeared in the fields */
   QPAT_ENOCONV = 4,     /* diffusion solve hit its iteration cap */
-  QPAT_ETIMEOUT = 5,    /* a bounded device wait (grid barrier) gave up */
+  QPAT_ETIMEOUT = 5,    /* a bounded device wait gave up: a grid barrier of a cooperative solve,
+                           or the wait for the bulk copies of a propagation pass */
   QPAT_ENOMEM = 6,      /* device allocation failed */
   QPAT_ECUDA = 7        /* any other CUDA runtime error */
 } qpat_status;
@@ -126,7 +127,8 @@ const char* qpat_last_error(const qpat_ctx* ctx);
 qpat_status qpat_get_sizes(const qpat_ctx* ctx, long long out[6]);
 
 /* Wait for the context's stream and report device-side failures found by
- * the kernels since the last check (ENONFINITE).  Clears the flags. */
+ * the kernels since the last check (ENONFINITE; ETIMEOUT when a pass's
+ * bounded wait for its bulk copies gave up).  Clears the flags. */
 qpat_status qpat_sync(qpat_ctx* ctx);
 
 /* H_a (Section 3.2.3): batch of initial pressures -> sensor series.
