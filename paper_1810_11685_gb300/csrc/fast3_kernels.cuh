@@ -46,9 +46,22 @@ constexpr int kLine3Bufs = kLine3OneBuf ? 1 : 2;
 constexpr bool kLine3Pairs = QPAT_LINE3_PAIRS != 0;
 
 // Spectral lines per CTA of the 3D y and z passes (adjacent kx; measured on
-// GB300 at 288^3: 8 lines 9.3e9, 4 lines 8.7e9, 2 lines 6.3e9 cell-steps/s).
+// GB300 at 288^3: 8 lines 9.3e9, 4 lines 8.7e9, 2 lines 6.3e9 cell-steps/s;
+// with the present row pass, N_t 300: 8 lines 1.335e10, 16 lines in the z
+// pass 1.235e10, 16 lines in the y pass 1.205e10).
+#ifndef QPAT_Y3_CBW
+#define QPAT_Y3_CBW 8
+#endif
+#ifndef QPAT_Z3_CBW
+#define QPAT_Z3_CBW 8
+#endif
 template <int L>
-constexpr int cbw3() { return 8; }
+constexpr int cbw3() { return QPAT_Y3_CBW; }
+template <int L>
+constexpr int cbw3z() { return QPAT_Z3_CBW; }
+// Resident CTAs per SM the y and z passes are compiled for (two, or one for
+// 16 lines per CTA).
+constexpr int line3_minb(int cbw) { return cbw >= 16 ? 1 : 2; }
 
 // Resident CTAs per SM the 3D row pass is compiled for (registers capped to
 // fit; measured at 288^3: 6 1.171e10, 8 1.199e10, 9 1.174e10 cell-steps/s).
@@ -317,17 +330,18 @@ row3_fast(const Prop3<T> a) {
 // number of Stockham buffers in use).
 template <int L, int NSX, int CBW>
 __host__ __device__ constexpr int line3_stride() {
-  return kLine3Bufs * NSX * SGeom<L>::SL + ((16 / CBW - (kLine3Bufs * NSX * SGeom<L>::SL) % 16) + 16) % 16;
+  return kLine3Bufs * NSX * SGeom<L>::SL + ((col_pad_target(CBW) - (kLine3Bufs * NSX * SGeom<L>::SL) % 16) + 16) % 16;
 }
 
 // y pass over the (z = blockIdx.y, kx) lines of problem blockIdx.z.
 template <typename T, int L, int K, int INV>
-__global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT, 2)
+__global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT, line3_minb(cbw3<L>()))
 ypass3_fast(const Prop3<T> a, const int gather) {
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
   constexpr int SL = G::SL, CBW = cbw3<L>(), Q1 = G::Q1, QL = G::QL;
   constexpr int CS = line3_stride<L, K, CBW>();
+  static_assert(CS % 2 == 0 && SL % 2 == 0, "line buffers start on 16-byte boundaries");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % CBW;
   const int j = threadIdx.x / CBW;
@@ -366,14 +380,15 @@ ypass3_fast(const Prop3<T> a, const int gather) {
 
 // z pass over the (ky = blockIdx.y, kx) lines of problem blockIdx.z.
 template <typename T, int L, int PH>
-__global__ void __launch_bounds__(cbw3<L>() * SGeom<L>::TPT, 2)
+__global__ void __launch_bounds__(cbw3z<L>() * SGeom<L>::TPT, line3_minb(cbw3z<L>()))
 zpass3_fast(const Prop3<T> a) {
   constexpr int KIN = z3_kin(PH), KOUT = z3_kout(PH);
   constexpr int NSX = (KIN > KOUT ? KIN : KOUT);
   typedef typename V2<T>::t C;
   typedef SGeom<L> G;
-  constexpr int SL = G::SL, CBW = cbw3<L>(), Q1 = G::Q1, QL = G::QL;
+  constexpr int SL = G::SL, CBW = cbw3z<L>(), Q1 = G::Q1, QL = G::QL;
   constexpr int CS = line3_stride<L, NSX, CBW>();
+  static_assert(CS % 2 == 0 && SL % 2 == 0, "line buffers start on 16-byte boundaries");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % CBW;
   const int j = threadIdx.x / CBW;
@@ -424,10 +439,10 @@ zpass3_fast(const Prop3<T> a) {
   }
 }
 
-template <typename T, int L, int NSX>
+template <typename T, int L, int NSX, int CBW = cbw3<L>()>
 constexpr size_t line3_fast_smem() {
   typedef typename V2<T>::t C;
-  return ((size_t)L + (size_t)cbw3<L>() * line3_stride<L, NSX, cbw3<L>()>()) * sizeof(C);
+  return ((size_t)L + (size_t)CBW * line3_stride<L, NSX, CBW>()) * sizeof(C);
 }
 
 template <typename T, int L, int PH>
@@ -439,7 +454,7 @@ template <typename T, int L, int PH>
 void set_z3_fast_attr() {
   constexpr int NSX = z3_kin(PH) > z3_kout(PH) ? z3_kin(PH) : z3_kout(PH);
   cudaFuncSetAttribute(zpass3_fast<T, L, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)line3_fast_smem<T, L, NSX>());
+                       (int)line3_fast_smem<T, L, NSX, cbw3z<L>()>());
 }
 template <typename T, int L, int K, int INV>
 void set_y3_fast_attr() {
@@ -470,9 +485,9 @@ template <typename T, int L, int PH>
 void run_z3_fast(const Prop3<T>& a, int batch, cudaStream_t s) {
   typedef SGeom<L> G;
   constexpr int NSX = z3_kin(PH) > z3_kout(PH) ? z3_kin(PH) : z3_kout(PH);
-  constexpr int CBW = cbw3<L>();
+  constexpr int CBW = cbw3z<L>();
   const dim3 grid((a.nxh + CBW - 1) / CBW, a.ny, batch);
-  zpass3_fast<T, L, PH><<<grid, CBW * G::TPT, line3_fast_smem<T, L, NSX>(), s>>>(a);
+  zpass3_fast<T, L, PH><<<grid, CBW * G::TPT, line3_fast_smem<T, L, NSX, CBW>(), s>>>(a);
 }
 template <typename T, int L, int K, int INV>
 void run_y3_fast(const Prop3<T>& a, int gather, int batch, cudaStream_t s) {
